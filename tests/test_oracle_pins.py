@@ -1,0 +1,296 @@
+"""Pins for the FP64 oracle: checks against facts other than the oracle itself.
+
+Each test targets a family of plausible oracle mistakes:
+  * two-atom closed form        -> factor-of-2 / mass-weighting / sign / root-choice errors
+  * collinear chain closed form -> coupling signs s_k(a) s_l(a), wrong endpoint index
+  * finite-difference Jacobian  -> transposed operands in A, G evaluated at the wrong x
+  * quadratic convergence       -> any Jacobian error (inexact Newton converges linearly)
+  * SHAKE cross-check           -> anything that changes the root on non-collinear geometry
+  * brute-force root search     -> uniqueness of the root continuous with lambda = 0
+  * invariants                  -> momentum / angular momentum / displacement span
+  * pendulum worked example     -> the paper's printed energy errors (supplement Sec. 4)
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.special as ss
+
+from oracle import ilves_oracle as orc
+from paper_2503_13075_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------- helpers
+def sigma_of_lambda(s, lam):
+    """sigma(x(lambda)) by explicit loops over constraints (independent of the oracle)."""
+    x = s.x_unc.copy()
+    for k, (i, j) in enumerate(zip(s.atom_i, s.atom_j)):
+        rho = s.x_old[i] - s.x_old[j]
+        x[i] -= s.inv_mass[i] * 2.0 * rho * lam[k]
+        x[j] += s.inv_mass[j] * 2.0 * rho * lam[k]
+    out = np.empty(len(s.d))
+    for k, (i, j) in enumerate(zip(s.atom_i, s.atom_j)):
+        r = x[i] - x[j]
+        out[k] = r.dot(r) - s.d[k] ** 2
+    return out, x
+
+
+def small_tree(seed, n):
+    return wl.tree_molecules_of_sizes([n], seed=seed)
+
+
+# ---------------------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("w1,w2", [(1.0, 1.0), (1 / 1.008, 1 / 12.011), (0.0, 1.0), (1 / 32.06, 1 / 1.008)])
+def test_two_atom_closed_form(w1, w2):
+    """|s - c rho|^2 = d^2 with c = 2 lambda (w1 + w2); the small root is the Newton root."""
+    s = wl.two_atoms(d=0.1, w1=w1, w2=w2, seed=11, sigma=0.01)
+    res = orc.solve_system(s)
+    rho = s.x_old[0] - s.x_old[1]
+    sv = s.x_unc[0] - s.x_unc[1]
+    a, b, c0 = rho.dot(rho), sv.dot(rho), sv.dot(sv) - s.d[0] ** 2
+    c = (b - math.sqrt(b * b - a * c0)) / a
+    lam = c / (2.0 * (w1 + w2))
+    assert res.status[0] == orc.CONVERGED
+    assert abs(res.lam[0] - lam) <= 1e-12 * abs(lam)
+    x_exp = s.x_unc.copy()
+    x_exp[0] -= w1 * 2 * rho * lam
+    x_exp[1] += w2 * 2 * rho * lam
+    assert np.abs(res.x - x_exp).max() <= 1e-14
+    # paper's multiplier convention: lambda_paper = -2 lambda / h^2 (g = -sigma/2, x_unc carries h^2)
+    h = 0.002
+    lam_paper = -2.0 * res.lam[0] / h**2
+    Gp = -(s.x_old[0] - s.x_old[1])  # paper: dg/dq_a = -(q_a - q_b)
+    x_paper = s.x_unc[0] - h * h * w1 * Gp * lam_paper
+    assert np.allclose(x_paper, res.x[0], atol=1e-15)
+
+
+def test_collinear_chain_closed_form():
+    """All atoms and perturbations on one axis: r(lambda) is linear, lambda = B^-1 (s - d sign(rho))."""
+    rng = np.random.default_rng(5)
+    n = 12
+    d = rng.uniform(0.1, 0.15, n - 1)
+    xo = np.zeros((n, 3))
+    xo[1:, 0] = np.cumsum(d)
+    xu = xo.copy()
+    xu[:, 0] += rng.normal(0, 0.004, n)
+    w = 1.0 / rng.choice([1.008, 12.011, 15.999], n)
+    ai = np.arange(n - 1, dtype=np.int32)
+    aj = ai + 1
+    # swap endpoints of a few constraints to exercise both signs
+    flip = rng.random(n - 1) < 0.4
+    ai2 = np.where(flip, aj, ai).astype(np.int32)
+    aj2 = np.where(flip, ai, aj).astype(np.int32)
+    res = orc.solve(xo, xu, w, ai2, aj2, d)
+    rho = xo[ai2, 0] - xo[aj2, 0]
+    svec = xu[ai2, 0] - xu[aj2, 0]
+    B = np.zeros((n - 1, n - 1))
+    for k in range(n - 1):
+        for l in range(n - 1):
+            for a in {ai2[k], aj2[k]} & {ai2[l], aj2[l]}:
+                sk = 1.0 if a == ai2[k] else -1.0
+                sl = 1.0 if a == ai2[l] else -1.0
+                B[k, l] += 2.0 * rho[l] * sk * sl * w[a]
+    lam = np.linalg.solve(B, svec - d * np.sign(rho))
+    assert res.status[0] == orc.CONVERGED
+    np.testing.assert_allclose(res.lam, lam, rtol=1e-9, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------- Jacobian
+@pytest.mark.parametrize("seed,n", [(1, 8), (2, 25), (3, 40)])
+def test_jacobian_matches_finite_differences(seed, n):
+    """d sigma / d lambda = -A(x(lambda), x_old); sigma is quadratic so central differences are exact."""
+    s = small_tree(seed, n)
+    rng = np.random.default_rng(seed)
+    lam = rng.normal(0, 1e-3, len(s.d))
+    sig, x = sigma_of_lambda(s, lam)
+    A = orc.newton_matrix(x, s.x_old, s.inv_mass, s.atom_i.astype(np.int64), s.atom_j.astype(np.int64)).toarray()
+    h = 1e-4
+    J = np.empty_like(A)
+    for l in range(len(lam)):
+        e = np.zeros_like(lam)
+        e[l] = h
+        J[:, l] = (sigma_of_lambda(s, lam + e)[0] - sigma_of_lambda(s, lam - e)[0]) / (2 * h)
+    np.testing.assert_allclose(-J, A, atol=1e-9 * np.abs(A).max())
+    # structurally symmetric (pattern of the line graph), numerically nonsymmetric
+    assert np.array_equal(A != 0, A.T != 0)
+    assert np.abs(A - A.T).max() > 0
+
+
+def test_quadratic_convergence():
+    """Newton: e_{l+1} / e_l^2 stays bounded (supplement Sec. 2.3, quadratic convergence)."""
+    for s in (wl.chain64(), small_tree(9, 150)):
+        h = orc.solve_system(s, tol=1e-15).history
+        ratios = [h[l + 1] / h[l] ** 2 for l in range(len(h) - 1) if h[l + 1] > 1e-13]
+        assert len(ratios) >= 2
+        assert max(ratios) < 50.0, ratios
+        assert h[-1] < 1e-13
+
+
+# ---------------------------------------------------------------------------- independent solvers
+def shake(s, tol=1e-13, max_sweeps=5000):
+    """SHAKE: nonlinear Gauss-Seidel, one exact two-atom solve per constraint per sweep."""
+    x = s.x_unc.copy()
+    lam = np.zeros(len(s.d))
+    for _ in range(max_sweeps):
+        worst = 0.0
+        for k, (i, j) in enumerate(zip(s.atom_i, s.atom_j)):
+            rho = s.x_old[i] - s.x_old[j]
+            r = x[i] - x[j]
+            worst = max(worst, abs(r.dot(r) - s.d[k] ** 2) / s.d[k] ** 2)
+            wsum = s.inv_mass[i] + s.inv_mass[j]
+            a, b, c0 = rho.dot(rho), r.dot(rho), r.dot(r) - s.d[k] ** 2
+            c = (b - math.sqrt(b * b - a * c0)) / a
+            dl = c / (2 * wsum)
+            x[i] -= s.inv_mass[i] * 2 * rho * dl
+            x[j] += s.inv_mass[j] * 2 * rho * dl
+            lam[k] += dl
+        if worst <= tol:
+            return x, lam
+    raise AssertionError("SHAKE did not converge")
+
+
+@pytest.mark.parametrize("maker", [wl.chain64, lambda: small_tree(21, 60), lambda: small_tree(22, 120)])
+def test_shake_agreement(maker):
+    """ILVES-M and SHAKE solve the same equations (supplement Sec. 2.3 / Sec. 3): same root."""
+    s = maker()
+    res = orc.solve_system(s, tol=1e-13)
+    x_sh, lam_sh = shake(s)
+    assert np.abs(res.x - x_sh).max() <= 1e-10
+    np.testing.assert_allclose(res.lam, lam_sh, rtol=1e-7, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [31, 32])
+def test_bruteforce_root_is_unique_near_zero(seed):
+    """Tiny molecules: root finding from random starts lands on the oracle's root or far away."""
+    s = small_tree(seed, 6)
+    res = orc.solve_system(s)
+    f = lambda lam: sigma_of_lambda(s, lam)[0]
+    rng = np.random.default_rng(seed)
+    scale = np.abs(res.lam).max()
+    near = 0
+    for _ in range(12):
+        start = rng.normal(0, scale, len(s.d))
+        sol = so.fsolve(f, start, xtol=1e-14, full_output=True)
+        if sol[2] != 1:
+            continue
+        if np.abs(sol[0]).max() < 3 * scale:
+            near += 1
+            np.testing.assert_allclose(sol[0], res.lam, rtol=1e-7, atol=1e-12 * scale)
+    assert near >= 3
+
+
+# ---------------------------------------------------------------------------- invariants
+@pytest.mark.parametrize("maker", [wl.chain64, lambda: wl.tree_batch(n_mol=16, seed=3)])
+def test_invariants(maker):
+    s = maker()
+    res = orc.solve_system(s)
+    m = 1.0 / s.inv_mass
+    dx = res.x - s.x_unc
+    # momentum: sum_a m_a dx_a = 0 (each constraint force acts pairwise)
+    scale = np.abs(m[:, None] * dx).sum()
+    assert np.abs((m[:, None] * dx).sum(axis=0)).max() <= 1e-13 * scale
+    # angular momentum about the origin with the x_old lever arms: forces are parallel to rho_k
+    L = np.cross(s.x_old, m[:, None] * dx).sum(axis=0)
+    assert np.abs(L).max() <= 1e-12 * np.abs(np.cross(s.x_old, m[:, None] * dx)).sum()
+    # displacement lies in span(M^-1 G(x_old)^T): least squares returns the same lambda, ~0 residual
+    G0 = orc.constraint_jacobian(s.x_old, s.atom_i.astype(np.int64), s.atom_j.astype(np.int64), s.n_atoms)
+    B = -(np.repeat(s.inv_mass, 3)[:, None] * G0.T.toarray())
+    lam_ls, *_ = np.linalg.lstsq(B, dx.ravel(), rcond=None)
+    assert np.abs(B @ lam_ls - dx.ravel()).max() <= 1e-15 + 1e-12 * np.abs(dx).max()
+    np.testing.assert_allclose(lam_ls, res.lam, rtol=1e-8, atol=1e-14)
+    assert orc.max_relative_violation(res.x, s.atom_i, s.atom_j, s.d) <= 1e-12
+
+
+def test_feasible_input_needs_no_solve():
+    s = wl.chain64()
+    s.x_unc = s.x_old + np.array([0.3, -0.2, 0.1])
+    res = orc.solve_system(s)
+    assert res.iterations[0] == 0 and res.status[0] == orc.CONVERGED
+    assert np.all(res.lam == 0.0)
+
+
+def test_relabelling_and_endpoint_swap():
+    s = wl.tree_batch(n_mol=6, seed=4)
+    res = orc.solve_system(s)
+    rng = np.random.default_rng(0)
+    pa = rng.permutation(s.n_atoms)  # new index of old atom a is inv[a]
+    inv = np.empty_like(pa)
+    inv[pa] = np.arange(s.n_atoms)
+    pc = rng.permutation(s.n_constraints)
+    swap = rng.random(s.n_constraints) < 0.5
+    ai = np.where(swap, s.atom_j, s.atom_i)[pc]
+    aj = np.where(swap, s.atom_i, s.atom_j)[pc]
+    r2 = orc.solve(s.x_old[pa], s.x_unc[pa], s.inv_mass[pa], inv[ai], inv[aj], s.d[pc])
+    np.testing.assert_allclose(r2.x, res.x[pa], atol=1e-13)
+    np.testing.assert_allclose(r2.lam, res.lam[pc], rtol=1e-9, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------- degenerate cases
+def test_edge_cases():
+    empty = orc.solve(np.zeros((3, 3)), np.ones((3, 3)), np.ones(3), [], [], [])
+    assert empty.iterations.size == 0 and np.all(empty.x == 1.0)
+    # atoms outside any constraint pass through untouched
+    s = wl.chain64()
+    xo = np.vstack([s.x_old, [[5.0, 5.0, 5.0]]])
+    xu = np.vstack([s.x_unc, [[5.1, 5.0, 5.0]]])
+    r = orc.solve(xo, xu, np.append(s.inv_mass, 1.0), s.atom_i, s.atom_j, s.d)
+    assert np.all(r.x[-1] == xu[-1]) and r.status[0] == orc.CONVERGED
+    # non-finite input
+    xu2 = s.x_unc.copy()
+    xu2[3, 1] = np.nan
+    assert orc.solve(s.x_old, xu2, s.inv_mass, s.atom_i, s.atom_j, s.d).status[0] == orc.NONFINITE
+    # unreachable tolerance -> max_iter
+    r = orc.solve_system(s, tol=1e-30, max_iter=7)
+    assert r.status[0] == orc.MAX_ITER and r.iterations[0] == 7
+    # r . rho = 0 at lambda = 0: singular Newton matrix
+    xo = np.array([[0.0, 0, 0], [0.1, 0, 0]])
+    xu = np.array([[0.0, 0, 0], [0.0, 0.12, 0]])
+    r = orc.solve(xo, xu, np.ones(2), [0], [1], [0.1])
+    assert r.status[0] == orc.SINGULAR
+
+
+# ---------------------------------------------------------------------------- paper worked example
+def _pendulum_max_rel_energy_error(steps_per_period, periods=2.0):
+    """Leap-frog pendulum with the oracle as constraint solver (supplement Sec. 4 tables)."""
+    m, l, g = 1.0, 1.0, 9.82
+    pivot = np.array([0.0, l, 0.0])
+    q = np.zeros(3)
+    v0 = np.array([1.0, 0.0, 0.0])
+    theta = math.acos(1.0 - v0.dot(v0) / (2.0 * g * l))
+    period = 4.0 * math.sqrt(l / g) * ss.ellipk(math.sin(theta / 2.0) ** 2)
+    h = period / steps_per_period
+    f = np.array([0.0, -m * g, 0.0])
+    vh = v0 - 0.5 * h * (f / m + v0.dot(v0) / l * (pivot - q) / l)  # v_{-1/2}
+    e0 = 0.5 * m * v0.dot(v0) + m * g * q[1]
+    x_old = np.stack([pivot, q])
+    inv = np.array([0.0, 1.0 / m])
+    worst = 0.0
+    for _ in range(int(steps_per_period * periods)):
+        x_unc = x_old.copy()
+        x_unc[1] = x_old[1] + h * vh + h * h * f / m
+        res = orc.solve(x_old, x_unc, inv, [0], [1], [l], tol=1e-12)
+        assert res.status[0] == orc.CONVERGED
+        v_new = (res.x[1] - x_old[1]) / h
+        vk = 0.5 * (vh + v_new)
+        n = (x_old[1] - pivot) / np.linalg.norm(x_old[1] - pivot)
+        vk = vk - vk.dot(n) * n  # velocity at t_k tangent to the constraint
+        e = 0.5 * m * vk.dot(vk) + m * g * x_old[1][1]
+        worst = max(worst, abs(e - e0) / e0)
+        vh, x_old = v_new, res.x
+    return worst
+
+
+def test_pendulum_energy_error_matches_paper():
+    rows = np.loadtxt(os.path.join(GOLDEN, "pendulum_energy.txt"))
+    errs = []
+    for spp, log2_err in rows:
+        e = _pendulum_max_rel_energy_error(int(spp))
+        errs.append(e)
+        assert abs(math.log2(e) - log2_err) < 0.3, (spp, math.log2(e))
+    # second order in h: halving h divides the error by ~4
+    for a, b in zip(errs, errs[1:]):
+        assert 3.6 < a / b < 4.4
