@@ -1,0 +1,386 @@
+"""Benchmark: batched ILVES-M constraint solves on GB300, one JSON line on stdout.
+
+Workload (default): 4096 independent tree molecules of U{20..200} atoms
+(452,260 atoms, 448,164 constraints; seeded synthetic stand-ins for the paper's
+lipid-like molecules), tolerance 1e-12 on max |sigma| / d^2, mixed precision.
+A "step" is one ilves_solve over the whole batch with the inputs resident in HBM;
+L2 is flushed (a 256 MiB write) before every timed step, outside the timed window.
+
+Metric: atoms*solves/s = atoms in the batch * solves / device time (CUDA events on
+the launching stream).  The plain FP64 GPU solve of the same batch is timed in the
+same run.  `e2e` times the same solve through the Python API with pinned host
+buffers, the host->device copies of the inputs and device->host copies of x,
+lambda, iterations and status inside the timed region.
+
+--impl reference times the FP64 CPU oracle (the deliberately plain reference) on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atoms*solves/s at 1e-12 rel violation, mixed+batched vs plain FP64 GPU"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ilves", choices=["ilves", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--n-mol", type=int, default=4096)
+    p.add_argument("--tol", type=float, default=1e-12)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def workload(n_mol, seed):
+    from paper_2503_13075_gb300 import workloads as wl
+
+    return wl.tree_batch(n_mol=n_mol, seed=seed)
+
+
+def workload_name(s):
+    return (f"tree_batch: {s.n_molecules} tree molecules of U{{20..200}} atoms "
+            f"({s.n_atoms} atoms, {s.n_constraints} constraints), all bonds constrained")
+
+
+def algorithmic_bytes(s):
+    """Compulsory HBM traffic of one solve: x_old, x_unc, inv_mass, d in; x, lambda, status out."""
+    return 80 * s.n_atoms + 16 * s.n_constraints + 8 * s.n_molecules
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ilves" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(s_full, budget_s=12.0, seed=0):
+    """Times the oracle on whole molecules of the workload until ~budget_s of CPU work."""
+    from oracle import ilves_oracle as orc
+    from paper_2503_13075_gb300 import workloads as wl
+
+    ptr = s_full.mol_atom_ptr
+    n_take = min(s_full.n_molecules, 512)
+    a0, a1 = 0, int(ptr[n_take])
+    sel = (s_full.atom_i < a1)
+    sub = wl.System("sample", s_full.x_old[a0:a1], s_full.x_unc[a0:a1], s_full.inv_mass[a0:a1],
+                    s_full.atom_i[sel], s_full.atom_j[sel], s_full.d[sel])
+    atoms = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        r = orc.solve_system(sub, tol=1e-12)
+        atoms += sub.n_atoms
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    assert np.all(r.status == 0)
+    return atoms / dt, dt, f"first {n_take} molecules ({sub.n_atoms} atoms) of the workload, {reps} solves"
+
+
+def run_reference(args):
+    rank, world, local = dist_setup(args)
+    if rank != 0:
+        return
+    s = workload(args.n_mol, 1001)
+    from oracle import ilves_oracle as orc
+    from paper_2503_13075_gb300 import workloads as wl
+
+    ptr = s.mol_atom_ptr
+    n_take = min(s.n_molecules, 256)
+    a1 = int(ptr[n_take])
+    sel = s.atom_i < a1
+    sub = wl.System("sample", s.x_old[:a1], s.x_unc[:a1], s.inv_mass[:a1], s.atom_i[sel], s.atom_j[sel], s.d[sel])
+    for _ in range(args.warmup):
+        orc.solve_system(sub, tol=args.tol)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = orc.solve_system(sub, tol=args.tol)
+        times.append(time.perf_counter() - t0)
+    assert np.all(r.status == 0)
+    per_step = sum(times) / len(times)
+    value = sub.n_atoms / per_step
+    sample = f"first {n_take} molecules ({sub.n_atoms} atoms) of the workload per step"
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "atoms*solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(s), "tol": args.tol, "oracle": "FP64 Newton + SuperLU (scipy)"},
+        "cpu_baseline": {"value": value, "unit": "atoms*solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "atoms*solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def time_device(topo, dev_in, out, prec, tol, steps, warmup, flush, stream):
+    """Per-step CUDA-event time of ilves_solve (L2 flushed before each step)."""
+    import torch
+
+    xo, xu, w, d = dev_in
+    x, lam, it, st = out
+    for _ in range(warmup):
+        topo.solve(xo, xu, w, d, tol=tol, precision=prec, x_out=x, lambda_out=lam, iterations_out=it,
+                   status_out=st)
+    torch.cuda.synchronize()
+    times = []
+    launches = 0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        topo.solve(xo, xu, w, d, tol=tol, precision=prec, x_out=x, lambda_out=lam, iterations_out=it,
+                   status_out=st)
+        e1.record(stream)
+        launches += topo.last_launch_count()
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in times]
+    return ms, launches
+
+
+def run_ilves(args):
+    import torch
+
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from oracle import ilves_oracle as orc  # correctness gate on the timed outputs only
+    from paper_2503_13075_gb300 import binding as B
+
+    s = workload(args.n_mol, 1001 + 7919 * rank)  # weak scaling: every rank its own batch
+    topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dev_in = (f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d))
+    out = (torch.empty_like(dev_in[1]), torch.empty(s.n_constraints, dtype=torch.float64, device=dev),
+           torch.empty(topo.n_molecules, dtype=torch.int32, device=dev),
+           torch.empty(topo.n_molecules, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # plain FP64 comparator (same batch, same tolerance)
+    ms64, _ = time_device(topo, dev_in, out, "fp64", args.tol, max(3, args.steps // 4), 2, flush, stream)
+    ok64 = bool((out[3] == 0).all().item())
+    it64 = out[2].cpu().numpy()
+
+    clocks = None if args.no_clocks else ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    t_wall0 = time.perf_counter()
+    ms, launches = time_device(topo, dev_in, out, args.precision, args.tol, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop() if clocks else None
+    status = out[3].cpu().numpy()
+    iters = out[2].cpu().numpy()
+    x = out[0].cpu().numpy()
+    valid = bool(np.all(status == 0))
+    viol = orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d)
+    avg_err = orc.average_relative_error(x, s.atom_i, s.atom_j, s.d)
+
+    per_step_ms = sum(ms) / len(ms)
+    per_step_ms = max_over_ranks(per_step_ms, world, dev)
+    value = world * s.n_atoms / (per_step_ms * 1e-3)
+    per64 = sum(ms64) / len(ms64)
+    value64 = s.n_atoms / (per64 * 1e-3)
+
+    # end to end through the public API: pinned host buffers, copies inside the timed region
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (s.x_old, s.x_unc, s.inv_mass, s.d)]
+    hx = torch.empty(s.n_atoms, 3, dtype=torch.float64).pin_memory()
+    hl = torch.empty(s.n_constraints, dtype=torch.float64).pin_memory()
+    hi = torch.empty(topo.n_molecules, dtype=torch.int32).pin_memory()
+    hs = torch.empty(topo.n_molecules, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    e2e_ms = []
+    for k in range(e2e_steps + 2):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for dst, src in zip(dev_in, host):
+            dst.copy_(src, non_blocking=True)
+        topo.solve(*dev_in, tol=args.tol, precision=args.precision, x_out=out[0], lambda_out=out[1],
+                   iterations_out=out[2], status_out=out[3])
+        hx.copy_(out[0], non_blocking=True)
+        hl.copy_(out[1], non_blocking=True)
+        hi.copy_(out[2], non_blocking=True)
+        hs.copy_(out[3], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            e2e_ms.append(e0.elapsed_time(e1))
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = sum(t.numel() * t.element_size() for t in (hx, hl, hi, hs))
+    e2e_per = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
+    e2e_value = world * s.n_atoms / (e2e_per * 1e-3)
+
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    ab = algorithmic_bytes(s)
+    achieved = ab / (per_step_ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, sample = cpu_oracle_rate(s)
+        cpu = {"value": rate, "unit": "atoms*solves/s", "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": round(dt, 2)}
+    if rank != 0:
+        return
+    res = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "atoms*solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": per_step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64+f32" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": workload_name(s),
+            "precision": args.precision,
+            "tol": args.tol,
+            "warm_start": "none",
+            "l2": "flushed (256 MiB write) before every timed step",
+            "schedule": "persistent CTAs, one warp per molecule",
+        },
+        "valid": valid,
+        "max_rel_violation": viol,
+        "avg_rel_error": avg_err,
+        "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(iters)) if v},
+        "plain_fp64": {"value": value64, "ms_per_step": per64, "all_converged": ok64,
+                       "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(it64)) if v}},
+        "speedup_vs_plain_fp64": value / value64,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": ab, "kernel": "k_solve_small"},
+        "e2e": {"value": e2e_value, "unit": "atoms*solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_per},
+        "gpu_launches": launches,
+        "wall_s_timed_region": t_wall,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(res))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ilves(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * ilves.h -- C ABI of the GB300 (sm_103a) ILVES-M constraint solver.
+ *
+ * The library solves, for every molecule (connected component of the constraint
+ * graph) of a batch, the per-time-step constraint equations of constrained
+ * leap-frog / Verlet molecular dynamics (paper, supplement Sec. 2.3):
+ *
+ *   find lambda such that  sigma_k(x(lambda)) = |x_i - x_j|^2 - d_k^2 = 0  for all k,
+ *   x(lambda) = x_unc - M^-1 G(x_old)^T lambda,
+ *
+ * with Newton's method (ILVES-M, supplement Sec. 2.3, Newton equations for the
+ * constraint equation; supplement Sec. 3):
+ *
+ *   A(x(lambda_l), x_old) delta_l = sigma(x(lambda_l)),  lambda_{l+1} = lambda_l + delta_l,
+ *   A(x, y) = G(x) M^-1 G(y)^T   (supplement Sec. 2.3, definition of A),
+ *
+ * factorising A with a sparse LU in a fill-reducing elimination order computed
+ * once per topology (supplement Sec. 3), until max_k |sigma_k| / d_k^2 <= tol
+ * (supplement Sec. 4, stopping rule) or max_iter linear solves.
+ *
+ * Conventions
+ *  - sigma = -2 g with the paper's g_i = (d_i^2 - |q_a - q_b|^2) / 2 (supplement
+ *    Sec. 2.2), and h^2 is absorbed into lambda: the paper's multipliers are
+ *    lambda_paper = -2 lambda / h^2.  Positions do not depend on the convention.
+ *  - x_unc = q_k + h v_{k-1/2} + h^2 M^-1 f_ext(t_k) is the unconstrained update
+ *    (supplement Sec. 2.3, Eq. for phi_k); x_old = q_k.
+ *  - Atom arrays are (n_atoms, 3) row-major float64 (x, y, z per atom); constraint
+ *    arrays have n_constraints entries in the caller's constraint order.
+ *  - Molecules are the connected components of the constraint graph, numbered in
+ *    increasing order of their smallest atom index.  Atoms in no constraint are
+ *    copied from x_unc to x_out unchanged.
+ *  - "iterations" of a molecule is the number of linear solves performed.  The
+ *    convergence test precedes each solve, so a feasible x_unc needs 0.
+ *
+ * Memory and errors
+ *  - ilves_setup_topology takes HOST arrays and owns every device buffer it
+ *    allocates (pattern, schedule, workspace) until ilves_destroy_topology.
+ *  - ilves_solve takes DEVICE pointers owned by the caller, allocates nothing and
+ *    is stream-ordered on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *    It returns after enqueueing the work; results are valid once the stream
+ *    reaches that point.
+ *  - Return values report argument and launch failures only.  Numerical
+ *    failures are reported per molecule in mol_status_out.
+ *  - Functions are not thread-safe on the same topology object.
+ */
+#ifndef ILVES_H
+#define ILVES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ilves_topology ilves_topology; /* opaque */
+
+typedef enum {
+    ILVES_OK = 0,
+    ILVES_ERR_INVALID_ARG = 1, /* NULL pointer, negative size, unknown option */
+    ILVES_ERR_TOPOLOGY = 2,    /* index out of range, i == j, duplicate constraint */
+    ILVES_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    ILVES_ERR_OOM = 4,         /* device allocation failed during setup */
+    ILVES_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} ilves_status;
+
+/* Per-molecule outcome written to mol_status_out. */
+typedef enum {
+    ILVES_MOL_CONVERGED = 0,      /* max |sigma| / d^2 <= tol */
+    ILVES_MOL_MAX_ITER = 1,       /* tolerance not reached in max_iter solves */
+    ILVES_MOL_SINGULAR_PIVOT = 2, /* a pivot of the LU vanished (|u_jj| tiny) */
+    ILVES_MOL_NONFINITE = 3       /* a violation became NaN or Inf */
+} ilves_mol_status;
+
+/* Arithmetic of a solve.
+ *  FP64:     every step in float64 (the plain reference configuration).
+ *  MIXED:    Jacobian assembly, LU factorisation and triangular solves in float32;
+ *            violations, multiplier accumulation and position updates in float64.
+ *            The outer Newton loop acts as iterative refinement. */
+typedef enum { ILVES_PREC_FP64 = 0, ILVES_PREC_MIXED = 1 } ilves_precision;
+
+typedef struct {
+    int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;
+                                2 = rounds of independent low-degree pivots with `degree_slack` */
+    int32_t degree_slack;    /* ordering 2: admit pivots up to min degree + slack per round */
+    int32_t warps_per_cta;   /* 0 = autotuned; else 1..32 warps per persistent CTA */
+    int32_t ctas_per_sm;     /* 0 = autotuned; else 1..4 */
+    int32_t device;          /* CUDA device ordinal the topology lives on (-1 = current device,
+                                -2 = plan on the host only: no CUDA call, ilves_solve refused) */
+    int32_t max_warp_constraints; /* molecules larger than this use the multi-warp path (0 = auto) */
+} ilves_setup_opts;
+
+/* Fills `opts` with the defaults. */
+void ilves_default_opts(ilves_setup_opts* opts);
+
+/*
+ * Builds the solver's view of a constraint topology (supplement Sec. 3,
+ * initialisation): connected components (molecules), the line graph L(G) whose
+ * adjacency is the pattern of A, a fill-reducing elimination order per molecule,
+ * the symbolic LU pattern with its level schedule, the atom -> constraint
+ * incidence, and a work partition of molecules over persistent CTAs.  Everything
+ * is uploaded once to the device and reused by every ilves_solve.
+ *
+ *  n_atoms, n_constraints: sizes (>= 0).
+ *  atom_i, atom_j: HOST int32 arrays of n_constraints atom indices, 0 <= i,j < n_atoms,
+ *                  i != j, no two constraints on the same unordered pair.
+ *  opts: may be NULL (defaults).
+ *  out: receives the new topology; *out is NULL on error.
+ * Errors: ILVES_ERR_INVALID_ARG, ILVES_ERR_TOPOLOGY, ILVES_ERR_OOM, ILVES_ERR_CUDA.
+ */
+ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const int32_t* atom_i,
+                                  const int32_t* atom_j, const ilves_setup_opts* opts,
+                                  ilves_topology** out);
+
+/*
+ * One constraint solve for every molecule of the topology (the per-step hot path).
+ *
+ *  x_old     DEVICE float64 (n_atoms, 3): reference positions q_k (defines G(x_old)).
+ *  x_unc     DEVICE float64 (n_atoms, 3): unconstrained update.
+ *  inv_mass  DEVICE float64 (n_atoms): 1 / m_a >= 0 (0 = anchored atom).
+ *  d         DEVICE float64 (n_constraints): target distances d_k > 0.
+ *  tol       relative tolerance on |sigma_k| / d_k^2 (e.g. 1e-12).
+ *  max_iter  maximum number of linear solves per molecule (>= 0).
+ *  precision one of ilves_precision.
+ *  lambda0   DEVICE float32 (n_constraints) initial multipliers, or NULL for zero.
+ *  x_out     DEVICE float64 (n_atoms, 3): constrained positions (may alias x_unc).
+ *  lambda_out DEVICE float64 (n_constraints): multipliers, or NULL.
+ *  iterations_out DEVICE int32 (n_molecules): linear solves per molecule, or NULL.
+ *  mol_status_out DEVICE int32 (n_molecules): ilves_mol_status per molecule, or NULL.
+ *  stream    cudaStream_t to enqueue on.
+ * Errors: ILVES_ERR_INVALID_ARG (NULL required pointer, bad precision, max_iter < 0),
+ *         ILVES_ERR_CUDA (launch failure).  Allocates nothing.
+ */
+ilves_status ilves_solve(ilves_topology* topo, const double* x_old, const double* x_unc,
+                         const double* inv_mass, const double* d, double tol, int32_t max_iter,
+                         int32_t precision, const float* lambda0, double* x_out,
+                         double* lambda_out, int32_t* iterations_out, int32_t* mol_status_out,
+                         void* stream);
+
+/* Sizes of a topology (any pointer may be NULL):
+ *  n_molecules, nnz_factor (entries of L+U including fill, summed over molecules),
+ *  max_levels (largest level count of any molecule), n_fill (fill entries),
+ *  n_large (molecules on the multi-warp path). */
+ilves_status ilves_topology_info(const ilves_topology* topo, int32_t* n_molecules,
+                                 int64_t* nnz_factor, int32_t* max_levels, int64_t* n_fill,
+                                 int32_t* n_large);
+
+/* Copies per-molecule sizes to HOST arrays of n_molecules entries (any may be NULL):
+ * atoms, constraints, levels of the factorisation, and the 0-based global index of
+ * the molecule's first (smallest) atom. */
+ilves_status ilves_topology_molecules(const ilves_topology* topo, int32_t* atoms,
+                                      int32_t* constraints, int32_t* levels, int32_t* first_atom);
+
+/* Symbolic structure of molecule `mol` (HOST arrays; any may be NULL), for checking the
+ * planner: pos_gid[p] = global constraint id eliminated at position p (nc entries);
+ * level[p] = its level; N+(p) (later neighbours in the filled graph, as positions) is
+ * up_idx[up_ptr[p] .. up_ptr[p+1]) with up_ptr of nc+1 entries and up_idx of
+ * up_ptr[nc] entries (call once with up_idx = NULL to size it). */
+ilves_status ilves_topology_export_molecule(const ilves_topology* topo, int32_t mol, int32_t* pos_gid,
+                                            int32_t* level, int32_t* up_ptr, int32_t* up_idx);
+
+/* Releases every device and host buffer of the topology (NULL is ignored). */
+void ilves_destroy_topology(ilves_topology* topo);
+
+/* Static string naming a status code. */
+const char* ilves_status_string(int32_t status);
+
+/* Number of kernel launches the most recent ilves_solve on this topology enqueued. */
+int32_t ilves_last_launch_count(const ilves_topology* topo);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ILVES_H */

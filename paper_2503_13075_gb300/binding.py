@@ -1,0 +1,190 @@
+"""Thin Python binding of the ILVES C ABI (``include/ilves.h``).
+
+Argument marshalling only: torch tensors are checked (device, dtype, layout) and
+their device pointers handed to ``libilves.so``; every step of the solve runs in
+the library's CUDA kernels.  There is no CPU fallback: without the built library
+every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libilves.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ilves.h")
+
+FP64, MIXED = 0, 1
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE = 0, 1, 2, 3
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid topology", 3: "CUDA error", 4: "out of device memory",
+          5: "device wait timed out"}
+
+
+class IlvesError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class SetupOpts(ctypes.Structure):
+    _fields_ = [("ordering", ctypes.c_int32), ("degree_slack", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("max_warp_constraints", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"ILVES CUDA library missing at {LIB_PATH}; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D, VP = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    pi32 = ctypes.POINTER(I32)
+    pi64 = ctypes.POINTER(I64)
+    L.ilves_default_opts.argtypes = [ctypes.POINTER(SetupOpts)]
+    L.ilves_default_opts.restype = None
+    L.ilves_setup_topology.argtypes = [I32, I32, P, P, ctypes.POINTER(SetupOpts), ctypes.POINTER(P)]
+    L.ilves_setup_topology.restype = I32
+    L.ilves_solve.argtypes = [P, P, P, P, P, D, I32, I32, P, P, P, P, P, VP]
+    L.ilves_solve.restype = I32
+    L.ilves_topology_info.argtypes = [P, pi32, pi64, pi32, pi64, pi32]
+    L.ilves_topology_info.restype = I32
+    L.ilves_topology_molecules.argtypes = [P, P, P, P, P]
+    L.ilves_topology_molecules.restype = I32
+    L.ilves_topology_export_molecule.argtypes = [P, I32, P, P, P, P]
+    L.ilves_topology_export_molecule.restype = I32
+    L.ilves_destroy_topology.argtypes = [P]
+    L.ilves_destroy_topology.restype = None
+    L.ilves_status_string.argtypes = [I32]
+    L.ilves_status_string.restype = ctypes.c_char_p
+    L.ilves_last_launch_count.argtypes = [P]
+    L.ilves_last_launch_count.restype = I32
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of the functions ``include/ilves.h`` declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ilves_[a-z_]+)\s*\(", src)))
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else ctypes.c_void_p(a.data_ptr())
+
+
+def _check(code, where):
+    if code != 0:
+        raise IlvesError(code, where)
+
+
+class Topology:
+    """A constraint topology set up once and solved many times (``ilves_setup_topology``)."""
+
+    def __init__(self, n_atoms, atom_i, atom_j, ordering=0, degree_slack=2, warps_per_cta=0,
+                 ctas_per_sm=0, device=None, plan_only=False, max_warp_constraints=0):
+        L = lib()
+        ai = np.ascontiguousarray(atom_i, dtype=np.int32)
+        aj = np.ascontiguousarray(atom_j, dtype=np.int32)
+        if ai.shape != aj.shape or ai.ndim != 1:
+            raise ValueError("atom_i and atom_j must be 1-D arrays of equal length")
+        o = SetupOpts()
+        L.ilves_default_opts(ctypes.byref(o))
+        o.ordering, o.degree_slack = ordering, degree_slack
+        o.warps_per_cta, o.ctas_per_sm = warps_per_cta, ctas_per_sm
+        o.max_warp_constraints = max_warp_constraints
+        if plan_only:
+            o.device = -2
+        elif device is not None:
+            o.device = int(device)
+        h = ctypes.c_void_p()
+        _check(L.ilves_setup_topology(int(n_atoms), ai.size, _ptr(ai), _ptr(aj), ctypes.byref(o), ctypes.byref(h)),
+               "ilves_setup_topology")
+        self._h = h
+        self.n_atoms = int(n_atoms)
+        self.n_constraints = int(ai.size)
+        self.plan_only = plan_only
+        n = ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        ml = ctypes.c_int32()
+        fill = ctypes.c_int64()
+        nl = ctypes.c_int32()
+        _check(L.ilves_topology_info(h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(ml), ctypes.byref(fill),
+                                     ctypes.byref(nl)), "ilves_topology_info")
+        self.n_molecules, self.nnz_factor, self.max_levels = n.value, nnz.value, ml.value
+        self.n_fill, self.n_large = fill.value, nl.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ilves_destroy_topology(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def molecules(self):
+        """Per-molecule (atoms, constraints, levels, first_atom) as int32 numpy arrays."""
+        n = self.n_molecules
+        out = [np.zeros(n, np.int32) for _ in range(4)]
+        _check(lib().ilves_topology_molecules(self._h, *[_ptr(a) for a in out]), "ilves_topology_molecules")
+        return tuple(out)
+
+    def export_molecule(self, mol):
+        """(pos_gid, level, up_ptr, up_idx) of one molecule's symbolic factorisation."""
+        atoms, cons, _, _ = self.molecules()
+        nc = int(cons[mol])
+        pos = np.zeros(nc, np.int32)
+        lev = np.zeros(nc, np.int32)
+        ptr = np.zeros(nc + 1, np.int32)
+        L = lib()
+        _check(L.ilves_topology_export_molecule(self._h, int(mol), _ptr(pos), _ptr(lev), _ptr(ptr), None),
+               "export")
+        idx = np.zeros(max(1, int(ptr[-1])), np.int32)
+        _check(L.ilves_topology_export_molecule(self._h, int(mol), None, None, None, _ptr(idx)), "export")
+        return pos, lev, ptr, idx[: ptr[-1]]
+
+    def last_launch_count(self):
+        return int(lib().ilves_last_launch_count(self._h))
+
+    def solve(self, x_old, x_unc, inv_mass, d, tol=1e-12, max_iter=25, precision="mixed", lambda0=None,
+              x_out=None, lambda_out=None, iterations_out=None, status_out=None, stream=None):
+        """One ``ilves_solve`` on device tensors; returns (x, lambda, iterations, status)."""
+        import torch
+
+        if self.plan_only:
+            raise RuntimeError("topology was planned on the host only")
+        dev = x_unc.device
+        if dev.type != "cuda":
+            raise ValueError("ilves_solve takes CUDA tensors")
+        for name, t, shape in (("x_old", x_old, (self.n_atoms, 3)), ("x_unc", x_unc, (self.n_atoms, 3)),
+                               ("inv_mass", inv_mass, (self.n_atoms,)), ("d", d, (self.n_constraints,))):
+            if t.dtype != torch.float64 or tuple(t.shape) != shape or not t.is_contiguous() or t.device != dev:
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape {shape}")
+        if lambda0 is not None and (lambda0.dtype != torch.float32 or lambda0.numel() != self.n_constraints
+                                    or not lambda0.is_contiguous()):
+            raise ValueError("lambda0 must be a contiguous float32 tensor of n_constraints entries")
+        x_out = torch.empty_like(x_unc) if x_out is None else x_out
+        lambda_out = torch.empty(self.n_constraints, dtype=torch.float64, device=dev) if lambda_out is None else lambda_out
+        iterations_out = (torch.empty(self.n_molecules, dtype=torch.int32, device=dev)
+                          if iterations_out is None else iterations_out)
+        status_out = torch.empty(self.n_molecules, dtype=torch.int32, device=dev) if status_out is None else status_out
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().ilves_solve(self._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), float(tol), int(max_iter),
+                                 prec, None if lambda0 is None else _ptr(lambda0), _ptr(x_out), _ptr(lambda_out),
+                                 _ptr(iterations_out), _ptr(status_out), ctypes.c_void_p(s)), "ilves_solve")
+        return x_out, lambda_out, iterations_out, status_out

@@ -1,0 +1,118 @@
+// internal.h -- data layouts shared by the host planner (topology.cpp) and the
+// CUDA kernels (solve.cu).  Not part of the public ABI.
+//
+// Every molecule is described by a "program": a compact, 16-byte aligned blob of
+// 16-bit indices that a team of threads (one warp, or one CTA for large molecules)
+// copies next to its numerical state and then interprets once per Newton iteration.
+//
+// Constraint numbering inside a molecule is the ELIMINATION POSITION p (0..nc-1):
+// pivots are sorted by level, so the pivots of one level are contiguous.
+//
+// LU form: A = L U with L unit lower triangular and U upper triangular (diagonal
+// d_j).  L is stored unscaled, Lt[q,j] = L[q,j] d_j, together with inv_j = 1 / d_j,
+// so that every entry is computed by the same division-free expression:
+//   DIAG j        d_j     = a_jj - sum_m Lt[j,m] inv_m U[m,j];   inv_j = 1 / d_j
+//                 y_j     = sigma_j - sum_m Lt[j,m] inv_m y_m     (forward solve, fused)
+//   U (j,q)       U[j,q]  = a_jq - sum_m Lt[j,m] inv_m U[m,q]    for q in N+(j)
+//   L (q,j)       Lt[q,j] = a_qj - sum_m Lt[q,m] inv_m U[m,j]    for q in N+(j)
+// where N+(j) are the later neighbours of j in the filled graph and m runs over
+// earlier pivots adjacent to both row and column.  Task t writes value slot t.
+// Within a level the DIAG tasks come first, then for each pivot its U row and its
+// L column.  The backward solve is delta_j = inv_j (y_j - sum_{q in N+(j)} U[j,q] delta_q).
+#pragma once
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define ILVES_HD __host__ __device__ __forceinline__
+#else
+#define ILVES_HD inline
+#endif
+
+namespace ilves {
+
+constexpr uint32_t kNoAtom32 = 0xFFFFFFFFu;
+
+// Program words.  IdxT is uint16_t for molecules run by one warp (compact, staged in
+// shared memory) and uint32_t for large molecules run by a whole CTA.
+//   Task: row, col of the target entry; atomsign = (shared atom << 1) | (sign
+//         product < 0), all-ones for fill entries and diagonals; tstart = first term.
+//         Task t's terms are [tstart_t, tstart_{t+1}); a sentinel task ends the list.
+//   Term: l = slot of Lt[row, m], u = slot of Ut[m, col], m = the earlier pivot.
+//   Piv:  diag = first slot of the pivot's U row (its L column follows), nup = |N+(pivot)|.
+//   ConA: local atom ids (i, j) of the constraint at position p.
+// inc[e] = p << 1 | (atom is the second atom of constraint p)
+template <class IdxT> struct Task { IdxT row, col, atomsign, tstart; };
+template <class IdxT> struct ConA { IdxT i, j; };
+template <class IdxT> struct Term { IdxT l, u, m, pad; };
+template <class IdxT> struct Piv { IdxT diag, nup; };
+
+ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
+
+struct ProgLayout {
+    uint32_t con_atoms, con_gid, piv, lvl_task, lvl_piv, inc_ptr, inc, tasks, terms, bytes;
+};
+
+template <class IdxT>
+ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t nterm,
+                                uint32_t nlevel) {
+    ProgLayout L;
+    const uint32_t ix = (uint32_t)sizeof(IdxT);
+    uint32_t o = 0;
+    L.con_atoms = o; o = align16(o + 2u * ix * nc);
+    L.con_gid = o;   o = align16(o + 4u * nc);
+    L.piv = o;       o = align16(o + 2u * ix * nc);
+    L.lvl_task = o;  o = align16(o + ix * (nlevel + 1));
+    L.lvl_piv = o;   o = align16(o + ix * (nlevel + 1));
+    L.inc_ptr = o;   o = align16(o + ix * (na + 1));
+    L.inc = o;       o = align16(o + ix * 2u * nc);
+    L.tasks = o;     o = align16(o + 4u * ix * (ntask + 1));
+    L.terms = o;     o = align16(o + 4u * ix * nterm);
+    L.bytes = o;
+    return L;
+}
+
+// Numerical state of one molecule (after its program).  hp_bytes = 8 (float64 state),
+// lp_bytes = factor element size (4 for float32, 8 for float64); 3-vectors of the
+// factor precision are padded to 4 elements.  Atom arrays have na + 1 entries: the
+// extra atom has zero weight and is what fill entries of the pattern point at.
+struct StateLayout {
+    uint32_t x, w, wf, rho, d2, told2, lam, rhof, rf, cdiag, inv, y, vals, bytes;
+};
+
+ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t lp_bytes,
+                                  uint32_t hp_bytes) {
+    StateLayout S;
+    const uint32_t vp = 4u * lp_bytes;
+    uint32_t o = 0;
+    S.x = o;      o = align16(o + 3u * hp_bytes * na);   // SoA: x[0..na), y[..], z[..]
+    S.w = o;      o = align16(o + hp_bytes * (na + 1));
+    S.wf = o;     o = align16(o + 4u * (na + 1));
+    S.rho = o;    o = align16(o + 3u * hp_bytes * nc);   // SoA
+    S.d2 = o;     o = align16(o + hp_bytes * nc);
+    S.told2 = o;  o = align16(o + hp_bytes * nc);
+    S.lam = o;    o = align16(o + hp_bytes * nc);
+    S.rhof = o;   o = align16(o + vp * nc);
+    S.rf = o;     o = align16(o + vp * nc);
+    S.cdiag = o;  o = align16(o + lp_bytes * nc);
+    S.inv = o;    o = align16(o + lp_bytes * nc);
+    S.y = o;      o = align16(o + lp_bytes * nc);
+    S.vals = o;   o = align16(o + lp_bytes * ntask);
+    S.bytes = o;
+    return S;
+}
+
+// One molecule as the kernels see it (56 bytes).
+struct MolDesc {
+    int64_t blob_off;    // byte offset of the program blob in the blob buffer (16-B aligned)
+    int64_t work_off;    // large path: byte offset of the numerical state in the workspace
+    int32_t atom_base;   // first global atom if the molecule's atoms are contiguous, else -1
+    int32_t gid_off;     // offset of this molecule's global atom ids in atom_gid[]
+    int32_t mol_id;      // output index (molecules ordered by smallest atom)
+    int32_t nterm;
+    int32_t ntask;
+    int32_t na, nc;
+    int32_t nlevel;
+    int32_t pad;
+};
+
+}  // namespace ilves

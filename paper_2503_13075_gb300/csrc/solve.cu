@@ -1,0 +1,739 @@
+// solve.cu -- sm_103a kernels and C ABI of the ILVES-M constraint solver.
+//
+// One Newton solve per molecule (supplement Sec. 2.3, ILVES-M):
+//   S1  rho_k = x_old,i - x_old,j;  x = x_unc - M^-1 G(x_old)^T lambda0
+//   S2  sigma_k = |x_i - x_j|^2 - d_k^2; stop when max |sigma_k| / d_k^2 <= tol (Sec. 4)
+//   S3  A = G(x) M^-1 G(x_old)^T assembled on the fly inside the factor tasks:
+//         A_kk = 4 (w_i + w_j) r_k . rho_k,   A_kl = 4 s_k(a) s_l(a) w_a r_k . rho_l
+//   S4  sparse LU (Crout form Lt * Ut) in the planner's elimination order, level by level
+//   S5  forward substitution fused into the DIAG tasks, backward substitution by level;
+//       lambda += delta
+//   S6  x_a -= w_a sum_{k at a} s_k(a) 2 delta_k rho_k;  back to S2
+// All of a molecule's state lives next to its program: in shared memory for molecules
+// run by one warp (the batched persistent kernel), in a global workspace for large
+// molecules run by a whole CTA.  No host round trip happens inside the Newton loop.
+//
+// Precision modes: FP64 runs every step in float64.  MIXED keeps S2, the lambda
+// accumulation and S6 in float64 and runs S3-S5 in float32 (the outer Newton loop is
+// the iterative refinement).  On this GPU the float64 pipe issues about two FMAs per
+// clock per SM and also executes f64<->f32 conversions, so the conversions between
+// the two precisions are done with integer bit operations (exact widening, truncating
+// narrowing) instead.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ilves.h"
+#include "internal.h"
+#include "topology_impl.h"
+
+namespace ilves {
+
+// ------------------------------------------------------------------------------------
+// precision policies
+// ------------------------------------------------------------------------------------
+struct ModeFP64 {
+    using LP = double;
+    struct V4 { double x, y, z, w; };
+    static constexpr int id = ILVES_PREC_FP64;
+    static constexpr double pivot_rel = 1e-13;
+};
+struct ModeMixed {
+    using LP = float;
+    using V4 = float4;
+    static constexpr int id = ILVES_PREC_MIXED;
+    static constexpr float pivot_rel = 1e-5f;
+};
+
+// float64 -> float32 by truncation, on the integer pipe.  Values below float's normal
+// range become signed zero, values above it (never nm-scale coordinates) infinity.
+__device__ __forceinline__ float narrow(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;  // rebias 1023 -> 127
+    unsigned r = sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    r = e <= 0 ? sign : r;
+    r = e >= 255 ? (sign | 0x7F800000u) : r;
+    return __uint_as_float(r);
+}
+
+// float32 -> float64, exact, on the integer pipe (subnormal floats flush to zero).
+__device__ __forceinline__ double widen(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u;
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned mant = b & 0x7FFFFFu;
+    unsigned hi = sign | ((e + 896u) << 20) | (mant >> 3);
+    unsigned lo = mant << 29;
+    hi = e == 0 ? sign : hi;
+    lo = e == 0 ? 0u : lo;
+    hi = e == 255 ? (sign | 0x7FF00000u | (mant >> 3)) : hi;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <class LP> __device__ __forceinline__ LP to_lp(double v);
+template <> __device__ __forceinline__ float to_lp<float>(double v) { return narrow(v); }
+template <> __device__ __forceinline__ double to_lp<double>(double v) { return v; }
+__device__ __forceinline__ double to_hp(float v) { return widen(v); }
+__device__ __forceinline__ double to_hp(double v) { return v; }
+
+// |s| <= t for t >= 0 by comparing bit patterns (NaN compares false)
+__device__ __forceinline__ bool abs_le(double s, double t) {
+    const long long sb = __double_as_longlong(s) & 0x7FFFFFFFFFFFFFFFll;
+    return sb <= __double_as_longlong(t);
+}
+__device__ __forceinline__ bool nonfinite(double s) {
+    return (__double_as_longlong(s) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+}
+__device__ __forceinline__ float lp_abs(float v) { return fabsf(v); }
+__device__ __forceinline__ double lp_abs(double v) { return fabs(v); }
+__device__ __forceinline__ float lp_rcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double lp_rcp(double a) { return 1.0 / a; }
+
+// ------------------------------------------------------------------------------------
+// teams
+// ------------------------------------------------------------------------------------
+struct WarpTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ bool all(bool p) const { return __all_sync(0xFFFFFFFFu, p); }
+    __device__ __forceinline__ bool any(bool p) const { return __any_sync(0xFFFFFFFFu, p); }
+};
+struct BlockTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x; }
+    __device__ __forceinline__ int size() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ bool all(bool p) const { return __syncthreads_and(p) != 0; }
+    __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+};
+
+struct SolveArgs {
+    const double* x_old;
+    const double* x_unc;
+    const double* inv_mass;
+    const double* d;
+    const float* lambda0;
+    double* x_out;
+    double* lambda_out;
+    int32_t* iterations_out;
+    int32_t* status_out;
+    const int32_t* atom_gid;
+    double tol;
+    int32_t max_iter;
+};
+
+// ------------------------------------------------------------------------------------
+// one molecule, one team
+// ------------------------------------------------------------------------------------
+template <class Mode, class IdxT, class Team>
+__device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
+                               const SolveArgs& A) {
+    using LP = typename Mode::LP;
+    using V4 = typename Mode::V4;
+    const int na = D.na, nc = D.nc;
+    const ProgLayout PL = prog_layout<IdxT>(na, nc, D.ntask, D.nterm, D.nlevel);
+    const StateLayout SL = state_layout(na, nc, D.ntask, sizeof(LP), 8);
+    const ConA<IdxT>* con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
+    const int32_t* con_gid = reinterpret_cast<const int32_t*>(prog + PL.con_gid);
+    const Piv<IdxT>* piv = reinterpret_cast<const Piv<IdxT>*>(prog + PL.piv);
+    const IdxT* lvl_task = reinterpret_cast<const IdxT*>(prog + PL.lvl_task);
+    const IdxT* lvl_piv = reinterpret_cast<const IdxT*>(prog + PL.lvl_piv);
+    const IdxT* inc_ptr = reinterpret_cast<const IdxT*>(prog + PL.inc_ptr);
+    const IdxT* inc = reinterpret_cast<const IdxT*>(prog + PL.inc);
+    const Task<IdxT>* tasks = reinterpret_cast<const Task<IdxT>*>(prog + PL.tasks);
+    const Term<IdxT>* terms = reinterpret_cast<const Term<IdxT>*>(prog + PL.terms);
+    double* X = reinterpret_cast<double*>(st + SL.x);  // SoA x | y | z
+    double* W = reinterpret_cast<double*>(st + SL.w);
+    float* WF = reinterpret_cast<float*>(st + SL.wf);
+    double* RHO = reinterpret_cast<double*>(st + SL.rho);  // SoA
+    double* D2 = reinterpret_cast<double*>(st + SL.d2);
+    double* TD2 = reinterpret_cast<double*>(st + SL.told2);
+    double* LAM = reinterpret_cast<double*>(st + SL.lam);
+    V4* RHOF = reinterpret_cast<V4*>(st + SL.rhof);
+    V4* RF = reinterpret_cast<V4*>(st + SL.rf);
+    LP* CD = reinterpret_cast<LP*>(st + SL.cdiag);
+    LP* INV = reinterpret_cast<LP*>(st + SL.inv);
+    LP* Y = reinterpret_cast<LP*>(st + SL.y);
+    LP* V = reinterpret_cast<LP*>(st + SL.vals);
+    const int r0 = tm.rank(), ts = tm.size();
+    const IdxT no_atom = (IdxT)~(IdxT)0;
+
+    auto gid_of = [&](int a) -> int64_t {
+        return D.atom_base >= 0 ? (int64_t)D.atom_base + a : (int64_t)A.atom_gid[D.gid_off + a];
+    };
+    // ---- S1: reference geometry
+    for (int a = r0; a < na; a += ts) {
+        const int64_t g = gid_of(a);
+        X[a] = A.x_old[3 * g];
+        X[na + a] = A.x_old[3 * g + 1];
+        X[2 * na + a] = A.x_old[3 * g + 2];
+        const double w = A.inv_mass[g];
+        W[a] = w;
+        WF[a] = narrow(w);
+    }
+    if (r0 == 0) {  // zero-weight atom referenced by fill entries
+        W[na] = 0.0;
+        WF[na] = 0.0f;
+    }
+    tm.sync();
+    for (int p = r0; p < nc; p += ts) {
+        const int i = con[p].i, j = con[p].j;
+        const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+        RHO[p] = rx;
+        RHO[nc + p] = ry;
+        RHO[2 * nc + p] = rz;
+        V4 v;
+        v.x = to_lp<LP>(rx);
+        v.y = to_lp<LP>(ry);
+        v.z = to_lp<LP>(rz);
+        v.w = LP(0);
+        RHOF[p] = v;
+        const int32_t g = con_gid[p];
+        const double dd = A.d[g];
+        D2[p] = dd * dd;
+        TD2[p] = A.tol * (dd * dd);
+        CD[p] = LP(4) * (to_lp<LP>(W[i]) + to_lp<LP>(W[j]));
+        const float l0 = A.lambda0 ? A.lambda0[g] : 0.0f;
+        LAM[p] = widen(l0);
+        Y[p] = (LP)l0;
+    }
+    tm.sync();
+    for (int a = r0; a < na; a += ts) {
+        const int64_t g = gid_of(a);
+        X[a] = A.x_unc[3 * g];
+        X[na + a] = A.x_unc[3 * g + 1];
+        X[2 * na + a] = A.x_unc[3 * g + 2];
+    }
+    tm.sync();
+
+    // ---- S6: x -= M^-1 G(x_old)^T Y   (Y holds delta, or lambda0 before the loop)
+    auto update_positions = [&]() {
+        for (int a = r0; a < na; a += ts) {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            const int e1 = inc_ptr[a + 1];
+            for (int e = inc_ptr[a]; e < e1; ++e) {
+                const unsigned v = inc[e];
+                const int p = (int)(v >> 1);
+                const LP dl = Y[p];
+                const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
+                ax = fma(c, RHO[p], ax);
+                ay = fma(c, RHO[nc + p], ay);
+                az = fma(c, RHO[2 * nc + p], az);
+            }
+            const double w = W[a];
+            X[a] = fma(-w, ax, X[a]);
+            X[na + a] = fma(-w, ay, X[na + a]);
+            X[2 * na + a] = fma(-w, az, X[2 * na + a]);
+        }
+    };
+    if (A.lambda0) {
+        update_positions();
+        tm.sync();
+    }
+
+    int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
+    for (int it = 0;; ++it) {
+        // ---- S2: violations (float64), Jacobian rows and right-hand side (factor precision)
+        bool conv = true, bad = false;
+        for (int p = r0; p < nc; p += ts) {
+            const int i = con[p].i, j = con[p].j;
+            const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+            const double s = fma(rx, rx, fma(ry, ry, fma(rz, rz, -D2[p])));
+            conv = conv && abs_le(s, TD2[p]);
+            bad = bad || nonfinite(s);
+            V4 v;
+            v.x = to_lp<LP>(rx);
+            v.y = to_lp<LP>(ry);
+            v.z = to_lp<LP>(rz);
+            v.w = LP(0);
+            RF[p] = v;
+            Y[p] = to_lp<LP>(s);
+        }
+        if (tm.any(bad)) {
+            status = ILVES_MOL_NONFINITE;
+            iters = it;
+            break;
+        }
+        if (tm.all(conv)) {
+            status = ILVES_MOL_CONVERGED;
+            iters = it;
+            break;
+        }
+        if (it >= A.max_iter) break;
+        tm.sync();
+        // ---- S3 + S4 + forward half of S5, one level at a time
+        bool singular = false;
+        for (int l = 0; l < D.nlevel; ++l) {
+            const int p0 = lvl_piv[l], np = lvl_piv[l + 1] - p0;
+            const int t0 = lvl_task[l], t1 = lvl_task[l + 1];
+            for (int k = r0; k < np; k += ts) {  // DIAG tasks: pivot, 1 / pivot, forward solve
+                const int p = p0 + k, t = t0 + k;
+                const V4 rr = RF[p], pp = RHOF[p];
+                const LP a = CD[p] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+                LP s = a, yv = Y[p];
+                const int e1 = tasks[t + 1].tstart;
+                for (int e = tasks[t].tstart; e < e1; ++e) {
+                    const Term<IdxT> tr = terms[e];
+                    const LP li = V[tr.l] * INV[tr.m];
+                    s -= li * V[tr.u];
+                    yv -= li * Y[tr.m];
+                }
+                singular = singular || !(lp_abs(s) > Mode::pivot_rel * lp_abs(a));
+                V[t] = s;
+                INV[p] = lp_rcp(s);
+                Y[p] = yv;
+            }
+            for (int t = t0 + np + r0; t < t1; t += ts) {  // U and L entries, one code path
+                const Task<IdxT> tk = tasks[t];
+                const int e1 = tasks[t + 1].tstart;
+                const V4 rr = RF[tk.row], pp = RHOF[tk.col];
+                const int at = tk.atomsign >> 1;
+                LP wv;
+                if constexpr (sizeof(LP) == 8) wv = (LP)W[at];
+                else wv = (LP)WF[at];
+                const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
+                LP s = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+                for (int e = tk.tstart; e < e1; ++e) {
+                    const Term<IdxT> tr = terms[e];
+                    s -= V[tr.l] * INV[tr.m] * V[tr.u];
+                }
+                V[t] = s;
+            }
+            tm.sync();
+        }
+        if (tm.any(singular)) {
+            status = ILVES_MOL_SINGULAR_PIVOT;
+            iters = it;
+            break;
+        }
+        // ---- backward half of S5
+        for (int l = D.nlevel - 1; l >= 0; --l) {
+            const int p1 = lvl_piv[l + 1];
+            for (int p = lvl_piv[l] + r0; p < p1; p += ts) {
+                const int us = piv[p].diag, nu = piv[p].nup;
+                LP dl = Y[p];
+                for (int k = 0; k < nu; ++k) dl -= V[us + k] * Y[tasks[us + k].col];
+                Y[p] = dl * INV[p];
+            }
+            tm.sync();
+        }
+        // ---- lambda += delta (float64), S6
+        for (int p = r0; p < nc; p += ts) LAM[p] += to_hp(Y[p]);
+        update_positions();
+        tm.sync();
+    }
+    // ---- S7: outputs
+    for (int a = r0; a < na; a += ts) {
+        const int64_t g = gid_of(a);
+        A.x_out[3 * g] = X[a];
+        A.x_out[3 * g + 1] = X[na + a];
+        A.x_out[3 * g + 2] = X[2 * na + a];
+    }
+    if (A.lambda_out)
+        for (int p = r0; p < nc; p += ts) A.lambda_out[con_gid[p]] = LAM[p];
+    if (r0 == 0) {
+        if (A.iterations_out) A.iterations_out[D.mol_id] = iters;
+        if (A.status_out) A.status_out[D.mol_id] = status;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------
+struct SmallSched {
+    const int32_t* cta_round_ptr;
+    const int32_t* round_ptr;
+    const int32_t* round_mol;
+    const int32_t* round_off;
+};
+
+// Persistent batched kernel: each CTA walks its rounds; in a round, warp w solves one
+// molecule in its slice of the shared-memory arena.  The program blob is staged
+// into shared memory with 16-byte loads before the Newton loop.
+template <class Mode>
+__global__ void __launch_bounds__(1024, 1)
+k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
+              SolveArgs A) {
+    extern __shared__ __align__(16) uint8_t arena[];
+    const WarpTeam tm;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x;
+    const int rb = S.cta_round_ptr[c], re = S.cta_round_ptr[c + 1];
+    for (int r = rb; r < re; ++r) {
+        const int m0 = S.round_ptr[r], m1 = S.round_ptr[r + 1];
+        if (warp < m1 - m0) {
+            const MolDesc D = desc[S.round_mol[m0 + warp]];
+            uint8_t* slice = arena + S.round_off[m0 + warp];
+            const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel);
+            const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
+            uint4* dst = reinterpret_cast<uint4*>(slice);
+            const int n16 = (int)(PL.bytes >> 4);
+            for (int k = lane; k < n16; k += 32) dst[k] = __ldg(src + k);
+            __syncwarp();
+            solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.bytes, A);
+        }
+        __syncthreads();
+    }
+}
+
+// Large molecules: one CTA per molecule, program and state in global memory.
+template <class Mode>
+__global__ void __launch_bounds__(512, 1)
+k_solve_large(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, uint8_t* work,
+              SolveArgs A) {
+    const BlockTeam tm;
+    const MolDesc D = desc[blockIdx.x];
+    solve_molecule<Mode, uint32_t, BlockTeam>(tm, D, blob + D.blob_off, work + D.work_off, A);
+}
+
+__global__ void k_copy_free(const int32_t* __restrict__ idx, int n, const double* __restrict__ x_unc,
+                            double* __restrict__ x_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int64_t g = idx[i];
+        x_out[3 * g] = x_unc[3 * g];
+        x_out[3 * g + 1] = x_unc[3 * g + 1];
+        x_out[3 * g + 2] = x_unc[3 * g + 2];
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------
+template <class T>
+static cudaError_t upload(T** dptr, const std::vector<T>& v) {
+    *dptr = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dptr, v.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void free_device(ilves_topology* T) {
+    auto f = [](void* p) {
+        if (p) cudaFree(p);
+    };
+    f(T->d_desc);
+    f(T->d_blob);
+    f(T->d_atom_gid);
+    f(T->d_free_atoms);
+    f(T->d_work);
+    for (auto& s : T->sched) {
+        f(s.cta_round_ptr);
+        f(s.round_ptr);
+        f(s.round_mol);
+        f(s.round_off);
+        s = DeviceSchedule{};
+    }
+    if (T->side_stream) cudaStreamDestroy((cudaStream_t)T->side_stream);
+    if (T->ev_fork) cudaEventDestroy((cudaEvent_t)T->ev_fork);
+    if (T->ev_join) cudaEventDestroy((cudaEvent_t)T->ev_join);
+    T->d_desc = nullptr;
+    T->d_blob = nullptr;
+    T->d_atom_gid = nullptr;
+    T->d_free_atoms = nullptr;
+    T->d_work = nullptr;
+    T->side_stream = T->ev_fork = T->ev_join = nullptr;
+}
+
+template <class Mode>
+static const void* small_kernel() {
+    return (const void*)k_solve_small<Mode>;
+}
+
+static ilves_status to_status(cudaError_t e) {
+    if (e == cudaSuccess) return ILVES_OK;
+    if (e == cudaErrorMemoryAllocation) return ILVES_ERR_OOM;
+    return ILVES_ERR_CUDA;
+}
+
+static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o) {
+    cudaError_t e;
+    int dev = o.device;
+    if (dev < 0) {
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return to_status(e);
+    } else if ((e = cudaSetDevice(dev)) != cudaSuccess) {
+        return to_status(e);
+    }
+    T->device = dev;
+    int n_sm = 0, smem_optin = 0, smem_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    T->n_sm = n_sm;
+    const int ctas_per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, 4) : 1;
+    const int arena = std::min(smem_optin, smem_sm / ctas_per_sm - 1024) & ~15;
+    // molecules whose slice does not fit an arena take the CTA-per-molecule path
+    for (auto& M : T->mols)
+        if (!M.large && footprint(M, ILVES_PREC_FP64) > (uint32_t)arena) M.large = true;
+    // descriptors, program blobs, atom ids
+    std::vector<int32_t> order;
+    for (int32_t m = 0; m < T->n_mol; ++m)
+        if (!T->mols[m].large) order.push_back(m);
+    T->n_small = (int32_t)order.size();
+    for (int32_t m = 0; m < T->n_mol; ++m)
+        if (T->mols[m].large) order.push_back(m);
+    T->n_large = T->n_mol - T->n_small;
+    std::vector<int32_t> desc_index(T->n_mol);
+    std::vector<MolDesc> desc(T->n_mol);
+    std::vector<int32_t> gids;
+    int64_t boff = 0, woff = 0;
+    for (int32_t k = 0; k < T->n_mol; ++k) {
+        const int32_t m = order[k];
+        const MolHost& M = T->mols[m];
+        desc_index[m] = k;
+        MolDesc& D = desc[k];
+        D.blob_off = boff;
+        boff += (program_blob_bytes(T, m) + 15) & ~int64_t(15);
+        const int32_t na = (int32_t)M.atoms.size();
+        D.atom_base = (M.atoms.back() - M.atoms.front() == na - 1) ? M.atoms.front() : -1;
+        D.gid_off = (int32_t)gids.size();
+        gids.insert(gids.end(), M.atoms.begin(), M.atoms.end());
+        D.mol_id = m;
+        D.nterm = M.nterm;
+        D.ntask = M.ntask;
+        D.na = na;
+        D.nc = (int32_t)M.cons.size();
+        D.nlevel = M.nlevel;
+        D.pad = 0;
+        D.work_off = 0;
+        if (M.large) {
+            D.work_off = woff;
+            woff += (state_layout(na, D.nc, M.ntask, 8, 8).bytes + 255) & ~int64_t(255);
+        }
+    }
+    std::vector<uint8_t> blob((size_t)std::max<int64_t>(boff, 16), 0);
+    for (int32_t k = 0; k < T->n_mol; ++k) program_write_blob(T, order[k], blob.data() + desc[k].blob_off);
+    T->blob_bytes = boff;
+    T->work_bytes = woff;
+    if ((e = upload(&T->d_desc, desc)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_blob, blob)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_atom_gid, gids)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_free_atoms, T->free_atoms)) != cudaSuccess) return to_status(e);
+    if (woff > 0 && (e = cudaMalloc((void**)&T->d_work, woff)) != cudaSuccess) return to_status(e);
+    // persistent schedules, one per precision mode
+    for (int mode = 0; mode < 2; ++mode) {
+        std::vector<uint32_t> fps;
+        for (int32_t m = 0; m < T->n_mol; ++m)
+            if (!T->mols[m].large) fps.push_back(footprint(T->mols[m], mode));
+        int warps = o.warps_per_cta;
+        if (warps <= 0) {
+            // enough warps to fill the arena with typical molecules
+            std::vector<uint32_t> s = fps;
+            uint32_t med = 1;
+            if (!s.empty()) {
+                std::nth_element(s.begin(), s.begin() + s.size() / 2, s.end());
+                med = std::max<uint32_t>(1, s[s.size() / 2]);
+            }
+            warps = std::max(1, std::min(32, (int)(arena / med)));
+        }
+        warps = std::max(1, std::min(32, warps));
+        HostSchedule HS;
+        build_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
+        for (auto& km : HS.round_mol) km = desc_index[km];
+        DeviceSchedule& DS = T->sched[mode];
+        DS.n_cta = HS.n_cta;
+        DS.warps = HS.warps;
+        DS.arena = HS.arena;
+        if ((e = upload(&DS.cta_round_ptr, HS.cta_round_ptr)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.round_ptr, HS.round_ptr)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.round_mol, HS.round_mol)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.round_off, HS.round_off)) != cudaSuccess) return to_status(e);
+    }
+    if (T->n_large > 0) {
+        cudaStream_t s;
+        cudaEvent_t a, b;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return to_status(e);
+        T->side_stream = s;
+        if ((e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess) return to_status(e);
+        T->ev_fork = a;
+        if ((e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess) return to_status(e);
+        T->ev_join = b;
+    }
+    T->on_device = true;
+    return ILVES_OK;
+}
+
+template <class Mode>
+static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStream_t stream) {
+    cudaError_t e;
+    int launches = 0;
+    const DeviceSchedule& DS = T->sched[Mode::id];
+    if (!T->smem_attr_set[Mode::id]) {
+        e = cudaFuncSetAttribute(small_kernel<Mode>(), cudaFuncAttributeMaxDynamicSharedMemorySize, DS.arena);
+        if (e != cudaSuccess) return to_status(e);
+        T->smem_attr_set[Mode::id] = true;
+    }
+    if (T->n_large > 0) {
+        cudaStream_t side = (cudaStream_t)T->side_stream;
+        if ((e = cudaEventRecord((cudaEvent_t)T->ev_fork, stream)) != cudaSuccess) return to_status(e);
+        if ((e = cudaStreamWaitEvent(side, (cudaEvent_t)T->ev_fork, 0)) != cudaSuccess) return to_status(e);
+        k_solve_large<Mode><<<T->n_large, T->large_threads, 0, side>>>(T->d_desc + T->n_small, T->d_blob,
+                                                                       T->d_work, A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+        ++launches;
+        if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
+    }
+    if (T->n_small > 0) {
+        SmallSched S{DS.cta_round_ptr, DS.round_ptr, DS.round_mol, DS.round_off};
+        k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+        ++launches;
+    }
+    const int nf = (int)T->free_atoms.size();
+    if (nf > 0 && A.x_out != A.x_unc) {
+        k_copy_free<<<(nf + 255) / 256, 256, 0, stream>>>(T->d_free_atoms, nf, A.x_unc, A.x_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+        ++launches;
+    }
+    if (T->n_large > 0) {
+        if ((e = cudaStreamWaitEvent(stream, (cudaEvent_t)T->ev_join, 0)) != cudaSuccess) return to_status(e);
+    }
+    T->last_launches = launches;
+    return ILVES_OK;
+}
+
+}  // namespace ilves
+
+using namespace ilves;
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" void ilves_default_opts(ilves_setup_opts* o) {
+    if (!o) return;
+    o->ordering = 0;
+    o->degree_slack = 2;
+    o->warps_per_cta = 0;
+    o->ctas_per_sm = 0;
+    o->device = -1;
+    o->max_warp_constraints = 0;
+}
+
+extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const int32_t* atom_i,
+                                             const int32_t* atom_j, const ilves_setup_opts* opts,
+                                             ilves_topology** out) {
+    if (!out) return ILVES_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_atoms < 0 || n_constraints < 0) return ILVES_ERR_INVALID_ARG;
+    if (n_constraints > 0 && (!atom_i || !atom_j)) return ILVES_ERR_INVALID_ARG;
+    ilves_setup_opts o;
+    ilves_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.ordering < 0 || o.ordering > 2 || o.degree_slack < 0 || o.warps_per_cta < 0 ||
+        o.warps_per_cta > 32 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4)
+        return ILVES_ERR_INVALID_ARG;
+    ilves_topology* T = new ilves_topology();
+    ilves_status s = plan_topology(T, n_atoms, n_constraints, atom_i, atom_j, o);
+    if (s == ILVES_OK && o.device != -2) s = upload_topology(T, o);
+    if (s != ILVES_OK) {
+        free_device(T);
+        free_programs(T);
+        delete T;
+        return s;
+    }
+    *out = T;
+    return ILVES_OK;
+}
+
+extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, const double* x_unc,
+                                    const double* inv_mass, const double* d, double tol, int32_t max_iter,
+                                    int32_t precision, const float* lambda0, double* x_out, double* lambda_out,
+                                    int32_t* iterations_out, int32_t* mol_status_out, void* stream) {
+    if (!T || !T->on_device) return ILVES_ERR_INVALID_ARG;
+    if (max_iter < 0 || !(tol >= 0.0)) return ILVES_ERR_INVALID_ARG;
+    if (T->n_atoms > 0 && (!x_old || !x_unc || !inv_mass || !x_out)) return ILVES_ERR_INVALID_ARG;
+    if (T->n_c > 0 && !d) return ILVES_ERR_INVALID_ARG;
+    SolveArgs A;
+    A.x_old = x_old;
+    A.x_unc = x_unc;
+    A.inv_mass = inv_mass;
+    A.d = d;
+    A.lambda0 = lambda0;
+    A.x_out = x_out;
+    A.lambda_out = lambda_out;
+    A.iterations_out = iterations_out;
+    A.status_out = mol_status_out;
+    A.atom_gid = T->d_atom_gid;
+    A.tol = tol;
+    A.max_iter = max_iter;
+    cudaStream_t s = (cudaStream_t)stream;
+    T->last_launches = 0;
+    switch (precision) {
+        case ILVES_PREC_FP64: return launch_mode<ModeFP64>(T, A, s);
+        case ILVES_PREC_MIXED: return launch_mode<ModeMixed>(T, A, s);
+        default: return ILVES_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" ilves_status ilves_topology_info(const ilves_topology* T, int32_t* n_molecules, int64_t* nnz_factor,
+                                            int32_t* max_levels, int64_t* n_fill, int32_t* n_large) {
+    if (!T) return ILVES_ERR_INVALID_ARG;
+    int64_t nnz = 0, fill = 0;
+    int32_t ml = 0, nl = 0;
+    for (const auto& M : T->mols) {
+        nnz += M.ntask;
+        fill += M.n_fill;
+        ml = std::max(ml, M.nlevel);
+        nl += M.large ? 1 : 0;
+    }
+    if (n_molecules) *n_molecules = T->n_mol;
+    if (nnz_factor) *nnz_factor = nnz;
+    if (max_levels) *max_levels = ml;
+    if (n_fill) *n_fill = fill;
+    if (n_large) *n_large = nl;
+    return ILVES_OK;
+}
+
+extern "C" ilves_status ilves_topology_molecules(const ilves_topology* T, int32_t* atoms, int32_t* constraints,
+                                                 int32_t* levels, int32_t* first_atom) {
+    if (!T) return ILVES_ERR_INVALID_ARG;
+    for (int32_t m = 0; m < T->n_mol; ++m) {
+        const MolHost& M = T->mols[m];
+        if (atoms) atoms[m] = (int32_t)M.atoms.size();
+        if (constraints) constraints[m] = (int32_t)M.cons.size();
+        if (levels) levels[m] = M.nlevel;
+        if (first_atom) first_atom[m] = M.atoms.front();
+    }
+    return ILVES_OK;
+}
+
+extern "C" ilves_status ilves_topology_export_molecule(const ilves_topology* T, int32_t mol, int32_t* pos_gid,
+                                                       int32_t* level, int32_t* up_ptr, int32_t* up_idx) {
+    if (!T || mol < 0 || mol >= T->n_mol) return ILVES_ERR_INVALID_ARG;
+    program_export(T, mol, pos_gid, level, up_ptr, up_idx);
+    return ILVES_OK;
+}
+
+extern "C" void ilves_destroy_topology(ilves_topology* T) {
+    if (!T) return;
+    if (T->on_device) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (T->device >= 0 && cur != T->device) cudaSetDevice(T->device);
+        free_device(T);
+        if (cur >= 0 && cur != T->device) cudaSetDevice(cur);
+    }
+    free_programs(T);
+    delete T;
+}
+
+extern "C" const char* ilves_status_string(int32_t s) {
+    switch (s) {
+        case ILVES_OK: return "ok";
+        case ILVES_ERR_INVALID_ARG: return "invalid argument";
+        case ILVES_ERR_TOPOLOGY: return "invalid topology";
+        case ILVES_ERR_CUDA: return "CUDA error";
+        case ILVES_ERR_OOM: return "out of device memory";
+        case ILVES_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int32_t ilves_last_launch_count(const ilves_topology* T) { return T ? T->last_launches : 0; }

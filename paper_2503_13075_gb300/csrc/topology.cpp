@@ -1,0 +1,516 @@
+// topology.cpp -- host-side setup of the ILVES constraint topology (no CUDA calls).
+//
+// Implements the initialisation the paper performs once per neighbour-list
+// rebuild (supplement Sec. 3): constraint graph G -> connected components
+// (molecules) -> line graph L(G), whose adjacency is the sparsity pattern of the
+// Newton matrix A (supplement Sec. 2.3: a_ij = 0 unless bonds i and j share an
+// atom) -> fill-reducing elimination order -> symbolic LU.  On top of that it
+// compiles, per molecule, the level-scheduled task program the CUDA kernels
+// interpret, and partitions the molecules over persistent CTAs.
+//
+// Elimination order.  The paper uses an approximate-minimum-degree order per
+// partition (supplement Sec. 3).  Here the order is chosen for a GPU team that
+// synchronises once per elimination-tree level: pivots are eliminated in rounds,
+// each round taking a greedy independent set of the vertices whose current degree
+// is at most (minimum degree + slack).  slack = 0 is a multiple-minimum-degree
+// order; a larger slack admits a little more fill for far fewer levels (on a
+// chain it becomes cyclic reduction).  The slack is chosen per molecule by a cost
+// model of the kernel (level passes + work), see choose_order().
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <iterator>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "ilves.h"
+#include "internal.h"
+#include "topology_impl.h"
+
+namespace ilves {
+
+static int32_t uf_find(std::vector<int32_t>& p, int32_t a) {
+    while (p[a] != a) {
+        p[a] = p[p[a]];
+        a = p[a];
+    }
+    return a;
+}
+
+// ------------------------------------------------------------------------------------
+// elimination by rounds of independent low-degree vertices
+// ------------------------------------------------------------------------------------
+struct Elimination {
+    std::vector<std::vector<int32_t>> nplus;  // neighbours at elimination time (local ids)
+    std::vector<int32_t> order;               // elimination sequence
+    int64_t n_fill = 0;
+};
+
+// dst := (dst U src) \ {skip}; both sorted
+static void sorted_merge_into(std::vector<int32_t>& dst, const std::vector<int32_t>& src, int32_t skip,
+                              std::vector<int32_t>& tmp) {
+    tmp.clear();
+    tmp.reserve(dst.size() + src.size());
+    size_t i = 0, j = 0;
+    while (i < dst.size() || j < src.size()) {
+        int32_t v;
+        if (j >= src.size() || (i < dst.size() && dst[i] < src[j])) {
+            v = dst[i++];
+        } else if (i >= dst.size() || src[j] < dst[i]) {
+            v = src[j++];
+        } else {
+            v = dst[i++];
+            ++j;
+        }
+        if (v != skip) tmp.push_back(v);
+    }
+    dst.swap(tmp);
+}
+
+static Elimination eliminate_rounds(int32_t n, std::vector<std::vector<int32_t>> H, int32_t slack,
+                                    bool one_per_round) {
+    Elimination E;
+    E.nplus.assign(n, {});
+    E.order.reserve(n);
+    std::vector<int32_t> stamp(n, -1);
+    std::vector<char> alive(n, 1);
+    int32_t remaining = n, rnd = 0;
+    std::vector<std::pair<int32_t, int32_t>> dv;
+    std::vector<int32_t> chosen, tmp;
+    int64_t added = 0;
+    while (remaining > 0) {
+        dv.clear();
+        for (int32_t v = 0; v < n; ++v)
+            if (alive[v]) dv.push_back({(int32_t)H[v].size(), v});
+        std::sort(dv.begin(), dv.end());
+        const int32_t mind = dv[0].first;
+        chosen.clear();
+        for (auto& pr : dv) {
+            const int32_t dg = pr.first, v = pr.second;
+            if (dg > mind + slack) break;
+            if (stamp[v] == rnd) continue;
+            chosen.push_back(v);
+            stamp[v] = rnd;
+            for (int32_t u : H[v]) stamp[u] = rnd;
+            if (one_per_round) break;
+        }
+        for (int32_t v : chosen) {
+            E.nplus[v] = H[v];
+            for (int32_t x : H[v]) {
+                auto& hx = H[x];
+                hx.erase(std::lower_bound(hx.begin(), hx.end(), v));
+                const size_t before = hx.size();
+                sorted_merge_into(hx, H[v], x, tmp);
+                added += (int64_t)(hx.size() - before);
+            }
+            H[v].clear();
+            H[v].shrink_to_fit();
+            alive[v] = 0;
+            E.order.push_back(v);
+        }
+        remaining -= (int32_t)chosen.size();
+        ++rnd;
+    }
+    E.n_fill = added / 2;
+    return E;
+}
+
+// ------------------------------------------------------------------------------------
+// per-molecule program
+// ------------------------------------------------------------------------------------
+struct Program {
+    int32_t nlevel = 0;
+    std::vector<int32_t> pos_con;            // local constraint id at each position
+    std::vector<int32_t> level;              // per position
+    std::vector<std::vector<int32_t>> up;    // N+(p) as sorted positions
+    std::vector<int32_t> diag_task;          // per position: slot of its DIAG task
+    std::vector<int32_t> ustart;             // per position: first slot of its U row (then L column)
+    std::vector<TaskW> tasks;                // + sentinel
+    std::vector<TermW> terms;
+    std::vector<int32_t> lvl_task, lvl_piv;
+    int64_t passes_factor = 0, passes_solve = 0;
+    int64_t n_fill = 0;
+};
+
+static Program compile(int32_t nc, const Elimination& E, const std::vector<int32_t>& ci,
+                       const std::vector<int32_t>& cj, int32_t team, int32_t na_dummy) {
+    Program P;
+    P.n_fill = E.n_fill;
+    // dependency levels: a pivot runs after every earlier pivot adjacent to it
+    std::vector<int32_t> lev(nc, 0);
+    for (int32_t v : E.order)
+        for (int32_t x : E.nplus[v]) lev[x] = std::max(lev[x], lev[v] + 1);
+    std::vector<int32_t> seqidx(nc);
+    for (int32_t i = 0; i < nc; ++i) seqidx[E.order[i]] = i;
+    P.pos_con.resize(nc);
+    std::iota(P.pos_con.begin(), P.pos_con.end(), 0);
+    std::sort(P.pos_con.begin(), P.pos_con.end(), [&](int32_t a, int32_t b) {
+        return lev[a] != lev[b] ? lev[a] < lev[b] : seqidx[a] < seqidx[b];
+    });
+    std::vector<int32_t> pos_of(nc);
+    for (int32_t p = 0; p < nc; ++p) pos_of[P.pos_con[p]] = p;
+    P.level.resize(nc);
+    P.up.assign(nc, {});
+    for (int32_t p = 0; p < nc; ++p) {
+        const int32_t v = P.pos_con[p];
+        P.level[p] = lev[v];
+        for (int32_t x : E.nplus[v]) P.up[p].push_back(pos_of[x]);
+        std::sort(P.up[p].begin(), P.up[p].end());
+    }
+    P.nlevel = nc ? P.level[nc - 1] + 1 : 0;
+    std::vector<std::vector<int32_t>> dn(nc);  // N-(p), ascending
+    for (int32_t m = 0; m < nc; ++m)
+        for (int32_t q : P.up[m]) dn[q].push_back(m);
+    // level boundaries (positions)
+    P.lvl_piv.assign(P.nlevel + 1, nc);
+    for (int32_t p = nc - 1; p >= 0; --p) P.lvl_piv[P.level[p]] = p;
+    // task slots: per level, the DIAG tasks of its pivots, then per pivot its U row and L column
+    P.diag_task.resize(nc);
+    P.ustart.resize(nc);
+    P.lvl_task.assign(P.nlevel + 1, 0);
+    int32_t t = 0;
+    for (int32_t l = 0; l < P.nlevel; ++l) {
+        P.lvl_task[l] = t;
+        for (int32_t p = P.lvl_piv[l]; p < P.lvl_piv[l + 1]; ++p) P.diag_task[p] = t++;
+        for (int32_t p = P.lvl_piv[l]; p < P.lvl_piv[l + 1]; ++p) {
+            P.ustart[p] = t;
+            t += 2 * (int32_t)P.up[p].size();
+        }
+    }
+    P.lvl_task[P.nlevel] = t;
+    auto kpos = [&](int32_t m, int32_t q) {
+        const auto& u = P.up[m];
+        return (int32_t)(std::lower_bound(u.begin(), u.end(), q) - u.begin());
+    };
+    auto slot_U = [&](int32_t m, int32_t q) { return P.ustart[m] + kpos(m, q); };
+    auto slot_L = [&](int32_t q, int32_t m) { return P.ustart[m] + (int32_t)P.up[m].size() + kpos(m, q); };
+    // shared atom and sign product s_a(atom) s_b(atom) of two constraints of the graph;
+    // fill entries point at a dummy atom of zero weight (index na) so they assemble to 0
+    auto atomsign = [&](int32_t pa, int32_t pb) -> uint32_t {
+        const int32_t a = P.pos_con[pa], b = P.pos_con[pb];
+        const uint32_t ai = ci[a], aj = cj[a], bi = ci[b], bj = cj[b];
+        if (ai == bi) return ai << 1;         // (+1)(+1)
+        if (aj == bj) return aj << 1;         // (-1)(-1)
+        if (ai == bj) return (ai << 1) | 1u;  // (+1)(-1)
+        if (aj == bi) return (aj << 1) | 1u;  // (-1)(+1)
+        return (uint32_t)na_dummy << 1;       // fill entry
+    };
+    std::vector<int32_t> ms;
+    auto common = [&](int32_t a, int32_t b) {
+        ms.clear();
+        std::set_intersection(dn[a].begin(), dn[a].end(), dn[b].begin(), dn[b].end(),
+                              std::back_inserter(ms));
+    };
+    P.tasks.assign(t + 1, TaskW{0, 0, 0, 0});
+    std::vector<std::vector<TermW>> tterms(t);
+    for (int32_t p = 0; p < nc; ++p) {
+        const int32_t td = P.diag_task[p];
+        P.tasks[td] = {(uint32_t)p, (uint32_t)p, kNoAtom32, 0u};
+        for (int32_t m : dn[p]) tterms[td].push_back({(uint32_t)slot_L(p, m), (uint32_t)slot_U(m, p), (uint32_t)m, 0u});
+        const int32_t nu = (int32_t)P.up[p].size();
+        for (int32_t k = 0; k < nu; ++k) {
+            const int32_t q = P.up[p][k];
+            const int32_t tu = P.ustart[p] + k, tl = P.ustart[p] + nu + k;
+            P.tasks[tu] = {(uint32_t)p, (uint32_t)q, atomsign(p, q), 0u};
+            common(p, q);
+            for (int32_t m : ms) tterms[tu].push_back({(uint32_t)slot_L(p, m), (uint32_t)slot_U(m, q), (uint32_t)m, 0u});
+            P.tasks[tl] = {(uint32_t)q, (uint32_t)p, atomsign(q, p), 0u};
+            for (int32_t m : ms) tterms[tl].push_back({(uint32_t)slot_L(q, m), (uint32_t)slot_U(m, p), (uint32_t)m, 0u});
+        }
+    }
+    for (int32_t k = 0; k < t; ++k) {
+        P.tasks[k].tstart = (uint32_t)P.terms.size();
+        P.terms.insert(P.terms.end(), tterms[k].begin(), tterms[k].end());
+    }
+    P.tasks[t] = {0u, 0u, kNoAtom32, (uint32_t)P.terms.size()};  // sentinel
+    for (int32_t l = 0; l < P.nlevel; ++l) {
+        P.passes_factor += (P.lvl_task[l + 1] - P.lvl_task[l] + team - 1) / team;
+        P.passes_solve += (P.lvl_piv[l + 1] - P.lvl_piv[l] + team - 1) / team;
+    }
+    return P;
+}
+
+// Kernel cost model (cycles per Newton iteration for one team): a level pass costs
+// roughly one shared-memory round trip plus a few FMAs; work is spread over lanes.
+static double program_cost(const Program& P, int32_t team) {
+    const double pass_lat = 90.0;
+    const double work = (double)P.tasks.size() * 6.0 + (double)P.terms.size() * 4.0;
+    return pass_lat * (double)(P.passes_factor + P.passes_solve) + work / team;
+}
+
+static Program choose_order(int32_t nc, int32_t na, const std::vector<std::vector<int32_t>>& adj,
+                            const std::vector<int32_t>& ci, const std::vector<int32_t>& cj,
+                            const ilves_setup_opts& o, int32_t team) {
+    if (o.ordering == 1) return compile(nc, eliminate_rounds(nc, adj, 0, true), ci, cj, team, na);
+    if (o.ordering == 2) return compile(nc, eliminate_rounds(nc, adj, o.degree_slack, false), ci, cj, team, na);
+    Program best;
+    double best_cost = 1e300;
+    const bool big = nc > 4096;
+    for (int32_t slack : {0, 1, 2, 3, 5}) {
+        if (big && slack != 2) continue;  // large systems: one fixed order keeps setup fast
+        Program P = compile(nc, eliminate_rounds(nc, adj, slack, false), ci, cj, team, na);
+        const double c = program_cost(P, team);
+        if (c < best_cost) {
+            best_cost = c;
+            best = std::move(P);
+        }
+    }
+    return best;
+}
+
+// ------------------------------------------------------------------------------------
+// blob writers (16-bit program for warp molecules, 32-bit for large molecules)
+// ------------------------------------------------------------------------------------
+template <class IdxT>
+static ProgLayout layout_for(const MolHost& M) {
+    return prog_layout<IdxT>((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(), (uint32_t)M.ntask,
+                             (uint32_t)M.nterm, (uint32_t)M.nlevel);
+}
+
+template <class IdxT>
+static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
+    const ProgLayout L = layout_for<IdxT>(M);
+    std::memset(dst, 0, L.bytes);
+    auto* con = reinterpret_cast<ConA<IdxT>*>(dst + L.con_atoms);
+    auto* con_gid = reinterpret_cast<int32_t*>(dst + L.con_gid);
+    auto* piv = reinterpret_cast<Piv<IdxT>*>(dst + L.piv);
+    auto* lvl_task = reinterpret_cast<IdxT*>(dst + L.lvl_task);
+    auto* lvl_piv = reinterpret_cast<IdxT*>(dst + L.lvl_piv);
+    auto* inc_ptr = reinterpret_cast<IdxT*>(dst + L.inc_ptr);
+    auto* inc = reinterpret_cast<IdxT*>(dst + L.inc);
+    auto* tasks = reinterpret_cast<Task<IdxT>*>(dst + L.tasks);
+    auto* terms = reinterpret_cast<Term<IdxT>*>(dst + L.terms);
+    const int32_t nc = (int32_t)M.cons.size(), na = (int32_t)M.atoms.size();
+    for (int32_t p = 0; p < nc; ++p) {
+        const int32_t c = P.pos_con[p];
+        con[p].i = (IdxT)M.ci[c];
+        con[p].j = (IdxT)M.cj[c];
+        con_gid[p] = M.cons[c];
+        piv[p].diag = (IdxT)P.ustart[p];
+        piv[p].nup = (IdxT)P.up[p].size();
+    }
+    for (int32_t l = 0; l <= P.nlevel; ++l) {
+        lvl_task[l] = (IdxT)P.lvl_task[l];
+        lvl_piv[l] = (IdxT)P.lvl_piv[l];
+    }
+    std::vector<int32_t> cnt(na + 1, 0);
+    for (int32_t p = 0; p < nc; ++p) {
+        ++cnt[con[p].i + 1];
+        ++cnt[con[p].j + 1];
+    }
+    for (int32_t a = 0; a < na; ++a) cnt[a + 1] += cnt[a];
+    for (int32_t a = 0; a <= na; ++a) inc_ptr[a] = (IdxT)cnt[a];
+    std::vector<int32_t> fillp(cnt.begin(), cnt.end() - 1);
+    for (int32_t p = 0; p < nc; ++p) {
+        inc[fillp[con[p].i]++] = (IdxT)((uint32_t)p << 1);
+        inc[fillp[con[p].j]++] = (IdxT)(((uint32_t)p << 1) | 1u);
+    }
+    const IdxT no_atom = (IdxT)~(IdxT)0;
+    for (size_t t = 0; t < P.tasks.size(); ++t) {
+        const TaskW& w = P.tasks[t];
+        tasks[t].row = (IdxT)w.row;
+        tasks[t].col = (IdxT)w.col;
+        tasks[t].atomsign = w.atomsign == kNoAtom32 ? no_atom : (IdxT)w.atomsign;  // DIAG / sentinel
+        tasks[t].tstart = (IdxT)w.tstart;
+    }
+    for (size_t k = 0; k < P.terms.size(); ++k) {
+        terms[k].l = (IdxT)P.terms[k].l;
+        terms[k].u = (IdxT)P.terms[k].u;
+        terms[k].m = (IdxT)P.terms[k].m;
+        terms[k].pad = 0;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// planning entry points (used by the C ABI in solve.cu)
+// ------------------------------------------------------------------------------------
+ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, const int32_t* ai,
+                           const int32_t* aj, const ilves_setup_opts& o) {
+    T->n_atoms = n_atoms;
+    T->n_c = n_c;
+    for (int32_t k = 0; k < n_c; ++k) {
+        if (ai[k] < 0 || ai[k] >= n_atoms || aj[k] < 0 || aj[k] >= n_atoms || ai[k] == aj[k])
+            return ILVES_ERR_TOPOLOGY;
+    }
+    {
+        std::vector<uint64_t> keys(n_c);
+        for (int32_t k = 0; k < n_c; ++k) {
+            const uint64_t a = (uint64_t)std::min(ai[k], aj[k]), b = (uint64_t)std::max(ai[k], aj[k]);
+            keys[k] = (a << 32) | b;
+        }
+        std::sort(keys.begin(), keys.end());
+        for (int32_t k = 1; k < n_c; ++k)
+            if (keys[k] == keys[k - 1]) return ILVES_ERR_TOPOLOGY;
+    }
+    // connected components; the root of each is its smallest atom
+    std::vector<int32_t> par(n_atoms);
+    std::iota(par.begin(), par.end(), 0);
+    for (int32_t k = 0; k < n_c; ++k) {
+        const int32_t a = uf_find(par, ai[k]), b = uf_find(par, aj[k]);
+        if (a != b) par[std::max(a, b)] = std::min(a, b);
+    }
+    std::vector<char> used(n_atoms, 0);
+    for (int32_t k = 0; k < n_c; ++k) used[ai[k]] = used[aj[k]] = 1;
+    std::vector<int32_t> mol_of_root(n_atoms, -1);
+    int32_t n_mol = 0;
+    for (int32_t a = 0; a < n_atoms; ++a) {
+        if (!used[a]) {
+            T->free_atoms.push_back(a);
+            continue;
+        }
+        const int32_t r = uf_find(par, a);
+        if (mol_of_root[r] < 0) mol_of_root[r] = n_mol++;
+    }
+    T->mols.assign(n_mol, MolHost{});
+    for (int32_t a = 0; a < n_atoms; ++a)
+        if (used[a]) T->mols[mol_of_root[uf_find(par, a)]].atoms.push_back(a);
+    for (int32_t k = 0; k < n_c; ++k) T->mols[mol_of_root[uf_find(par, ai[k])]].cons.push_back(k);
+    T->n_mol = n_mol;
+    std::vector<int32_t> local(n_atoms, -1);
+    const int32_t warp_limit = o.max_warp_constraints > 0 ? o.max_warp_constraints : 1024;
+    T->progs.assign(n_mol, nullptr);
+    std::vector<std::vector<int32_t>> inc, adj;
+    for (int32_t m = 0; m < n_mol; ++m) {
+        MolHost& M = T->mols[m];
+        const int32_t na = (int32_t)M.atoms.size(), nc = (int32_t)M.cons.size();
+        for (int32_t a = 0; a < na; ++a) local[M.atoms[a]] = a;
+        M.ci.resize(nc);
+        M.cj.resize(nc);
+        inc.assign(na, {});
+        for (int32_t c = 0; c < nc; ++c) {
+            const int32_t k = M.cons[c];
+            M.ci[c] = local[ai[k]];
+            M.cj[c] = local[aj[k]];
+            inc[M.ci[c]].push_back(c);
+            inc[M.cj[c]].push_back(c);
+        }
+        adj.assign(nc, {});
+        for (int32_t a = 0; a < na; ++a)
+            for (int32_t x : inc[a])
+                for (int32_t y : inc[a])
+                    if (x != y) adj[x].push_back(y);
+        for (auto& v : adj) {
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+        }
+        M.large = nc > warp_limit || na > 65535;
+        Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : 32));
+        if (!M.large && (P->tasks.size() > 65000 || P->terms.size() > 65000)) {
+            M.large = true;
+            *P = choose_order(nc, na, adj, M.ci, M.cj, o, 1024);
+        }
+        M.nlevel = P->nlevel;
+        M.ntask = (int32_t)P->tasks.size() - 1;
+        M.nterm = (int32_t)P->terms.size();
+        M.n_fill = P->n_fill;
+        M.passes = P->passes_factor + P->passes_solve;
+        T->progs[m] = P;
+    }
+    return ILVES_OK;
+}
+
+int64_t program_blob_bytes(const ilves_topology* T, int32_t m) {
+    const MolHost& M = T->mols[m];
+    return M.large ? layout_for<uint32_t>(M).bytes : layout_for<uint16_t>(M).bytes;
+}
+
+void program_write_blob(const ilves_topology* T, int32_t m, uint8_t* dst) {
+    const MolHost& M = T->mols[m];
+    if (M.large)
+        write_blob<uint32_t>(dst, M, *T->progs[m]);
+    else
+        write_blob<uint16_t>(dst, M, *T->progs[m]);
+}
+
+void program_export(const ilves_topology* T, int32_t m, int32_t* pos_gid, int32_t* level,
+                    int32_t* up_ptr, int32_t* up_idx) {
+    const MolHost& M = T->mols[m];
+    const Program& P = *T->progs[m];
+    const int32_t nc = (int32_t)M.cons.size();
+    int32_t e = 0;
+    for (int32_t p = 0; p < nc; ++p) {
+        if (pos_gid) pos_gid[p] = M.cons[P.pos_con[p]];
+        if (level) level[p] = P.level[p];
+        if (up_ptr) up_ptr[p] = e;
+        for (int32_t q : P.up[p]) {
+            if (up_idx) up_idx[e] = q;
+            ++e;
+        }
+    }
+    if (up_ptr) up_ptr[nc] = e;
+}
+
+void free_programs(ilves_topology* T) {
+    for (Program* P : T->progs) delete P;
+    T->progs.clear();
+}
+
+// bytes of one molecule's shared-memory slice for a precision mode
+uint32_t footprint(const MolHost& M, int mode) {
+    const uint32_t lp = mode == ILVES_PREC_FP64 ? 8u : 4u;
+    const ProgLayout L = layout_for<uint16_t>(M);
+    const StateLayout S = state_layout((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(),
+                                       (uint32_t)M.ntask, lp, 8u);
+    return L.bytes + S.bytes;
+}
+
+// LPT of molecules over CTAs, then rounds per CTA packed into the shared-memory arena.
+void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
+                    HostSchedule& S) {
+    S.n_cta = n_cta;
+    S.warps = warps;
+    S.arena = arena;
+    S.cta_round_ptr.assign(n_cta + 1, 0);
+    S.round_ptr.assign(1, 0);
+    S.round_mol.clear();
+    S.round_off.clear();
+    std::vector<int32_t> small;
+    std::vector<uint32_t> fp(T->n_mol, 0);
+    for (int32_t m = 0; m < T->n_mol; ++m)
+        if (!T->mols[m].large) {
+            small.push_back(m);
+            fp[m] = footprint(T->mols[m], mode);
+        }
+    auto cost = [&](int32_t m) {
+        const MolHost& M = T->mols[m];
+        return 90.0 * (double)M.passes + (6.0 * M.ntask + 4.0 * M.nterm + 60.0 * M.cons.size()) / 32.0;
+    };
+    std::sort(small.begin(), small.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+    using Item = std::pair<double, int32_t>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int32_t c = 0; c < n_cta; ++c) heap.push({0.0, c});
+    std::vector<std::vector<int32_t>> per(n_cta);
+    for (int32_t m : small) {
+        const Item it = heap.top();
+        heap.pop();
+        per[it.second].push_back(m);
+        heap.push({it.first + cost(m), it.second});
+    }
+    for (int32_t c = 0; c < n_cta; ++c) {
+        auto& v = per[c];
+        std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return fp[a] > fp[b]; });
+        size_t i = 0;
+        while (i < v.size()) {
+            uint32_t used = 0;
+            int32_t cnt = 0;
+            while (i < v.size() && cnt < warps) {
+                const uint32_t f = fp[v[i]];
+                if (used + f > (uint32_t)arena) break;
+                S.round_mol.push_back(v[i]);
+                S.round_off.push_back((int32_t)used);
+                used += f;
+                ++cnt;
+                ++i;
+            }
+            if (cnt == 0) {  // cannot happen: molecules above the arena are routed to the large path
+                ++i;
+                continue;
+            }
+            S.round_ptr.push_back((int32_t)S.round_mol.size());
+        }
+        S.cta_round_ptr[c + 1] = (int32_t)S.round_ptr.size() - 1;
+    }
+}
+
+}  // namespace ilves

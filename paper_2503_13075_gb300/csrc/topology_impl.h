@@ -1,0 +1,78 @@
+// topology_impl.h -- host-side structures of an ilves_topology (not public ABI).
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "ilves.h"
+#include "internal.h"
+
+namespace ilves {
+
+struct TaskW { uint32_t row, col, atomsign, tstart; };
+struct TermW { uint32_t l, u, m, pad; };
+
+struct MolHost {
+    std::vector<int32_t> atoms;      // global atom ids, ascending
+    std::vector<int32_t> cons;       // global constraint ids, ascending (local constraint id order)
+    std::vector<int32_t> ci, cj;     // per local constraint: local atom ids
+    bool large = false;
+    int32_t nlevel = 0, ntask = 0, nterm = 0, n_fill = 0;
+    int64_t passes = 0;
+};
+
+struct Program;  // topology.cpp
+
+struct HostSchedule {
+    int32_t n_cta = 0, warps = 0, arena = 0;
+    std::vector<int32_t> cta_round_ptr, round_ptr, round_mol, round_off;
+};
+
+struct DeviceSchedule {
+    int32_t n_cta = 0, warps = 0, arena = 0;
+    int32_t* cta_round_ptr = nullptr;
+    int32_t* round_ptr = nullptr;
+    int32_t* round_mol = nullptr;  // index into the small-molecule descriptor array
+    int32_t* round_off = nullptr;
+};
+
+}  // namespace ilves
+
+struct ilves_topology {
+    int32_t n_atoms = 0, n_c = 0, n_mol = 0;
+    std::vector<ilves::MolHost> mols;
+    std::vector<ilves::Program*> progs;  // owned
+    std::vector<int32_t> free_atoms;
+    // device side
+    int32_t device = -1;
+    bool on_device = false;
+    int32_t n_sm = 0;
+    ilves::MolDesc* d_desc = nullptr;        // all molecules (small first, then large)
+    int32_t n_small = 0, n_large = 0;
+    uint8_t* d_blob = nullptr;
+    int64_t blob_bytes = 0;
+    int32_t* d_atom_gid = nullptr;
+    int32_t* d_free_atoms = nullptr;
+    uint8_t* d_work = nullptr;               // large-molecule numerical state
+    int64_t work_bytes = 0;
+    ilves::DeviceSchedule sched[3];          // per precision mode
+    void* side_stream = nullptr;             // cudaStream_t for the large-molecule kernel
+    void* ev_fork = nullptr;
+    void* ev_join = nullptr;
+    int32_t large_threads = 512;
+    int32_t last_launches = 0;
+    bool smem_attr_set[3] = {false, false, false};
+};
+
+namespace ilves {
+ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, const int32_t* ai,
+                           const int32_t* aj, const ilves_setup_opts& o);
+uint32_t footprint(const MolHost& M, int mode);
+void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
+                    HostSchedule& S);
+int64_t program_blob_bytes(const ilves_topology* T, int32_t m);
+void program_write_blob(const ilves_topology* T, int32_t m, uint8_t* dst);
+void program_export(const ilves_topology* T, int32_t m, int32_t* pos_gid, int32_t* level,
+                    int32_t* up_ptr, int32_t* up_idx);
+void free_programs(ilves_topology* T);
+}  // namespace ilves

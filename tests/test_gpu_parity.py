@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bounds (stated for every result): max_k |sigma_k| / d_k^2 <= tol (1e-12) recomputed
+in float64 from the returned positions; positions within 1e-10 nm of the oracle;
+multipliers within 1e-8 relative (plus a small absolute floor); per-molecule
+iterations equal to the oracle's +-1 and identical statuses.  Both precision modes
+meet the same bounds (the mixed mode reaches them through the outer Newton loop).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ilves_oracle as orc  # noqa: E402
+from paper_2503_13075_gb300 import binding as B  # noqa: E402
+from paper_2503_13075_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+PRECS = ["fp64", "mixed"]
+TOL = 1e-12
+X_TOL = 1e-10
+LAM_RTOL = 1e-8
+
+
+def to_dev(s):
+    dev = torch.device("cuda:0")
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    return f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d)
+
+
+def run(s, precision, topo=None, **kw):
+    t = topo or B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    xo, xu, w, d = to_dev(s)
+    x, lam, it, st = t.solve(xo, xu, w, d, precision=precision, **kw)
+    torch.cuda.synchronize()
+    return t, x.cpu().numpy(), lam.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+
+
+def compare(s, ref, x, lam, it, st, tol=TOL, it_slack=1):
+    assert np.array_equal(st, ref.status), (np.unique(st, return_counts=True), np.unique(ref.status, return_counts=True))
+    ok = st == orc.CONVERGED
+    assert np.abs(it[ok] - ref.iterations[ok]).max(initial=0) <= it_slack
+    sig = orc.violation(x, s.atom_i.astype(np.int64), s.atom_j.astype(np.int64), s.d)
+    conv_c = ok[ref.mol_of_constraint]
+    assert (np.abs(sig[conv_c]) / s.d[conv_c] ** 2).max(initial=0) <= tol
+    assert np.abs(x - ref.x).max(initial=0) <= X_TOL
+    scale = np.abs(ref.lam).max(initial=0)
+    assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * scale)
+
+
+@pytest.fixture(scope="module")
+def trees():
+    s = wl.tree_batch(n_mol=256, seed=1001)
+    return s, orc.solve_system(s, tol=TOL)
+
+
+@pytest.fixture(scope="module")
+def trees_full():
+    s = wl.tree_batch()
+    return s, orc.solve_system(s, tol=TOL)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_chain64(prec):
+    s = wl.chain64()
+    ref = orc.solve_system(s, tol=TOL)
+    t, x, lam, it, st = run(s, prec)
+    compare(s, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tree_batch_256(prec, trees):
+    s, ref = trees
+    t, x, lam, it, st = run(s, prec)
+    compare(s, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tree_batch_full_4096(prec, trees_full):
+    s, ref = trees_full
+    t, x, lam, it, st = run(s, prec)
+    compare(s, ref, x, lam, it, st)
+    assert t.last_launch_count() >= 1
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_protein_like_large_path(prec):
+    s = wl.protein_like(n_atoms=20000, seed=1002)
+    ref = orc.solve_system(s, tol=TOL)
+    t, x, lam, it, st = run(s, prec)
+    assert t.n_large == 1
+    compare(s, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_warp_path_forced_to_large_path(prec):
+    """The CTA-per-molecule path on ordinary molecules gives the same results."""
+    s = wl.tree_batch(n_mol=20, seed=77)
+    ref = orc.solve_system(s, tol=TOL)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, max_warp_constraints=10)
+    assert t.n_large > 0
+    _, x, lam, it, st = run(s, prec, topo=t)
+    compare(s, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_two_atoms_closed_form(prec):
+    s = wl.two_atoms(d=0.1, w1=1 / 1.008, w2=1 / 12.011, seed=3, sigma=0.01)
+    t, x, lam, it, st = run(s, prec)
+    rho = s.x_old[0] - s.x_old[1]
+    sv = s.x_unc[0] - s.x_unc[1]
+    a, b, c0 = rho @ rho, sv @ rho, sv @ sv - s.d[0] ** 2
+    c = (b - np.sqrt(b * b - a * c0)) / a
+    lam_cf = c / (2 * (s.inv_mass[0] + s.inv_mass[1]))
+    assert st[0] == B.CONVERGED
+    assert abs(lam[0] - lam_cf) <= 1e-11 * abs(lam_cf)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_permuted_atoms_and_constraints(prec):
+    """Non-contiguous molecules (scattered atom ids) and shuffled constraints."""
+    s = wl.tree_batch(n_mol=40, seed=8)
+    rng = np.random.default_rng(2)
+    pa = rng.permutation(s.n_atoms)
+    inv = np.empty_like(pa)
+    inv[pa] = np.arange(s.n_atoms)
+    pc = rng.permutation(s.n_constraints)
+    sw = rng.random(s.n_constraints) < 0.5
+    s2 = wl.System("perm", s.x_old[pa], s.x_unc[pa], s.inv_mass[pa],
+                   inv[np.where(sw, s.atom_j, s.atom_i)[pc]].astype(np.int32),
+                   inv[np.where(sw, s.atom_i, s.atom_j)[pc]].astype(np.int32), s.d[pc])
+    ref = orc.solve_system(s2, tol=TOL)
+    t, x, lam, it, st = run(s2, prec)
+    compare(s2, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases(prec):
+    dev = torch.device("cuda:0")
+    # no constraints at all: x_out = x_unc
+    t = B.Topology(4, [], [])
+    xo = torch.zeros(4, 3, dtype=torch.float64, device=dev)
+    xu = torch.rand(4, 3, dtype=torch.float64, device=dev)
+    x, lam, it, st = t.solve(xo, xu, torch.ones(4, dtype=torch.float64, device=dev),
+                             torch.zeros(0, dtype=torch.float64, device=dev), precision=prec)
+    assert torch.equal(x, xu)
+    # unconstrained atoms pass through; anchored atom (w = 0) stays put
+    s = wl.chain64()
+    xo_ = np.vstack([s.x_old, [[9.0, 9.0, 9.0]]])
+    xu_ = np.vstack([s.x_unc, [[9.1, 9.0, 9.0]]])
+    w_ = np.append(s.inv_mass, 1.0)
+    w_[0] = 0.0
+    s2 = wl.System("c", xo_, xu_, w_, s.atom_i, s.atom_j, s.d)
+    ref = orc.solve_system(s2, tol=TOL)
+    _, x, lam, it, st = run(s2, prec)
+    compare(s2, ref, x, lam, it, st)
+    assert np.array_equal(x[-1], xu_[-1]) and np.array_equal(x[0], xu_[0])
+    # feasible input: 0 solves, lambda = 0
+    s3 = wl.chain64()
+    s3.x_unc = s3.x_old + np.array([0.2, 0.0, -0.1])
+    _, x, lam, it, st = run(s3, prec)
+    assert it[0] == 0 and st[0] == B.CONVERGED and np.all(lam == 0)
+    # NaN input -> NONFINITE; unreachable tolerance -> MAX_ITER after exactly max_iter solves
+    s4 = wl.chain64()
+    s4.x_unc = s4.x_unc.copy()
+    s4.x_unc[5, 1] = np.nan
+    _, x, lam, it, st = run(s4, prec)
+    assert st[0] == B.NONFINITE
+    _, x, lam, it, st = run(wl.chain64(), prec, tol=1e-30, max_iter=6)
+    assert st[0] == B.MAX_ITER and it[0] == 6
+    # r . rho = 0 at lambda = 0: singular pivot
+    s5 = wl.System("sing", np.array([[0.0, 0, 0], [0.1, 0, 0]]), np.array([[0.0, 0, 0], [0.0, 0.12, 0]]),
+                   np.ones(2), np.array([0], np.int32), np.array([1], np.int32), np.array([0.1]))
+    _, x, lam, it, st = run(s5, prec)
+    assert st[0] == B.SINGULAR_PIVOT
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_warm_start_and_aliasing(prec, trees):
+    s, ref = trees
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    xo, xu, w, d = to_dev(s)
+    lam0 = torch.from_numpy(ref.lam.astype(np.float32)).cuda()
+    xu2 = xu.clone()
+    x, lam, it, st = t.solve(xo, xu2, w, d, precision=prec, lambda0=lam0, x_out=xu2)  # x_out aliases x_unc
+    torch.cuda.synchronize()
+    x, lam, it, st = x.cpu().numpy(), lam.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    assert np.all(st == B.CONVERGED)
+    assert it.max() <= 2  # a float32 copy of the exact multipliers leaves ~1e-7 relative error
+    assert np.abs(x - ref.x).max() <= X_TOL
+    sig = orc.violation(x, s.atom_i.astype(np.int64), s.atom_j.astype(np.int64), s.d)
+    assert (np.abs(sig) / s.d ** 2).max() <= TOL
+
+
+def test_repeated_solves_are_deterministic(trees):
+    s, ref = trees
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    outs = [run(s, "mixed", topo=t)[1] for _ in range(3)]
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])

@@ -1,0 +1,143 @@
+"""Host-side checks of the C-ABI library: symbol exports, validation, symbolic LU.
+
+These run without a GPU: topologies are planned with device = -2 (host only).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2503_13075_gb300 import binding as B
+from paper_2503_13075_gb300 import workloads as wl
+
+
+def test_library_exports_every_header_symbol():
+    L = B.lib()
+    names = B.header_functions()
+    assert "ilves_solve" in names and "ilves_setup_topology" in names
+    for n in names:
+        assert hasattr(L, n), n
+        assert ctypes.cast(getattr(L, n), ctypes.c_void_p).value
+
+
+@pytest.mark.parametrize("ai,aj,code", [([0], [5], 2), ([1], [1], 2), ([0, 1], [1, 0], 2), ([0, 2], [1, 1], 0)])
+def test_topology_validation(ai, aj, code):
+    if code == 0:
+        t = B.Topology(3, ai, aj, plan_only=True)
+        assert t.n_molecules == 1
+    else:
+        with pytest.raises(B.IlvesError) as e:
+            B.Topology(3, ai, aj, plan_only=True)
+        assert e.value.code == code
+
+
+def test_invalid_arguments():
+    with pytest.raises(B.IlvesError) as e:
+        B.Topology(-1, [], [], plan_only=True)
+    assert e.value.code == 1
+    with pytest.raises(B.IlvesError) as e:
+        B.Topology(4, [0], [1], ordering=7, plan_only=True)
+    assert e.value.code == 1
+
+
+def _line_graph(ai, aj):
+    inc = {}
+    for k, (i, j) in enumerate(zip(ai, aj)):
+        inc.setdefault(int(i), []).append(k)
+        inc.setdefault(int(j), []).append(k)
+    adj = [set() for _ in ai]
+    for ks in inc.values():
+        for x in ks:
+            adj[x].update(ks)
+            adj[x].discard(x)
+    return adj
+
+
+def _check_molecule(topo, s, m, rng):
+    pos_gid, level, ptr, idx = topo.export_molecule(m)
+    nc = pos_gid.size
+    up = [set(idx[ptr[p]:ptr[p + 1]].tolist()) for p in range(nc)]
+    pos_of = {int(g): p for p, g in enumerate(pos_gid)}
+    ai, aj = s.atom_i[pos_gid], s.atom_j[pos_gid]
+    adj = _line_graph(ai, aj)  # in position numbering
+    # 1. the pattern of A (line graph) is inside the filled pattern
+    for p in range(nc):
+        for q in adj[p]:
+            lo, hi = min(p, q), max(p, q)
+            assert hi in up[lo]
+    # 2. every pivot's later neighbours form a clique of later pivots (elimination closure)
+    for p in range(nc):
+        u = sorted(up[p])
+        assert all(q > p for q in u)
+        for a_ in range(len(u)):
+            for b_ in range(a_ + 1, len(u)):
+                assert u[b_] in up[u[a_]]
+    # 3. levels: sorted, and a pivot's later neighbours sit on higher levels
+    assert np.all(np.diff(level) >= 0)
+    for p in range(nc):
+        for q in up[p]:
+            assert level[q] > level[p]
+    # 4. numeric: LU without pivoting of a random diagonally dominant matrix on A's pattern
+    #    in this order has no entry outside the symbolic pattern
+    if nc <= 300:
+        A = np.zeros((nc, nc))
+        for p in range(nc):
+            for q in adj[p]:
+                A[p, q] = rng.normal()
+            A[p, p] = 10.0 + len(adj[p])
+        U = A.copy()
+        Lm = np.eye(nc)
+        for k in range(nc):
+            for i in range(k + 1, nc):
+                if U[i, k] != 0.0:
+                    Lm[i, k] = U[i, k] / U[k, k]
+                    U[i, :] -= Lm[i, k] * U[k, :]
+        allowed = np.eye(nc, dtype=bool)
+        for p in range(nc):
+            for q in up[p]:
+                allowed[p, q] = allowed[q, p] = True
+        nz = (np.abs(U) > 1e-12) | (np.abs(Lm) > 1e-12)
+        assert not np.any(nz & ~allowed)
+    return pos_of
+
+
+@pytest.mark.parametrize("ordering,slack", [(0, 2), (1, 0), (2, 0), (2, 3)])
+def test_symbolic_factorisation_chain_and_trees(ordering, slack):
+    rng = np.random.default_rng(0)
+    for s in (wl.chain64(), wl.tree_batch(n_mol=12, seed=17)):
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, ordering=ordering, degree_slack=slack, plan_only=True)
+        atoms, cons, levels, first = t.molecules()
+        assert t.n_molecules == s.n_molecules
+        assert np.array_equal(first, s.mol_atom_ptr[:-1])
+        assert np.array_equal(atoms, np.diff(s.mol_atom_ptr))
+        for m in range(t.n_molecules):
+            _check_molecule(t, s, m, rng)
+
+
+def test_symbolic_factorisation_rings_and_cliques():
+    """Protein-like fragment: CH3 groups form K4 cliques with their H-H distances."""
+    rng = np.random.default_rng(1)
+    s = wl.protein_like(n_atoms=600, seed=5)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
+    assert t.n_molecules == 1
+    _check_molecule(t, s, 0, rng)
+
+
+def test_level_counts_are_small():
+    """The rounds ordering keeps the level count near log scale (chain) / tree depth."""
+    c = wl.chain64()
+    t1 = B.Topology(c.n_atoms, c.atom_i, c.atom_j, ordering=1, plan_only=True)
+    t0 = B.Topology(c.n_atoms, c.atom_i, c.atom_j, plan_only=True)
+    assert t1.max_levels >= 30  # one pivot per step on a chain: ~n/2 levels
+    assert t0.max_levels <= 8  # cyclic-reduction-like
+    s = wl.tree_batch(n_mol=64, seed=3)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
+    assert t.molecules()[2].mean() < 12
+
+
+def test_free_atoms_and_empty():
+    t = B.Topology(5, [], [], plan_only=True)
+    assert t.n_molecules == 0
+    t = B.Topology(6, [0, 4], [1, 5], plan_only=True)
+    atoms, cons, levels, first = t.molecules()
+    assert list(first) == [0, 4] and list(cons) == [1, 1]
