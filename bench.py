@@ -42,7 +42,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ilves", choices=["ilves", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_df"])
     p.add_argument("--n-mol", type=int, default=4096)
     p.add_argument("--tol", type=float, default=1e-12)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -263,10 +263,19 @@ def run_ilves(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # plain FP64 comparator (same batch, same tolerance)
+    # plain FP64 comparator and the float-float variant (same batch, same tolerance)
     ms64, _ = time_device(topo, dev_in, out, "fp64", args.tol, max(3, args.steps // 4), 2, flush, stream)
     ok64 = bool((out[3] == 0).all().item())
     it64 = out[2].cpu().numpy()
+    alt = {}
+    for prec in ("mixed", "mixed_df"):
+        if prec == args.precision:
+            continue
+        msa, _ = time_device(topo, dev_in, out, prec, args.tol, max(3, args.steps // 4), 2, flush, stream)
+        xa = out[0].cpu().numpy()
+        alt[prec] = {"value": s.n_atoms / (sum(msa) / len(msa) * 1e-3), "ms_per_step": sum(msa) / len(msa),
+                     "all_converged": bool((out[3] == 0).all().item()),
+                     "max_rel_violation": orc.max_relative_violation(xa, s.atom_i, s.atom_j, s.d)}
 
     clocks = None if args.no_clocks else ClockSampler(local)
     barrier(world)
@@ -344,7 +353,7 @@ def run_ilves(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64+f32" if args.precision == "mixed" else "f64",
+        "dtype": {"mixed": "f64+f32", "fp64": "f64", "mixed_df": "f32x2+f32"}[args.precision],
         "data": "synthetic",
         "config": {
             "workload": workload_name(s),
@@ -361,6 +370,7 @@ def run_ilves(args):
         "plain_fp64": {"value": value64, "ms_per_step": per64, "all_converged": ok64,
                        "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(it64)) if v}},
         "speedup_vs_plain_fp64": value / value64,
+        "other_precisions": alt,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ab, "kernel": "k_solve_small"},

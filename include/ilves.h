@@ -75,8 +75,13 @@ typedef enum {
  *  FP64:     every step in float64 (the plain reference configuration).
  *  MIXED:    Jacobian assembly, LU factorisation and triangular solves in float32;
  *            violations, multiplier accumulation and position updates in float64.
- *            The outer Newton loop acts as iterative refinement. */
-typedef enum { ILVES_PREC_FP64 = 0, ILVES_PREC_MIXED = 1 } ilves_precision;
+ *            The outer Newton loop acts as iterative refinement.
+ *  MIXED_DF: as MIXED, but the float64-class steps run in float-float arithmetic
+ *            (unevaluated sums of two float32 words, about 48 significant bits) on
+ *            the float32 units, on displacements x - x_unc whose magnitude keeps the
+ *            absolute rounding error far below the tolerance.  Inputs and outputs
+ *            stay float64. */
+typedef enum { ILVES_PREC_FP64 = 0, ILVES_PREC_MIXED = 1, ILVES_PREC_MIXED_DF = 2 } ilves_precision;
 
 typedef struct {
     int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;

@@ -17,8 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libilves.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ilves.h")
 
-FP64, MIXED = 0, 1
-PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+FP64, MIXED, MIXED_DF = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_df": MIXED_DF}
 CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE = 0, 1, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid topology", 3: "CUDA error", 4: "out of device memory",
           5: "device wait timed out"}

@@ -37,14 +37,33 @@ constexpr uint32_t kNoAtom32 = 0xFFFFFFFFu;
 //   Task: row, col of the target entry; atomsign = (shared atom << 1) | (sign
 //         product < 0), all-ones for fill entries and diagonals; tstart = first term.
 //         Task t's terms are [tstart_t, tstart_{t+1}); a sentinel task ends the list.
-//   Term: l = slot of Lt[row, m], u = slot of Ut[m, col], m = the earlier pivot.
+//   Term: l = slot of Lt[row, m], u = slot of U[m, col], m = the earlier pivot.
 //   Piv:  diag = first slot of the pivot's U row (its L column follows), nup = |N+(pivot)|.
 //   ConA: local atom ids (i, j) of the constraint at position p.
 // inc[e] = p << 1 | (atom is the second atom of constraint p)
 template <class IdxT> struct Task { IdxT row, col, atomsign, tstart; };
 template <class IdxT> struct ConA { IdxT i, j; };
-template <class IdxT> struct Term { IdxT l, u, m, pad; };
 template <class IdxT> struct Piv { IdxT diag, nup; };
+
+// Term words.  Warp-sized molecules (fewer than 256 constraints and 4096 slots) pack a
+// term in 32 bits: l (12) | u (12) << 12 | m (8) << 24.  Large molecules use 4 x 32 bits.
+struct TermWide { uint32_t l, u, m, pad; };
+template <class IdxT> struct TermOf;
+template <> struct TermOf<uint16_t> {
+    using T = uint32_t;
+    static ILVES_HD uint32_t l(T t) { return t & 0xFFFu; }
+    static ILVES_HD uint32_t u(T t) { return (t >> 12) & 0xFFFu; }
+    static ILVES_HD uint32_t m(T t) { return t >> 24; }
+    static ILVES_HD T make(uint32_t l, uint32_t u, uint32_t m) { return l | (u << 12) | (m << 24); }
+};
+template <> struct TermOf<uint32_t> {
+    using T = TermWide;
+    static ILVES_HD uint32_t l(T t) { return t.l; }
+    static ILVES_HD uint32_t u(T t) { return t.u; }
+    static ILVES_HD uint32_t m(T t) { return t.m; }
+    static ILVES_HD T make(uint32_t l, uint32_t u, uint32_t m) { return TermWide{l, u, m, 0u}; }
+};
+constexpr uint32_t kCompactMaxConstraints = 256, kCompactMaxSlots = 4096;
 
 ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 
@@ -66,34 +85,35 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
     L.inc_ptr = o;   o = align16(o + ix * (na + 1));
     L.inc = o;       o = align16(o + ix * 2u * nc);
     L.tasks = o;     o = align16(o + 4u * ix * (ntask + 1));
-    L.terms = o;     o = align16(o + 4u * ix * nterm);
+    L.terms = o;     o = align16(o + (uint32_t)sizeof(typename TermOf<IdxT>::T) * nterm);
     L.bytes = o;
     return L;
 }
 
-// Numerical state of one molecule (after its program).  hp_bytes = 8 (float64 state),
-// lp_bytes = factor element size (4 for float32, 8 for float64); 3-vectors of the
-// factor precision are padded to 4 elements.  Atom arrays have na + 1 entries: the
-// extra atom has zero weight and is what fill entries of the pattern point at.
+// Numerical state of one molecule (after its program).  Float64-class values (float64,
+// or float-float pairs of the same size) take 8 bytes; lp_bytes is the factor element
+// size (4 for float32, 8 for float64); 3-vectors of the factor precision are padded to 4
+// elements.  Atom arrays have na + 1 entries: the extra atom has zero weight and is what
+// fill entries of the pattern point at.  The factor-precision weight array `wl` continues
+// with one entry per constraint, w_i + w_j, which DIAG tasks use as their "shared atom".  With `disp` the state keeps displacements
+// x - x_unc and the per-constraint differences s_k = x_unc,i - x_unc,j.
 struct StateLayout {
-    uint32_t x, w, wf, rho, d2, told2, lam, rhof, rf, cdiag, inv, y, vals, bytes;
+    uint32_t x, w, wl, rho, s, d2, lam, rhof, rf, inv, y, vals, bytes;
 };
 
-ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t lp_bytes,
-                                  uint32_t hp_bytes) {
+ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t lp_bytes, bool disp) {
     StateLayout S;
     const uint32_t vp = 4u * lp_bytes;
     uint32_t o = 0;
-    S.x = o;      o = align16(o + 3u * hp_bytes * na);   // SoA: x[0..na), y[..], z[..]
-    S.w = o;      o = align16(o + hp_bytes * (na + 1));
-    S.wf = o;     o = align16(o + 4u * (na + 1));
-    S.rho = o;    o = align16(o + 3u * hp_bytes * nc);   // SoA
-    S.d2 = o;     o = align16(o + hp_bytes * nc);
-    S.told2 = o;  o = align16(o + hp_bytes * nc);
-    S.lam = o;    o = align16(o + hp_bytes * nc);
+    S.x = o;      o = align16(o + 24u * na);             // SoA: x[0..na), y[..], z[..]
+    S.w = o;      o = align16(o + 8u * (na + 1));
+    S.wl = o;     o = align16(o + lp_bytes * (na + 1 + nc));
+    S.rho = o;    o = align16(o + 24u * nc);             // SoA
+    S.s = o;      o = align16(o + (disp ? 24u * nc : 0u));
+    S.d2 = o;     o = align16(o + 8u * nc);
+    S.lam = o;    o = align16(o + 8u * nc);
     S.rhof = o;   o = align16(o + vp * nc);
     S.rf = o;     o = align16(o + vp * nc);
-    S.cdiag = o;  o = align16(o + lp_bytes * nc);
     S.inv = o;    o = align16(o + lp_bytes * nc);
     S.y = o;      o = align16(o + lp_bytes * nc);
     S.vals = o;   o = align16(o + lp_bytes * ntask);

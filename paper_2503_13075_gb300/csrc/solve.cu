@@ -40,12 +40,21 @@ struct ModeFP64 {
     using LP = double;
     struct V4 { double x, y, z, w; };
     static constexpr int id = ILVES_PREC_FP64;
+    static constexpr bool df = false;
     static constexpr double pivot_rel = 1e-13;
 };
 struct ModeMixed {
     using LP = float;
     using V4 = float4;
     static constexpr int id = ILVES_PREC_MIXED;
+    static constexpr bool df = false;
+    static constexpr float pivot_rel = 1e-5f;
+};
+struct ModeMixedDF {
+    using LP = float;
+    using V4 = float4;
+    static constexpr int id = ILVES_PREC_MIXED_DF;
+    static constexpr bool df = true;
     static constexpr float pivot_rel = 1e-5f;
 };
 
@@ -90,10 +99,71 @@ __device__ __forceinline__ bool abs_le(double s, double t) {
 __device__ __forceinline__ bool nonfinite(double s) {
     return (__double_as_longlong(s) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
 }
+__device__ __forceinline__ bool nonfinite(float s) { return (__float_as_uint(s) & 0x7F800000u) == 0x7F800000u; }
 __device__ __forceinline__ float lp_abs(float v) { return fabsf(v); }
 __device__ __forceinline__ double lp_abs(double v) { return fabs(v); }
 __device__ __forceinline__ float lp_rcp(float a) { return __frcp_rn(a); }
 __device__ __forceinline__ double lp_rcp(double a) { return 1.0 / a; }
+
+// ------------------------------------------------------------------------------------
+// float-float arithmetic: a value is the unevaluated sum hi + lo of two float32 words
+// with |lo| <= ulp(hi) / 2.  Building blocks: Knuth's two-sum, Dekker's fast two-sum
+// (|a| >= |b|) and the FMA-based exact product.  Additions use the short form
+// (two-sum of the high words, low words added once): its absolute error is about
+// 2^-24 |lo| parts, i.e. 2^-48 of the operands, which is what the error budget of the
+// displacement formulation needs.
+// ------------------------------------------------------------------------------------
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    fast_two_sum(s, e, s, e);
+    return {s, e};
+}
+__device__ __forceinline__ dfloat df_sub(dfloat a, dfloat b) { return df_add(a, dfloat{-b.hi, -b.lo}); }
+__device__ __forceinline__ dfloat df_add_f(dfloat a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    e = __fadd_rn(e, a.lo);
+    fast_two_sum(s, e, s, e);
+    return {s, e};
+}
+__device__ __forceinline__ dfloat df_mul_f(dfloat a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    fast_two_sum(p, e, p, e);
+    return {p, e};
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    fast_two_sum(p, e, p, e);
+    return {p, e};
+}
+// float64 -> float-float: hi = the truncated leading 24 bits (integer pipe), lo = the
+// rounded remainder (one float64 subtraction)
+__device__ __forceinline__ dfloat df_split(double v) {
+    const float hi = narrow(v);
+    return {hi, __double2float_rn(v - widen(hi))};
+}
+__device__ __forceinline__ double df_join(dfloat a) { return widen(a.hi) + widen(a.lo); }
+__device__ __forceinline__ dfloat as_df(double v) { return *reinterpret_cast<dfloat*>(&v); }
+__device__ __forceinline__ double as_bits(dfloat v) { return *reinterpret_cast<double*>(&v); }
 
 // ------------------------------------------------------------------------------------
 // teams
@@ -131,14 +201,19 @@ struct SolveArgs {
 // ------------------------------------------------------------------------------------
 // one molecule, one team
 // ------------------------------------------------------------------------------------
+// Float64-class arrays (X, W, RHO, S, D2, LAM) hold float64 values, or in the
+// float-float mode dfloat pairs stored in the same 8 bytes.  In the float64 modes X
+// holds absolute positions; in the float-float mode it holds displacements x - x_unc
+// and S holds s_k = x_unc,i - x_unc,j, so that r_k = s_k + (dx_i - dx_j).
 template <class Mode, class IdxT, class Team>
 __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
                                const SolveArgs& A) {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
+    constexpr bool DF = Mode::df;
     const int na = D.na, nc = D.nc;
     const ProgLayout PL = prog_layout<IdxT>(na, nc, D.ntask, D.nterm, D.nlevel);
-    const StateLayout SL = state_layout(na, nc, D.ntask, sizeof(LP), 8);
+    const StateLayout SL = state_layout(na, nc, D.ntask, sizeof(LP), DF);
     const ConA<IdxT>* con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
     const int32_t* con_gid = reinterpret_cast<const int32_t*>(prog + PL.con_gid);
     const Piv<IdxT>* piv = reinterpret_cast<const Piv<IdxT>*>(prog + PL.piv);
@@ -147,47 +222,45 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
     const IdxT* inc_ptr = reinterpret_cast<const IdxT*>(prog + PL.inc_ptr);
     const IdxT* inc = reinterpret_cast<const IdxT*>(prog + PL.inc);
     const Task<IdxT>* tasks = reinterpret_cast<const Task<IdxT>*>(prog + PL.tasks);
-    const Term<IdxT>* terms = reinterpret_cast<const Term<IdxT>*>(prog + PL.terms);
+    using TO = TermOf<IdxT>;
+    const typename TO::T* terms = reinterpret_cast<const typename TO::T*>(prog + PL.terms);
     double* X = reinterpret_cast<double*>(st + SL.x);  // SoA x | y | z
     double* W = reinterpret_cast<double*>(st + SL.w);
-    float* WF = reinterpret_cast<float*>(st + SL.wf);
+    LP* WL = reinterpret_cast<LP*>(st + SL.wl);  // assembly weights (factor precision)
     double* RHO = reinterpret_cast<double*>(st + SL.rho);  // SoA
+    double* SK = reinterpret_cast<double*>(st + SL.s);     // SoA (float-float mode)
     double* D2 = reinterpret_cast<double*>(st + SL.d2);
-    double* TD2 = reinterpret_cast<double*>(st + SL.told2);
+    const double tol = A.tol;
+    const float tolf = (float)A.tol;
     double* LAM = reinterpret_cast<double*>(st + SL.lam);
     V4* RHOF = reinterpret_cast<V4*>(st + SL.rhof);
     V4* RF = reinterpret_cast<V4*>(st + SL.rf);
-    LP* CD = reinterpret_cast<LP*>(st + SL.cdiag);
     LP* INV = reinterpret_cast<LP*>(st + SL.inv);
     LP* Y = reinterpret_cast<LP*>(st + SL.y);
     LP* V = reinterpret_cast<LP*>(st + SL.vals);
     const int r0 = tm.rank(), ts = tm.size();
-    const IdxT no_atom = (IdxT)~(IdxT)0;
 
     auto gid_of = [&](int a) -> int64_t {
         return D.atom_base >= 0 ? (int64_t)D.atom_base + a : (int64_t)A.atom_gid[D.gid_off + a];
     };
-    // ---- S1: reference geometry
+    // ---- S1: reference geometry (x_old staged through X), weights
     for (int a = r0; a < na; a += ts) {
         const int64_t g = gid_of(a);
         X[a] = A.x_old[3 * g];
         X[na + a] = A.x_old[3 * g + 1];
         X[2 * na + a] = A.x_old[3 * g + 2];
         const double w = A.inv_mass[g];
-        W[a] = w;
-        WF[a] = narrow(w);
+        W[a] = DF ? as_bits(df_split(w)) : w;
+        WL[a] = to_lp<LP>(w);
     }
     if (r0 == 0) {  // zero-weight atom referenced by fill entries
         W[na] = 0.0;
-        WF[na] = 0.0f;
+        WL[na] = LP(0);
     }
     tm.sync();
     for (int p = r0; p < nc; p += ts) {
         const int i = con[p].i, j = con[p].j;
         const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
-        RHO[p] = rx;
-        RHO[nc + p] = ry;
-        RHO[2 * nc + p] = rz;
         V4 v;
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
@@ -196,40 +269,80 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
         RHOF[p] = v;
         const int32_t g = con_gid[p];
         const double dd = A.d[g];
-        D2[p] = dd * dd;
-        TD2[p] = A.tol * (dd * dd);
-        CD[p] = LP(4) * (to_lp<LP>(W[i]) + to_lp<LP>(W[j]));
+        if constexpr (DF) {
+            RHO[p] = as_bits(df_split(rx));
+            RHO[nc + p] = as_bits(df_split(ry));
+            RHO[2 * nc + p] = as_bits(df_split(rz));
+            D2[p] = as_bits(df_split(dd * dd));
+        } else {
+            RHO[p] = rx;
+            RHO[nc + p] = ry;
+            RHO[2 * nc + p] = rz;
+            D2[p] = dd * dd;
+        }
+        WL[na + 1 + p] = WL[i] + WL[j];
         const float l0 = A.lambda0 ? A.lambda0[g] : 0.0f;
-        LAM[p] = widen(l0);
+        LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         Y[p] = (LP)l0;
     }
     tm.sync();
     for (int a = r0; a < na; a += ts) {
-        const int64_t g = gid_of(a);
-        X[a] = A.x_unc[3 * g];
-        X[na + a] = A.x_unc[3 * g + 1];
-        X[2 * na + a] = A.x_unc[3 * g + 2];
+        if constexpr (DF) {  // displacements start at zero
+            X[a] = 0.0;
+            X[na + a] = 0.0;
+            X[2 * na + a] = 0.0;
+        } else {
+            const int64_t g = gid_of(a);
+            X[a] = A.x_unc[3 * g];
+            X[na + a] = A.x_unc[3 * g + 1];
+            X[2 * na + a] = A.x_unc[3 * g + 2];
+        }
+    }
+    if constexpr (DF) {
+        for (int p = r0; p < nc; p += ts) {
+            const int64_t gi = gid_of(con[p].i), gj = gid_of(con[p].j);
+            SK[p] = as_bits(df_split(A.x_unc[3 * gi] - A.x_unc[3 * gj]));
+            SK[nc + p] = as_bits(df_split(A.x_unc[3 * gi + 1] - A.x_unc[3 * gj + 1]));
+            SK[2 * nc + p] = as_bits(df_split(A.x_unc[3 * gi + 2] - A.x_unc[3 * gj + 2]));
+        }
     }
     tm.sync();
 
     // ---- S6: x -= M^-1 G(x_old)^T Y   (Y holds delta, or lambda0 before the loop)
     auto update_positions = [&]() {
         for (int a = r0; a < na; a += ts) {
-            double ax = 0.0, ay = 0.0, az = 0.0;
             const int e1 = inc_ptr[a + 1];
-            for (int e = inc_ptr[a]; e < e1; ++e) {
-                const unsigned v = inc[e];
-                const int p = (int)(v >> 1);
-                const LP dl = Y[p];
-                const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
-                ax = fma(c, RHO[p], ax);
-                ay = fma(c, RHO[nc + p], ay);
-                az = fma(c, RHO[2 * nc + p], az);
+            if constexpr (DF) {
+                dfloat ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
+                for (int e = inc_ptr[a]; e < e1; ++e) {
+                    const unsigned v = inc[e];
+                    const int p = (int)(v >> 1);
+                    const float dl = (float)Y[p];
+                    const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
+                    ax = df_add(ax, df_mul_f(as_df(RHO[p]), c));
+                    ay = df_add(ay, df_mul_f(as_df(RHO[nc + p]), c));
+                    az = df_add(az, df_mul_f(as_df(RHO[2 * nc + p]), c));
+                }
+                const dfloat w = as_df(W[a]);
+                X[a] = as_bits(df_sub(as_df(X[a]), df_mul(w, ax)));
+                X[na + a] = as_bits(df_sub(as_df(X[na + a]), df_mul(w, ay)));
+                X[2 * na + a] = as_bits(df_sub(as_df(X[2 * na + a]), df_mul(w, az)));
+            } else {
+                double ax = 0.0, ay = 0.0, az = 0.0;
+                for (int e = inc_ptr[a]; e < e1; ++e) {
+                    const unsigned v = inc[e];
+                    const int p = (int)(v >> 1);
+                    const LP dl = Y[p];
+                    const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
+                    ax = fma(c, RHO[p], ax);
+                    ay = fma(c, RHO[nc + p], ay);
+                    az = fma(c, RHO[2 * nc + p], az);
+                }
+                const double w = W[a];
+                X[a] = fma(-w, ax, X[a]);
+                X[na + a] = fma(-w, ay, X[na + a]);
+                X[2 * na + a] = fma(-w, az, X[2 * na + a]);
             }
-            const double w = W[a];
-            X[a] = fma(-w, ax, X[a]);
-            X[na + a] = fma(-w, ay, X[na + a]);
-            X[2 * na + a] = fma(-w, az, X[2 * na + a]);
         }
     };
     if (A.lambda0) {
@@ -239,21 +352,49 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
 
     int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
     for (int it = 0;; ++it) {
-        // ---- S2: violations (float64), Jacobian rows and right-hand side (factor precision)
+        // ---- S2: violations (float64 class), Jacobian rows and right-hand side
         bool conv = true, bad = false;
         for (int p = r0; p < nc; p += ts) {
             const int i = con[p].i, j = con[p].j;
-            const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
-            const double s = fma(rx, rx, fma(ry, ry, fma(rz, rz, -D2[p])));
-            conv = conv && abs_le(s, TD2[p]);
-            bad = bad || nonfinite(s);
             V4 v;
-            v.x = to_lp<LP>(rx);
-            v.y = to_lp<LP>(ry);
-            v.z = to_lp<LP>(rz);
+            if constexpr (DF) {
+                const dfloat rx = df_add(as_df(SK[p]), df_sub(as_df(X[i]), as_df(X[j])));
+                const dfloat ry = df_add(as_df(SK[nc + p]), df_sub(as_df(X[na + i]), as_df(X[na + j])));
+                const dfloat rz = df_add(as_df(SK[2 * nc + p]), df_sub(as_df(X[2 * na + i]), as_df(X[2 * na + j])));
+                const dfloat d2 = as_df(D2[p]);
+                // |r|^2 - d^2: exact products of the high words, two-sums of the big terms,
+                // every rounding error collected in a small tail
+                const float px = __fmul_rn(rx.hi, rx.hi), ex = __fmaf_rn(rx.hi, rx.hi, -px);
+                const float py = __fmul_rn(ry.hi, ry.hi), ey = __fmaf_rn(ry.hi, ry.hi, -py);
+                const float pz = __fmul_rn(rz.hi, rz.hi), ez = __fmaf_rn(rz.hi, rz.hi, -pz);
+                float s1, e1, s2, e2, s3, e3;
+                two_sum(px, py, s1, e1);
+                two_sum(s1, pz, s2, e2);
+                two_sum(s2, -d2.hi, s3, e3);
+                float cross = __fmul_rn(rx.hi, rx.lo);
+                cross = __fmaf_rn(ry.hi, ry.lo, cross);
+                cross = __fmaf_rn(rz.hi, rz.lo, cross);
+                const float tail = ((ex + ey) + (ez + e1)) + ((e2 + e3) - d2.lo) + (cross + cross);
+                const float sg = s3 + tail;
+                conv = conv && fabsf(sg) <= tolf * d2.hi;
+                bad = bad || nonfinite(sg);
+                v.x = rx.hi;
+                v.y = ry.hi;
+                v.z = rz.hi;
+                Y[p] = sg;
+            } else {
+                const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+                const double d2 = D2[p];
+                const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
+                conv = conv && abs_le(sg, tol * d2);
+                bad = bad || nonfinite(sg);
+                v.x = to_lp<LP>(rx);
+                v.y = to_lp<LP>(ry);
+                v.z = to_lp<LP>(rz);
+                Y[p] = to_lp<LP>(sg);
+            }
             v.w = LP(0);
             RF[p] = v;
-            Y[p] = to_lp<LP>(s);
         }
         if (tm.any(bad)) {
             status = ILVES_MOL_NONFINITE;
@@ -272,38 +413,33 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
         for (int l = 0; l < D.nlevel; ++l) {
             const int p0 = lvl_piv[l], np = lvl_piv[l + 1] - p0;
             const int t0 = lvl_task[l], t1 = lvl_task[l + 1];
-            for (int k = r0; k < np; k += ts) {  // DIAG tasks: pivot, 1 / pivot, forward solve
-                const int p = p0 + k, t = t0 + k;
-                const V4 rr = RF[p], pp = RHOF[p];
-                const LP a = CD[p] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
-                LP s = a, yv = Y[p];
-                const int e1 = tasks[t + 1].tstart;
-                for (int e = tasks[t].tstart; e < e1; ++e) {
-                    const Term<IdxT> tr = terms[e];
-                    const LP li = V[tr.l] * INV[tr.m];
-                    s -= li * V[tr.u];
-                    yv -= li * Y[tr.m];
-                }
-                singular = singular || !(lp_abs(s) > Mode::pivot_rel * lp_abs(a));
-                V[t] = s;
-                INV[p] = lp_rcp(s);
-                Y[p] = yv;
-            }
-            for (int t = t0 + np + r0; t < t1; t += ts) {  // U and L entries, one code path
+            // one pass over the level's tasks with a single code path: the first np tasks are
+            // the DIAG tasks of the level's pivots (their "shared atom" is the pseudo-atom
+            // carrying w_i + w_j), which also produce 1 / pivot and the forward-solve entry
+            for (int t = t0 + r0; t < t1; t += ts) {
                 const Task<IdxT> tk = tasks[t];
+                const bool diag = t < t0 + np;
                 const int e1 = tasks[t + 1].tstart;
                 const V4 rr = RF[tk.row], pp = RHOF[tk.col];
                 const int at = tk.atomsign >> 1;
-                LP wv;
-                if constexpr (sizeof(LP) == 8) wv = (LP)W[at];
-                else wv = (LP)WF[at];
+                const LP wv = WL[at];
                 const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
-                LP s = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+                const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+                LP s = a, yv = LP(0);
+#pragma unroll 2
                 for (int e = tk.tstart; e < e1; ++e) {
-                    const Term<IdxT> tr = terms[e];
-                    s -= V[tr.l] * INV[tr.m] * V[tr.u];
+                    const auto tr = terms[e];
+                    const int m = TO::m(tr);
+                    const LP li = V[TO::l(tr)] * INV[m];
+                    s -= li * V[TO::u(tr)];
+                    yv += li * Y[m];
                 }
                 V[t] = s;
+                if (diag) {
+                    singular = singular || !(lp_abs(s) > Mode::pivot_rel * lp_abs(a));
+                    INV[tk.row] = lp_rcp(s);
+                    Y[tk.row] -= yv;
+                }
             }
             tm.sync();
         }
@@ -323,20 +459,29 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
             }
             tm.sync();
         }
-        // ---- lambda += delta (float64), S6
-        for (int p = r0; p < nc; p += ts) LAM[p] += to_hp(Y[p]);
+        // ---- lambda += delta (float64 class), S6
+        for (int p = r0; p < nc; p += ts) {
+            if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(LAM[p]), (float)Y[p]));
+            else LAM[p] += to_hp(Y[p]);
+        }
         update_positions();
         tm.sync();
     }
     // ---- S7: outputs
     for (int a = r0; a < na; a += ts) {
         const int64_t g = gid_of(a);
-        A.x_out[3 * g] = X[a];
-        A.x_out[3 * g + 1] = X[na + a];
-        A.x_out[3 * g + 2] = X[2 * na + a];
+        if constexpr (DF) {
+            A.x_out[3 * g] = A.x_unc[3 * g] + df_join(as_df(X[a]));
+            A.x_out[3 * g + 1] = A.x_unc[3 * g + 1] + df_join(as_df(X[na + a]));
+            A.x_out[3 * g + 2] = A.x_unc[3 * g + 2] + df_join(as_df(X[2 * na + a]));
+        } else {
+            A.x_out[3 * g] = X[a];
+            A.x_out[3 * g + 1] = X[na + a];
+            A.x_out[3 * g + 2] = X[2 * na + a];
+        }
     }
     if (A.lambda_out)
-        for (int p = r0; p < nc; p += ts) A.lambda_out[con_gid[p]] = LAM[p];
+        for (int p = r0; p < nc; p += ts) A.lambda_out[con_gid[p]] = DF ? df_join(as_df(LAM[p])) : LAM[p];
     if (r0 == 0) {
         if (A.iterations_out) A.iterations_out[D.mol_id] = iters;
         if (A.status_out) A.status_out[D.mol_id] = status;
@@ -374,7 +519,16 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
             const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
             uint4* dst = reinterpret_cast<uint4*>(slice);
             const int n16 = (int)(PL.bytes >> 4);
-            for (int k = lane; k < n16; k += 32) dst[k] = __ldg(src + k);
+            int k = lane;
+            for (; k + 96 < n16; k += 128) {  // four independent 16-byte loads in flight per lane
+                const uint4 a0 = __ldg(src + k), a1 = __ldg(src + k + 32), a2 = __ldg(src + k + 64),
+                            a3 = __ldg(src + k + 96);
+                dst[k] = a0;
+                dst[k + 32] = a1;
+                dst[k + 64] = a2;
+                dst[k + 96] = a3;
+            }
+            for (; k < n16; k += 32) dst[k] = __ldg(src + k);
             __syncwarp();
             solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.bytes, A);
         }
@@ -505,7 +659,7 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         D.work_off = 0;
         if (M.large) {
             D.work_off = woff;
-            woff += (state_layout(na, D.nc, M.ntask, 8, 8).bytes + 255) & ~int64_t(255);
+            woff += (std::max(state_layout(na, D.nc, M.ntask, 8, false).bytes, state_layout(na, D.nc, M.ntask, 4, true).bytes) + 255) & ~int64_t(255);
         }
     }
     std::vector<uint8_t> blob((size_t)std::max<int64_t>(boff, 16), 0);
@@ -518,7 +672,7 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     if ((e = upload(&T->d_free_atoms, T->free_atoms)) != cudaSuccess) return to_status(e);
     if (woff > 0 && (e = cudaMalloc((void**)&T->d_work, woff)) != cudaSuccess) return to_status(e);
     // persistent schedules, one per precision mode
-    for (int mode = 0; mode < 2; ++mode) {
+    for (int mode = 0; mode < 3; ++mode) {
         std::vector<uint32_t> fps;
         for (int32_t m = 0; m < T->n_mol; ++m)
             if (!T->mols[m].large) fps.push_back(footprint(T->mols[m], mode));
@@ -668,6 +822,7 @@ extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, cons
     switch (precision) {
         case ILVES_PREC_FP64: return launch_mode<ModeFP64>(T, A, s);
         case ILVES_PREC_MIXED: return launch_mode<ModeMixed>(T, A, s);
+        case ILVES_PREC_MIXED_DF: return launch_mode<ModeMixedDF>(T, A, s);
         default: return ILVES_ERR_INVALID_ARG;
     }
 }

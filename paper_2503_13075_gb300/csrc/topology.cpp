@@ -206,7 +206,8 @@ static Program compile(int32_t nc, const Elimination& E, const std::vector<int32
     std::vector<std::vector<TermW>> tterms(t);
     for (int32_t p = 0; p < nc; ++p) {
         const int32_t td = P.diag_task[p];
-        P.tasks[td] = {(uint32_t)p, (uint32_t)p, kNoAtom32, 0u};
+        // DIAG: a_pp = 4 (w_i + w_j) r_p . rho_p; the pseudo-atom na + 1 + p carries w_i + w_j
+        P.tasks[td] = {(uint32_t)p, (uint32_t)p, (uint32_t)(na_dummy + 1 + p) << 1, 0u};
         for (int32_t m : dn[p]) tterms[td].push_back({(uint32_t)slot_L(p, m), (uint32_t)slot_U(m, p), (uint32_t)m, 0u});
         const int32_t nu = (int32_t)P.up[p].size();
         for (int32_t k = 0; k < nu; ++k) {
@@ -280,7 +281,7 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
     auto* inc_ptr = reinterpret_cast<IdxT*>(dst + L.inc_ptr);
     auto* inc = reinterpret_cast<IdxT*>(dst + L.inc);
     auto* tasks = reinterpret_cast<Task<IdxT>*>(dst + L.tasks);
-    auto* terms = reinterpret_cast<Term<IdxT>*>(dst + L.terms);
+    auto* terms = reinterpret_cast<typename TermOf<IdxT>::T*>(dst + L.terms);
     const int32_t nc = (int32_t)M.cons.size(), na = (int32_t)M.atoms.size();
     for (int32_t p = 0; p < nc; ++p) {
         const int32_t c = P.pos_con[p];
@@ -315,10 +316,7 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
         tasks[t].tstart = (IdxT)w.tstart;
     }
     for (size_t k = 0; k < P.terms.size(); ++k) {
-        terms[k].l = (IdxT)P.terms[k].l;
-        terms[k].u = (IdxT)P.terms[k].u;
-        terms[k].m = (IdxT)P.terms[k].m;
-        terms[k].pad = 0;
+        terms[k] = TermOf<IdxT>::make(P.terms[k].l, P.terms[k].u, P.terms[k].m);
     }
 }
 
@@ -394,9 +392,9 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             std::sort(v.begin(), v.end());
             v.erase(std::unique(v.begin(), v.end()), v.end());
         }
-        M.large = nc > warp_limit || na > 65535;
+        M.large = nc > warp_limit || nc >= (int32_t)kCompactMaxConstraints || na + 1 + nc > 32000;
         Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : 32));
-        if (!M.large && (P->tasks.size() > 65000 || P->terms.size() > 65000)) {
+        if (!M.large && (P->tasks.size() >= kCompactMaxSlots || P->terms.size() > 65000)) {
             M.large = true;
             *P = choose_order(nc, na, adj, M.ci, M.cj, o, 1024);
         }
@@ -450,8 +448,8 @@ void free_programs(ilves_topology* T) {
 uint32_t footprint(const MolHost& M, int mode) {
     const uint32_t lp = mode == ILVES_PREC_FP64 ? 8u : 4u;
     const ProgLayout L = layout_for<uint16_t>(M);
-    const StateLayout S = state_layout((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(),
-                                       (uint32_t)M.ntask, lp, 8u);
+    const StateLayout S = state_layout((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(), (uint32_t)M.ntask,
+                                       lp, mode == ILVES_PREC_MIXED_DF);
     return L.bytes + S.bytes;
 }
 

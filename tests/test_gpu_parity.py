@@ -16,7 +16,7 @@ from paper_2503_13075_gb300 import binding as B  # noqa: E402
 from paper_2503_13075_gb300 import workloads as wl  # noqa: E402
 
 pytestmark = pytest.mark.gpu
-PRECS = ["fp64", "mixed"]
+PRECS = ["fp64", "mixed", "mixed_df"]
 TOL = 1e-12
 X_TOL = 1e-10
 LAM_RTOL = 1e-8
@@ -195,5 +195,6 @@ def test_warm_start_and_aliasing(prec, trees):
 def test_repeated_solves_are_deterministic(trees):
     s, ref = trees
     t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
-    outs = [run(s, "mixed", topo=t)[1] for _ in range(3)]
-    assert all(np.array_equal(outs[0], o) for o in outs[1:])
+    for prec in PRECS:
+        outs = [run(s, prec, topo=t)[1] for _ in range(3)]
+        assert all(np.array_equal(outs[0], o) for o in outs[1:])
