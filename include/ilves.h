@@ -60,7 +60,8 @@ typedef enum {
     ILVES_ERR_TOPOLOGY = 2,    /* index out of range, i == j, duplicate constraint */
     ILVES_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
     ILVES_ERR_OOM = 4,         /* device allocation failed during setup */
-    ILVES_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+    ILVES_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    ILVES_ERR_TOO_LARGE = 6    /* the scratch a call needs exceeds the library's static maximum */
 } ilves_status;
 
 /* Per-molecule outcome written to mol_status_out. */
@@ -140,6 +141,41 @@ ilves_status ilves_solve(ilves_topology* topo, const double* x_old, const double
                          int32_t precision, const float* lambda0, double* x_out,
                          double* lambda_out, int32_t* iterations_out, int32_t* mol_status_out,
                          void* stream);
+
+/*
+ * Allocation-free variant of ilves_solve.  The paper has no counterpart; this entry
+ * point exists for callers that cannot allocate device memory when they solve: for
+ * example an MD engine that reserves the device memory pool for its own buffers after
+ * start-up, or code that must not call cudaMalloc / cudaFree because those may
+ * synchronise the device in the middle of an asynchronous time-stepping pipeline.
+ *
+ * Semantics, arguments and results are those of ilves_solve.  The difference: molecules
+ * too large for one warp (the CTA-per-molecule path) keep their solver state in one
+ * file-scope device array of ilves_static_scratch_bytes() bytes (16 MiB) instead of the
+ * topology's workspace.  Every GPU that loads the library holds that array until exit.
+ *  - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *  - The topology must have been set up on the CURRENT device.  The first call on a
+ *    device looks up the array's device address (cudaGetSymbolAddress) and may load the
+ *    library's device code; make that first call before any stream capture.
+ *  - Returns ILVES_ERR_TOO_LARGE, without launching anything, when the topology's
+ *    large-molecule state (ilves_topology_workspace_bytes) exceeds the static maximum.
+ *  - All calls share the one array.  Each call writes every scratch location before it
+ *    reads it, so nothing needs clearing between calls, but calls that overlap on the
+ *    GPU (other streams, other threads, or ilves_solve_static_scratch on two topologies
+ *    at once) race on the array: serialise them.
+ */
+ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_old, const double* x_unc,
+                                        const double* inv_mass, const double* d, double tol,
+                                        int32_t max_iter, int32_t precision, const float* lambda0,
+                                        double* x_out, double* lambda_out, int32_t* iterations_out,
+                                        int32_t* mol_status_out, void* stream);
+
+/* Size in bytes of the static scratch array used by ilves_solve_static_scratch. */
+int64_t ilves_static_scratch_bytes(void);
+
+/* Bytes of large-molecule solver state a topology needs (its workspace, or the part of
+ * the static scratch array ilves_solve_static_scratch would use). */
+int64_t ilves_topology_workspace_bytes(const ilves_topology* topo);
 
 /* Sizes of a topology (any pointer may be NULL):
  *  n_molecules, nnz_factor (entries of L+U including fill, summed over molecules),

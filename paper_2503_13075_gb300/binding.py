@@ -21,7 +21,7 @@ FP64, MIXED, MIXED_DF = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_df": MIXED_DF}
 CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE = 0, 1, 2, 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid topology", 3: "CUDA error", 4: "out of device memory",
-          5: "device wait timed out"}
+          5: "device wait timed out", 6: "scratch needed exceeds the static maximum"}
 
 
 class IlvesError(RuntimeError):
@@ -69,6 +69,12 @@ def lib():
     L.ilves_status_string.restype = ctypes.c_char_p
     L.ilves_last_launch_count.argtypes = [P]
     L.ilves_last_launch_count.restype = I32
+    L.ilves_solve_static_scratch.argtypes = [P, P, P, P, P, D, I32, I32, P, P, P, P, P, VP]
+    L.ilves_solve_static_scratch.restype = I32
+    L.ilves_static_scratch_bytes.argtypes = []
+    L.ilves_static_scratch_bytes.restype = I64
+    L.ilves_topology_workspace_bytes.argtypes = [P]
+    L.ilves_topology_workspace_bytes.restype = I64
     _lib = L
     return L
 
@@ -160,8 +166,18 @@ class Topology:
     def last_launch_count(self):
         return int(lib().ilves_last_launch_count(self._h))
 
+    def workspace_bytes(self):
+        return int(lib().ilves_topology_workspace_bytes(self._h))
+
+    def solve_static_scratch(self, *args, **kw):
+        """``ilves_solve_static_scratch``: as ``solve``, but the large-molecule state lives in the
+        library's static device array, so the call itself allocates nothing on the device.
+        (This Python wrapper still creates output tensors when none are passed.)"""
+        return self.solve(*args, _entry="ilves_solve_static_scratch", **kw)
+
     def solve(self, x_old, x_unc, inv_mass, d, tol=1e-12, max_iter=25, precision="mixed", lambda0=None,
-              x_out=None, lambda_out=None, iterations_out=None, status_out=None, stream=None):
+              x_out=None, lambda_out=None, iterations_out=None, status_out=None, stream=None,
+              _entry="ilves_solve"):
         """One ``ilves_solve`` on device tensors; returns (x, lambda, iterations, status)."""
         import torch
 
@@ -184,7 +200,8 @@ class Topology:
         status_out = torch.empty(self.n_molecules, dtype=torch.int32, device=dev) if status_out is None else status_out
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        _check(lib().ilves_solve(self._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), float(tol), int(max_iter),
-                                 prec, None if lambda0 is None else _ptr(lambda0), _ptr(x_out), _ptr(lambda_out),
-                                 _ptr(iterations_out), _ptr(status_out), ctypes.c_void_p(s)), "ilves_solve")
+        fn = getattr(lib(), _entry)
+        _check(fn(self._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), float(tol), int(max_iter),
+                  prec, None if lambda0 is None else _ptr(lambda0), _ptr(x_out), _ptr(lambda_out),
+                  _ptr(iterations_out), _ptr(status_out), ctypes.c_void_p(s)), _entry)
         return x_out, lambda_out, iterations_out, status_out

@@ -25,6 +25,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ilves.h"
@@ -753,6 +754,72 @@ static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStrea
     return ILVES_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Allocation-free variant (see ilves_solve_static_scratch in ilves.h).  The state of
+// CTA-per-molecule solves lives in this file-scope device array instead of the
+// topology's workspace.  Host code must not pass the symbol itself to a kernel (in host
+// code it names a host-side stand-in); its device address is looked up once per device.
+// ------------------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mutex;
+static void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up on first use).
+static ilves_status static_scratch_address(int dev, uint8_t** out) {
+    if (dev < 0 || dev >= kMaxDevices) return ILVES_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) return ILVES_ERR_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = reinterpret_cast<uint8_t*>(g_scratch_addr[dev]);
+    return ILVES_OK;
+}
+
+template <class Mode>
+static ilves_status launch_mode_static(ilves_topology* T, const SolveArgs& A, cudaStream_t stream,
+                                       uint8_t* scratch) {
+    cudaError_t e;
+    int launches = 0;
+    const DeviceSchedule& DS = T->sched[Mode::id];
+    if (!T->smem_attr_set[Mode::id]) {
+        e = cudaFuncSetAttribute(small_kernel<Mode>(), cudaFuncAttributeMaxDynamicSharedMemorySize, DS.arena);
+        if (e != cudaSuccess) return to_status(e);
+        T->smem_attr_set[Mode::id] = true;
+    }
+    if (T->n_large > 0) {
+        cudaStream_t side = (cudaStream_t)T->side_stream;
+        if ((e = cudaEventRecord((cudaEvent_t)T->ev_fork, stream)) != cudaSuccess) return to_status(e);
+        if ((e = cudaStreamWaitEvent(side, (cudaEvent_t)T->ev_fork, 0)) != cudaSuccess) return to_status(e);
+        k_solve_large<Mode><<<T->n_large, T->large_threads, 0, side>>>(T->d_desc + T->n_small, T->d_blob, scratch, A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+        ++launches;
+        if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
+    }
+    if (T->n_small > 0) {
+        SmallSched S{DS.cta_round_ptr, DS.round_ptr, DS.round_mol, DS.round_off};
+        k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+        ++launches;
+    }
+    const int nf = (int)T->free_atoms.size();
+    if (nf > 0 && A.x_out != A.x_unc) {
+        k_copy_free<<<(nf + 255) / 256, 256, 0, stream>>>(T->d_free_atoms, nf, A.x_unc, A.x_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+        ++launches;
+    }
+    if (T->n_large > 0) {
+        if ((e = cudaStreamWaitEvent(stream, (cudaEvent_t)T->ev_join, 0)) != cudaSuccess) return to_status(e);
+    }
+    T->last_launches = launches;
+    return ILVES_OK;
+}
+
 }  // namespace ilves
 
 using namespace ilves;
@@ -827,6 +894,49 @@ extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, cons
     }
 }
 
+extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const double* x_old, const double* x_unc,
+                                                   const double* inv_mass, const double* d, double tol,
+                                                   int32_t max_iter, int32_t precision, const float* lambda0,
+                                                   double* x_out, double* lambda_out, int32_t* iterations_out,
+                                                   int32_t* mol_status_out, void* stream) {
+    if (!T || !T->on_device) return ILVES_ERR_INVALID_ARG;
+    if (max_iter < 0 || !(tol >= 0.0)) return ILVES_ERR_INVALID_ARG;
+    if (T->n_atoms > 0 && (!x_old || !x_unc || !inv_mass || !x_out)) return ILVES_ERR_INVALID_ARG;
+    if (T->n_c > 0 && !d) return ILVES_ERR_INVALID_ARG;
+    if (precision < ILVES_PREC_FP64 || precision > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
+    if ((uint64_t)T->work_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ILVES_ERR_CUDA;
+    if (dev != T->device) return ILVES_ERR_INVALID_ARG;
+    uint8_t* scratch = nullptr;
+    ilves_status st = static_scratch_address(dev, &scratch);
+    if (st != ILVES_OK) return st;
+    SolveArgs A;
+    A.x_old = x_old;
+    A.x_unc = x_unc;
+    A.inv_mass = inv_mass;
+    A.d = d;
+    A.lambda0 = lambda0;
+    A.x_out = x_out;
+    A.lambda_out = lambda_out;
+    A.iterations_out = iterations_out;
+    A.status_out = mol_status_out;
+    A.atom_gid = T->d_atom_gid;
+    A.tol = tol;
+    A.max_iter = max_iter;
+    cudaStream_t s = (cudaStream_t)stream;
+    T->last_launches = 0;
+    switch (precision) {
+        case ILVES_PREC_FP64: return launch_mode_static<ModeFP64>(T, A, s, scratch);
+        case ILVES_PREC_MIXED: return launch_mode_static<ModeMixed>(T, A, s, scratch);
+        default: return launch_mode_static<ModeMixedDF>(T, A, s, scratch);
+    }
+}
+
+extern "C" int64_t ilves_static_scratch_bytes(void) { return (int64_t)kStaticScratchBytes; }
+
+extern "C" int64_t ilves_topology_workspace_bytes(const ilves_topology* T) { return T ? T->work_bytes : 0; }
+
 extern "C" ilves_status ilves_topology_info(const ilves_topology* T, int32_t* n_molecules, int64_t* nnz_factor,
                                             int32_t* max_levels, int64_t* n_fill, int32_t* n_large) {
     if (!T) return ILVES_ERR_INVALID_ARG;
@@ -887,6 +997,7 @@ extern "C" const char* ilves_status_string(int32_t s) {
         case ILVES_ERR_CUDA: return "CUDA error";
         case ILVES_ERR_OOM: return "out of device memory";
         case ILVES_ERR_TIMEOUT: return "device wait timed out";
+        case ILVES_ERR_TOO_LARGE: return "scratch needed exceeds the static maximum";
         default: return "unknown status";
     }
 }

@@ -1,0 +1,68 @@
+"""The allocation-free entry point ilves_solve_static_scratch against ilves_solve.
+
+Callers that cannot allocate device memory while they solve (an MD engine that has
+reserved the device memory pool for its own buffers, or a time-stepping pipeline that
+must not call cudaMalloc / cudaFree because they can synchronise the device) use
+ilves_solve_static_scratch.  It keeps the state of the CTA-per-molecule path in one
+static device array instead of the topology's workspace.  These tests check, through
+the C ABI, that two calls in a row give the results of ilves_solve within the parity
+tolerances used by the other GPU tests, and that an oversized topology is rejected.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2503_13075_gb300 import binding as B  # noqa: E402
+from paper_2503_13075_gb300 import workloads as wl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+X_TOL = 1e-10
+LAM_RTOL = 1e-8
+
+
+def _dev(s):
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+    return f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d)
+
+
+def _host(outs):
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in outs]
+
+
+def _same(ref, got):
+    x0, l0, i0, s0 = ref
+    x1, l1, i1, s1 = got
+    assert np.array_equal(s0, s1) and np.array_equal(i0, i1)
+    assert np.abs(x1 - x0).max(initial=0) <= X_TOL
+    scale = np.abs(l0).max(initial=0)
+    assert np.all(np.abs(l1 - l0) <= LAM_RTOL * np.abs(l0) + 1e-10 * scale)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("case", ["protein_like", "forced_large"])
+def test_static_scratch_matches_solve(case, prec):
+    if case == "protein_like":
+        s = wl.protein_like(n_atoms=20000, seed=1002)
+        topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    else:  # a batch where most molecules take the CTA-per-molecule path, some the warp path
+        s = wl.tree_batch(n_mol=24, seed=77)
+        topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j, max_warp_constraints=40)
+    assert topo.n_large > 0
+    assert 0 < topo.workspace_bytes() <= B.lib().ilves_static_scratch_bytes()
+    dev_in = _dev(s)
+    ref = _host(topo.solve(*dev_in, precision=prec))
+    assert np.all(ref[3] == B.CONVERGED)
+    for _ in range(2):  # the array keeps the previous call's contents; results must not depend on them
+        got = _host(topo.solve_static_scratch(*dev_in, precision=prec))
+        _same(ref, got)
+
+
+def test_static_scratch_rejects_oversized_topology():
+    s = wl.protein_like(n_atoms=100_000, seed=1002)
+    topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    assert topo.workspace_bytes() > B.lib().ilves_static_scratch_bytes()
+    with pytest.raises(B.IlvesError) as e:
+        topo.solve_static_scratch(*_dev(s), precision="mixed")
+    assert e.value.code == 6
