@@ -177,6 +177,67 @@ int64_t ilves_static_scratch_bytes(void);
  * the static scratch array ilves_solve_static_scratch would use). */
 int64_t ilves_topology_workspace_bytes(const ilves_topology* topo);
 
+/* ---------------------------------------------------------------------------------
+ * Learned warm start.  The paper starts Newton from lambda_0 = 0 (supplement Sec. 2.3);
+ * these entry points add a small network that predicts lambda_0 from local geometry.
+ * The Newton loop of ilves_solve is unchanged and still decides convergence.
+ *
+ * Features (16 per constraint k with atoms i, j; s = x_unc,i - x_unc,j,
+ * rho = x_old,i - x_old,j, W = w_i + w_j), float32:
+ *   f0 = (s.s - d^2)/d^2, f1 = s.rho/d^2 - 1, f2 = (w_i - w_j)/W, f3 = |s - rho|^2/d^2,
+ *   and for 4 neighbour slots (line-graph neighbours sharing atom i: slots 0-1, sharing
+ *   atom j: slots 2-3, ascending constraint id, missing -> zeros), neighbour l sharing a:
+ *   (s_l.s_l - d_l^2)/d_l^2,  s_k(a) s_l(a) s.rho_l/(d d_l),  w_a/W.
+ * Target: y = lambda * scale, scale = 4 W s.rho / d^2; lambda_0 = y / scale.
+ * Network: 16 -> 128 -> ReLU -> 128 -> ReLU -> 1; bfloat16 inputs and W1, W2 (first
+ * hidden layer rounded to bfloat16), float32 accumulation, biases and output layer.
+ * Parameters (float32, ILVES_MLP_PARAMS values): W1 [128][16] (out x in), b1[128],
+ * W2 [128][128], b2[128], w3[128], b3.
+ * ------------------------------------------------------------------------------- */
+#define ILVES_MLP_FEATURES 16
+#define ILVES_MLP_HIDDEN 128
+#define ILVES_MLP_PARAMS 18817
+
+typedef struct ilves_mlp ilves_mlp; /* opaque: parameters, Adam state, activation buffers */
+
+/* Number of float32 parameters (ILVES_MLP_PARAMS). */
+int64_t ilves_mlp_param_count(void);
+
+/* Creates a network on the current device with He-uniform weights drawn from `seed` and
+ * activation buffers for up to max_batch training rows (allocates device memory). */
+ilves_status ilves_mlp_create(int32_t max_batch, uint64_t seed, ilves_mlp** out);
+void ilves_mlp_destroy(ilves_mlp* mlp);
+
+/* Copies the float32 parameters from / to HOST memory (synchronous; setting resets Adam). */
+ilves_status ilves_mlp_set_params(ilves_mlp* mlp, const float* host_params);
+ilves_status ilves_mlp_get_params(const ilves_mlp* mlp, float* host_params);
+
+/* Features (DEVICE float32, n_constraints x 16) and target scales (n_constraints, may be
+ * NULL) of every constraint of the topology.  Inputs as for ilves_solve. */
+ilves_status ilves_mlp_features(const ilves_topology* topo, const double* x_old, const double* x_unc,
+                                const double* inv_mass, const double* d, float* features, float* scale,
+                                void* stream);
+
+/* Inference on n feature rows (DEVICE): y (n floats). */
+ilves_status ilves_mlp_forward(const ilves_mlp* mlp, const float* features, int32_t n, float* y, void* stream);
+
+/* One fused kernel computing features, the network and lambda_0 = y / scale for every
+ * constraint (DEVICE float32 lambda0, n_constraints), ready for ilves_solve's lambda0.
+ * mlp == NULL gives the diagonal (Jacobi) guess lambda_0 = sigma_0 / A_kk at x_unc. */
+ilves_status ilves_warm_start(const ilves_mlp* mlp, const ilves_topology* topo, const double* x_old,
+                              const double* x_unc, const double* inv_mass, const double* d, float* lambda0,
+                              void* stream);
+
+/* Mean-squared-error gradient (DEVICE float32, ILVES_MLP_PARAMS values, may be NULL)
+ * and loss (DEVICE float, may be NULL) on n <= max_batch rows; parameters unchanged. */
+ilves_status ilves_mlp_gradient(ilves_mlp* mlp, const float* features, const float* target, int32_t n,
+                                float* grad, float* loss, void* stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on n <= max_batch
+ * rows; the loss before the step goes to loss (DEVICE float, may be NULL). */
+ilves_status ilves_mlp_train_step(ilves_mlp* mlp, const float* features, const float* target, int32_t n,
+                                  float lr, float* loss, void* stream);
+
 /* Sizes of a topology (any pointer may be NULL):
  *  n_molecules, nnz_factor (entries of L+U including fill, summed over molecules),
  *  max_levels (largest level count of any molecule), n_fill (fill entries),

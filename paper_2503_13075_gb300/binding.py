@@ -75,6 +75,25 @@ def lib():
     L.ilves_static_scratch_bytes.restype = I64
     L.ilves_topology_workspace_bytes.argtypes = [P]
     L.ilves_topology_workspace_bytes.restype = I64
+    L.ilves_mlp_param_count.argtypes = []
+    L.ilves_mlp_param_count.restype = I64
+    L.ilves_mlp_create.argtypes = [I32, ctypes.c_uint64, ctypes.POINTER(P)]
+    L.ilves_mlp_create.restype = I32
+    L.ilves_mlp_destroy.argtypes = [P]
+    L.ilves_mlp_destroy.restype = None
+    for n in ("ilves_mlp_set_params", "ilves_mlp_get_params"):
+        getattr(L, n).argtypes = [P, P]
+        getattr(L, n).restype = I32
+    L.ilves_mlp_features.argtypes = [P, P, P, P, P, P, P, VP]
+    L.ilves_mlp_features.restype = I32
+    L.ilves_mlp_forward.argtypes = [P, P, I32, P, VP]
+    L.ilves_mlp_forward.restype = I32
+    L.ilves_warm_start.argtypes = [P, P, P, P, P, P, P, VP]
+    L.ilves_warm_start.restype = I32
+    L.ilves_mlp_gradient.argtypes = [P, P, P, I32, P, P, VP]
+    L.ilves_mlp_gradient.restype = I32
+    L.ilves_mlp_train_step.argtypes = [P, P, P, I32, ctypes.c_float, P, VP]
+    L.ilves_mlp_train_step.restype = I32
     _lib = L
     return L
 
@@ -205,3 +224,113 @@ class Topology:
                   prec, None if lambda0 is None else _ptr(lambda0), _ptr(x_out), _ptr(lambda_out),
                   _ptr(iterations_out), _ptr(status_out), ctypes.c_void_p(s)), _entry)
         return x_out, lambda_out, iterations_out, status_out
+
+
+def _stream(dev, stream=None):
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream)
+
+
+def _check_tensor(name, t, dtype, numel):
+    import torch
+
+    if t.dtype != dtype or t.numel() != numel or not t.is_contiguous() or t.device.type != "cuda":
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor with {numel} elements")
+
+
+class Mlp:
+    """The warm-start network (``ilves_mlp_*``): 16 -> 128 -> 128 -> 1, bfloat16 weights."""
+
+    N_FEATURES = 16
+
+    def __init__(self, max_batch=65536, seed=0):
+        L = lib()
+        h = ctypes.c_void_p()
+        _check(L.ilves_mlp_create(int(max_batch), ctypes.c_uint64(seed), ctypes.byref(h)), "ilves_mlp_create")
+        self._h = h
+        self.max_batch = int(max_batch)
+        self.n_params = int(L.ilves_mlp_param_count())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ilves_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib().ilves_mlp_get_params(self._h, _ptr(out)), "ilves_mlp_get_params")
+        return out
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError("wrong parameter count")
+        _check(lib().ilves_mlp_set_params(self._h, _ptr(a)), "ilves_mlp_set_params")
+
+    def save(self, path):
+        np.save(path, self.get_params())
+
+    def load(self, path):
+        self.set_params(np.load(path))
+
+    def forward(self, features, stream=None):
+        import torch
+
+        n = features.shape[0]
+        _check_tensor("features", features, torch.float32, n * self.N_FEATURES)
+        y = torch.empty(n, dtype=torch.float32, device=features.device)
+        _check(lib().ilves_mlp_forward(self._h, _ptr(features), n, _ptr(y), _stream(features.device, stream)),
+               "ilves_mlp_forward")
+        return y
+
+    def gradient(self, features, target, stream=None):
+        import torch
+
+        n = features.shape[0]
+        _check_tensor("features", features, torch.float32, n * self.N_FEATURES)
+        _check_tensor("target", target, torch.float32, n)
+        g = torch.empty(self.n_params, dtype=torch.float32, device=features.device)
+        loss = torch.empty(1, dtype=torch.float32, device=features.device)
+        _check(lib().ilves_mlp_gradient(self._h, _ptr(features), _ptr(target), n, _ptr(g), _ptr(loss),
+                                        _stream(features.device, stream)), "ilves_mlp_gradient")
+        return g, loss
+
+    def train_step(self, features, target, lr, loss_out=None, stream=None):
+        import torch
+
+        n = features.shape[0]
+        _check_tensor("features", features, torch.float32, n * self.N_FEATURES)
+        _check_tensor("target", target, torch.float32, n)
+        _check(lib().ilves_mlp_train_step(self._h, _ptr(features), _ptr(target), n, ctypes.c_float(lr),
+                                          None if loss_out is None else _ptr(loss_out),
+                                          _stream(features.device, stream)), "ilves_mlp_train_step")
+
+
+def features(topo, x_old, x_unc, inv_mass, d, stream=None):
+    """``ilves_mlp_features``: (features (n_c, 16) float32, scale (n_c,) float32) on the device."""
+    import torch
+
+    dev = x_unc.device
+    f = torch.empty(topo.n_constraints, 16, dtype=torch.float32, device=dev)
+    sc = torch.empty(topo.n_constraints, dtype=torch.float32, device=dev)
+    _check(lib().ilves_mlp_features(topo._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), _ptr(f), _ptr(sc),
+                                    _stream(dev, stream)), "ilves_mlp_features")
+    return f, sc
+
+
+def warm_start(mlp, topo, x_old, x_unc, inv_mass, d, out=None, stream=None):
+    """``ilves_warm_start``: lambda_0 (float32, n_c) from the network, or the diagonal guess if mlp is None."""
+    import torch
+
+    dev = x_unc.device
+    out = torch.empty(topo.n_constraints, dtype=torch.float32, device=dev) if out is None else out
+    _check(lib().ilves_warm_start(None if mlp is None else mlp._h, topo._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass),
+                                  _ptr(d), _ptr(out), _stream(dev, stream)), "ilves_warm_start")
+    return out

@@ -31,6 +31,7 @@
 #include "ilves.h"
 #include "internal.h"
 #include "topology_impl.h"
+#include "devmath.cuh"
 
 namespace ilves {
 
@@ -58,33 +59,6 @@ struct ModeMixedDF {
     static constexpr bool df = true;
     static constexpr float pivot_rel = 1e-5f;
 };
-
-// float64 -> float32 by truncation, on the integer pipe.  Values below float's normal
-// range become signed zero, values above it (never nm-scale coordinates) infinity.
-__device__ __forceinline__ float narrow(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-    const unsigned sign = hi & 0x80000000u;
-    const int e = (int)((hi >> 20) & 0x7FFu) - 896;  // rebias 1023 -> 127
-    unsigned r = sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-    r = e <= 0 ? sign : r;
-    r = e >= 255 ? (sign | 0x7F800000u) : r;
-    return __uint_as_float(r);
-}
-
-// float32 -> float64, exact, on the integer pipe (subnormal floats flush to zero).
-__device__ __forceinline__ double widen(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned sign = b & 0x80000000u;
-    const unsigned e = (b >> 23) & 0xFFu;
-    const unsigned mant = b & 0x7FFFFFu;
-    unsigned hi = sign | ((e + 896u) << 20) | (mant >> 3);
-    unsigned lo = mant << 29;
-    hi = e == 0 ? sign : hi;
-    lo = e == 0 ? 0u : lo;
-    hi = e == 255 ? (sign | 0x7FF00000u | (mant >> 3)) : hi;
-    return __hiloint2double((int)hi, (int)lo);
-}
 
 template <class LP> __device__ __forceinline__ LP to_lp(double v);
 template <> __device__ __forceinline__ float to_lp<float>(double v) { return narrow(v); }
@@ -578,6 +552,10 @@ static void free_device(ilves_topology* T) {
     f(T->d_blob);
     f(T->d_atom_gid);
     f(T->d_free_atoms);
+    f(T->d_con_i);
+    f(T->d_con_j);
+    f(T->d_nbr);
+    f(T->d_nbr_atom);
     f(T->d_work);
     for (auto& s : T->sched) {
         f(s.cta_round_ptr);
@@ -593,6 +571,7 @@ static void free_device(ilves_topology* T) {
     T->d_blob = nullptr;
     T->d_atom_gid = nullptr;
     T->d_free_atoms = nullptr;
+    T->d_con_i = T->d_con_j = T->d_nbr = T->d_nbr_atom = nullptr;
     T->d_work = nullptr;
     T->side_stream = T->ev_fork = T->ev_join = nullptr;
 }
@@ -671,6 +650,10 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     if ((e = upload(&T->d_blob, blob)) != cudaSuccess) return to_status(e);
     if ((e = upload(&T->d_atom_gid, gids)) != cudaSuccess) return to_status(e);
     if ((e = upload(&T->d_free_atoms, T->free_atoms)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_con_i, T->con_i)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_con_j, T->con_j)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_nbr, T->nbr)) != cudaSuccess) return to_status(e);
+    if ((e = upload(&T->d_nbr_atom, T->nbr_atom)) != cudaSuccess) return to_status(e);
     if (woff > 0 && (e = cudaMalloc((void**)&T->d_work, woff)) != cudaSuccess) return to_status(e);
     // persistent schedules, one per precision mode
     for (int mode = 0; mode < 3; ++mode) {

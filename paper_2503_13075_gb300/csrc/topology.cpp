@@ -365,6 +365,36 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
         if (used[a]) T->mols[mol_of_root[uf_find(par, a)]].atoms.push_back(a);
     for (int32_t k = 0; k < n_c; ++k) T->mols[mol_of_root[uf_find(par, ai[k])]].cons.push_back(k);
     T->n_mol = n_mol;
+    // neighbour table used by the learned warm start's features
+    T->con_i.assign(ai, ai + n_c);
+    T->con_j.assign(aj, aj + n_c);
+    T->nbr.assign((size_t)n_c * 4, -1);
+    T->nbr_atom.assign((size_t)n_c * 4, -1);
+    {
+        std::vector<int32_t> deg(n_atoms + 1, 0);
+        for (int32_t k = 0; k < n_c; ++k) {
+            ++deg[ai[k] + 1];
+            ++deg[aj[k] + 1];
+        }
+        for (int32_t a = 0; a < n_atoms; ++a) deg[a + 1] += deg[a];
+        std::vector<int32_t> inc_all(2 * (size_t)n_c), fillp(deg.begin(), deg.end() - 1);
+        for (int32_t k = 0; k < n_c; ++k) {  // constraints at each atom, ascending ids
+            inc_all[fillp[ai[k]]++] = k;
+            inc_all[fillp[aj[k]]++] = k;
+        }
+        for (int32_t k = 0; k < n_c; ++k) {
+            for (int side = 0; side < 2; ++side) {
+                const int32_t a = side ? aj[k] : ai[k];
+                int32_t slot = 2 * side;
+                for (int32_t e = deg[a]; e < deg[a + 1] && slot < 2 * side + 2; ++e) {
+                    if (inc_all[e] == k) continue;
+                    T->nbr[(size_t)k * 4 + slot] = inc_all[e];
+                    T->nbr_atom[(size_t)k * 4 + slot] = a;
+                    ++slot;
+                }
+            }
+        }
+    }
     std::vector<int32_t> local(n_atoms, -1);
     const int32_t warp_limit = o.max_warp_constraints > 0 ? o.max_warp_constraints : 1024;
     T->progs.assign(n_mol, nullptr);

@@ -43,6 +43,9 @@ struct ilves_topology {
     std::vector<ilves::MolHost> mols;
     std::vector<ilves::Program*> progs;  // owned
     std::vector<int32_t> free_atoms;
+    // per global constraint: atoms, and up to 4 line-graph neighbours (2 sharing atom_i,
+    // then 2 sharing atom_j; -1 = none) with the global id of the shared atom
+    std::vector<int32_t> con_i, con_j, nbr, nbr_atom;
     // device side
     int32_t device = -1;
     bool on_device = false;
@@ -53,6 +56,10 @@ struct ilves_topology {
     int64_t blob_bytes = 0;
     int32_t* d_atom_gid = nullptr;
     int32_t* d_free_atoms = nullptr;
+    int32_t* d_con_i = nullptr;
+    int32_t* d_con_j = nullptr;
+    int32_t* d_nbr = nullptr;       // n_c x 4
+    int32_t* d_nbr_atom = nullptr;  // n_c x 4
     uint8_t* d_work = nullptr;               // large-molecule numerical state
     int64_t work_bytes = 0;
     ilves::DeviceSchedule sched[3];          // per precision mode
