@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-precision comparators")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--warm-start", default="diag", choices=["none", "diag", "mlp"],
+                   help="initial multipliers: zero, diagonal (Jacobi) guess, or the learned network")
     return p.parse_args()
 
 
@@ -219,15 +221,33 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def time_device(topo, dev_in, out, prec, tol, steps, warmup, flush, stream):
-    """Per-step CUDA-event time of ilves_solve (L2 flushed before each step)."""
-    import torch
+WS_LAUNCHES = {"none": 0, "diag": 1, "mlp": 2}  # kernels a warm start adds per step
+
+
+def make_step(topo, dev_in, out, prec, tol, ws, mlp, lam0):
+    """One timed unit: optional warm start (diag / mlp kernels) + ilves_solve."""
+    from paper_2503_13075_gb300 import binding as B
 
     xo, xu, w, d = dev_in
     x, lam, it, st = out
+
+    def step():
+        l0 = None
+        if ws != "none":
+            l0 = B.warm_start(mlp if ws == "mlp" else None, topo, xo, xu, w, d, out=lam0)
+        topo.solve(xo, xu, w, d, tol=tol, precision=prec, lambda0=l0, x_out=x, lambda_out=lam,
+                   iterations_out=it, status_out=st)
+        return topo.last_launch_count() + WS_LAUNCHES[ws]
+
+    return step
+
+
+def time_device(step, steps, warmup, flush, stream):
+    """Per-step CUDA-event time (L2 flushed before each step, outside the events)."""
+    import torch
+
     for _ in range(warmup):
-        topo.solve(xo, xu, w, d, tol=tol, precision=prec, x_out=x, lambda_out=lam, iterations_out=it,
-                   status_out=st)
+        step()
     torch.cuda.synchronize()
     times = []
     launches = 0
@@ -236,14 +256,32 @@ def time_device(topo, dev_in, out, prec, tol, steps, warmup, flush, stream):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        topo.solve(xo, xu, w, d, tol=tol, precision=prec, x_out=x, lambda_out=lam, iterations_out=it,
-                   status_out=st)
+        launches += step()
         e1.record(stream)
-        launches += topo.last_launch_count()
         times.append((e0, e1))
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in times]
     return ms, launches
+
+
+def train_warm_start(dev, seed=3001):
+    """Trains the warm-start network on a tree batch of another seed (plain FP64 solver labels)."""
+    import torch
+
+    from paper_2503_13075_gb300 import binding as B
+    from paper_2503_13075_gb300 import warmstart as ws
+
+    t0 = time.perf_counter()
+    feat, y, ok = ws.tree_training_set(n_mol=4096, seed=seed, dev=dev)
+    t1 = time.perf_counter()
+    mlp = B.Mlp(max_batch=8192, seed=1)
+    losses = ws.train(mlp, feat, y, epochs=30, batch=8192, lr=3e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    info = {"train_pairs": int(feat.shape[0]), "labels_converged": bool(ok), "epochs": 30,
+            "final_mse": losses[-1], "target_variance": float(y.var().item()),
+            "data_s": round(t1 - t0, 2), "train_s": round(time.perf_counter() - t1, 2),
+            "train_seed": seed}
+    return mlp, info
 
 
 def run_ilves(args):
@@ -262,32 +300,44 @@ def run_ilves(args):
     out = (torch.empty_like(dev_in[1]), torch.empty(s.n_constraints, dtype=torch.float64, device=dev),
            torch.empty(topo.n_molecules, dtype=torch.int32, device=dev),
            torch.empty(topo.n_molecules, dtype=torch.int32, device=dev))
+    lam0 = torch.empty(s.n_constraints, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # plain FP64 comparator and the other precision (same batch, same tolerance)
-    alt, value64, per64, ok64, it64 = {}, None, None, None, None
-    if not args.no_compare:
-        ms64, _ = time_device(topo, dev_in, out, "fp64", args.tol, max(3, args.steps // 4), 2, flush, stream)
-        ok64 = bool((out[3] == 0).all().item())
-        it64 = out[2].cpu().numpy()
-        per64 = sum(ms64) / len(ms64)
-        value64 = s.n_atoms / (per64 * 1e-3)
-        for prec in ("mixed", "mixed_df"):
-            if prec == args.precision:
-                continue
-            msa, _ = time_device(topo, dev_in, out, prec, args.tol, max(3, args.steps // 4), 2, flush, stream)
-            xa = out[0].cpu().numpy()
-            alt[prec] = {"value": s.n_atoms / (sum(msa) / len(msa) * 1e-3), "ms_per_step": sum(msa) / len(msa),
-                         "all_converged": bool((out[3] == 0).all().item()),
-                         "max_rel_violation": orc.max_relative_violation(xa, s.atom_i, s.atom_j, s.d)}
+    mlp, mlp_info = None, None
+    if args.warm_start == "mlp" or not args.no_compare:
+        mlp, mlp_info = train_warm_start(dev)
 
-    def roll(seconds):  # keep the GPU busy with the same solve (clock sampling window)
+    def check():
+        st = out[3].cpu().numpy()
+        xa = out[0].cpu().numpy()
+        return bool(np.all(st == 0)), orc.max_relative_violation(xa, s.atom_i, s.atom_j, s.d), out[2].cpu().numpy()
+
+    # ablation ladder: plain FP64 -> mixed -> float-float, each with zero / diagonal / learned start
+    ablation = []
+    value64 = per64 = None
+    if not args.no_compare:
+        for prec in ("fp64", "mixed", "mixed_df"):
+            for wsn in ("none", "diag", "mlp"):
+                if prec == args.precision and wsn == args.warm_start:
+                    continue
+                step = make_step(topo, dev_in, out, prec, args.tol, wsn, mlp, lam0)
+                msa, _ = time_device(step, max(3, args.steps // 4), 2, flush, stream)
+                ok, viol, it = check()
+                per = sum(msa) / len(msa)
+                ablation.append({"precision": prec, "warm_start": wsn, "ms_per_step": per,
+                                 "value": s.n_atoms / (per * 1e-3), "all_converged": ok, "max_rel_violation": viol,
+                                 "mean_iterations": float(it.mean())})
+                if prec == "fp64" and wsn == "none":
+                    value64, per64 = s.n_atoms / (per * 1e-3), per
+
+    step = make_step(topo, dev_in, out, args.precision, args.tol, args.warm_start, mlp, lam0)
+
+    def roll(seconds):  # keep the GPU busy with the same step (clock sampling window)
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < seconds:
             for _ in range(20):
-                topo.solve(*dev_in, tol=args.tol, precision=args.precision, x_out=out[0], lambda_out=out[1],
-                           iterations_out=out[2], status_out=out[3])
+                step()
             torch.cuda.synchronize()
 
     clocks = None if args.no_clocks else ClockSampler(local)
@@ -297,19 +347,32 @@ def run_ilves(args):
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    ms, launches = time_device(topo, dev_in, out, args.precision, args.tol, args.steps, args.warmup, flush, stream)
+    ms, launches = time_device(step, args.steps, args.warmup, flush, stream)
     torch.cuda.synchronize()
     barrier(world)
     t_wall = time.perf_counter() - t_wall0
     if clocks:
         roll(0.3)
     clk = clocks.stop() if clocks else None
-    status = out[3].cpu().numpy()
-    iters = out[2].cpu().numpy()
+    valid, viol, iters = check()
     x = out[0].cpu().numpy()
-    valid = bool(np.all(status == 0))
-    viol = orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d)
     avg_err = orc.average_relative_error(x, s.atom_i, s.atom_j, s.d)
+    # kernel-only time of the dominant kernel (the solve) for the roofline: same step, solve events only
+    solve_ms = []
+    if args.warm_start != "none":
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            l0 = B.warm_start(mlp if args.warm_start == "mlp" else None, topo, *dev_in, out=lam0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            topo.solve(*dev_in, tol=args.tol, precision=args.precision, lambda0=l0, x_out=out[0],
+                       lambda_out=out[1], iterations_out=out[2], status_out=out[3])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            solve_ms.append(e0.elapsed_time(e1))
+    else:
+        solve_ms = ms
 
     per_step_ms = sum(ms) / len(ms)
     per_step_ms = max_over_ranks(per_step_ms, world, dev)
@@ -330,8 +393,7 @@ def run_ilves(args):
         e0.record(stream)
         for dst, src in zip(dev_in, host):
             dst.copy_(src, non_blocking=True)
-        topo.solve(*dev_in, tol=args.tol, precision=args.precision, x_out=out[0], lambda_out=out[1],
-                   iterations_out=out[2], status_out=out[3])
+        step()
         hx.copy_(out[0], non_blocking=True)
         hl.copy_(out[1], non_blocking=True)
         hi.copy_(out[2], non_blocking=True)
@@ -348,7 +410,8 @@ def run_ilves(args):
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     ab = algorithmic_bytes(s)
-    achieved = ab / (per_step_ms * 1e-3) / 1e9
+    solve_per = sum(solve_ms) / len(solve_ms)
+    achieved = ab / (solve_per * 1e-3) / 1e9
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, sample = cpu_oracle_rate(s)
@@ -372,8 +435,8 @@ def run_ilves(args):
         "config": {
             "workload": workload_name(s),
             "precision": args.precision,
+            "warm_start": args.warm_start,
             "tol": args.tol,
-            "warm_start": "none",
             "l2": "flushed (256 MiB write) before every timed step",
             "schedule": "persistent CTAs, one warp per molecule",
         },
@@ -381,14 +444,14 @@ def run_ilves(args):
         "max_rel_violation": viol,
         "avg_rel_error": avg_err,
         "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(iters)) if v},
-        "plain_fp64": None if value64 is None else {
-            "value": value64, "ms_per_step": per64, "all_converged": ok64,
-            "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(it64)) if v}},
+        "plain_fp64": None if value64 is None else {"value": value64, "ms_per_step": per64,
+                                                    "precision": "fp64", "warm_start": "none"},
         "speedup_vs_plain_fp64": None if value64 is None else value / value64,
-        "other_precisions": alt,
+        "ablation": ablation,
+        "warm_start_training": mlp_info,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": ab, "kernel": "k_solve_small"},
+                     "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
+                     "kernel": "k_solve_small", "kernel_ms": solve_per},
         "e2e": {"value": e2e_value, "unit": "atoms*solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_per},
         "gpu_launches": launches,

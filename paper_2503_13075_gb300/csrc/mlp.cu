@@ -51,7 +51,10 @@ struct FeatArgs {
     const int32_t* con_j;
     const int32_t* nbr;
     const int32_t* nbr_atom;
+    float4* ws_con;    // per constraint: (s.xyz, sigma0 / d^2), (rho.xyz, d)
+    float* ws_atom;    // per atom: inverse mass
     int32_t n_c;
+    int32_t n_atoms;
 };
 
 __device__ __forceinline__ float3 ld3(const double* x, int64_t a) {
@@ -60,35 +63,53 @@ __device__ __forceinline__ float3 ld3(const double* x, int64_t a) {
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-// The 16 features and the target scale of constraint k (float32 from truncated inputs).
-__device__ void constraint_features(const FeatArgs& F, int k, float* f, float& scale) {
+// Prep pass: per-constraint float32 geometry and per-atom weights into the topology's
+// warm-start workspace, so the feature stage gathers 32 bytes per neighbour instead of
+// four float64 atom positions.
+__global__ void k_ws_prep(FeatArgs F) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < F.n_c) {
+        const int i = F.con_i[k], j = F.con_j[k];
+        const float3 s = sub3(ld3(F.x_unc, i), ld3(F.x_unc, j));
+        const float3 r = sub3(ld3(F.x_old, i), ld3(F.x_old, j));
+        const float dk = narrow(F.d[k]), d2 = dk * dk;
+        F.ws_con[2 * k] = make_float4(s.x, s.y, s.z, (dot3(s, s) - d2) / d2);
+        F.ws_con[2 * k + 1] = make_float4(r.x, r.y, r.z, dk);
+    }
+    if (k < F.n_atoms) F.ws_atom[k] = narrow(F.inv_mass[k]);
+}
+
+// Features of constraint k from the workspace; `half` selects which half of the 16
+// features this lane writes (two lanes per row): half 0 = own terms + slots 0-1,
+// half 1 = slots 2-3 (the scale is produced by half 0).
+__device__ __forceinline__ void ws_features(const FeatArgs& F, int k, int half, float* f, float& scale) {
+    const float4 s4 = F.ws_con[2 * k], r4 = F.ws_con[2 * k + 1];
     const int i = F.con_i[k], j = F.con_j[k];
-    const float3 s = sub3(ld3(F.x_unc, i), ld3(F.x_unc, j));
-    const float3 r = sub3(ld3(F.x_old, i), ld3(F.x_old, j));
-    const float dk = narrow(F.d[k]), d2 = dk * dk;
-    const float wi = narrow(F.inv_mass[i]), wj = narrow(F.inv_mass[j]), W = wi + wj;
-    const float inv_d2 = 1.0f / d2, inv_w = W > 0.f ? 1.0f / W : 0.f;
+    const float wi = F.ws_atom[i], wj = F.ws_atom[j], W = wi + wj;
+    const float inv_w = W > 0.f ? 1.0f / W : 0.f;
+    const float dk = r4.w, inv_d2 = 1.0f / (dk * dk);
+    const float3 s = make_float3(s4.x, s4.y, s4.z), r = make_float3(r4.x, r4.y, r4.z);
     const float sr = dot3(s, r);
-    const float3 sm = sub3(s, r);
-    f[0] = (dot3(s, s) - d2) * inv_d2;
-    f[1] = sr * inv_d2 - 1.0f;
-    f[2] = (wi - wj) * inv_w;
-    f[3] = dot3(sm, sm) * inv_d2;
-    scale = 4.0f * W * sr * inv_d2;
+    if (half == 0) {
+        const float3 sm = sub3(s, r);
+        f[0] = s4.w;
+        f[1] = sr * inv_d2 - 1.0f;
+        f[2] = (wi - wj) * inv_w;
+        f[3] = dot3(sm, sm) * inv_d2;
+        scale = 4.0f * W * sr * inv_d2;
+    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int qq = 0; qq < 2; ++qq) {
+        const int q = 2 * half + qq;
         const int l = F.nbr[4 * k + q];
         float g0 = 0.f, g1 = 0.f, g2 = 0.f;
         if (l >= 0) {
             const int a = F.nbr_atom[4 * k + q];
-            const int il = F.con_i[l], jl = F.con_j[l];
-            const float3 sl = sub3(ld3(F.x_unc, il), ld3(F.x_unc, jl));
-            const float3 rl = sub3(ld3(F.x_old, il), ld3(F.x_old, jl));
-            const float dl = narrow(F.d[l]);
-            const float sgn = ((a == i) == (a == il)) ? 1.f : -1.f;
-            g0 = (dot3(sl, sl) - dl * dl) / (dl * dl);
-            g1 = sgn * dot3(s, rl) / (dk * dl);
-            g2 = narrow(F.inv_mass[a]) * inv_w;
+            const float4 sl4 = F.ws_con[2 * l], rl4 = F.ws_con[2 * l + 1];
+            const float sgn = ((a == i) == (a == F.con_i[l])) ? 1.f : -1.f;
+            g0 = sl4.w;
+            g1 = sgn * dot3(s, make_float3(rl4.x, rl4.y, rl4.z)) / (dk * rl4.w);
+            g2 = F.ws_atom[a] * inv_w;
         }
         f[4 + 3 * q] = g0;
         f[5 + 3 * q] = g1;
@@ -99,21 +120,26 @@ __device__ void constraint_features(const FeatArgs& F, int k, float* f, float& s
 __global__ void k_features(FeatArgs F, float* __restrict__ feat, float* __restrict__ scale) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= F.n_c) return;
-    float f[NF], sc;
-    constraint_features(F, k, f, sc);
+    float f[NF], sc = 0.f;
+    ws_features(F, k, 0, f, sc);
+    ws_features(F, k, 1, f, sc);
 #pragma unroll
     for (int q = 0; q < NF; ++q) feat[(int64_t)k * NF + q] = f[q];
     if (scale) scale[k] = sc;
 }
 
-// Jacobi guess lambda_0 = sigma_0 / A_kk at x_unc (no network): y = f0.
+// Jacobi guess lambda_0 = sigma_0 / A_kk at x_unc (no network): y = f0, own terms only.
 __global__ void k_diag_guess(FeatArgs F, float* __restrict__ lambda0) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= F.n_c) return;
-    float f[NF], sc;
-    constraint_features(F, k, f, sc);
-    const float l0 = f[0] / sc;
-    lambda0[k] = (sc != 0.f && isfinite(l0)) ? l0 : 0.f;
+    const int i = F.con_i[k], j = F.con_j[k];
+    const float3 s = sub3(ld3(F.x_unc, i), ld3(F.x_unc, j));
+    const float3 r = sub3(ld3(F.x_old, i), ld3(F.x_old, j));
+    const float dk = narrow(F.d[k]), d2 = dk * dk;
+    const float W = narrow(F.inv_mass[i]) + narrow(F.inv_mass[j]);
+    const float a = 4.0f * W * dot3(s, r);
+    const float l0 = (dot3(s, s) - d2) / a;
+    lambda0[k] = (a != 0.f && isfinite(l0)) ? l0 : 0.f;
 }
 
 // ------------------------------------------------------------------------------------
@@ -150,8 +176,24 @@ k_mlp_forward(MlpWeights Wt, const float* __restrict__ X, int n, FeatArgs F, flo
     __shared__ float b1s[NH], b2s[NH], w3s[NH];
     __shared__ float fs[FWD_WARPS][16][NF + 1];
     __shared__ float scs[FWD_WARPS][16];
-    for (int e = threadIdx.x; e < NH * NF; e += blockDim.x) w1s[(e / NF) * W1_LD + (e % NF)] = Wt.w1[e];
-    for (int e = threadIdx.x; e < NH * NH; e += blockDim.x) w2s[(e / NH) * W2_LD + (e % NH)] = Wt.w2[e];
+    {  // stage the bfloat16 weights with 16-byte loads (8 values), all loads issued before the stores
+        const uint4* g1 = reinterpret_cast<const uint4*>(Wt.w1);
+        const uint4* g2 = reinterpret_cast<const uint4*>(Wt.w2);
+        constexpr int N1 = NH * NF / 8, N2 = NH * NH / 8, PER = N2 / (FWD_WARPS * 32);
+        uint4 v[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) v[u] = __ldg(g2 + threadIdx.x + u * FWD_WARPS * 32);
+        for (int e = threadIdx.x; e < N1; e += blockDim.x) {
+            const int row = (e * 8) / NF, col = (e * 8) % NF;
+            *reinterpret_cast<uint4*>(w1s + row * W1_LD + col) = __ldg(g1 + e);
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * FWD_WARPS * 32;
+            const int row = (e * 8) / NH, col = (e * 8) % NH;
+            *reinterpret_cast<uint4*>(w2s + row * W2_LD + col) = v[u];
+        }
+    }
     for (int e = threadIdx.x; e < NH; e += blockDim.x) {
         b1s[e] = Wt.params[P_B1 + e];
         b2s[e] = Wt.params[P_B2 + e];
@@ -164,24 +206,31 @@ k_mlp_forward(MlpWeights Wt, const float* __restrict__ X, int n, FeatArgs F, flo
     const int n_tiles = (n + 15) / 16;
     for (int tile = blockIdx.x * FWD_WARPS + warp; tile < n_tiles; tile += gridDim.x * FWD_WARPS) {
         const int r0 = tile * 16;
-        // ---- input rows into shared memory (features computed here in the fused mode)
-        if (lane < 16) {
-            const int row = r0 + lane;
+        // ---- input rows into shared memory; in the fused mode two lanes build each row's
+        //      features from the warm-start workspace (lane r: own terms + slots 0-1,
+        //      lane r + 16: slots 2-3)
+        {
+            const int rl = lane & 15, half = lane >> 4, row = r0 + rl;
             float f[NF], sc = 0.f;
+#pragma unroll
+            for (int c = 0; c < NF; ++c) f[c] = 0.f;
             if (row < n) {
                 if constexpr (kFused) {
-                    constraint_features(F, row, f, sc);
-                } else {
+                    ws_features(F, row, half, f, sc);
+                } else if (half == 0) {
 #pragma unroll
                     for (int c = 0; c < NF; ++c) f[c] = X[(int64_t)row * NF + c];
                 }
-            } else {
-#pragma unroll
-                for (int c = 0; c < NF; ++c) f[c] = 0.f;
             }
+            if (half == 0) {
 #pragma unroll
-            for (int c = 0; c < NF; ++c) fs[warp][lane][c] = f[c];
-            scs[warp][lane] = sc;
+                for (int c = 0; c < 10; ++c) fs[warp][rl][c] = f[c];
+                scs[warp][rl] = sc;
+            }
+            if (kFused ? half == 1 : half == 0) {
+#pragma unroll
+                for (int c = 10; c < NF; ++c) fs[warp][rl][c] = f[c];
+            }
         }
         __syncwarp();
         const uint32_t a0 = pack_bf16(fs[warp][g][2 * q], fs[warp][g][2 * q + 1]);
@@ -385,13 +434,19 @@ static FeatArgs feat_args(const ilves_topology* T, const double* x_old, const do
     F.con_j = T->d_con_j;
     F.nbr = T->d_nbr;
     F.nbr_atom = T->d_nbr_atom;
+    F.ws_con = reinterpret_cast<float4*>(T->d_ws_con);
+    F.ws_atom = T->d_ws_atom;
     F.n_c = T->n_c;
+    F.n_atoms = T->n_atoms;
     return F;
 }
 
+// one wave of persistent blocks (4 per SM fit the 47 KB of shared memory each)
 static int fwd_grid(int n) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = (n + 15) / 16;
-    return std::max(1, std::min((tiles + FWD_WARPS - 1) / FWD_WARPS, 152 * 8));
+    return std::max(1, std::min((tiles + FWD_WARPS - 1) / FWD_WARPS, sms * 4));
 }
 
 extern "C" int64_t ilves_mlp_param_count(void) { return P_N; }
@@ -469,6 +524,8 @@ extern "C" ilves_status ilves_mlp_features(const ilves_topology* T, const double
     if (T->n_c == 0) return ILVES_OK;
     if (!x_old || !x_unc || !inv_mass || !d) return ILVES_ERR_INVALID_ARG;
     const FeatArgs F = feat_args(T, x_old, x_unc, inv_mass, d);
+    const int np = std::max(T->n_c, T->n_atoms);
+    k_ws_prep<<<(np + 255) / 256, 256, 0, (cudaStream_t)stream>>>(F);
     k_features<<<(T->n_c + 127) / 128, 128, 0, (cudaStream_t)stream>>>(F, features, scale);
     return mlp_status(cudaGetLastError());
 }
@@ -495,6 +552,8 @@ extern "C" ilves_status ilves_warm_start(const ilves_mlp* M, const ilves_topolog
         k_diag_guess<<<(T->n_c + 127) / 128, 128, 0, (cudaStream_t)stream>>>(F, lambda0);
     } else {
         const MlpWeights Wt{M->w1b, M->w2b, M->params};
+        const int np = std::max(T->n_c, T->n_atoms);
+        k_ws_prep<<<(np + 255) / 256, 256, 0, (cudaStream_t)stream>>>(F);
         k_mlp_forward<true, false><<<fwd_grid(T->n_c), FWD_WARPS * 32, 0, (cudaStream_t)stream>>>(
             Wt, nullptr, T->n_c, F, lambda0, nullptr, nullptr);
     }

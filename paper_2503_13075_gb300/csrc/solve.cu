@@ -556,6 +556,8 @@ static void free_device(ilves_topology* T) {
     f(T->d_con_j);
     f(T->d_nbr);
     f(T->d_nbr_atom);
+    f(T->d_ws_con);
+    f(T->d_ws_atom);
     f(T->d_work);
     for (auto& s : T->sched) {
         f(s.cta_round_ptr);
@@ -572,6 +574,7 @@ static void free_device(ilves_topology* T) {
     T->d_atom_gid = nullptr;
     T->d_free_atoms = nullptr;
     T->d_con_i = T->d_con_j = T->d_nbr = T->d_nbr_atom = nullptr;
+    T->d_ws_con = T->d_ws_atom = nullptr;
     T->d_work = nullptr;
     T->side_stream = T->ev_fork = T->ev_join = nullptr;
 }
@@ -654,6 +657,10 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     if ((e = upload(&T->d_con_j, T->con_j)) != cudaSuccess) return to_status(e);
     if ((e = upload(&T->d_nbr, T->nbr)) != cudaSuccess) return to_status(e);
     if ((e = upload(&T->d_nbr_atom, T->nbr_atom)) != cudaSuccess) return to_status(e);
+    if (T->n_c > 0 && (e = cudaMalloc((void**)&T->d_ws_con, (size_t)T->n_c * 8 * sizeof(float))) != cudaSuccess)
+        return to_status(e);
+    if (T->n_atoms > 0 && (e = cudaMalloc((void**)&T->d_ws_atom, (size_t)T->n_atoms * sizeof(float))) != cudaSuccess)
+        return to_status(e);
     if (woff > 0 && (e = cudaMalloc((void**)&T->d_work, woff)) != cudaSuccess) return to_status(e);
     // persistent schedules, one per precision mode
     for (int mode = 0; mode < 3; ++mode) {

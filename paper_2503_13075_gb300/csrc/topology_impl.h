@@ -60,6 +60,8 @@ struct ilves_topology {
     int32_t* d_con_j = nullptr;
     int32_t* d_nbr = nullptr;       // n_c x 4
     int32_t* d_nbr_atom = nullptr;  // n_c x 4
+    float* d_ws_con = nullptr;      // warm-start workspace: n_c x 8 floats (s, sigma0/d^2, rho, d)
+    float* d_ws_atom = nullptr;     // n_atoms floats (inverse masses)
     uint8_t* d_work = nullptr;               // large-molecule numerical state
     int64_t work_bytes = 0;
     ilves::DeviceSchedule sched[3];          // per precision mode
