@@ -467,15 +467,16 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
 // kernels
 // ------------------------------------------------------------------------------------
 struct SmallSched {
-    const int32_t* cta_round_ptr;
-    const int32_t* round_ptr;
-    const int32_t* round_mol;
-    const int32_t* round_off;
+    const int32_t* cta_slot_ptr;
+    const int32_t* slot_ptr;
+    const int32_t* slot_mol;
+    const int32_t* slot_off;
 };
 
-// Persistent batched kernel: each CTA walks its rounds; in a round, warp w solves one
-// molecule in its slice of the shared-memory arena.  The program blob is staged
-// into shared memory with 16-byte loads before the Newton loop.
+// Persistent batched kernel: warp w of CTA c owns one slot (a fixed slice of the CTA's
+// shared-memory arena) and solves its queue of molecules one after the other; warps
+// never wait for each other.  Each molecule's program blob is staged into the slice
+// with 16-byte loads before its Newton loop.
 template <class Mode>
 __global__ void __launch_bounds__(1024, 1)
 k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
@@ -483,31 +484,29 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
     extern __shared__ __align__(16) uint8_t arena[];
     const WarpTeam tm;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = blockIdx.x;
-    const int rb = S.cta_round_ptr[c], re = S.cta_round_ptr[c + 1];
-    for (int r = rb; r < re; ++r) {
-        const int m0 = S.round_ptr[r], m1 = S.round_ptr[r + 1];
-        if (warp < m1 - m0) {
-            const MolDesc D = desc[S.round_mol[m0 + warp]];
-            uint8_t* slice = arena + S.round_off[m0 + warp];
-            const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel);
-            const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
-            uint4* dst = reinterpret_cast<uint4*>(slice);
-            const int n16 = (int)(PL.bytes >> 4);
-            int k = lane;
-            for (; k + 96 < n16; k += 128) {  // four independent 16-byte loads in flight per lane
-                const uint4 a0 = __ldg(src + k), a1 = __ldg(src + k + 32), a2 = __ldg(src + k + 64),
-                            a3 = __ldg(src + k + 96);
-                dst[k] = a0;
-                dst[k + 32] = a1;
-                dst[k + 64] = a2;
-                dst[k + 96] = a3;
-            }
-            for (; k < n16; k += 32) dst[k] = __ldg(src + k);
-            __syncwarp();
-            solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.bytes, A);
+    const int slot = S.cta_slot_ptr[blockIdx.x] + warp;
+    if (slot >= S.cta_slot_ptr[blockIdx.x + 1]) return;
+    uint8_t* slice = arena + S.slot_off[slot];
+    const int q1 = S.slot_ptr[slot + 1];
+    for (int q = S.slot_ptr[slot]; q < q1; ++q) {
+        const MolDesc D = desc[S.slot_mol[q]];
+        const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel);
+        const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
+        uint4* dst = reinterpret_cast<uint4*>(slice);
+        const int n16 = (int)(PL.bytes >> 4);
+        int k = lane;
+        for (; k + 96 < n16; k += 128) {  // four independent 16-byte loads in flight per lane
+            const uint4 a0 = __ldg(src + k), a1 = __ldg(src + k + 32), a2 = __ldg(src + k + 64),
+                        a3 = __ldg(src + k + 96);
+            dst[k] = a0;
+            dst[k + 32] = a1;
+            dst[k + 64] = a2;
+            dst[k + 96] = a3;
         }
-        __syncthreads();
+        for (; k < n16; k += 32) dst[k] = __ldg(src + k);
+        __syncwarp();
+        solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.bytes, A);
+        __syncwarp();
     }
 }
 
@@ -560,10 +559,10 @@ static void free_device(ilves_topology* T) {
     f(T->d_ws_atom);
     f(T->d_work);
     for (auto& s : T->sched) {
-        f(s.cta_round_ptr);
-        f(s.round_ptr);
-        f(s.round_mol);
-        f(s.round_off);
+        f(s.cta_slot_ptr);
+        f(s.slot_ptr);
+        f(s.slot_mol);
+        f(s.slot_off);
         s = DeviceSchedule{};
     }
     if (T->side_stream) cudaStreamDestroy((cudaStream_t)T->side_stream);
@@ -667,29 +666,20 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         std::vector<uint32_t> fps;
         for (int32_t m = 0; m < T->n_mol; ++m)
             if (!T->mols[m].large) fps.push_back(footprint(T->mols[m], mode));
-        int warps = o.warps_per_cta;
-        if (warps <= 0) {
-            // enough warps to fill the arena with typical molecules
-            std::vector<uint32_t> s = fps;
-            uint32_t med = 1;
-            if (!s.empty()) {
-                std::nth_element(s.begin(), s.begin() + s.size() / 2, s.end());
-                med = std::max<uint32_t>(1, s[s.size() / 2]);
-            }
-            warps = std::max(1, std::min(32, (int)(arena / med)));
-        }
+        // auto: the largest warp count per CTA whose slices fit the arena (searched downwards)
+        int warps = o.warps_per_cta > 0 ? o.warps_per_cta : 32;
         warps = std::max(1, std::min(32, warps));
         HostSchedule HS;
         build_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
-        for (auto& km : HS.round_mol) km = desc_index[km];
+        for (auto& km : HS.slot_mol) km = desc_index[km];
         DeviceSchedule& DS = T->sched[mode];
         DS.n_cta = HS.n_cta;
         DS.warps = HS.warps;
         DS.arena = HS.arena;
-        if ((e = upload(&DS.cta_round_ptr, HS.cta_round_ptr)) != cudaSuccess) return to_status(e);
-        if ((e = upload(&DS.round_ptr, HS.round_ptr)) != cudaSuccess) return to_status(e);
-        if ((e = upload(&DS.round_mol, HS.round_mol)) != cudaSuccess) return to_status(e);
-        if ((e = upload(&DS.round_off, HS.round_off)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.cta_slot_ptr, HS.cta_slot_ptr)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.slot_ptr, HS.slot_ptr)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.slot_mol, HS.slot_mol)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.slot_off, HS.slot_off)) != cudaSuccess) return to_status(e);
     }
     if (T->n_large > 0) {
         cudaStream_t s;
@@ -726,7 +716,7 @@ static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStrea
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
     }
     if (T->n_small > 0) {
-        SmallSched S{DS.cta_round_ptr, DS.round_ptr, DS.round_mol, DS.round_off};
+        SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off};
         k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;
@@ -792,7 +782,7 @@ static ilves_status launch_mode_static(ilves_topology* T, const SolveArgs& A, cu
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
     }
     if (T->n_small > 0) {
-        SmallSched S{DS.cta_round_ptr, DS.round_ptr, DS.round_mol, DS.round_off};
+        SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off};
         k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;

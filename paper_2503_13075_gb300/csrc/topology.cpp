@@ -483,61 +483,74 @@ uint32_t footprint(const MolHost& M, int mode) {
     return L.bytes + S.bytes;
 }
 
-// LPT of molecules over CTAs, then rounds per CTA packed into the shared-memory arena.
+// Warp-slot schedule.  Warp-sized molecules, sorted by shared-memory footprint, are cut
+// into G = n_cta * warps consecutive groups of about equal estimated cost; each group is
+// the queue of one warp and gets a fixed slice sized for its largest molecule.  Groups
+// are dealt to CTAs in snake order, so every CTA mixes large and small slices, and the
+// warps of a CTA never wait for each other.  If some CTA's slices overflow its arena,
+// the number of warps per CTA is reduced and the cut repeated.
 void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
                     HostSchedule& S) {
-    S.n_cta = n_cta;
-    S.warps = warps;
-    S.arena = arena;
-    S.cta_round_ptr.assign(n_cta + 1, 0);
-    S.round_ptr.assign(1, 0);
-    S.round_mol.clear();
-    S.round_off.clear();
     std::vector<int32_t> small;
     std::vector<uint32_t> fp(T->n_mol, 0);
-    for (int32_t m = 0; m < T->n_mol; ++m)
-        if (!T->mols[m].large) {
-            small.push_back(m);
-            fp[m] = footprint(T->mols[m], mode);
-        }
-    auto cost = [&](int32_t m) {
+    std::vector<double> cost(T->n_mol, 0.0);
+    for (int32_t m = 0; m < T->n_mol; ++m) {
         const MolHost& M = T->mols[m];
-        return 90.0 * (double)M.passes + (6.0 * M.ntask + 4.0 * M.nterm + 60.0 * M.cons.size()) / 32.0;
-    };
-    std::sort(small.begin(), small.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
-    using Item = std::pair<double, int32_t>;
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
-    for (int32_t c = 0; c < n_cta; ++c) heap.push({0.0, c});
-    std::vector<std::vector<int32_t>> per(n_cta);
-    for (int32_t m : small) {
-        const Item it = heap.top();
-        heap.pop();
-        per[it.second].push_back(m);
-        heap.push({it.first + cost(m), it.second});
+        if (M.large) continue;
+        small.push_back(m);
+        fp[m] = footprint(M, mode);
+        cost[m] = 90.0 * (double)M.passes + (6.0 * M.ntask + 4.0 * M.nterm + 60.0 * M.cons.size()) / 32.0;
     }
-    for (int32_t c = 0; c < n_cta; ++c) {
-        auto& v = per[c];
-        std::sort(v.begin(), v.end(), [&](int32_t a, int32_t b) { return fp[a] > fp[b]; });
-        size_t i = 0;
-        while (i < v.size()) {
-            uint32_t used = 0;
-            int32_t cnt = 0;
-            while (i < v.size() && cnt < warps) {
-                const uint32_t f = fp[v[i]];
-                if (used + f > (uint32_t)arena) break;
-                S.round_mol.push_back(v[i]);
-                S.round_off.push_back((int32_t)used);
-                used += f;
-                ++cnt;
-                ++i;
-            }
-            if (cnt == 0) {  // cannot happen: molecules above the arena are routed to the large path
-                ++i;
-                continue;
-            }
-            S.round_ptr.push_back((int32_t)S.round_mol.size());
+    std::sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
+        return fp[a] != fp[b] ? fp[a] > fp[b] : a < b;
+    });
+    double total = 0.0;
+    for (int32_t m : small) total += cost[m];
+    for (int32_t w = std::max(1, std::min(32, warps)); w >= 1; --w) {
+        const int64_t G = (int64_t)n_cta * w;
+        // consecutive groups of ~equal cost (a group closes once the cumulative cost reaches
+        // its quantile; with fewer molecules than groups some groups stay empty)
+        std::vector<std::vector<int32_t>> groups(G);
+        double acc = 0.0;
+        int64_t g = 0;
+        for (int32_t m : small) {
+            groups[g].push_back(m);
+            acc += cost[m];
+            if (g + 1 < G && acc >= total * (double)(g + 1) / (double)G) ++g;
         }
-        S.cta_round_ptr[c + 1] = (int32_t)S.round_ptr.size() - 1;
+        // snake deal to CTAs
+        std::vector<std::vector<int32_t>> cta_groups(n_cta);
+        for (int64_t gi = 0; gi < G; ++gi) {
+            if (groups[gi].empty()) continue;
+            const int64_t r = gi / n_cta, k = gi % n_cta;
+            cta_groups[(r % 2 == 0) ? k : n_cta - 1 - k].push_back((int32_t)gi);
+        }
+        bool fits = true;
+        for (int32_t c = 0; c < n_cta && fits; ++c) {
+            uint64_t used = 0;
+            for (int32_t g : cta_groups[c]) used += fp[groups[g].front()];
+            fits = used <= (uint64_t)arena;
+        }
+        if (!fits && w > 1) continue;
+        S.n_cta = n_cta;
+        S.warps = 1;
+        S.arena = arena;
+        S.cta_slot_ptr.assign(1, 0);
+        S.slot_ptr.assign(1, 0);
+        S.slot_mol.clear();
+        S.slot_off.clear();
+        for (int32_t c = 0; c < n_cta; ++c) {
+            uint32_t off = 0;
+            for (int32_t g : cta_groups[c]) {
+                S.slot_off.push_back((int32_t)off);
+                off += fp[groups[g].front()];
+                for (int32_t m : groups[g]) S.slot_mol.push_back(m);
+                S.slot_ptr.push_back((int32_t)S.slot_mol.size());
+            }
+            S.cta_slot_ptr.push_back((int32_t)S.slot_off.size());
+            S.warps = std::max<int32_t>(S.warps, (int32_t)cta_groups[c].size());
+        }
+        return;
     }
 }
 

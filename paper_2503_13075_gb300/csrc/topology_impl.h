@@ -23,17 +23,20 @@ struct MolHost {
 
 struct Program;  // topology.cpp
 
+// Persistent schedule of the warp-per-molecule kernel: CTA c owns warp slots
+// [cta_slot_ptr[c], cta_slot_ptr[c+1]); slot s has a fixed shared-memory slice at byte
+// offset slot_off[s] and solves molecules slot_mol[slot_ptr[s] .. slot_ptr[s+1]) in order.
 struct HostSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
-    std::vector<int32_t> cta_round_ptr, round_ptr, round_mol, round_off;
+    std::vector<int32_t> cta_slot_ptr, slot_ptr, slot_mol, slot_off;
 };
 
 struct DeviceSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
-    int32_t* cta_round_ptr = nullptr;
-    int32_t* round_ptr = nullptr;
-    int32_t* round_mol = nullptr;  // index into the small-molecule descriptor array
-    int32_t* round_off = nullptr;
+    int32_t* cta_slot_ptr = nullptr;
+    int32_t* slot_ptr = nullptr;
+    int32_t* slot_mol = nullptr;  // index into the small-molecule descriptor array
+    int32_t* slot_off = nullptr;
 };
 
 }  // namespace ilves
