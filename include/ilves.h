@@ -69,7 +69,9 @@ typedef enum {
     ILVES_MOL_CONVERGED = 0,      /* max |sigma| / d^2 <= tol */
     ILVES_MOL_MAX_ITER = 1,       /* tolerance not reached in max_iter solves */
     ILVES_MOL_SINGULAR_PIVOT = 2, /* a pivot of the LU vanished (|u_jj| tiny) */
-    ILVES_MOL_NONFINITE = 3       /* a violation became NaN or Inf */
+    ILVES_MOL_NONFINITE = 3,      /* a violation became NaN or Inf */
+    ILVES_MOL_WAIT_TIMEOUT = 4    /* partitioned solve: a bounded wait for other CTAs gave up;
+                                     the molecule's outputs are not valid */
 } ilves_mol_status;
 
 /* Arithmetic of a solve.
@@ -88,11 +90,14 @@ typedef struct {
     int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;
                                 2 = rounds of independent low-degree pivots with `degree_slack` */
     int32_t degree_slack;    /* ordering 2: admit pivots up to min degree + slack per round */
-    int32_t warps_per_cta;   /* 0 = autotuned; else 1..32 warps per persistent CTA */
+    int32_t warps_per_cta;   /* 0 = autotuned; else 1..16 warps per persistent CTA */
     int32_t ctas_per_sm;     /* 0 = autotuned; else 1..4 */
     int32_t device;          /* CUDA device ordinal the topology lives on (-1 = current device,
                                 -2 = plan on the host only: no CUDA call, ilves_solve refused) */
     int32_t max_warp_constraints; /* molecules larger than this use the multi-warp path (0 = auto) */
+    int32_t partition_min_constraints; /* molecules with at least this many constraints are
+                                          partitioned over many CTAs (0 = 4096) */
+    int32_t part_constraints;      /* target constraints per part of a partitioned molecule (0 = 256) */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */

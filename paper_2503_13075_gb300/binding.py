@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ilves.h")
 
 FP64, MIXED, MIXED_DF = 0, 1, 2
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_df": MIXED_DF}
-CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE = 0, 1, 2, 3
+CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE, WAIT_TIMEOUT = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid topology", 3: "CUDA error", 4: "out of device memory",
           5: "device wait timed out", 6: "scratch needed exceeds the static maximum"}
 
@@ -33,7 +33,8 @@ class IlvesError(RuntimeError):
 class SetupOpts(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("degree_slack", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("max_warp_constraints", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("max_warp_constraints", ctypes.c_int32),
+                ("partition_min_constraints", ctypes.c_int32), ("part_constraints", ctypes.c_int32)]
 
 
 _lib = None
@@ -118,7 +119,8 @@ class Topology:
     """A constraint topology set up once and solved many times (``ilves_setup_topology``)."""
 
     def __init__(self, n_atoms, atom_i, atom_j, ordering=0, degree_slack=2, warps_per_cta=0,
-                 ctas_per_sm=0, device=None, plan_only=False, max_warp_constraints=0):
+                 ctas_per_sm=0, device=None, plan_only=False, max_warp_constraints=0,
+                 partition_min_constraints=0, part_constraints=0):
         L = lib()
         ai = np.ascontiguousarray(atom_i, dtype=np.int32)
         aj = np.ascontiguousarray(atom_j, dtype=np.int32)
@@ -129,6 +131,8 @@ class Topology:
         o.ordering, o.degree_slack = ordering, degree_slack
         o.warps_per_cta, o.ctas_per_sm = warps_per_cta, ctas_per_sm
         o.max_warp_constraints = max_warp_constraints
+        o.partition_min_constraints = partition_min_constraints
+        o.part_constraints = part_constraints
         if plan_only:
             o.device = -2
         elif device is not None:

@@ -68,15 +68,21 @@ constexpr uint32_t kCompactMaxConstraints = 256, kCompactMaxSlots = 4096;
 ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 
 struct ProgLayout {
-    uint32_t con_atoms, con_gid, piv, lvl_task, lvl_piv, inc_ptr, inc, tasks, terms, bytes;
+    uint32_t seg, con_atoms, con_gid, piv, lvl_task, lvl_piv, inc_ptr, inc, tasks, terms, bytes;
 };
+
+// Segment table (n_seg + 1 rows of {first position, first level-table entry, first atom}):
+// one segment for an ordinary molecule; for a partitioned molecule one per part, then the
+// separators (constraints between parts), whose atom range is empty.
+struct SegRow { int32_t piv, lvl, atom; };
 
 template <class IdxT>
 ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t nterm,
-                                uint32_t nlevel) {
+                                uint32_t nlevel, uint32_t n_seg = 1) {
     ProgLayout L;
     const uint32_t ix = (uint32_t)sizeof(IdxT);
     uint32_t o = 0;
+    L.seg = o;       o = align16(o + 12u * (n_seg + 1));
     L.con_atoms = o; o = align16(o + 2u * ix * nc);
     L.con_gid = o;   o = align16(o + 4u * nc);
     L.piv = o;       o = align16(o + 2u * ix * nc);
@@ -131,8 +137,8 @@ struct MolDesc {
     int32_t nterm;
     int32_t ntask;
     int32_t na, nc;
-    int32_t nlevel;
-    int32_t pad;
+    int32_t nlevel;  // level-table entries - 1 (for one segment: its number of levels)
+    int32_t n_seg;   // 1, or parts + 1 for a partitioned molecule
 };
 
 }  // namespace ilves

@@ -174,203 +174,347 @@ struct SolveArgs {
 };
 
 // ------------------------------------------------------------------------------------
-// one molecule, one team
+// per-item operations on one molecule's program and state
 // ------------------------------------------------------------------------------------
 // Float64-class arrays (X, W, RHO, S, D2, LAM) hold float64 values, or in the
 // float-float mode dfloat pairs stored in the same 8 bytes.  In the float64 modes X
 // holds absolute positions; in the float-float mode it holds displacements x - x_unc
 // and S holds s_k = x_unc,i - x_unc,j, so that r_k = s_k + (dx_i - dx_j).
-template <class Mode, class IdxT, class Team>
-__device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
-                               const SolveArgs& A) {
+//
+// kCoh: the state lives in global memory and other CTAs write parts of it (partitioned
+// molecules), so mutable state is read through L2 (ld.global.cg) and never from a
+// possibly stale L1 line; the program is read-only and read through the texture path.
+template <bool kCoh, class T>
+__device__ __forceinline__ T lds(const T* p) {
+    if constexpr (kCoh) {
+        if constexpr (sizeof(T) == 32) {
+            T v;
+            const double2* q = reinterpret_cast<const double2*>(p);
+            *reinterpret_cast<double2*>(&v) = __ldcg(q);
+            reinterpret_cast<double2*>(&v)[1] = __ldcg(q + 1);
+            return v;
+        } else {
+            return __ldcg(p);
+        }
+    } else {
+        return *p;
+    }
+}
+template <bool kCoh, class T>
+__device__ __forceinline__ T ldp(const T* p) {
+    if constexpr (kCoh) {
+        T v;
+        if constexpr (sizeof(T) == 16) *reinterpret_cast<uint4*>(&v) = __ldg(reinterpret_cast<const uint4*>(p));
+        else if constexpr (sizeof(T) == 8) *reinterpret_cast<uint2*>(&v) = __ldg(reinterpret_cast<const uint2*>(p));
+        else if constexpr (sizeof(T) == 4) *reinterpret_cast<unsigned*>(&v) = __ldg(reinterpret_cast<const unsigned*>(p));
+        else *reinterpret_cast<unsigned short*>(&v) = __ldg(reinterpret_cast<const unsigned short*>(p));
+        return v;
+    } else {
+        return *p;
+    }
+}
+
+template <class Mode, class IdxT, bool kCoh>
+struct MolView {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
-    constexpr bool DF = Mode::df;
-    const int na = D.na, nc = D.nc;
-    const ProgLayout PL = prog_layout<IdxT>(na, nc, D.ntask, D.nterm, D.nlevel);
-    const StateLayout SL = state_layout(na, nc, D.ntask, sizeof(LP), DF);
-    const ConA<IdxT>* con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
-    const int32_t* con_gid = reinterpret_cast<const int32_t*>(prog + PL.con_gid);
-    const Piv<IdxT>* piv = reinterpret_cast<const Piv<IdxT>*>(prog + PL.piv);
-    const IdxT* lvl_task = reinterpret_cast<const IdxT*>(prog + PL.lvl_task);
-    const IdxT* lvl_piv = reinterpret_cast<const IdxT*>(prog + PL.lvl_piv);
-    const IdxT* inc_ptr = reinterpret_cast<const IdxT*>(prog + PL.inc_ptr);
-    const IdxT* inc = reinterpret_cast<const IdxT*>(prog + PL.inc);
-    const Task<IdxT>* tasks = reinterpret_cast<const Task<IdxT>*>(prog + PL.tasks);
     using TO = TermOf<IdxT>;
-    const typename TO::T* terms = reinterpret_cast<const typename TO::T*>(prog + PL.terms);
-    double* X = reinterpret_cast<double*>(st + SL.x);  // SoA x | y | z
-    double* W = reinterpret_cast<double*>(st + SL.w);
-    LP* WL = reinterpret_cast<LP*>(st + SL.wl);  // assembly weights (factor precision)
-    double* RHO = reinterpret_cast<double*>(st + SL.rho);  // SoA
-    double* SK = reinterpret_cast<double*>(st + SL.s);     // SoA (float-float mode)
-    double* D2 = reinterpret_cast<double*>(st + SL.d2);
-    const double tol = A.tol;
-    const float tolf = (float)A.tol;
-    double* LAM = reinterpret_cast<double*>(st + SL.lam);
-    V4* RHOF = reinterpret_cast<V4*>(st + SL.rhof);
-    V4* RF = reinterpret_cast<V4*>(st + SL.rf);
-    LP* INV = reinterpret_cast<LP*>(st + SL.inv);
-    LP* Y = reinterpret_cast<LP*>(st + SL.y);
-    LP* V = reinterpret_cast<LP*>(st + SL.vals);
-    const int r0 = tm.rank(), ts = tm.size();
+    static constexpr bool DF = Mode::df;
+    int na, nc;
+    const SegRow* seg;
+    const ConA<IdxT>* con;
+    const int32_t* con_gid;
+    const Piv<IdxT>* piv;
+    const IdxT* lvl_task;
+    const IdxT* lvl_piv;
+    const IdxT* inc_ptr;
+    const IdxT* inc;
+    const Task<IdxT>* tasks;
+    const typename TO::T* terms;
+    double *X, *W, *RHO, *SK, *D2, *LAM;
+    LP *WL, *INV, *Y, *V;
+    V4 *RHOF, *RF;
+    const MolDesc* D;
+    const SolveArgs* A;
 
-    auto gid_of = [&](int a) -> int64_t {
-        return D.atom_base >= 0 ? (int64_t)D.atom_base + a : (int64_t)A.atom_gid[D.gid_off + a];
-    };
-    // ---- S1: reference geometry (x_old staged through X), weights
-    for (int a = r0; a < na; a += ts) {
-        const int64_t g = gid_of(a);
-        X[a] = A.x_old[3 * g];
-        X[na + a] = A.x_old[3 * g + 1];
-        X[2 * na + a] = A.x_old[3 * g + 2];
-        const double w = A.inv_mass[g];
+    __device__ __forceinline__ void init(const MolDesc& d, const uint8_t* prog, uint8_t* st, const SolveArgs& a) {
+        D = &d;
+        A = &a;
+        na = d.na;
+        nc = d.nc;
+        const ProgLayout PL = prog_layout<IdxT>(na, nc, d.ntask, d.nterm, d.nlevel, d.n_seg);
+        const StateLayout SL = state_layout(na, nc, d.ntask, sizeof(LP), DF);
+        seg = reinterpret_cast<const SegRow*>(prog + PL.seg);
+        con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
+        con_gid = reinterpret_cast<const int32_t*>(prog + PL.con_gid);
+        piv = reinterpret_cast<const Piv<IdxT>*>(prog + PL.piv);
+        lvl_task = reinterpret_cast<const IdxT*>(prog + PL.lvl_task);
+        lvl_piv = reinterpret_cast<const IdxT*>(prog + PL.lvl_piv);
+        inc_ptr = reinterpret_cast<const IdxT*>(prog + PL.inc_ptr);
+        inc = reinterpret_cast<const IdxT*>(prog + PL.inc);
+        tasks = reinterpret_cast<const Task<IdxT>*>(prog + PL.tasks);
+        terms = reinterpret_cast<const typename TO::T*>(prog + PL.terms);
+        X = reinterpret_cast<double*>(st + SL.x);
+        W = reinterpret_cast<double*>(st + SL.w);
+        WL = reinterpret_cast<LP*>(st + SL.wl);
+        RHO = reinterpret_cast<double*>(st + SL.rho);
+        SK = reinterpret_cast<double*>(st + SL.s);
+        D2 = reinterpret_cast<double*>(st + SL.d2);
+        LAM = reinterpret_cast<double*>(st + SL.lam);
+        RHOF = reinterpret_cast<V4*>(st + SL.rhof);
+        RF = reinterpret_cast<V4*>(st + SL.rf);
+        INV = reinterpret_cast<LP*>(st + SL.inv);
+        Y = reinterpret_cast<LP*>(st + SL.y);
+        V = reinterpret_cast<LP*>(st + SL.vals);
+    }
+    __device__ __forceinline__ int64_t gid(int a) const {
+        return D->atom_base >= 0 ? (int64_t)D->atom_base + a : (int64_t)A->atom_gid[D->gid_off + a];
+    }
+    __device__ __forceinline__ ConA<IdxT> cons(int p) const { return ldp<kCoh>(con + p); }
+
+    // ---- S1
+    // weights of atom a; with stage_ref, x_old is staged in X for s1_constraint
+    __device__ __forceinline__ void s1_atom(int a, bool stage_ref) {
+        const int64_t g = gid(a);
+        if (stage_ref) {
+            X[a] = A->x_old[3 * g];
+            X[na + a] = A->x_old[3 * g + 1];
+            X[2 * na + a] = A->x_old[3 * g + 2];
+        }
+        const double w = A->inv_mass[g];
         W[a] = DF ? as_bits(df_split(w)) : w;
         WL[a] = to_lp<LP>(w);
     }
-    if (r0 == 0) {  // zero-weight atom referenced by fill entries
+    __device__ __forceinline__ void s1_dummy() {
         W[na] = 0.0;
         WL[na] = LP(0);
     }
-    tm.sync();
-    for (int p = r0; p < nc; p += ts) {
-        const int i = con[p].i, j = con[p].j;
-        const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+    // rho, assembly data, lambda0 of constraint p; ref_staged: x_old staged in X (else global)
+    __device__ __forceinline__ void s1_constraint(int p, bool ref_staged) {
+        const ConA<IdxT> c = cons(p);
+        const int i = c.i, j = c.j;
+        const int64_t gi = gid(i), gj = gid(j);
+        double rx, ry, rz;
+        if (ref_staged) {
+            rx = X[i] - X[j];
+            ry = X[na + i] - X[na + j];
+            rz = X[2 * na + i] - X[2 * na + j];
+        } else {
+            rx = A->x_old[3 * gi] - A->x_old[3 * gj];
+            ry = A->x_old[3 * gi + 1] - A->x_old[3 * gj + 1];
+            rz = A->x_old[3 * gi + 2] - A->x_old[3 * gj + 2];
+        }
         V4 v;
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
         v.z = to_lp<LP>(rz);
         v.w = LP(0);
         RHOF[p] = v;
-        const int32_t g = con_gid[p];
-        const double dd = A.d[g];
+        const int32_t g = ldp<kCoh>(con_gid + p);
+        const double dd = A->d[g];
         if constexpr (DF) {
             RHO[p] = as_bits(df_split(rx));
             RHO[nc + p] = as_bits(df_split(ry));
             RHO[2 * nc + p] = as_bits(df_split(rz));
             D2[p] = as_bits(df_split(dd * dd));
+            SK[p] = as_bits(df_split(A->x_unc[3 * gi] - A->x_unc[3 * gj]));
+            SK[nc + p] = as_bits(df_split(A->x_unc[3 * gi + 1] - A->x_unc[3 * gj + 1]));
+            SK[2 * nc + p] = as_bits(df_split(A->x_unc[3 * gi + 2] - A->x_unc[3 * gj + 2]));
         } else {
             RHO[p] = rx;
             RHO[nc + p] = ry;
             RHO[2 * nc + p] = rz;
             D2[p] = dd * dd;
         }
-        WL[na + 1 + p] = WL[i] + WL[j];
-        const float l0 = A.lambda0 ? A.lambda0[g] : 0.0f;
+        WL[na + 1 + p] = to_lp<LP>(A->inv_mass[gi]) + to_lp<LP>(A->inv_mass[gj]);
+        const float l0 = A->lambda0 ? A->lambda0[g] : 0.0f;
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         Y[p] = (LP)l0;
     }
-    tm.sync();
-    for (int a = r0; a < na; a += ts) {
+    __device__ __forceinline__ void s1_atom_unc(int a) {
         if constexpr (DF) {  // displacements start at zero
             X[a] = 0.0;
             X[na + a] = 0.0;
             X[2 * na + a] = 0.0;
         } else {
-            const int64_t g = gid_of(a);
-            X[a] = A.x_unc[3 * g];
-            X[na + a] = A.x_unc[3 * g + 1];
-            X[2 * na + a] = A.x_unc[3 * g + 2];
+            const int64_t g = gid(a);
+            X[a] = A->x_unc[3 * g];
+            X[na + a] = A->x_unc[3 * g + 1];
+            X[2 * na + a] = A->x_unc[3 * g + 2];
         }
     }
-    if constexpr (DF) {
-        for (int p = r0; p < nc; p += ts) {
-            const int64_t gi = gid_of(con[p].i), gj = gid_of(con[p].j);
-            SK[p] = as_bits(df_split(A.x_unc[3 * gi] - A.x_unc[3 * gj]));
-            SK[nc + p] = as_bits(df_split(A.x_unc[3 * gi + 1] - A.x_unc[3 * gj + 1]));
-            SK[2 * nc + p] = as_bits(df_split(A.x_unc[3 * gi + 2] - A.x_unc[3 * gj + 2]));
-        }
-    }
-    tm.sync();
 
-    // ---- S6: x -= M^-1 G(x_old)^T Y   (Y holds delta, or lambda0 before the loop)
-    auto update_positions = [&]() {
-        for (int a = r0; a < na; a += ts) {
-            const int e1 = inc_ptr[a + 1];
-            if constexpr (DF) {
-                dfloat ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
-                for (int e = inc_ptr[a]; e < e1; ++e) {
-                    const unsigned v = inc[e];
-                    const int p = (int)(v >> 1);
-                    const float dl = (float)Y[p];
-                    const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
-                    ax = df_add(ax, df_mul_f(as_df(RHO[p]), c));
-                    ay = df_add(ay, df_mul_f(as_df(RHO[nc + p]), c));
-                    az = df_add(az, df_mul_f(as_df(RHO[2 * nc + p]), c));
-                }
-                const dfloat w = as_df(W[a]);
-                X[a] = as_bits(df_sub(as_df(X[a]), df_mul(w, ax)));
-                X[na + a] = as_bits(df_sub(as_df(X[na + a]), df_mul(w, ay)));
-                X[2 * na + a] = as_bits(df_sub(as_df(X[2 * na + a]), df_mul(w, az)));
-            } else {
-                double ax = 0.0, ay = 0.0, az = 0.0;
-                for (int e = inc_ptr[a]; e < e1; ++e) {
-                    const unsigned v = inc[e];
-                    const int p = (int)(v >> 1);
-                    const LP dl = Y[p];
-                    const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
-                    ax = fma(c, RHO[p], ax);
-                    ay = fma(c, RHO[nc + p], ay);
-                    az = fma(c, RHO[2 * nc + p], az);
-                }
-                const double w = W[a];
-                X[a] = fma(-w, ax, X[a]);
-                X[na + a] = fma(-w, ay, X[na + a]);
-                X[2 * na + a] = fma(-w, az, X[2 * na + a]);
+    // ---- S6: x_a -= w_a sum_k s_k(a) 2 Y_k rho_k   (Y holds delta, or lambda0)
+    __device__ __forceinline__ void update_atom(int a) {
+        const int e1 = ldp<kCoh>(inc_ptr + a + 1);
+        if constexpr (DF) {
+            dfloat ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
+            for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
+                const unsigned v = ldp<kCoh>(inc + e);
+                const int p = (int)(v >> 1);
+                const float dl = (float)lds<kCoh>(Y + p);
+                const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
+                ax = df_add(ax, df_mul_f(as_df(lds<kCoh>(RHO + p)), c));
+                ay = df_add(ay, df_mul_f(as_df(lds<kCoh>(RHO + nc + p)), c));
+                az = df_add(az, df_mul_f(as_df(lds<kCoh>(RHO + 2 * nc + p)), c));
             }
+            const dfloat w = as_df(lds<kCoh>(W + a));
+            X[a] = as_bits(df_sub(as_df(lds<kCoh>(X + a)), df_mul(w, ax)));
+            X[na + a] = as_bits(df_sub(as_df(lds<kCoh>(X + na + a)), df_mul(w, ay)));
+            X[2 * na + a] = as_bits(df_sub(as_df(lds<kCoh>(X + 2 * na + a)), df_mul(w, az)));
+        } else {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
+                const unsigned v = ldp<kCoh>(inc + e);
+                const int p = (int)(v >> 1);
+                const LP dl = lds<kCoh>(Y + p);
+                const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
+                ax = fma(c, lds<kCoh>(RHO + p), ax);
+                ay = fma(c, lds<kCoh>(RHO + nc + p), ay);
+                az = fma(c, lds<kCoh>(RHO + 2 * nc + p), az);
+            }
+            const double w = lds<kCoh>(W + a);
+            X[a] = fma(-w, ax, lds<kCoh>(X + a));
+            X[na + a] = fma(-w, ay, lds<kCoh>(X + na + a));
+            X[2 * na + a] = fma(-w, az, lds<kCoh>(X + 2 * na + a));
         }
-    };
-    if (A.lambda0) {
-        update_positions();
+    }
+
+    // ---- S2: violation of constraint p (float64 class), Jacobian row, right-hand side
+    __device__ __forceinline__ void violation(int p, bool& conv, bool& bad) {
+        const ConA<IdxT> cc = cons(p);
+        const int i = cc.i, j = cc.j;
+        V4 v;
+        if constexpr (DF) {
+            const dfloat rx = df_add(as_df(lds<kCoh>(SK + p)), df_sub(as_df(lds<kCoh>(X + i)), as_df(lds<kCoh>(X + j))));
+            const dfloat ry = df_add(as_df(lds<kCoh>(SK + nc + p)),
+                                     df_sub(as_df(lds<kCoh>(X + na + i)), as_df(lds<kCoh>(X + na + j))));
+            const dfloat rz = df_add(as_df(lds<kCoh>(SK + 2 * nc + p)),
+                                     df_sub(as_df(lds<kCoh>(X + 2 * na + i)), as_df(lds<kCoh>(X + 2 * na + j))));
+            const dfloat d2 = as_df(lds<kCoh>(D2 + p));
+            // |r|^2 - d^2: exact products of the high words, two-sums of the big terms,
+            // every rounding error collected in a small tail
+            const float px = __fmul_rn(rx.hi, rx.hi), ex = __fmaf_rn(rx.hi, rx.hi, -px);
+            const float py = __fmul_rn(ry.hi, ry.hi), ey = __fmaf_rn(ry.hi, ry.hi, -py);
+            const float pz = __fmul_rn(rz.hi, rz.hi), ez = __fmaf_rn(rz.hi, rz.hi, -pz);
+            float s1, e1, s2, e2, s3, e3;
+            two_sum(px, py, s1, e1);
+            two_sum(s1, pz, s2, e2);
+            two_sum(s2, -d2.hi, s3, e3);
+            float cross = __fmul_rn(rx.hi, rx.lo);
+            cross = __fmaf_rn(ry.hi, ry.lo, cross);
+            cross = __fmaf_rn(rz.hi, rz.lo, cross);
+            const float tail = ((ex + ey) + (ez + e1)) + ((e2 + e3) - d2.lo) + (cross + cross);
+            const float sg = s3 + tail;
+            conv = conv && fabsf(sg) <= (float)A->tol * d2.hi;
+            bad = bad || nonfinite(sg);
+            v.x = rx.hi;
+            v.y = ry.hi;
+            v.z = rz.hi;
+            Y[p] = sg;
+        } else {
+            const double rx = lds<kCoh>(X + i) - lds<kCoh>(X + j);
+            const double ry = lds<kCoh>(X + na + i) - lds<kCoh>(X + na + j);
+            const double rz = lds<kCoh>(X + 2 * na + i) - lds<kCoh>(X + 2 * na + j);
+            const double d2 = lds<kCoh>(D2 + p);
+            const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
+            conv = conv && abs_le(sg, A->tol * d2);
+            bad = bad || nonfinite(sg);
+            v.x = to_lp<LP>(rx);
+            v.y = to_lp<LP>(ry);
+            v.z = to_lp<LP>(rz);
+            Y[p] = to_lp<LP>(sg);
+        }
+        v.w = LP(0);
+        RF[p] = v;
+    }
+
+    // ---- S3 + S4 + forward S5: one task; DIAG tasks (diag = true) also produce 1/pivot and
+    //      the forward-solve entry.  Every entry is a - sum_m Lt[row,m] inv_m U[m,col].
+    __device__ __forceinline__ void task(int t, bool diag, bool& singular) {
+        const Task<IdxT> tk = ldp<kCoh>(tasks + t);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        const V4 rr = lds<kCoh>(RF + tk.row), pp = lds<kCoh>(RHOF + tk.col);
+        const LP wv = lds<kCoh>(WL + (tk.atomsign >> 1));
+        const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
+        const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+        LP sacc = a, yv = LP(0);
+#pragma unroll 2
+        for (int e = tk.tstart; e < e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            const LP li = lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(INV + m);
+            sacc -= li * lds<kCoh>(V + TO::u(tr));
+            yv += li * lds<kCoh>(Y + m);
+        }
+        V[t] = sacc;
+        if (diag) {
+            singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+            INV[tk.row] = lp_rcp(sacc);
+            Y[tk.row] = lds<kCoh>(Y + tk.row) - yv;
+        }
+    }
+
+    // ---- backward S5 for pivot p: delta_p = inv_p (y_p - sum_q U[p,q] delta_q)
+    __device__ __forceinline__ void backward(int p) {
+        const Piv<IdxT> pv = ldp<kCoh>(piv + p);
+        const int us = pv.diag, nu = pv.nup;
+        LP dl = lds<kCoh>(Y + p);
+        for (int k = 0; k < nu; ++k) dl -= lds<kCoh>(V + us + k) * lds<kCoh>(Y + ldp<kCoh>(tasks + us + k).col);
+        Y[p] = dl * lds<kCoh>(INV + p);
+    }
+
+    __device__ __forceinline__ void lambda_acc(int p) {
+        if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(lds<kCoh>(LAM + p)), (float)lds<kCoh>(Y + p)));
+        else LAM[p] = lds<kCoh>(LAM + p) + to_hp(lds<kCoh>(Y + p));
+    }
+
+    // ---- S7
+    __device__ __forceinline__ void out_atom(int a) {
+        const int64_t g = gid(a);
+        if constexpr (DF) {
+            A->x_out[3 * g] = A->x_unc[3 * g] + df_join(as_df(lds<kCoh>(X + a)));
+            A->x_out[3 * g + 1] = A->x_unc[3 * g + 1] + df_join(as_df(lds<kCoh>(X + na + a)));
+            A->x_out[3 * g + 2] = A->x_unc[3 * g + 2] + df_join(as_df(lds<kCoh>(X + 2 * na + a)));
+        } else {
+            A->x_out[3 * g] = lds<kCoh>(X + a);
+            A->x_out[3 * g + 1] = lds<kCoh>(X + na + a);
+            A->x_out[3 * g + 2] = lds<kCoh>(X + 2 * na + a);
+        }
+    }
+    __device__ __forceinline__ void out_lambda(int p) {
+        const double l = lds<kCoh>(LAM + p);
+        A->lambda_out[ldp<kCoh>(con_gid + p)] = DF ? df_join(as_df(l)) : l;
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// one molecule, one team (a warp with state in shared memory, or a CTA with state in a
+// global workspace)
+// ------------------------------------------------------------------------------------
+template <class Mode, class IdxT, class Team>
+__device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
+                               const SolveArgs& A) {
+    MolView<Mode, IdxT, false> M;
+    M.init(D, prog, st, A);
+    const int na = D.na, nc = D.nc;
+    const int r0 = tm.rank(), ts = tm.size();
+    // ---- S1
+    for (int a = r0; a < na; a += ts) M.s1_atom(a, true);
+    if (r0 == 0) M.s1_dummy();
+    tm.sync();
+    for (int p = r0; p < nc; p += ts) M.s1_constraint(p, true);
+    tm.sync();
+    for (int a = r0; a < na; a += ts) M.s1_atom_unc(a);
+    tm.sync();
+    if (A.lambda0) {  // x = x_unc - M^-1 G(x_old)^T lambda0
+        for (int a = r0; a < na; a += ts) M.update_atom(a);
         tm.sync();
     }
-
     int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
     for (int it = 0;; ++it) {
-        // ---- S2: violations (float64 class), Jacobian rows and right-hand side
         bool conv = true, bad = false;
-        for (int p = r0; p < nc; p += ts) {
-            const int i = con[p].i, j = con[p].j;
-            V4 v;
-            if constexpr (DF) {
-                const dfloat rx = df_add(as_df(SK[p]), df_sub(as_df(X[i]), as_df(X[j])));
-                const dfloat ry = df_add(as_df(SK[nc + p]), df_sub(as_df(X[na + i]), as_df(X[na + j])));
-                const dfloat rz = df_add(as_df(SK[2 * nc + p]), df_sub(as_df(X[2 * na + i]), as_df(X[2 * na + j])));
-                const dfloat d2 = as_df(D2[p]);
-                // |r|^2 - d^2: exact products of the high words, two-sums of the big terms,
-                // every rounding error collected in a small tail
-                const float px = __fmul_rn(rx.hi, rx.hi), ex = __fmaf_rn(rx.hi, rx.hi, -px);
-                const float py = __fmul_rn(ry.hi, ry.hi), ey = __fmaf_rn(ry.hi, ry.hi, -py);
-                const float pz = __fmul_rn(rz.hi, rz.hi), ez = __fmaf_rn(rz.hi, rz.hi, -pz);
-                float s1, e1, s2, e2, s3, e3;
-                two_sum(px, py, s1, e1);
-                two_sum(s1, pz, s2, e2);
-                two_sum(s2, -d2.hi, s3, e3);
-                float cross = __fmul_rn(rx.hi, rx.lo);
-                cross = __fmaf_rn(ry.hi, ry.lo, cross);
-                cross = __fmaf_rn(rz.hi, rz.lo, cross);
-                const float tail = ((ex + ey) + (ez + e1)) + ((e2 + e3) - d2.lo) + (cross + cross);
-                const float sg = s3 + tail;
-                conv = conv && fabsf(sg) <= tolf * d2.hi;
-                bad = bad || nonfinite(sg);
-                v.x = rx.hi;
-                v.y = ry.hi;
-                v.z = rz.hi;
-                Y[p] = sg;
-            } else {
-                const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
-                const double d2 = D2[p];
-                const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
-                conv = conv && abs_le(sg, tol * d2);
-                bad = bad || nonfinite(sg);
-                v.x = to_lp<LP>(rx);
-                v.y = to_lp<LP>(ry);
-                v.z = to_lp<LP>(rz);
-                Y[p] = to_lp<LP>(sg);
-            }
-            v.w = LP(0);
-            RF[p] = v;
-        }
+        for (int p = r0; p < nc; p += ts) M.violation(p, conv, bad);
         if (tm.any(bad)) {
             status = ILVES_MOL_NONFINITE;
             iters = it;
@@ -383,39 +527,12 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
         }
         if (it >= A.max_iter) break;
         tm.sync();
-        // ---- S3 + S4 + forward half of S5, one level at a time
+        // one pass per level; the first np tasks of a level are its DIAG tasks
         bool singular = false;
         for (int l = 0; l < D.nlevel; ++l) {
-            const int p0 = lvl_piv[l], np = lvl_piv[l + 1] - p0;
-            const int t0 = lvl_task[l], t1 = lvl_task[l + 1];
-            // one pass over the level's tasks with a single code path: the first np tasks are
-            // the DIAG tasks of the level's pivots (their "shared atom" is the pseudo-atom
-            // carrying w_i + w_j), which also produce 1 / pivot and the forward-solve entry
-            for (int t = t0 + r0; t < t1; t += ts) {
-                const Task<IdxT> tk = tasks[t];
-                const bool diag = t < t0 + np;
-                const int e1 = tasks[t + 1].tstart;
-                const V4 rr = RF[tk.row], pp = RHOF[tk.col];
-                const int at = tk.atomsign >> 1;
-                const LP wv = WL[at];
-                const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
-                const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
-                LP s = a, yv = LP(0);
-#pragma unroll 2
-                for (int e = tk.tstart; e < e1; ++e) {
-                    const auto tr = terms[e];
-                    const int m = TO::m(tr);
-                    const LP li = V[TO::l(tr)] * INV[m];
-                    s -= li * V[TO::u(tr)];
-                    yv += li * Y[m];
-                }
-                V[t] = s;
-                if (diag) {
-                    singular = singular || !(lp_abs(s) > Mode::pivot_rel * lp_abs(a));
-                    INV[tk.row] = lp_rcp(s);
-                    Y[tk.row] -= yv;
-                }
-            }
+            const int p0 = M.lvl_piv[l], np = M.lvl_piv[l + 1] - p0;
+            const int t0 = M.lvl_task[l], t1 = M.lvl_task[l + 1];
+            for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
             tm.sync();
         }
         if (tm.any(singular)) {
@@ -423,41 +540,193 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
             iters = it;
             break;
         }
-        // ---- backward half of S5
         for (int l = D.nlevel - 1; l >= 0; --l) {
-            const int p1 = lvl_piv[l + 1];
-            for (int p = lvl_piv[l] + r0; p < p1; p += ts) {
-                const int us = piv[p].diag, nu = piv[p].nup;
-                LP dl = Y[p];
-                for (int k = 0; k < nu; ++k) dl -= V[us + k] * Y[tasks[us + k].col];
-                Y[p] = dl * INV[p];
-            }
+            const int p1 = M.lvl_piv[l + 1];
+            for (int p = M.lvl_piv[l] + r0; p < p1; p += ts) M.backward(p);
             tm.sync();
         }
-        // ---- lambda += delta (float64 class), S6
-        for (int p = r0; p < nc; p += ts) {
-            if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(LAM[p]), (float)Y[p]));
-            else LAM[p] += to_hp(Y[p]);
-        }
-        update_positions();
+        for (int p = r0; p < nc; p += ts) M.lambda_acc(p);
+        for (int a = r0; a < na; a += ts) M.update_atom(a);
         tm.sync();
     }
-    // ---- S7: outputs
-    for (int a = r0; a < na; a += ts) {
-        const int64_t g = gid_of(a);
-        if constexpr (DF) {
-            A.x_out[3 * g] = A.x_unc[3 * g] + df_join(as_df(X[a]));
-            A.x_out[3 * g + 1] = A.x_unc[3 * g + 1] + df_join(as_df(X[na + a]));
-            A.x_out[3 * g + 2] = A.x_unc[3 * g + 2] + df_join(as_df(X[2 * na + a]));
-        } else {
-            A.x_out[3 * g] = X[a];
-            A.x_out[3 * g + 1] = X[na + a];
-            A.x_out[3 * g + 2] = X[2 * na + a];
-        }
-    }
+    for (int a = r0; a < na; a += ts) M.out_atom(a);
     if (A.lambda_out)
-        for (int p = r0; p < nc; p += ts) A.lambda_out[con_gid[p]] = DF ? df_join(as_df(LAM[p])) : LAM[p];
+        for (int p = r0; p < nc; p += ts) M.out_lambda(p);
     if (r0 == 0) {
+        if (A.iterations_out) A.iterations_out[D.mol_id] = iters;
+        if (A.status_out) A.status_out[D.mol_id] = status;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// partitioned molecule: all CTAs of a cooperative launch (supplement Sec. 3: private
+// partitions eliminated in parallel, contributions to the shared partition, the shared
+// block factorised by one worker, back substitution in parallel)
+// ------------------------------------------------------------------------------------
+constexpr long long kSpinBudget = 1ll << 22;  // bounded wait: ~0.3 s of polling per launch
+
+// Arrive on a monotone 64-bit counter and wait (bounded) until every CTA of this barrier
+// generation arrived.  Returns false if the wait gave up.
+__device__ __forceinline__ bool grid_sync(unsigned long long* ctr, unsigned n_blocks, long long& budget) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long arrived = atomicAdd(ctr, 1ull) + 1ull;
+        const unsigned long long target = ((arrived + n_blocks - 1) / n_blocks) * (unsigned long long)n_blocks;
+        int good = 1;
+        while (*reinterpret_cast<volatile unsigned long long*>(ctr) < target) {
+            if (--budget <= 0) {
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct PartSync {
+    unsigned long long barrier;
+    int notconv[4];
+    int bad[4];
+    int singular[4];
+    int timeout;
+};
+
+template <class Mode>
+__global__ void __launch_bounds__(256)
+k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, uint8_t* work, PartSync* sync,
+               SolveArgs A) {
+    const MolDesc D = *desc;
+    MolView<Mode, uint32_t, true> M;
+    M.init(D, blob + D.blob_off, work + D.work_off, A);
+    const int n_parts = D.n_seg - 1;
+    const SegRow* seg = M.seg;
+    const int sep0 = __ldg(&seg[n_parts].piv), nsep = D.nc - sep0;
+    const int G = gridDim.x, b = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
+    const unsigned nb = gridDim.x;
+    long long budget = kSpinBudget;
+    auto part_atoms = [&](int q, int& a0, int& a1) {
+        a0 = __ldg(&seg[q].atom);
+        a1 = __ldg(&seg[q + 1].atom);
+    };
+    // constraints owned by this CTA: the interior pivots of its parts, and every G-th separator
+    auto for_owned = [&](auto&& f) {
+        for (int q = b; q < n_parts; q += G) {
+            const int p1 = __ldg(&seg[q + 1].piv);
+            for (int p = __ldg(&seg[q].piv) + r0; p < p1; p += ts) f(p);
+        }
+        for (int k = b + G * r0; k < nsep; k += G * ts) f(sep0 + k);
+    };
+    auto for_my_atoms = [&](auto&& f) {
+        for (int q = b; q < n_parts; q += G) {
+            int a0, a1;
+            part_atoms(q, a0, a1);
+            for (int a = a0 + r0; a < a1; a += ts) f(a);
+        }
+    };
+    // ---- S1 (reference geometry straight from global x_old: separators span parts)
+    for_my_atoms([&](int a) { M.s1_atom(a, false); });
+    if (b == 0 && r0 == 0) M.s1_dummy();
+    for_owned([&](int p) { M.s1_constraint(p, false); });
+    for_my_atoms([&](int a) { M.s1_atom_unc(a); });
+    bool alive = grid_sync(&sync->barrier, nb, budget);
+    if (alive && A.lambda0) {
+        for_my_atoms([&](int a) { M.update_atom(a); });
+        alive = grid_sync(&sync->barrier, nb, budget);
+    }
+    int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
+    for (int it = 0; alive; ++it) {
+        const int slot = it & 3;
+        // ---- violations of owned constraints, global vote
+        bool conv = true, bad = false;
+        for_owned([&](int p) { M.violation(p, conv, bad); });
+        const int nconv_block = __syncthreads_count(!conv);
+        const int bad_block = __syncthreads_or(bad);
+        if (r0 == 0) {
+            if (nconv_block) atomicAdd(&sync->notconv[slot], nconv_block);
+            if (bad_block) atomicOr(&sync->bad[slot], 1);
+        }
+        if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+        const int any_bad = __ldcg(&sync->bad[slot]), any_nc = __ldcg(&sync->notconv[slot]);
+        if (b == 0 && r0 == 0) {  // free the slot used two iterations from now
+            sync->notconv[(it + 2) & 3] = 0;
+            sync->bad[(it + 2) & 3] = 0;
+            sync->singular[(it + 2) & 3] = 0;
+        }
+        if (any_bad) {
+            status = ILVES_MOL_NONFINITE;
+            iters = it;
+            break;
+        }
+        if (any_nc == 0) {
+            status = ILVES_MOL_CONVERGED;
+            iters = it;
+            break;
+        }
+        if (it >= A.max_iter) break;
+        // ---- phase A: every part factorises its interior (and its rows/columns towards
+        //      the separators) level by level
+        bool singular = false;
+        for (int q = b; q < n_parts; q += G) {
+            const int l0 = __ldg(&seg[q].lvl), l1 = __ldg(&seg[q + 1].lvl) - 1;
+            for (int l = l0; l < l1; ++l) {
+                const int p0 = __ldg(M.lvl_piv + l), np = __ldg(M.lvl_piv + l + 1) - p0;
+                const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
+                for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                __syncthreads();
+            }
+        }
+        if (__syncthreads_or(singular) && r0 == 0) atomicOr(&sync->singular[slot], 1);
+        if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+        // ---- phase B: CTA 0 factorises the separator block (the Schur complement) and
+        //      solves it forward and backward
+        if (b == 0) {
+            bool sing = false;
+            const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
+            for (int l = l0; l < l1; ++l) {
+                const int p0 = __ldg(M.lvl_piv + l), np = __ldg(M.lvl_piv + l + 1) - p0;
+                const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
+                for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, sing);
+                __syncthreads();
+            }
+            if (__syncthreads_or(sing) && r0 == 0) atomicOr(&sync->singular[slot], 1);
+            for (int l = l1 - 1; l >= l0; --l) {
+                const int p1 = __ldg(M.lvl_piv + l + 1);
+                for (int p = __ldg(M.lvl_piv + l) + r0; p < p1; p += ts) M.backward(p);
+                __syncthreads();
+            }
+        }
+        if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+        if (__ldcg(&sync->singular[slot])) {
+            status = ILVES_MOL_SINGULAR_PIVOT;
+            iters = it;
+            break;
+        }
+        // ---- phase D: back substitution inside every part, multipliers, positions
+        for (int q = b; q < n_parts; q += G) {
+            const int l0 = __ldg(&seg[q].lvl), l1 = __ldg(&seg[q + 1].lvl) - 1;
+            for (int l = l1 - 1; l >= l0; --l) {
+                const int p1 = __ldg(M.lvl_piv + l + 1);
+                for (int p = __ldg(M.lvl_piv + l) + r0; p < p1; p += ts) M.backward(p);
+                __syncthreads();
+            }
+        }
+        for_owned([&](int p) { M.lambda_acc(p); });
+        for_my_atoms([&](int a) { M.update_atom(a); });
+        if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+    }
+    if (!alive) {
+        status = ILVES_MOL_WAIT_TIMEOUT;
+        if (r0 == 0) atomicOr(&sync->timeout, 1);
+    }
+    for_my_atoms([&](int a) { M.out_atom(a); });
+    if (A.lambda_out) for_owned([&](int p) { M.out_lambda(p); });
+    if (b == 0 && r0 == 0) {
         if (A.iterations_out) A.iterations_out[D.mol_id] = iters;
         if (A.status_out) A.status_out[D.mol_id] = status;
     }
@@ -478,7 +747,7 @@ struct SmallSched {
 // never wait for each other.  Each molecule's program blob is staged into the slice
 // with 16-byte loads before its Newton loop.
 template <class Mode>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(512, 1)
 k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
               SolveArgs A) {
     extern __shared__ __align__(16) uint8_t arena[];
@@ -490,7 +759,7 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
     const int q1 = S.slot_ptr[slot + 1];
     for (int q = S.slot_ptr[slot]; q < q1; ++q) {
         const MolDesc D = desc[S.slot_mol[q]];
-        const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel);
+        const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg);
         const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
         uint4* dst = reinterpret_cast<uint4*>(slice);
         const int n16 = (int)(PL.bytes >> 4);
@@ -557,6 +826,7 @@ static void free_device(ilves_topology* T) {
     f(T->d_nbr_atom);
     f(T->d_ws_con);
     f(T->d_ws_atom);
+    f(T->d_sync);
     f(T->d_work);
     for (auto& s : T->sched) {
         f(s.cta_slot_ptr);
@@ -574,6 +844,7 @@ static void free_device(ilves_topology* T) {
     T->d_free_atoms = nullptr;
     T->d_con_i = T->d_con_j = T->d_nbr = T->d_nbr_atom = nullptr;
     T->d_ws_con = T->d_ws_atom = nullptr;
+    T->d_sync = nullptr;
     T->d_work = nullptr;
     T->side_stream = T->ev_fork = T->ev_join = nullptr;
 }
@@ -614,10 +885,17 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         if (!T->mols[m].large) order.push_back(m);
     T->n_small = (int32_t)order.size();
     for (int32_t m = 0; m < T->n_mol; ++m)
-        if (T->mols[m].large) order.push_back(m);
-    T->n_large = T->n_mol - T->n_small;
+        if (T->mols[m].large && !T->mols[m].parted) order.push_back(m);
+    T->n_large = (int32_t)order.size() - T->n_small;
+    T->parted_desc.clear();
+    for (int32_t m = 0; m < T->n_mol; ++m)
+        if (T->mols[m].parted) {
+            T->parted_desc.push_back((int32_t)order.size());
+            order.push_back(m);
+        }
     std::vector<int32_t> desc_index(T->n_mol);
     std::vector<MolDesc> desc(T->n_mol);
+    T->desc_mol = order;
     std::vector<int32_t> gids;
     int64_t boff = 0, woff = 0;
     for (int32_t k = 0; k < T->n_mol; ++k) {
@@ -637,7 +915,7 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         D.na = na;
         D.nc = (int32_t)M.cons.size();
         D.nlevel = M.nlevel;
-        D.pad = 0;
+        D.n_seg = M.n_seg;
         D.work_off = 0;
         if (M.large) {
             D.work_off = woff;
@@ -661,14 +939,18 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     if (T->n_atoms > 0 && (e = cudaMalloc((void**)&T->d_ws_atom, (size_t)T->n_atoms * sizeof(float))) != cudaSuccess)
         return to_status(e);
     if (woff > 0 && (e = cudaMalloc((void**)&T->d_work, woff)) != cudaSuccess) return to_status(e);
+    if (!T->parted_desc.empty()) {
+        T->sync_bytes = (int64_t)T->parted_desc.size() * (int64_t)sizeof(PartSync);
+        if ((e = cudaMalloc((void**)&T->d_sync, T->sync_bytes)) != cudaSuccess) return to_status(e);
+    }
     // persistent schedules, one per precision mode
     for (int mode = 0; mode < 3; ++mode) {
         std::vector<uint32_t> fps;
         for (int32_t m = 0; m < T->n_mol; ++m)
             if (!T->mols[m].large) fps.push_back(footprint(T->mols[m], mode));
         // auto: the largest warp count per CTA whose slices fit the arena (searched downwards)
-        int warps = o.warps_per_cta > 0 ? o.warps_per_cta : 32;
-        warps = std::max(1, std::min(32, warps));
+        int warps = o.warps_per_cta > 0 ? o.warps_per_cta : 16;
+        warps = std::max(1, std::min(16, warps));
         HostSchedule HS;
         build_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
         for (auto& km : HS.slot_mol) km = desc_index[km];
@@ -681,7 +963,7 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         if ((e = upload(&DS.slot_mol, HS.slot_mol)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_off, HS.slot_off)) != cudaSuccess) return to_status(e);
     }
-    if (T->n_large > 0) {
+    if (T->n_large > 0 || !T->parted_desc.empty()) {
         cudaStream_t s;
         cudaEvent_t a, b;
         if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return to_status(e);
@@ -695,8 +977,13 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     return ILVES_OK;
 }
 
+// Enqueues every kernel of one solve on `stream`: the CTA-per-molecule kernel and the
+// cooperative launches of partitioned molecules on the topology's side stream (fork /
+// join through events), the warp-per-molecule kernel and the copy of unconstrained atoms
+// on `stream`.  `work` holds the large molecules' state, `sync` their barrier areas.
 template <class Mode>
-static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStream_t stream) {
+static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream_t stream, uint8_t* work,
+                               uint8_t* sync) {
     cudaError_t e;
     int launches = 0;
     const DeviceSchedule& DS = T->sched[Mode::id];
@@ -705,14 +992,37 @@ static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStrea
         if (e != cudaSuccess) return to_status(e);
         T->smem_attr_set[Mode::id] = true;
     }
-    if (T->n_large > 0) {
+    const bool side_work = T->n_large > 0 || !T->parted_desc.empty();
+    if (side_work) {
         cudaStream_t side = (cudaStream_t)T->side_stream;
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_fork, stream)) != cudaSuccess) return to_status(e);
         if ((e = cudaStreamWaitEvent(side, (cudaEvent_t)T->ev_fork, 0)) != cudaSuccess) return to_status(e);
-        k_solve_large<Mode><<<T->n_large, T->large_threads, 0, side>>>(T->d_desc + T->n_small, T->d_blob,
-                                                                       T->d_work, A);
-        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
-        ++launches;
+        if (T->n_large > 0) {
+            k_solve_large<Mode><<<T->n_large, T->large_threads, 0, side>>>(T->d_desc + T->n_small, T->d_blob, work, A);
+            if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
+            ++launches;
+        }
+        if (!T->parted_desc.empty()) {
+            int per_sm = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>, T->parted_threads, 0)) !=
+                cudaSuccess)
+                return to_status(e);
+            const int max_grid = std::max(1, per_sm * T->n_sm);
+            if ((e = cudaMemsetAsync(sync, 0, T->sync_bytes, side)) != cudaSuccess) return to_status(e);
+            for (size_t k = 0; k < T->parted_desc.size(); ++k) {
+                const int32_t di = T->parted_desc[k];
+                const int n_parts = T->mols[T->desc_mol[di]].n_seg - 1;
+                const MolDesc* dptr = T->d_desc + di;
+                PartSync* sp = reinterpret_cast<PartSync*>(sync) + k;
+                SolveArgs Aa = A;
+                void* args[] = {(void*)&dptr, (void*)&T->d_blob, (void*)&work, (void*)&sp, (void*)&Aa};
+                const dim3 grid(std::min(n_parts, max_grid)), block(T->parted_threads);
+                if ((e = cudaLaunchCooperativeKernel((const void*)k_solve_parted<Mode>, grid, block, args, 0, side)) !=
+                    cudaSuccess)
+                    return to_status(e);
+                ++launches;
+            }
+        }
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
     }
     if (T->n_small > 0) {
@@ -727,11 +1037,16 @@ static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStrea
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;
     }
-    if (T->n_large > 0) {
+    if (side_work) {
         if ((e = cudaStreamWaitEvent(stream, (cudaEvent_t)T->ev_join, 0)) != cudaSuccess) return to_status(e);
     }
     T->last_launches = launches;
     return ILVES_OK;
+}
+
+template <class Mode>
+static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStream_t stream) {
+    return launch_all<Mode>(T, A, stream, T->d_work, T->d_sync);
 }
 
 // ------------------------------------------------------------------------------------
@@ -761,45 +1076,6 @@ static ilves_status static_scratch_address(int dev, uint8_t** out) {
     return ILVES_OK;
 }
 
-template <class Mode>
-static ilves_status launch_mode_static(ilves_topology* T, const SolveArgs& A, cudaStream_t stream,
-                                       uint8_t* scratch) {
-    cudaError_t e;
-    int launches = 0;
-    const DeviceSchedule& DS = T->sched[Mode::id];
-    if (!T->smem_attr_set[Mode::id]) {
-        e = cudaFuncSetAttribute(small_kernel<Mode>(), cudaFuncAttributeMaxDynamicSharedMemorySize, DS.arena);
-        if (e != cudaSuccess) return to_status(e);
-        T->smem_attr_set[Mode::id] = true;
-    }
-    if (T->n_large > 0) {
-        cudaStream_t side = (cudaStream_t)T->side_stream;
-        if ((e = cudaEventRecord((cudaEvent_t)T->ev_fork, stream)) != cudaSuccess) return to_status(e);
-        if ((e = cudaStreamWaitEvent(side, (cudaEvent_t)T->ev_fork, 0)) != cudaSuccess) return to_status(e);
-        k_solve_large<Mode><<<T->n_large, T->large_threads, 0, side>>>(T->d_desc + T->n_small, T->d_blob, scratch, A);
-        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
-        ++launches;
-        if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
-    }
-    if (T->n_small > 0) {
-        SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off};
-        k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
-        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
-        ++launches;
-    }
-    const int nf = (int)T->free_atoms.size();
-    if (nf > 0 && A.x_out != A.x_unc) {
-        k_copy_free<<<(nf + 255) / 256, 256, 0, stream>>>(T->d_free_atoms, nf, A.x_unc, A.x_out);
-        if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
-        ++launches;
-    }
-    if (T->n_large > 0) {
-        if ((e = cudaStreamWaitEvent(stream, (cudaEvent_t)T->ev_join, 0)) != cudaSuccess) return to_status(e);
-    }
-    T->last_launches = launches;
-    return ILVES_OK;
-}
-
 }  // namespace ilves
 
 using namespace ilves;
@@ -815,6 +1091,8 @@ extern "C" void ilves_default_opts(ilves_setup_opts* o) {
     o->ctas_per_sm = 0;
     o->device = -1;
     o->max_warp_constraints = 0;
+    o->partition_min_constraints = 0;
+    o->part_constraints = 0;
 }
 
 extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const int32_t* atom_i,
@@ -828,7 +1106,7 @@ extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constrai
     ilves_default_opts(&o);
     if (opts) o = *opts;
     if (o.ordering < 0 || o.ordering > 2 || o.degree_slack < 0 || o.warps_per_cta < 0 ||
-        o.warps_per_cta > 32 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4)
+        o.warps_per_cta > 16 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4)
         return ILVES_ERR_INVALID_ARG;
     ilves_topology* T = new ilves_topology();
     ilves_status s = plan_topology(T, n_atoms, n_constraints, atom_i, atom_j, o);
@@ -884,7 +1162,8 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     if (T->n_atoms > 0 && (!x_old || !x_unc || !inv_mass || !x_out)) return ILVES_ERR_INVALID_ARG;
     if (T->n_c > 0 && !d) return ILVES_ERR_INVALID_ARG;
     if (precision < ILVES_PREC_FP64 || precision > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
-    if ((uint64_t)T->work_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
+    const uint64_t work_aligned = ((uint64_t)T->work_bytes + 255) & ~uint64_t(255);
+    if (work_aligned + (uint64_t)T->sync_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return ILVES_ERR_CUDA;
     if (dev != T->device) return ILVES_ERR_INVALID_ARG;
@@ -906,16 +1185,19 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     A.max_iter = max_iter;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
+    uint8_t* sync = scratch + work_aligned;
     switch (precision) {
-        case ILVES_PREC_FP64: return launch_mode_static<ModeFP64>(T, A, s, scratch);
-        case ILVES_PREC_MIXED: return launch_mode_static<ModeMixed>(T, A, s, scratch);
-        default: return launch_mode_static<ModeMixedDF>(T, A, s, scratch);
+        case ILVES_PREC_FP64: return launch_all<ModeFP64>(T, A, s, scratch, sync);
+        case ILVES_PREC_MIXED: return launch_all<ModeMixed>(T, A, s, scratch, sync);
+        default: return launch_all<ModeMixedDF>(T, A, s, scratch, sync);
     }
 }
 
 extern "C" int64_t ilves_static_scratch_bytes(void) { return (int64_t)kStaticScratchBytes; }
 
-extern "C" int64_t ilves_topology_workspace_bytes(const ilves_topology* T) { return T ? T->work_bytes : 0; }
+extern "C" int64_t ilves_topology_workspace_bytes(const ilves_topology* T) {
+    return T ? ((T->work_bytes + 255) & ~int64_t(255)) + T->sync_bytes : 0;
+}
 
 extern "C" ilves_status ilves_topology_info(const ilves_topology* T, int32_t* n_molecules, int64_t* nnz_factor,
                                             int32_t* max_levels, int64_t* n_fill, int32_t* n_large) {

@@ -17,6 +17,7 @@
 // chain it becomes cyclic reduction).  The slack is chosen per molecule by a cost
 // model of the kernel (level passes + work), see choose_order().
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <iterator>
@@ -68,8 +69,10 @@ static void sorted_merge_into(std::vector<int32_t>& dst, const std::vector<int32
     dst.swap(tmp);
 }
 
+// stage (optional): vertices of a higher stage become eligible only once every vertex of a
+// lower stage is eliminated (used to eliminate the separators of a partition last).
 static Elimination eliminate_rounds(int32_t n, std::vector<std::vector<int32_t>> H, int32_t slack,
-                                    bool one_per_round) {
+                                    bool one_per_round, const std::vector<int8_t>* stage = nullptr) {
     Elimination E;
     E.nplus.assign(n, {});
     E.order.reserve(n);
@@ -79,10 +82,15 @@ static Elimination eliminate_rounds(int32_t n, std::vector<std::vector<int32_t>>
     std::vector<std::pair<int32_t, int32_t>> dv;
     std::vector<int32_t> chosen, tmp;
     int64_t added = 0;
+    int8_t cur_stage = 0;
+    std::vector<int32_t> left_in_stage(2, 0);
+    if (stage)
+        for (int32_t v = 0; v < n; ++v) ++left_in_stage[(*stage)[v]];
     while (remaining > 0) {
+        if (stage && left_in_stage[cur_stage] == 0) ++cur_stage;
         dv.clear();
         for (int32_t v = 0; v < n; ++v)
-            if (alive[v]) dv.push_back({(int32_t)H[v].size(), v});
+            if (alive[v] && (!stage || (*stage)[v] == cur_stage)) dv.push_back({(int32_t)H[v].size(), v});
         std::sort(dv.begin(), dv.end());
         const int32_t mind = dv[0].first;
         chosen.clear();
@@ -108,6 +116,7 @@ static Elimination eliminate_rounds(int32_t n, std::vector<std::vector<int32_t>>
             H[v].shrink_to_fit();
             alive[v] = 0;
             E.order.push_back(v);
+            if (stage) --left_in_stage[(*stage)[v]];
         }
         remaining -= (int32_t)chosen.size();
         ++rnd;
@@ -128,24 +137,36 @@ struct Program {
     std::vector<int32_t> ustart;             // per position: first slot of its U row (then L column)
     std::vector<TaskW> tasks;                // + sentinel
     std::vector<TermW> terms;
-    std::vector<int32_t> lvl_task, lvl_piv;
+    std::vector<int32_t> lvl_task, lvl_piv;  // per segment: n_lev + 1 entries, concatenated
+    // segments: parts of a partitioned molecule (then the separators), or one segment
+    int32_t n_seg = 1;
+    std::vector<int32_t> seg_piv, seg_lvl, seg_atom;  // n_seg + 1 each
     int64_t passes_factor = 0, passes_solve = 0;
     int64_t n_fill = 0;
 };
 
+// seg (optional): segment of every local constraint (a part, or n_seg - 1 for the
+// separators); positions are ordered by segment, then level; levels count only
+// dependencies inside the same segment (earlier segments are complete before a later
+// segment starts).
 static Program compile(int32_t nc, const Elimination& E, const std::vector<int32_t>& ci,
-                       const std::vector<int32_t>& cj, int32_t team, int32_t na_dummy) {
+                       const std::vector<int32_t>& cj, int32_t team, int32_t na_dummy,
+                       const std::vector<int32_t>* seg = nullptr, int32_t n_seg = 1,
+                       const std::vector<int32_t>* seg_atom = nullptr) {
     Program P;
     P.n_fill = E.n_fill;
-    // dependency levels: a pivot runs after every earlier pivot adjacent to it
+    P.n_seg = n_seg;
+    auto sg = [&](int32_t v) { return seg ? (*seg)[v] : 0; };
     std::vector<int32_t> lev(nc, 0);
     for (int32_t v : E.order)
-        for (int32_t x : E.nplus[v]) lev[x] = std::max(lev[x], lev[v] + 1);
+        for (int32_t x : E.nplus[v])
+            if (sg(x) == sg(v)) lev[x] = std::max(lev[x], lev[v] + 1);
     std::vector<int32_t> seqidx(nc);
     for (int32_t i = 0; i < nc; ++i) seqidx[E.order[i]] = i;
     P.pos_con.resize(nc);
     std::iota(P.pos_con.begin(), P.pos_con.end(), 0);
     std::sort(P.pos_con.begin(), P.pos_con.end(), [&](int32_t a, int32_t b) {
+        if (sg(a) != sg(b)) return sg(a) < sg(b);
         return lev[a] != lev[b] ? lev[a] < lev[b] : seqidx[a] < seqidx[b];
     });
     std::vector<int32_t> pos_of(nc);
@@ -158,27 +179,47 @@ static Program compile(int32_t nc, const Elimination& E, const std::vector<int32
         for (int32_t x : E.nplus[v]) P.up[p].push_back(pos_of[x]);
         std::sort(P.up[p].begin(), P.up[p].end());
     }
-    P.nlevel = nc ? P.level[nc - 1] + 1 : 0;
     std::vector<std::vector<int32_t>> dn(nc);  // N-(p), ascending
     for (int32_t m = 0; m < nc; ++m)
         for (int32_t q : P.up[m]) dn[q].push_back(m);
-    // level boundaries (positions)
-    P.lvl_piv.assign(P.nlevel + 1, nc);
-    for (int32_t p = nc - 1; p >= 0; --p) P.lvl_piv[P.level[p]] = p;
-    // task slots: per level, the DIAG tasks of its pivots, then per pivot its U row and L column
+    // segment boundaries and per-segment level boundaries (positions)
+    P.seg_piv.assign(n_seg + 1, nc);
+    for (int32_t p = nc - 1; p >= 0; --p) P.seg_piv[sg(P.pos_con[p])] = p;
+    for (int32_t g = n_seg - 1; g >= 0; --g) P.seg_piv[g] = std::min(P.seg_piv[g], P.seg_piv[g + 1]);
+    P.seg_lvl.assign(n_seg + 1, 0);
+    P.lvl_piv.clear();
+    std::vector<int32_t> seg_nlev(n_seg, 0);
+    for (int32_t g = 0; g < n_seg; ++g) {
+        const int32_t p0 = P.seg_piv[g], p1 = P.seg_piv[g + 1];
+        const int32_t nl = p1 > p0 ? P.level[p1 - 1] + 1 : 0;
+        seg_nlev[g] = nl;
+        P.seg_lvl[g] = (int32_t)P.lvl_piv.size();
+        std::vector<int32_t> starts(nl + 1, p1);
+        for (int32_t p = p1 - 1; p >= p0; --p) starts[P.level[p]] = p;
+        P.lvl_piv.insert(P.lvl_piv.end(), starts.begin(), starts.end());
+    }
+    P.seg_lvl[n_seg] = (int32_t)P.lvl_piv.size();
+    P.nlevel = (int32_t)P.lvl_piv.size() - 1;  // one segment: its level count
+    P.seg_atom.assign(n_seg + 1, 0);
+    if (seg_atom) P.seg_atom = *seg_atom;
+    // task slots: per segment and level, the DIAG tasks of its pivots, then per pivot its
+    // U row and L column
     P.diag_task.resize(nc);
     P.ustart.resize(nc);
-    P.lvl_task.assign(P.nlevel + 1, 0);
+    P.lvl_task.assign(P.lvl_piv.size(), 0);
     int32_t t = 0;
-    for (int32_t l = 0; l < P.nlevel; ++l) {
-        P.lvl_task[l] = t;
-        for (int32_t p = P.lvl_piv[l]; p < P.lvl_piv[l + 1]; ++p) P.diag_task[p] = t++;
-        for (int32_t p = P.lvl_piv[l]; p < P.lvl_piv[l + 1]; ++p) {
-            P.ustart[p] = t;
-            t += 2 * (int32_t)P.up[p].size();
+    for (int32_t g = 0; g < n_seg; ++g) {
+        const int32_t b = P.seg_lvl[g];
+        for (int32_t l = 0; l < seg_nlev[g]; ++l) {
+            P.lvl_task[b + l] = t;
+            for (int32_t p = P.lvl_piv[b + l]; p < P.lvl_piv[b + l + 1]; ++p) P.diag_task[p] = t++;
+            for (int32_t p = P.lvl_piv[b + l]; p < P.lvl_piv[b + l + 1]; ++p) {
+                P.ustart[p] = t;
+                t += 2 * (int32_t)P.up[p].size();
+            }
         }
+        P.lvl_task[b + seg_nlev[g]] = t;
     }
-    P.lvl_task[P.nlevel] = t;
     auto kpos = [&](int32_t m, int32_t q) {
         const auto& u = P.up[m];
         return (int32_t)(std::lower_bound(u.begin(), u.end(), q) - u.begin());
@@ -225,11 +266,55 @@ static Program compile(int32_t nc, const Elimination& E, const std::vector<int32
         P.terms.insert(P.terms.end(), tterms[k].begin(), tterms[k].end());
     }
     P.tasks[t] = {0u, 0u, kNoAtom32, (uint32_t)P.terms.size()};  // sentinel
-    for (int32_t l = 0; l < P.nlevel; ++l) {
-        P.passes_factor += (P.lvl_task[l + 1] - P.lvl_task[l] + team - 1) / team;
-        P.passes_solve += (P.lvl_piv[l + 1] - P.lvl_piv[l] + team - 1) / team;
+    for (int32_t g = 0; g < n_seg; ++g) {
+        const int32_t b = P.seg_lvl[g];
+        for (int32_t l = 0; l < seg_nlev[g]; ++l) {
+            P.passes_factor += (P.lvl_task[b + l + 1] - P.lvl_task[b + l] + team - 1) / team;
+            P.passes_solve += (P.lvl_piv[b + l + 1] - P.lvl_piv[b + l] + team - 1) / team;
+        }
     }
     return P;
+}
+
+// Greedy partition of a molecule's atoms (already in index order) into n_parts
+// contiguous parts, after the paper's description (supplement Sec. 3): atoms are taken in
+// order while the part is below target + offset; the last atom of a part is chosen among
+// the sizes within maxDeviation of the target by cut edges (penalty cutPenalty per edge
+// crossing the boundary) and distance to the target size.  O(|E|).
+static std::vector<int32_t> partition_atoms(int32_t na, const std::vector<int32_t>& ci,
+                                            const std::vector<int32_t>& cj, int32_t n_parts,
+                                            double max_dev = 0.05, double cut_penalty = 10.0) {
+    std::vector<std::vector<int32_t>> nb(na);
+    for (size_t k = 0; k < ci.size(); ++k) {
+        nb[ci[k]].push_back(cj[k]);
+        nb[cj[k]].push_back(ci[k]);
+    }
+    std::vector<int32_t> bounds{0};
+    int32_t a0 = 0;
+    for (int32_t p = 0; p + 1 < n_parts && a0 < na; ++p) {
+        const double target = (double)(na - a0) / (double)(n_parts - p);
+        const int32_t lo = std::max(a0 + 1, (int32_t)std::floor(a0 + target * (1.0 - max_dev)));
+        const int32_t hi = std::min(na - 1, (int32_t)std::ceil(a0 + target * (1.0 + max_dev)));
+        // open = edges from [a0, e) to [e, na): sweep e upwards from a0
+        int64_t open = 0;
+        int32_t best_e = std::min(na - 1, std::max(lo, a0 + 1));
+        double best = 1e300;
+        for (int32_t e = a0 + 1; e <= hi; ++e) {
+            const int32_t u = e - 1;  // atom u joins the part
+            for (int32_t v : nb[u]) open += (v >= e) ? 1 : ((v >= a0 && v < u) ? -1 : 0);
+            if (e < lo) continue;
+            const double score = cut_penalty * (double)open + std::fabs((double)(e - a0) - target);
+            if (score < best) {
+                best = score;
+                best_e = e;
+            }
+        }
+        if (best_e <= a0) break;
+        bounds.push_back(best_e);
+        a0 = best_e;
+    }
+    bounds.push_back(na);
+    return bounds;
 }
 
 // Kernel cost model (cycles per Newton iteration for one team): a level pass costs
@@ -266,13 +351,15 @@ static Program choose_order(int32_t nc, int32_t na, const std::vector<std::vecto
 template <class IdxT>
 static ProgLayout layout_for(const MolHost& M) {
     return prog_layout<IdxT>((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(), (uint32_t)M.ntask,
-                             (uint32_t)M.nterm, (uint32_t)M.nlevel);
+                             (uint32_t)M.nterm, (uint32_t)M.nlevel, (uint32_t)M.n_seg);
 }
 
 template <class IdxT>
 static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
     const ProgLayout L = layout_for<IdxT>(M);
     std::memset(dst, 0, L.bytes);
+    auto* seg = reinterpret_cast<SegRow*>(dst + L.seg);
+    for (int32_t g = 0; g <= P.n_seg; ++g) seg[g] = SegRow{P.seg_piv[g], P.seg_lvl[g], P.seg_atom[g]};
     auto* con = reinterpret_cast<ConA<IdxT>*>(dst + L.con_atoms);
     auto* con_gid = reinterpret_cast<int32_t*>(dst + L.con_gid);
     auto* piv = reinterpret_cast<Piv<IdxT>*>(dst + L.piv);
@@ -291,7 +378,7 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
         piv[p].diag = (IdxT)P.ustart[p];
         piv[p].nup = (IdxT)P.up[p].size();
     }
-    for (int32_t l = 0; l <= P.nlevel; ++l) {
+    for (size_t l = 0; l < P.lvl_piv.size(); ++l) {
         lvl_task[l] = (IdxT)P.lvl_task[l];
         lvl_piv[l] = (IdxT)P.lvl_piv[l];
     }
@@ -423,6 +510,37 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             v.erase(std::unique(v.begin(), v.end()), v.end());
         }
         M.large = nc > warp_limit || nc >= (int32_t)kCompactMaxConstraints || na + 1 + nc > 32000;
+        const int32_t part_min = o.partition_min_constraints > 0 ? o.partition_min_constraints : 4096;
+        if (nc >= part_min) {
+            // partitioned: parts of ~part_size constraints eliminated first, separators last
+            M.large = M.parted = true;
+            const int32_t part_size = o.part_constraints > 0 ? o.part_constraints : 256;
+            const int32_t n_parts = std::max(2, std::min(8192, (nc + part_size - 1) / part_size));
+            std::vector<int32_t> bounds = partition_atoms(na, M.ci, M.cj, n_parts);
+            const int32_t np = (int32_t)bounds.size() - 1;
+            std::vector<int32_t> part_of(na);
+            for (int32_t q = 0; q < np; ++q)
+                for (int32_t a = bounds[q]; a < bounds[q + 1]; ++a) part_of[a] = q;
+            std::vector<int32_t> seg(nc);
+            std::vector<int8_t> stage(nc);
+            for (int32_t c = 0; c < nc; ++c) {
+                const bool inner = part_of[M.ci[c]] == part_of[M.cj[c]];
+                seg[c] = inner ? part_of[M.ci[c]] : np;
+                stage[c] = inner ? 0 : 1;
+            }
+            std::vector<int32_t> seg_atom(bounds);
+            seg_atom.push_back(na);  // the separator segment owns no atoms
+            Elimination E = eliminate_rounds(nc, adj, 2, false, &stage);
+            Program* P = new Program(compile(nc, E, M.ci, M.cj, 256, na, &seg, np + 1, &seg_atom));
+            M.n_seg = np + 1;
+            M.nlevel = P->nlevel;
+            M.ntask = (int32_t)P->tasks.size() - 1;
+            M.nterm = (int32_t)P->terms.size();
+            M.n_fill = P->n_fill;
+            M.passes = P->passes_factor + P->passes_solve;
+            T->progs[m] = P;
+            continue;
+        }
         Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : 32));
         if (!M.large && (P->tasks.size() >= kCompactMaxSlots || P->terms.size() > 65000)) {
             M.large = true;

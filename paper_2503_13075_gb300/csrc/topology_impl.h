@@ -17,6 +17,8 @@ struct MolHost {
     std::vector<int32_t> cons;       // global constraint ids, ascending (local constraint id order)
     std::vector<int32_t> ci, cj;     // per local constraint: local atom ids
     bool large = false;
+    bool parted = false;  // partitioned: solved by a cooperative multi-CTA launch
+    int32_t n_seg = 1;
     int32_t nlevel = 0, ntask = 0, nterm = 0, n_fill = 0;
     int64_t passes = 0;
 };
@@ -72,6 +74,12 @@ struct ilves_topology {
     void* ev_fork = nullptr;
     void* ev_join = nullptr;
     int32_t large_threads = 512;
+    std::vector<int32_t> parted_desc;        // descriptor indices of partitioned molecules
+    uint8_t* d_sync = nullptr;               // per partitioned molecule: barrier counter + flags
+    int64_t sync_bytes = 0;
+    std::vector<int32_t> desc_mol;           // molecule id of each descriptor
+    int32_t parted_threads = 256;
+    int32_t parted_max_ctas = 0;
     int32_t last_launches = 0;
     bool smem_attr_set[3] = {false, false, false};
 };

@@ -141,3 +141,44 @@ def test_free_atoms_and_empty():
     t = B.Topology(6, [0, 4], [1, 5], plan_only=True)
     atoms, cons, levels, first = t.molecules()
     assert list(first) == [0, 4] and list(cons) == [1, 1]
+
+
+def test_partitioned_molecule_structure():
+    """Large molecules are cut into contiguous atom parts; separators (constraints between
+    parts) come last, every pivot's later neighbours are later positions, and the
+    symbolic closure holds across the whole molecule."""
+    s = wl.protein_like(n_atoms=3000, seed=21)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, partition_min_constraints=1000,
+                   part_constraints=200)
+    assert t.n_large == 1
+    pos_gid, level, ptr, idx = t.export_molecule(0)
+    nc = pos_gid.size
+    up = [set(idx[ptr[p]:ptr[p + 1]].tolist()) for p in range(nc)]
+    for p in range(nc):
+        u = sorted(up[p])
+        assert all(q > p for q in u)
+        for a_ in range(len(u)):
+            for b_ in range(a_ + 1, len(u)):
+                assert u[b_] in up[u[a_]]
+    # the pattern of A is inside the filled pattern
+    adj = _line_graph(s.atom_i[pos_gid], s.atom_j[pos_gid])
+    for p in range(nc):
+        for q in adj[p]:
+            assert max(p, q) in up[min(p, q)]
+    # segments (levels restart at every segment): each part's constraints lie inside one
+    # contiguous block of atoms, blocks are disjoint, and the last segment (separators)
+    # holds exactly the constraints that cross blocks
+    ai, aj = s.atom_i[pos_gid], s.atom_j[pos_gid]
+    starts = [0] + [p for p in range(1, nc) if level[p] < level[p - 1]] + [nc]
+    assert len(starts) >= 5
+    blocks = []
+    for g in range(len(starts) - 2):
+        seg_atoms = np.concatenate([ai[starts[g]:starts[g + 1]], aj[starts[g]:starts[g + 1]]])
+        blocks.append((seg_atoms.min(), seg_atoms.max()))
+    blocks.sort()
+    for (lo0, hi0), (lo1, hi1) in zip(blocks, blocks[1:]):
+        assert hi0 < lo1
+    def block_of(a):
+        return next((k for k, (lo, hi) in enumerate(blocks) if lo <= a <= hi), -1)
+    for p in range(starts[-2], nc):  # separators cross blocks (or touch a block-less atom)
+        assert block_of(ai[p]) != block_of(aj[p]) or block_of(ai[p]) == -1
