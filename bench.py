@@ -49,18 +49,31 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-precision comparators")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="tree_batch", choices=["tree_batch", "protein_like", "chain64"],
+                   help="tree_batch (default line); protein_like / chain64 print lines for the other configurations")
+    p.add_argument("--method", default="newton", choices=["newton", "chord"],
+                   help="ILVES-M (Newton) or ILVES-F (chord: A(x_old, x_old) factorised once)")
     p.add_argument("--warm-start", default="diag", choices=["none", "diag", "mlp"],
                    help="initial multipliers: zero, diagonal (Jacobi) guess, or the learned network")
     return p.parse_args()
 
 
-def workload(n_mol, seed):
+def workload(name, n_mol, seed):
     from paper_2503_13075_gb300 import workloads as wl
 
+    if name == "protein_like":
+        return wl.protein_like(seed=1002 + (seed - 1001))
+    if name == "chain64":
+        return wl.chain64(seed=1000 + (seed - 1001))
     return wl.tree_batch(n_mol=n_mol, seed=seed)
 
 
 def workload_name(s):
+    if s.name == "protein_like":
+        return (f"protein_like: one connected system of {s.n_atoms} atoms, {s.n_constraints} constraints "
+                f"({s.meta.get('n_angle_constraints', 0)} H-X-H angle distances), partitioned over CTAs")
+    if s.name == "chain64":
+        return "chain64: one 64-carbon chain, 63 bonds, batch of 1 (latency)"
     return (f"tree_batch: {s.n_molecules} tree molecules of U{{20..200}} atoms "
             f"({s.n_atoms} atoms, {s.n_constraints} constraints), all bonds constrained")
 
@@ -190,7 +203,7 @@ def run_reference(args):
     rank, world, local = dist_setup(args)
     if rank != 0:
         return
-    s = workload(args.n_mol, 1001)
+    s = workload(args.workload, args.n_mol, 1001)
     from oracle import ilves_oracle as orc
     from paper_2503_13075_gb300 import workloads as wl
 
@@ -224,7 +237,7 @@ def run_reference(args):
 WS_LAUNCHES = {"none": 0, "diag": 1, "mlp": 2}  # kernels a warm start adds per step
 
 
-def make_step(topo, dev_in, out, prec, tol, ws, mlp, lam0):
+def make_step(topo, dev_in, out, prec, tol, ws, mlp, lam0, method="newton"):
     """One timed unit: optional warm start (diag / mlp kernels) + ilves_solve."""
     from paper_2503_13075_gb300 import binding as B
 
@@ -236,7 +249,7 @@ def make_step(topo, dev_in, out, prec, tol, ws, mlp, lam0):
         if ws != "none":
             l0 = B.warm_start(mlp if ws == "mlp" else None, topo, xo, xu, w, d, out=lam0)
         topo.solve(xo, xu, w, d, tol=tol, precision=prec, lambda0=l0, x_out=x, lambda_out=lam,
-                   iterations_out=it, status_out=st)
+                   iterations_out=it, status_out=st, method=method, max_iter=60 if method == "chord" else 25)
         return topo.last_launch_count() + WS_LAUNCHES[ws]
 
     return step
@@ -293,7 +306,7 @@ def run_ilves(args):
     from oracle import ilves_oracle as orc  # correctness gate on the timed outputs only
     from paper_2503_13075_gb300 import binding as B
 
-    s = workload(args.n_mol, 1001 + 7919 * rank)  # weak scaling: every rank its own batch
+    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank)  # weak scaling: every rank its own batch
     topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
     f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     dev_in = (f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d))
@@ -305,7 +318,7 @@ def run_ilves(args):
     stream = torch.cuda.current_stream(dev)
 
     mlp, mlp_info = None, None
-    if args.warm_start == "mlp" or not args.no_compare:
+    if args.warm_start == "mlp" or (not args.no_compare and args.workload == "tree_batch"):
         mlp, mlp_info = train_warm_start(dev)
 
     def check():
@@ -317,21 +330,24 @@ def run_ilves(args):
     ablation = []
     value64 = per64 = None
     if not args.no_compare:
-        for prec in ("fp64", "mixed", "mixed_df"):
-            for wsn in ("none", "diag", "mlp"):
-                if prec == args.precision and wsn == args.warm_start:
-                    continue
-                step = make_step(topo, dev_in, out, prec, args.tol, wsn, mlp, lam0)
-                msa, _ = time_device(step, max(3, args.steps // 4), 2, flush, stream)
-                ok, viol, it = check()
-                per = sum(msa) / len(msa)
-                ablation.append({"precision": prec, "warm_start": wsn, "ms_per_step": per,
-                                 "value": s.n_atoms / (per * 1e-3), "all_converged": ok, "max_rel_violation": viol,
-                                 "mean_iterations": float(it.mean())})
-                if prec == "fp64" and wsn == "none":
-                    value64, per64 = s.n_atoms / (per * 1e-3), per
+        combos = [(p, w, "newton") for p in ("fp64", "mixed", "mixed_df") for w in ("none", "diag", "mlp")]
+        combos += [(p, w, "chord") for p in ("fp64", "mixed", "mixed_df") for w in ("none", "diag")]
+        for prec, wsn, meth in combos:
+            if (prec, wsn, meth) == (args.precision, args.warm_start, args.method):
+                continue
+            if wsn == "mlp" and mlp is None:
+                continue
+            step = make_step(topo, dev_in, out, prec, args.tol, wsn, mlp, lam0, meth)
+            msa, _ = time_device(step, max(3, args.steps // 4), 2, flush, stream)
+            ok, viol, it = check()
+            per = sum(msa) / len(msa)
+            ablation.append({"precision": prec, "warm_start": wsn, "method": meth, "ms_per_step": per,
+                             "value": s.n_atoms / (per * 1e-3), "all_converged": ok, "max_rel_violation": viol,
+                             "mean_iterations": float(it.mean())})
+            if (prec, wsn, meth) == ("fp64", "none", "newton"):
+                value64, per64 = s.n_atoms / (per * 1e-3), per
 
-    step = make_step(topo, dev_in, out, args.precision, args.tol, args.warm_start, mlp, lam0)
+    step = make_step(topo, dev_in, out, args.precision, args.tol, args.warm_start, mlp, lam0, args.method)
 
     def roll(seconds):  # keep the GPU busy with the same step (clock sampling window)
         t0 = time.perf_counter()
@@ -367,7 +383,8 @@ def run_ilves(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             topo.solve(*dev_in, tol=args.tol, precision=args.precision, lambda0=l0, x_out=out[0],
-                       lambda_out=out[1], iterations_out=out[2], status_out=out[3])
+                       lambda_out=out[1], iterations_out=out[2], status_out=out[3], method=args.method,
+                       max_iter=60 if args.method == "chord" else 25)
             e1.record(stream)
             torch.cuda.synchronize()
             solve_ms.append(e0.elapsed_time(e1))
@@ -436,9 +453,11 @@ def run_ilves(args):
             "workload": workload_name(s),
             "precision": args.precision,
             "warm_start": args.warm_start,
+            "method": {"newton": "ILVES-M (Newton)", "chord": "ILVES-F (chord)"}[args.method],
             "tol": args.tol,
             "l2": "flushed (256 MiB write) before every timed step",
-            "schedule": "persistent CTAs, one warp per molecule",
+            "schedule": ("cooperative CTAs over partitions + separator (Schur) block" if s.name == "protein_like"
+                         else "persistent CTAs, one warp per molecule"),
         },
         "valid": valid,
         "max_rel_violation": viol,
@@ -451,7 +470,8 @@ def run_ilves(args):
         "warm_start_training": mlp_info,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
-                     "kernel": "k_solve_small", "kernel_ms": solve_per},
+                     "kernel": "k_solve_small" if s.name != "protein_like" else "k_solve_parted",
+                     "kernel_ms": solve_per},
         "e2e": {"value": e2e_value, "unit": "atoms*solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_per},
         "gpu_launches": launches,

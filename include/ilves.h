@@ -86,6 +86,14 @@ typedef enum {
  *            stay float64. */
 typedef enum { ILVES_PREC_FP64 = 0, ILVES_PREC_MIXED = 1, ILVES_PREC_MIXED_DF = 2 } ilves_precision;
 
+/* Method flag, OR-ed into the precision argument of ilves_solve:
+ *  ILVES_CHORD selects ILVES-F (supplement Sec. 3, simplified Newton / chord method):
+ *  the symmetric matrix A(x_old, x_old) is factorised once per solve and reused by every
+ *  iteration, which then only substitutes forward and backward.  Convergence is linear,
+ *  so it needs more iterations than ILVES-M (the default, a fresh Newton matrix per
+ *  iteration) to reach the same tolerance. */
+#define ILVES_CHORD 256
+
 typedef struct {
     int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;
                                 2 = rounds of independent low-degree pivots with `degree_slack` */
@@ -131,7 +139,7 @@ ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const 
  *  d         DEVICE float64 (n_constraints): target distances d_k > 0.
  *  tol       relative tolerance on |sigma_k| / d_k^2 (e.g. 1e-12).
  *  max_iter  maximum number of linear solves per molecule (>= 0).
- *  precision one of ilves_precision.
+ *  precision one of ilves_precision, optionally OR-ed with ILVES_CHORD.
  *  lambda0   DEVICE float32 (n_constraints) initial multipliers, or NULL for zero.
  *  x_out     DEVICE float64 (n_atoms, 3): constrained positions (may alias x_unc).
  *  lambda_out DEVICE float64 (n_constraints): multipliers, or NULL.

@@ -18,6 +18,8 @@ What it computes (paper, supplement Sec. 2.2-2.3 and Sec. 4):
 * ILVES-M Newton iteration, Sec. 2.3 (Newton equations for the constraint equation):
   A(x(lambda_l), x_old) delta_l = sigma(x(lambda_l)),  lambda_{l+1} = lambda_l + delta_l
   (the paper writes z = -delta with its sign convention), started from lambda_0 = 0.
+* ILVES-F (``method="chord"``), supplement Sec. 3: the simplified Newton / chord method
+  with the constant symmetric matrix A(x_old, x_old), factorised once per solve.
 * Stopping rule, Sec. 4: stop when max_k |sigma_k| / d_k^2 <= tol or after max_iter
   linear solves.  The convergence test happens before each solve, so an already
   feasible x_unc needs 0 solves.
@@ -108,8 +110,8 @@ def newton_matrix(x, x_old, inv_mass, atom_i, atom_j):
     return (G @ Minv @ G0.T).tocsc()
 
 
-def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lambda0=None):
-    """ILVES-M exact Newton on every molecule; see the module docstring."""
+def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lambda0=None, method="newton"):
+    """ILVES-M exact Newton (or ILVES-F, method="chord") on every molecule; see the module docstring."""
     x_old = np.asarray(x_old, np.float64).reshape(-1, 3)
     x_unc = np.asarray(x_unc, np.float64).reshape(-1, 3)
     inv_mass = np.asarray(inv_mass, np.float64)
@@ -126,6 +128,11 @@ def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lam
     lam = np.zeros(n_c) if lambda0 is None else np.asarray(lambda0, np.float64).copy()
     active = np.ones(n_mol, bool)  # molecules still iterating
     history = []
+    chord_lu = None
+    if method == "chord":  # A(x_old, x_old), factorised once
+        chord_lu = spla.splu(newton_matrix(x_old, x_old, inv_mass, atom_i, atom_j), permc_spec="COLAMD")
+    elif method != "newton":
+        raise ValueError(method)
     for it in range(max_iter + 1):
         x = positions(lam, x_unc, inv_mass, G0)
         sigma = violation(x, atom_i, atom_j, d)
@@ -149,10 +156,14 @@ def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lam
             break
         # Newton step on the still-active molecules; finished ones keep lambda fixed
         row_active = active[mol]
-        A = newton_matrix(x, x_old, inv_mass, atom_i, atom_j)
-        A = _restrict(A, row_active)
         rhs = np.where(row_active, sigma, 0.0)
-        delta, singular_mols = _sparse_solve(A, rhs, mol, n_mol, row_active)
+        if chord_lu is not None:  # blocks are independent: finished molecules get delta = 0
+            delta = np.where(row_active, chord_lu.solve(rhs), 0.0)
+            singular_mols = np.zeros(n_mol, bool)
+        else:
+            A = newton_matrix(x, x_old, inv_mass, atom_i, atom_j)
+            A = _restrict(A, row_active)
+            delta, singular_mols = _sparse_solve(A, rhs, mol, n_mol, row_active)
         if singular_mols.any():
             status[singular_mols] = SINGULAR
             iters[singular_mols] = it

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libilves.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ilves.h")
 
 FP64, MIXED, MIXED_DF = 0, 1, 2
+CHORD = 256  # ILVES-F flag
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_df": MIXED_DF}
 CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE, WAIT_TIMEOUT = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid topology", 3: "CUDA error", 4: "out of device memory",
@@ -200,7 +201,7 @@ class Topology:
 
     def solve(self, x_old, x_unc, inv_mass, d, tol=1e-12, max_iter=25, precision="mixed", lambda0=None,
               x_out=None, lambda_out=None, iterations_out=None, status_out=None, stream=None,
-              _entry="ilves_solve"):
+              method="newton", _entry="ilves_solve"):
         """One ``ilves_solve`` on device tensors; returns (x, lambda, iterations, status)."""
         import torch
 
@@ -223,6 +224,10 @@ class Topology:
         status_out = torch.empty(self.n_molecules, dtype=torch.int32, device=dev) if status_out is None else status_out
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if method == "chord":
+            prec |= CHORD
+        elif method != "newton":
+            raise ValueError("method must be 'newton' (ILVES-M) or 'chord' (ILVES-F)")
         fn = getattr(lib(), _entry)
         _check(fn(self._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), float(tol), int(max_iter),
                   prec, None if lambda0 is None else _ptr(lambda0), _ptr(x_out), _ptr(lambda_out),

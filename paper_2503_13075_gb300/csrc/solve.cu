@@ -171,6 +171,7 @@ struct SolveArgs {
     const int32_t* atom_gid;
     double tol;
     int32_t max_iter;
+    int32_t chord;  // ILVES-F: factorise A(x_old, x_old) once, reuse it every iteration
 };
 
 // ------------------------------------------------------------------------------------
@@ -455,6 +456,21 @@ struct MolView {
         }
     }
 
+    // ---- forward S5 alone (ILVES-F iterations after the first): y_p -= sum_m L[p,m] y_m,
+    //      with the terms of pivot p's DIAG task t
+    __device__ __forceinline__ void forward(int t, int p) {
+        const int e0 = ldp<kCoh>(tasks + t).tstart, e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        LP yv = LP(0);
+        for (int e = e0; e < e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            yv += lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(INV + m) * lds<kCoh>(Y + m);
+        }
+        Y[p] = lds<kCoh>(Y + p) - yv;
+    }
+    // ILVES-F assembles A(x_old, x_old): the Jacobian rows are the reference bonds
+    __device__ __forceinline__ void chord_rows(int p) { RF[p] = lds<kCoh>(RHOF + p); }
+
     // ---- backward S5 for pivot p: delta_p = inv_p (y_p - sum_q U[p,q] delta_q)
     __device__ __forceinline__ void backward(int p) {
         const Piv<IdxT> pv = ldp<kCoh>(piv + p);
@@ -527,18 +543,30 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
         }
         if (it >= A.max_iter) break;
         tm.sync();
-        // one pass per level; the first np tasks of a level are its DIAG tasks
-        bool singular = false;
-        for (int l = 0; l < D.nlevel; ++l) {
-            const int p0 = M.lvl_piv[l], np = M.lvl_piv[l + 1] - p0;
-            const int t0 = M.lvl_task[l], t1 = M.lvl_task[l + 1];
-            for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
-            tm.sync();
-        }
-        if (tm.any(singular)) {
-            status = ILVES_MOL_SINGULAR_PIVOT;
-            iters = it;
-            break;
+        if (!A.chord || it == 0) {
+            if (A.chord) {  // ILVES-F: factorise A(x_old, x_old) once
+                for (int p = r0; p < nc; p += ts) M.chord_rows(p);
+                tm.sync();
+            }
+            // one pass per level; the first np tasks of a level are its DIAG tasks
+            bool singular = false;
+            for (int l = 0; l < D.nlevel; ++l) {
+                const int p0 = M.lvl_piv[l], np = M.lvl_piv[l + 1] - p0;
+                const int t0 = M.lvl_task[l], t1 = M.lvl_task[l + 1];
+                for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                tm.sync();
+            }
+            if (tm.any(singular)) {
+                status = ILVES_MOL_SINGULAR_PIVOT;
+                iters = it;
+                break;
+            }
+        } else {  // ILVES-F: forward substitution with the stored factor
+            for (int l = 0; l < D.nlevel; ++l) {
+                const int p0 = M.lvl_piv[l], p1 = M.lvl_piv[l + 1], t0 = M.lvl_task[l];
+                for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
+                tm.sync();
+            }
         }
         for (int l = D.nlevel - 1; l >= 0; --l) {
             const int p1 = M.lvl_piv[l + 1];
@@ -669,15 +697,23 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             break;
         }
         if (it >= A.max_iter) break;
+        const bool factor = !A.chord || it == 0;
+        if (A.chord && it == 0) {  // ILVES-F: assemble A(x_old, x_old) (rows of owned constraints)
+            for_owned([&](int p) { M.chord_rows(p); });
+            if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+        }
         // ---- phase A: every part factorises its interior (and its rows/columns towards
-        //      the separators) level by level
+        //      the separators) level by level; ILVES-F iterations only substitute forward
         bool singular = false;
         for (int q = b; q < n_parts; q += G) {
             const int l0 = __ldg(&seg[q].lvl), l1 = __ldg(&seg[q + 1].lvl) - 1;
             for (int l = l0; l < l1; ++l) {
-                const int p0 = __ldg(M.lvl_piv + l), np = __ldg(M.lvl_piv + l + 1) - p0;
+                const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
                 const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
-                for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                if (factor)
+                    for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                else
+                    for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
                 __syncthreads();
             }
         }
@@ -689,9 +725,12 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             bool sing = false;
             const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
             for (int l = l0; l < l1; ++l) {
-                const int p0 = __ldg(M.lvl_piv + l), np = __ldg(M.lvl_piv + l + 1) - p0;
+                const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
                 const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
-                for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, sing);
+                if (factor)
+                    for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, sing);
+                else
+                    for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
                 __syncthreads();
             }
             if (__syncthreads_or(sing) && r0 == 0) atomicOr(&sync->singular[slot], 1);
@@ -1142,9 +1181,10 @@ extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, cons
     A.atom_gid = T->d_atom_gid;
     A.tol = tol;
     A.max_iter = max_iter;
+    A.chord = (precision & ILVES_CHORD) ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
-    switch (precision) {
+    switch (precision & ~ILVES_CHORD) {
         case ILVES_PREC_FP64: return launch_mode<ModeFP64>(T, A, s);
         case ILVES_PREC_MIXED: return launch_mode<ModeMixed>(T, A, s);
         case ILVES_PREC_MIXED_DF: return launch_mode<ModeMixedDF>(T, A, s);
@@ -1161,7 +1201,8 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     if (max_iter < 0 || !(tol >= 0.0)) return ILVES_ERR_INVALID_ARG;
     if (T->n_atoms > 0 && (!x_old || !x_unc || !inv_mass || !x_out)) return ILVES_ERR_INVALID_ARG;
     if (T->n_c > 0 && !d) return ILVES_ERR_INVALID_ARG;
-    if (precision < ILVES_PREC_FP64 || precision > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
+    const int32_t prec_mode = precision & ~ILVES_CHORD;
+    if (prec_mode < ILVES_PREC_FP64 || prec_mode > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
     const uint64_t work_aligned = ((uint64_t)T->work_bytes + 255) & ~uint64_t(255);
     if (work_aligned + (uint64_t)T->sync_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
     int dev = -1;
@@ -1183,10 +1224,11 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     A.atom_gid = T->d_atom_gid;
     A.tol = tol;
     A.max_iter = max_iter;
+    A.chord = (precision & ILVES_CHORD) ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
     uint8_t* sync = scratch + work_aligned;
-    switch (precision) {
+    switch (prec_mode) {
         case ILVES_PREC_FP64: return launch_all<ModeFP64>(T, A, s, scratch, sync);
         case ILVES_PREC_MIXED: return launch_all<ModeMixed>(T, A, s, scratch, sync);
         default: return launch_all<ModeMixedDF>(T, A, s, scratch, sync);

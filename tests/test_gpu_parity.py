@@ -198,3 +198,27 @@ def test_repeated_solves_are_deterministic(trees):
     for prec in PRECS:
         outs = [run(s, prec, topo=t)[1] for _ in range(3)]
         assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["chain64", "trees", "protein_parted"])
+def test_chord_method_ilves_f(prec, case):
+    """ILVES-F: same root as the Newton oracle; iterations within +-1 of the chord oracle."""
+    if case == "chain64":
+        s = wl.chain64()
+        topo = None
+    elif case == "trees":
+        s = wl.tree_batch(n_mol=128, seed=1001)
+        topo = None
+    else:
+        s = wl.protein_like(n_atoms=12000, seed=1002)
+        topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000)
+        assert topo.n_large == 1
+    ref = orc.solve_system(s, tol=TOL)
+    ref_chord = orc.solve_system(s, tol=TOL, max_iter=60, method="chord")
+    t, x, lam, it, st = run(s, prec, topo=topo, method="chord", max_iter=60)
+    assert np.all(st == B.CONVERGED)
+    assert np.abs(it - ref_chord.iterations).max() <= 1
+    assert np.abs(x - ref.x).max() <= X_TOL
+    assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL
+    assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())

@@ -294,3 +294,20 @@ def test_pendulum_energy_error_matches_paper():
     # second order in h: halving h divides the error by ~4
     for a, b in zip(errs, errs[1:]):
         assert 3.6 < a / b < 4.4
+
+
+# ---------------------------------------------------------------------------- ILVES-F
+@pytest.mark.parametrize("maker", [wl.chain64, lambda: wl.tree_batch(n_mol=30, seed=7)])
+def test_chord_method_reaches_the_newton_root_linearly(maker):
+    """ILVES-F (supplement Sec. 3): same equations, same root; linear convergence."""
+    s = maker()
+    newton = orc.solve_system(s, tol=1e-13)
+    chord = orc.solve_system(s, tol=1e-13, max_iter=60, method="chord")
+    assert np.all(chord.status == orc.CONVERGED)
+    assert np.abs(chord.x - newton.x).max() <= 1e-10
+    np.testing.assert_allclose(chord.lam, newton.lam, rtol=1e-7, atol=1e-14)
+    assert chord.iterations.mean() > newton.iterations.mean()
+    if s.n_molecules == 1:  # linear: successive error ratios stay bounded below 1
+        h = [e for e in chord.history if e > 1e-12]
+        ratios = [b / a for a, b in zip(h, h[1:])]
+        assert max(ratios[1:]) < 0.5
