@@ -41,7 +41,9 @@
  *    reaches that point.
  *  - Return values report argument and launch failures only.  Numerical
  *    failures are reported per molecule in mol_status_out.
- *  - Functions are not thread-safe on the same topology object.
+ *  - Functions are not thread-safe on the same topology object, and the solves of one
+ *    topology must be ordered on one stream (large molecules use the topology's workspace);
+ *    solves of different topologies may run concurrently on different streams.
  */
 #ifndef ILVES_H
 #define ILVES_H
@@ -182,6 +184,9 @@ ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_ol
                                         int32_t max_iter, int32_t precision, const float* lambda0,
                                         double* x_out, double* lambda_out, int32_t* iterations_out,
                                         int32_t* mol_status_out, void* stream);
+
+/* Device memory (bytes) a set-up topology holds: programs, schedules, workspaces. */
+int64_t ilves_topology_device_bytes(const ilves_topology* topo);
 
 /* Size in bytes of the static scratch array used by ilves_solve_static_scratch. */
 int64_t ilves_static_scratch_bytes(void);

@@ -77,6 +77,8 @@ def lib():
     L.ilves_static_scratch_bytes.restype = I64
     L.ilves_topology_workspace_bytes.argtypes = [P]
     L.ilves_topology_workspace_bytes.restype = I64
+    L.ilves_topology_device_bytes.argtypes = [P]
+    L.ilves_topology_device_bytes.restype = I64
     L.ilves_mlp_param_count.argtypes = []
     L.ilves_mlp_param_count.restype = I64
     L.ilves_mlp_create.argtypes = [I32, ctypes.c_uint64, ctypes.POINTER(P)]
@@ -189,6 +191,9 @@ class Topology:
 
     def last_launch_count(self):
         return int(lib().ilves_last_launch_count(self._h))
+
+    def device_bytes(self):
+        return int(lib().ilves_topology_device_bytes(self._h))
 
     def workspace_bytes(self):
         return int(lib().ilves_topology_workspace_bytes(self._h))

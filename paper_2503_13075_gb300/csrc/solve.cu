@@ -1237,6 +1237,17 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
 
 extern "C" int64_t ilves_static_scratch_bytes(void) { return (int64_t)kStaticScratchBytes; }
 
+extern "C" int64_t ilves_topology_device_bytes(const ilves_topology* T) {
+    if (!T || !T->on_device) return 0;
+    int64_t b = T->blob_bytes + (int64_t)T->n_mol * (int64_t)sizeof(MolDesc) + T->work_bytes + T->sync_bytes;
+    b += 4 * (int64_t)T->n_atoms;                        // atom ids
+    b += 4 * (int64_t)T->free_atoms.size();
+    b += (int64_t)T->n_c * (4 + 4 + 16 + 16 + 32);      // atoms, neighbour table, warm-start workspace
+    b += 4 * (int64_t)T->n_atoms;                        // warm-start atom weights
+    for (const auto& sc : T->sched) b += 4 * (int64_t)(2 * sc.n_cta + 2 * T->n_small + 64);
+    return b;
+}
+
 extern "C" int64_t ilves_topology_workspace_bytes(const ilves_topology* T) {
     return T ? ((T->work_bytes + 255) & ~int64_t(255)) + T->sync_bytes : 0;
 }
