@@ -159,33 +159,21 @@ class ClockSampler:
 
 
 def dist_setup(args):
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2503_13075_gb300 import multirank as mr
 
-        backend = "nccl" if args.impl == "ilves" else "gloo"
-        dist.init_process_group(backend=backend)
-    return rank, world, local
+    return mr.init("nccl" if args.impl == "ilves" else "gloo")
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2503_13075_gb300 import multirank as mr
 
-        dist.barrier()
+    mr.barrier(world)
 
 
 def max_over_ranks(v, world, device=None):
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
+    from paper_2503_13075_gb300 import multirank as mr
 
-    t = torch.tensor([v], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return mr.max_over_ranks(v, world, device)
 
 
 def cpu_oracle_rate(s_full, budget_s=12.0, seed=0):
