@@ -18,6 +18,8 @@ a bounded sample of the same workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -44,6 +46,7 @@ def parse():
     p.add_argument("--impl", default="ilves", choices=["ilves", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "mixed_df"])
     p.add_argument("--n-mol", type=int, default=4096)
+    p.add_argument("--n-atoms", type=int, default=100_000, help="protein_like: atoms of the connected system")
     p.add_argument("--tol", type=float, default=1e-12)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -60,11 +63,11 @@ def parse():
     return p.parse_args()
 
 
-def workload(name, n_mol, seed):
+def workload(name, n_mol, seed, n_atoms=100_000):
     from paper_2503_13075_gb300 import workloads as wl
 
     if name == "protein_like":
-        return wl.protein_like(seed=1002 + (seed - 1001))
+        return wl.protein_like(n_atoms=n_atoms, seed=1002 + (seed - 1001))
     if name == "chain64":
         return wl.chain64(seed=1000 + (seed - 1001))
     return wl.tree_batch(n_mol=n_mol, seed=seed)
@@ -81,8 +84,37 @@ def workload_name(s):
 
 
 def algorithmic_bytes(s):
-    """Compulsory HBM traffic of one solve: x_old, x_unc, inv_mass, d in; x, lambda, status out."""
-    return 80 * s.n_atoms + 16 * s.n_constraints + 8 * s.n_molecules
+    """Compulsory HBM traffic of one solve: x_old, x_unc, inv_mass (56 B/atom), d and the
+    constrained pair (16 B/constraint) in; x (24 B/atom), lambda (8 B/constraint),
+    iterations and status (8 B/molecule) out."""
+    return 80 * s.n_atoms + 24 * s.n_constraints + 8 * s.n_molecules
+
+
+KERNEL_SOURCES = ("solve.cu", "internal.h", "devmath.cuh", "topology.cpp", "topology_impl.h")
+
+
+def kernel_sources_digest():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2503_13075_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, precision, n_atoms):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries in profiles/
+    (`traffic-record:` lines), scaled by atoms to this workload; None when no record
+    matches or the kernel sources changed since the counters were taken."""
+    digest = kernel_sources_digest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(tok.split("=", 1) for tok in line.split()[1:])
+                if kv.get("kernel") == kernel and kv.get("mode") == precision and kv.get("sources") == digest:
+                    return float(kv["dram_bytes"]) * n_atoms / float(kv["atoms"]), os.path.basename(path)
+    return None, None
 
 
 def max_rel_violation(x, atom_i, atom_j, d):
@@ -205,7 +237,7 @@ def run_reference(args):
     rank, world, local = dist_setup(args)
     if rank != 0:
         return
-    s = workload(args.workload, args.n_mol, 1001)
+    s = workload(args.workload, args.n_mol, 1001, args.n_atoms)
     from oracle import ilves_oracle as orc
     from paper_2503_13075_gb300 import workloads as wl
 
@@ -307,7 +339,7 @@ def run_ilves(args):
     dev = torch.device("cuda", local)
     from paper_2503_13075_gb300 import binding as B
 
-    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank)  # weak scaling: every rank its own batch
+    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank, args.n_atoms)  # weak scaling: every rank its own batch
     topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
     f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     dev_in = (f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d))
@@ -430,6 +462,8 @@ def run_ilves(args):
     ab = algorithmic_bytes(s)
     solve_per = sum(solve_ms) / len(solve_ms)
     achieved = ab / (solve_per * 1e-3) / 1e9
+    kname = "k_solve_parted" if s.name == "protein_like" else "k_solve_small"
+    traffic, traffic_src = (None, None) if args.method != "newton" else measured_traffic(kname, args.precision, s.n_atoms)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt, sample = cpu_oracle_rate(s)
@@ -470,8 +504,8 @@ def run_ilves(args):
         "ablation": ablation,
         "warm_start_training": mlp_info,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
-                     "kernel": "k_solve_small" if s.name != "protein_like" else "k_solve_parted",
+                     "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
+                     "kernel": kname,
                      "kernel_ms": solve_per},
         "e2e": {"value": e2e_value, "unit": "atoms*solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_per},

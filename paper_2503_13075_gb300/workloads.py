@@ -440,6 +440,24 @@ def protein_like(n_atoms: int = 100_000, seed: int = 1002, sigma: float = 0.004)
     return s
 
 
+def benzene_batch(n_mol: int = 64, seed: int = 1005, sigma: float = 0.003, box: float = 6.0) -> System:
+    """Benzene-like rings: six carbons in a planar hexagon (C-C 0.139 nm) with six
+    hydrogens (C-H 0.109 nm); all 12 bonds constrained (6-cycles in the constraint graph,
+    like the paper's pure-benzene system, supplement Sec. 6)."""
+    rng = np.random.default_rng(seed)
+    mols = []
+    for _ in range(n_mol):
+        q, _r = np.linalg.qr(rng.normal(size=(3, 3)))
+        ang = np.arange(6) * np.pi / 3.0
+        ring = np.stack([np.cos(ang), np.sin(ang), np.zeros(6)], axis=1)
+        pos = np.concatenate([0.139 * ring, (0.139 + 0.109) * ring]) @ q.T
+        elem = ["C"] * 6 + ["H"] * 6
+        bonds = [(k, (k + 1) % 6, 0.139) for k in range(6)] + [(k, k + 6, 0.109) for k in range(6)]
+        bonds = [(min(a, b), max(a, b), ln) for a, b, ln in bonds]
+        mols.append((elem, bonds, pos))
+    return _exact_lengths(_assemble(f"benzene{n_mol}", mols, rng, sigma, seed, box))
+
+
 def serving_sizes(n_req: int, seed: int, lo: int = 20, hi: int = 50_000) -> np.ndarray:
     """Log-uniform request sizes (atoms) for the serving loop."""
     rng = np.random.default_rng(seed)

@@ -182,3 +182,13 @@ def test_partitioned_molecule_structure():
         return next((k for k, (lo, hi) in enumerate(blocks) if lo <= a <= hi), -1)
     for p in range(starts[-2], nc):  # separators cross blocks (or touch a block-less atom)
         assert block_of(ai[p]) != block_of(aj[p]) or block_of(ai[p]) == -1
+
+
+def test_symbolic_factorisation_benzene_rings():
+    """6-cycles (benzene-like rings): closure and pattern checks with fill."""
+    rng = np.random.default_rng(4)
+    s = wl.benzene_batch(n_mol=3)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
+    assert t.n_molecules == 3 and t.n_fill > 0
+    for m in range(3):
+        _check_molecule(t, s, m, rng)
