@@ -278,6 +278,22 @@ ilves_status ilves_topology_molecules(const ilves_topology* topo, int32_t* atoms
 ilves_status ilves_topology_export_molecule(const ilves_topology* topo, int32_t mol, int32_t* pos_gid,
                                             int32_t* level, int32_t* up_ptr, int32_t* up_idx);
 
+/* Host-side plan of the batched kernel's warp-slot schedule for one precision mode
+ * (ILVES_PREC_*), as it would be built for a grid of n_cta CTAs with arena_bytes of
+ * shared memory each; no device is needed (introspection and tests).  Outputs (any may
+ * be NULL): n_slots, pool_n (molecules drawn at run time from the shared pool);
+ * per slot (HOST arrays of n_slots entries; call once with them NULL to size them):
+ * slot_cta (CTA of the slot), slot_bytes (its shared-memory slice), slot_queue (number
+ * of statically queued molecules); per molecule (n_molecules entries): mol_slot (slot
+ * whose queue holds it, -1 for the pool, -2 for molecules off the warp path) and
+ * mol_bytes (its shared-memory footprint in this mode, 0 off the warp path).  No
+ * counterpart in the paper: the schedule is this library's batching of independent
+ * molecules. */
+ilves_status ilves_topology_schedule(const ilves_topology* topo, int32_t precision, int32_t n_cta,
+                                     int32_t arena_bytes, int32_t* n_slots, int32_t* pool_n,
+                                     int32_t* slot_cta, int32_t* slot_bytes, int32_t* slot_queue,
+                                     int32_t* mol_slot, int32_t* mol_bytes);
+
 /* Releases every device and host buffer of the topology (NULL is ignored). */
 void ilves_destroy_topology(ilves_topology* topo);
 

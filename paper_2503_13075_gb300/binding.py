@@ -65,6 +65,8 @@ def lib():
     L.ilves_topology_molecules.restype = I32
     L.ilves_topology_export_molecule.argtypes = [P, I32, P, P, P, P]
     L.ilves_topology_export_molecule.restype = I32
+    L.ilves_topology_schedule.argtypes = [P, I32, I32, I32, P, P, P, P, P, P, P]
+    L.ilves_topology_schedule.restype = I32
     L.ilves_destroy_topology.argtypes = [P]
     L.ilves_destroy_topology.restype = None
     L.ilves_status_string.argtypes = [I32]
@@ -188,6 +190,24 @@ class Topology:
         idx = np.zeros(max(1, int(ptr[-1])), np.int32)
         _check(L.ilves_topology_export_molecule(self._h, int(mol), None, None, None, _ptr(idx)), "export")
         return pos, lev, ptr, idx[: ptr[-1]]
+
+    def schedule(self, precision="mixed", n_cta=152, arena_bytes=232448):
+        """Host plan of the batched kernel's warp slots (``ilves_topology_schedule``):
+        dict with slot_cta, slot_bytes, slot_queue (per slot), mol_slot (slot, -1 pool,
+        -2 off the warp path) and mol_bytes (per molecule), and pool_n."""
+        L = lib()
+        prec = PRECISIONS[precision]
+        ns, pn = ctypes.c_int32(), ctypes.c_int32()
+        _check(L.ilves_topology_schedule(self._h, prec, int(n_cta), int(arena_bytes), ctypes.byref(ns),
+                                         ctypes.byref(pn), None, None, None, None, None), "ilves_topology_schedule")
+        out = {k: np.zeros(ns.value, np.int32) for k in ("slot_cta", "slot_bytes", "slot_queue")}
+        out.update({k: np.zeros(self.n_molecules, np.int32) for k in ("mol_slot", "mol_bytes")})
+        _check(L.ilves_topology_schedule(self._h, prec, int(n_cta), int(arena_bytes), None, None,
+                                         *[_ptr(out[k]) for k in ("slot_cta", "slot_bytes", "slot_queue",
+                                                                  "mol_slot", "mol_bytes")]),
+               "ilves_topology_schedule")
+        out["pool_n"] = pn.value
+        return out
 
     def last_launch_count(self):
         return int(lib().ilves_last_launch_count(self._h))

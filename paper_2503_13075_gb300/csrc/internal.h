@@ -101,10 +101,14 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
 // size (4 for float32, 8 for float64); 3-vectors of the factor precision are padded to 4
 // elements.  Atom arrays have na + 1 entries: the extra atom has zero weight and is what
 // fill entries of the pattern point at.  The factor-precision weight array `wl` continues
-// with one entry per constraint, w_i + w_j, which DIAG tasks use as their "shared atom".  With `disp` the state keeps displacements
-// x - x_unc and the per-constraint differences s_k = x_unc,i - x_unc,j.
+// with one entry per constraint, w_i + w_j, which DIAG tasks use as their "shared atom".
+// With `disp` the state keeps displacements x - x_unc and the per-constraint differences
+// s_k = x_unc,i - x_unc,j.
+// `stage` (= rf, up to the end) is free until the first violation pass: the warp path
+// gathers x_old there (AoS, 24 B per atom) while it sets the molecule up; the region is
+// extended when the arrays after rf are smaller than that.
 struct StateLayout {
-    uint32_t x, w, wl, rho, s, d2, lam, rhof, rf, inv, y, vals, bytes;
+    uint32_t x, w, wl, rho, s, d2, lam, rhof, y, rf, inv, vals, stage, bytes;
 };
 
 ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t lp_bytes, bool disp) {
@@ -119,11 +123,13 @@ ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint
     S.d2 = o;     o = align16(o + 8u * nc);
     S.lam = o;    o = align16(o + 8u * nc);
     S.rhof = o;   o = align16(o + vp * nc);
+    S.y = o;      o = align16(o + (lp_bytes > 4u ? lp_bytes : 4u) * nc);
     S.rf = o;     o = align16(o + vp * nc);
     S.inv = o;    o = align16(o + lp_bytes * nc);
-    S.y = o;      o = align16(o + lp_bytes * nc);
     S.vals = o;   o = align16(o + lp_bytes * ntask);
-    S.bytes = o;
+    S.stage = S.rf;
+    const uint32_t stage_end = align16(S.stage + 24u * na);
+    S.bytes = o > stage_end ? o : stage_end;
     return S;
 }
 

@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ilves.h"
@@ -158,6 +159,25 @@ struct BlockTeam {
     __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
 };
 
+// Asynchronous global -> shared copies (cp.async): every copy of a batch is in flight at
+// once and lands without passing through registers; wait_all + a team barrier makes the
+// batch visible.  Both addresses are aligned to the copy size.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// hint: bring the 128-byte line holding p into L2 (no register, no fault on a valid address)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 struct SolveArgs {
     const double* x_old;
     const double* x_unc;
@@ -235,6 +255,7 @@ struct MolView {
     double *X, *W, *RHO, *SK, *D2, *LAM;
     LP *WL, *INV, *Y, *V;
     V4 *RHOF, *RF;
+    double* STG;  // x_old gathered AoS (warp path set-up only; aliases RF and later arrays)
     const MolDesc* D;
     const SolveArgs* A;
 
@@ -267,6 +288,7 @@ struct MolView {
         INV = reinterpret_cast<LP*>(st + SL.inv);
         Y = reinterpret_cast<LP*>(st + SL.y);
         V = reinterpret_cast<LP*>(st + SL.vals);
+        STG = reinterpret_cast<double*>(st + SL.stage);
     }
     __device__ __forceinline__ int64_t gid(int a) const {
         return D->atom_base >= 0 ? (int64_t)D->atom_base + a : (int64_t)A->atom_gid[D->gid_off + a];
@@ -343,6 +365,62 @@ struct MolView {
             X[na + a] = A->x_unc[3 * g + 1];
             X[2 * na + a] = A->x_unc[3 * g + 2];
         }
+    }
+
+    // ---- S1, shared-memory state: one batch of asynchronous gathers, then local passes.
+    // x_old -> STG (AoS); x_unc -> X (SoA; AoS in the float-float mode, where X is free
+    // until the displacements start); inv_mass -> W, d -> D2, lambda0 -> Y as raw values.
+    __device__ __forceinline__ void s1_gather(int r0, int ts) {
+        for (int e = r0; e < 3 * na; e += ts) {
+            const int a = e / 3, c = e - 3 * a;
+            const int64_t g = 3 * gid(a) + c;
+            cp_async8(STG + e, A->x_old + g);
+            cp_async8(DF ? X + e : X + c * na + a, A->x_unc + g);
+        }
+        for (int a = r0; a < na; a += ts) cp_async8(W + a, A->inv_mass + gid(a));
+        for (int p = r0; p < nc; p += ts) {
+            const int32_t g = ldp<kCoh>(con_gid + p);
+            cp_async8(D2 + p, A->d + g);
+            if (A->lambda0) cp_async4(reinterpret_cast<float*>(Y + p), A->lambda0 + g);
+        }
+        cp_async_wait_all();
+    }
+    __device__ __forceinline__ void s1_atom_local(int a) {
+        const double w = lds<kCoh>(W + a);
+        if constexpr (DF) W[a] = as_bits(df_split(w));
+        WL[a] = to_lp<LP>(w);
+    }
+    __device__ __forceinline__ void s1_constraint_local(int p) {
+        const ConA<IdxT> c = cons(p);
+        const int i = c.i, j = c.j;
+        const double rx = lds<kCoh>(STG + 3 * i) - lds<kCoh>(STG + 3 * j);
+        const double ry = lds<kCoh>(STG + 3 * i + 1) - lds<kCoh>(STG + 3 * j + 1);
+        const double rz = lds<kCoh>(STG + 3 * i + 2) - lds<kCoh>(STG + 3 * j + 2);
+        V4 v;
+        v.x = to_lp<LP>(rx);
+        v.y = to_lp<LP>(ry);
+        v.z = to_lp<LP>(rz);
+        v.w = LP(0);
+        RHOF[p] = v;
+        const double dd = lds<kCoh>(D2 + p);
+        if constexpr (DF) {
+            RHO[p] = as_bits(df_split(rx));
+            RHO[nc + p] = as_bits(df_split(ry));
+            RHO[2 * nc + p] = as_bits(df_split(rz));
+            D2[p] = as_bits(df_split(dd * dd));
+            SK[p] = as_bits(df_split(lds<kCoh>(X + 3 * i) - lds<kCoh>(X + 3 * j)));
+            SK[nc + p] = as_bits(df_split(lds<kCoh>(X + 3 * i + 1) - lds<kCoh>(X + 3 * j + 1)));
+            SK[2 * nc + p] = as_bits(df_split(lds<kCoh>(X + 3 * i + 2) - lds<kCoh>(X + 3 * j + 2)));
+        } else {
+            RHO[p] = rx;
+            RHO[nc + p] = ry;
+            RHO[2 * nc + p] = rz;
+            D2[p] = dd * dd;
+        }
+        WL[na + 1 + p] = lds<kCoh>(WL + i) + lds<kCoh>(WL + j);
+        const float l0 = A->lambda0 ? lds<kCoh>(reinterpret_cast<const float*>(Y + p)) : 0.0f;
+        LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
+        Y[p] = (LP)l0;
     }
 
     // ---- S6: x_a -= w_a sum_k s_k(a) 2 Y_k rho_k   (Y holds delta, or lambda0)
@@ -516,13 +594,27 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
     const int na = D.na, nc = D.nc;
     const int r0 = tm.rank(), ts = tm.size();
     // ---- S1
-    for (int a = r0; a < na; a += ts) M.s1_atom(a, true);
-    if (r0 == 0) M.s1_dummy();
-    tm.sync();
-    for (int p = r0; p < nc; p += ts) M.s1_constraint(p, true);
-    tm.sync();
-    for (int a = r0; a < na; a += ts) M.s1_atom_unc(a);
-    tm.sync();
+    if constexpr (std::is_same<Team, WarpTeam>::value) {
+        M.s1_gather(r0, ts);
+        tm.sync();
+        for (int a = r0; a < na; a += ts) M.s1_atom_local(a);
+        if (r0 == 0) M.s1_dummy();
+        tm.sync();
+        for (int p = r0; p < nc; p += ts) M.s1_constraint_local(p);
+        tm.sync();
+        if constexpr (Mode::df) {
+            for (int a = r0; a < na; a += ts) M.s1_atom_unc(a);
+            tm.sync();
+        }
+    } else {
+        for (int a = r0; a < na; a += ts) M.s1_atom(a, true);
+        if (r0 == 0) M.s1_dummy();
+        tm.sync();
+        for (int p = r0; p < nc; p += ts) M.s1_constraint(p, true);
+        tm.sync();
+        for (int a = r0; a < na; a += ts) M.s1_atom_unc(a);
+        tm.sync();
+    }
     if (A.lambda0) {  // x = x_unc - M^-1 G(x_old)^T lambda0
         for (int a = r0; a < na; a += ts) M.update_atom(a);
         tm.sync();
@@ -779,12 +871,25 @@ struct SmallSched {
     const int32_t* slot_ptr;
     const int32_t* slot_mol;
     const int32_t* slot_off;
+    const int32_t* pool_mol;
+    uint32_t* pool_ctr;  // {next ticket, slots done}
+    int32_t pool_n, n_slots;
 };
 
 // Persistent batched kernel: warp w of CTA c owns one slot (a fixed slice of the CTA's
-// shared-memory arena) and solves its queue of molecules one after the other; warps
-// never wait for each other.  Each molecule's program blob is staged into the slice
-// with 16-byte loads before its Newton loop.
+// shared-memory arena), solves its queue of molecules one after the other, then draws
+// molecules from the shared pool (one atomic ticket each) until the pool is empty; warps
+// never wait for each other.  Each molecule's program blob is staged into the slice with
+// asynchronous 16-byte copies, and the next queued molecule's program and atom inputs
+// are prefetched into L2 while the current one is solved.  The last warp to finish
+// resets the pool counters for the next launch.
+__device__ __forceinline__ int pool_ticket(const SmallSched& S) {
+    unsigned t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(S.pool_ctr, 1u);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    return t < (unsigned)S.pool_n ? __ldg(S.pool_mol + t) : -1;
+}
+
 template <class Mode>
 __global__ void __launch_bounds__(512, 1)
 k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
@@ -796,25 +901,46 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
     if (slot >= S.cta_slot_ptr[blockIdx.x + 1]) return;
     uint8_t* slice = arena + S.slot_off[slot];
     const int q1 = S.slot_ptr[slot + 1];
-    for (int q = S.slot_ptr[slot]; q < q1; ++q) {
-        const MolDesc D = desc[S.slot_mol[q]];
+    int q = S.slot_ptr[slot];
+    int mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S) : -1);
+    while (mol >= 0) {
+        const MolDesc D = desc[mol];
         const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg);
         const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
         uint4* dst = reinterpret_cast<uint4*>(slice);
         const int n16 = (int)(PL.bytes >> 4);
-        int k = lane;
-        for (; k + 96 < n16; k += 128) {  // four independent 16-byte loads in flight per lane
-            const uint4 a0 = __ldg(src + k), a1 = __ldg(src + k + 32), a2 = __ldg(src + k + 64),
-                        a3 = __ldg(src + k + 96);
-            dst[k] = a0;
-            dst[k + 32] = a1;
-            dst[k + 64] = a2;
-            dst[k + 96] = a3;
+        for (int k = lane; k < n16; k += 32) cp_async16(dst + k, src + k);  // all in flight
+        if (q + 1 < q1) {  // the next queued molecule's program and atom inputs into L2 meanwhile
+            const MolDesc Dn = desc[S.slot_mol[q + 1]];
+            const uint32_t nb = prog_layout<uint16_t>(Dn.na, Dn.nc, Dn.ntask, Dn.nterm, Dn.nlevel, Dn.n_seg).bytes;
+            const uint8_t* pb = blob + Dn.blob_off;
+            for (uint32_t o = 128u * lane; o < nb; o += 4096u) prefetch_l2(pb + o);
+            if (Dn.atom_base >= 0) {
+                const uint8_t* xo = reinterpret_cast<const uint8_t*>(A.x_old + 3 * (int64_t)Dn.atom_base);
+                const uint8_t* xu = reinterpret_cast<const uint8_t*>(A.x_unc + 3 * (int64_t)Dn.atom_base);
+                const uint8_t* wm = reinterpret_cast<const uint8_t*>(A.inv_mass + Dn.atom_base);
+                for (uint32_t o = 128u * lane; o < 24u * (uint32_t)Dn.na; o += 4096u) {
+                    prefetch_l2(xo + o);
+                    prefetch_l2(xu + o);
+                }
+                for (uint32_t o = 128u * lane; o < 8u * (uint32_t)Dn.na; o += 4096u) prefetch_l2(wm + o);
+            }
         }
-        for (; k < n16; k += 32) dst[k] = __ldg(src + k);
+        cp_async_wait_all();
         __syncwarp();
         solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.bytes, A);
         __syncwarp();
+        ++q;
+        mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S) : -1);
+    }
+    if (S.pool_n > 0 && lane == 0) {
+        __threadfence();  // this warp's last ticket is ordered before its "done"
+        const unsigned done = atomicAdd(S.pool_ctr + 1, 1u);
+        if (done == (unsigned)S.n_slots - 1u) {  // every warp has drawn its last ticket
+            __threadfence();
+            atomicExch(S.pool_ctr, 0u);
+            atomicExch(S.pool_ctr + 1, 0u);
+        }
     }
 }
 
@@ -872,6 +998,8 @@ static void free_device(ilves_topology* T) {
         f(s.slot_ptr);
         f(s.slot_mol);
         f(s.slot_off);
+        f(s.pool_mol);
+        f(s.pool_ctr);
         s = DeviceSchedule{};
     }
     if (T->side_stream) cudaStreamDestroy((cudaStream_t)T->side_stream);
@@ -993,10 +1121,17 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         HostSchedule HS;
         build_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
         for (auto& km : HS.slot_mol) km = desc_index[km];
+        for (auto& km : HS.pool_mol) km = desc_index[km];
         DeviceSchedule& DS = T->sched[mode];
         DS.n_cta = HS.n_cta;
         DS.warps = HS.warps;
         DS.arena = HS.arena;
+        DS.n_slots = (int32_t)HS.slot_off.size();
+        DS.pool_n = (int32_t)HS.pool_mol.size();
+        if (!HS.pool_mol.empty()) {
+            if ((e = upload(&DS.pool_mol, HS.pool_mol)) != cudaSuccess) return to_status(e);
+            if ((e = upload(&DS.pool_ctr, std::vector<uint32_t>(2, 0u))) != cudaSuccess) return to_status(e);
+        }
         if ((e = upload(&DS.cta_slot_ptr, HS.cta_slot_ptr)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_ptr, HS.slot_ptr)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_mol, HS.slot_mol)) != cudaSuccess) return to_status(e);
@@ -1065,7 +1200,8 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
     }
     if (T->n_small > 0) {
-        SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off};
+        SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off, DS.pool_mol, DS.pool_ctr,
+                     DS.pool_n, DS.n_slots};
         k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;
@@ -1288,6 +1424,35 @@ extern "C" ilves_status ilves_topology_export_molecule(const ilves_topology* T, 
                                                        int32_t* level, int32_t* up_ptr, int32_t* up_idx) {
     if (!T || mol < 0 || mol >= T->n_mol) return ILVES_ERR_INVALID_ARG;
     program_export(T, mol, pos_gid, level, up_ptr, up_idx);
+    return ILVES_OK;
+}
+
+extern "C" ilves_status ilves_topology_schedule(const ilves_topology* T, int32_t precision, int32_t n_cta,
+                                                int32_t arena_bytes, int32_t* n_slots, int32_t* pool_n,
+                                                int32_t* slot_cta, int32_t* slot_bytes, int32_t* slot_queue,
+                                                int32_t* mol_slot, int32_t* mol_bytes) {
+    if (!T || precision < 0 || precision > 2 || n_cta < 1 || arena_bytes < 1) return ILVES_ERR_INVALID_ARG;
+    HostSchedule HS;
+    build_schedule(const_cast<ilves_topology*>(T), precision, n_cta, 16, arena_bytes, HS);
+    const int32_t ns = (int32_t)HS.slot_off.size();
+    if (n_slots) *n_slots = ns;
+    if (pool_n) *pool_n = (int32_t)HS.pool_mol.size();
+    for (int32_t c = 0; c + 1 < (int32_t)HS.cta_slot_ptr.size(); ++c)
+        for (int32_t s = HS.cta_slot_ptr[c]; s < HS.cta_slot_ptr[c + 1]; ++s) {
+            if (slot_cta) slot_cta[s] = c;
+            if (slot_bytes) slot_bytes[s] = HS.slot_bytes[s];
+            if (slot_queue) slot_queue[s] = HS.slot_ptr[s + 1] - HS.slot_ptr[s];
+        }
+    if (mol_slot || mol_bytes) {
+        for (int32_t m = 0; m < T->n_mol; ++m) {
+            const bool warp = !T->mols[m].large;
+            if (mol_slot) mol_slot[m] = warp ? -1 : -2;
+            if (mol_bytes) mol_bytes[m] = warp ? (int32_t)footprint(T->mols[m], precision) : 0;
+        }
+        if (mol_slot)
+            for (int32_t s = 0; s < ns; ++s)
+                for (int32_t q = HS.slot_ptr[s]; q < HS.slot_ptr[s + 1]; ++q) mol_slot[HS.slot_mol[q]] = s;
+    }
     return ILVES_OK;
 }
 

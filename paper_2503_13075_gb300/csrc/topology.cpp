@@ -601,12 +601,18 @@ uint32_t footprint(const MolHost& M, int mode) {
     return L.bytes + S.bytes;
 }
 
-// Warp-slot schedule.  Warp-sized molecules, sorted by shared-memory footprint, are cut
-// into G = n_cta * warps consecutive groups of about equal estimated cost; each group is
-// the queue of one warp and gets a fixed slice sized for its largest molecule.  Groups
-// are dealt to CTAs in snake order, so every CTA mixes large and small slices, and the
-// warps of a CTA never wait for each other.  If some CTA's slices overflow its arena,
-// the number of warps per CTA is reduced and the cut repeated.
+// Warp-slot schedule.  Warp-sized molecules are sorted by shared-memory footprint
+// (largest first).  The smallest ones, holding about kPoolShare of the estimated cost,
+// form a pool that every warp draws from at run time once its own queue is done; they
+// fill the gaps of the static queues, so slots finish within about one small molecule
+// of each other.  The rest is cut into G = n_cta * warps consecutive queues: a queue
+// takes molecules while its estimated cost stays under the per-queue target, and
+// molecules that find no queue go to the front of the pool.  Each queue's slot gets a
+// fixed slice sized for its first (largest) molecule, queues are dealt to CTAs in snake
+// order, so every CTA mixes large and small slices, and the number of warps per CTA is
+// the largest that fits the arena.  Warps never wait for each other.
+constexpr double kPoolShare = 0.10, kQueueSlack = 1.05;
+
 void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
                     HostSchedule& S) {
     std::vector<int32_t> small;
@@ -624,30 +630,54 @@ void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, i
     });
     double total = 0.0;
     for (int32_t m : small) total += cost[m];
-    for (int32_t w = std::max(1, std::min(32, warps)); w >= 1; --w) {
+    // pool: the longest suffix whose cost stays within kPoolShare of the total
+    size_t cut = small.size();
+    double pool_cost = 0.0;
+    while (cut > 0 && pool_cost + cost[small[cut - 1]] <= kPoolShare * total) pool_cost += cost[small[--cut]];
+    const double head_cost = total - pool_cost;
+    for (int32_t w = std::max(1, std::min(16, warps)); w >= 1; --w) {
         const int64_t G = (int64_t)n_cta * w;
-        // consecutive groups of ~equal cost (a group closes once the cumulative cost reaches
-        // its quantile; with fewer molecules than groups some groups stay empty)
+        const double target = head_cost / (double)G * kQueueSlack;
         std::vector<std::vector<int32_t>> groups(G);
-        double acc = 0.0;
+        std::vector<int32_t> pool;
         int64_t g = 0;
-        for (int32_t m : small) {
+        double acc = 0.0;
+        for (size_t k = 0; k < cut; ++k) {
+            const int32_t m = small[k];
+            if (!groups[g].empty() && acc + cost[m] > target) {
+                if (g + 1 < G) {
+                    ++g;
+                    acc = 0.0;
+                } else {
+                    pool.push_back(m);
+                    continue;
+                }
+            }
             groups[g].push_back(m);
             acc += cost[m];
-            if (g + 1 < G && acc >= total * (double)(g + 1) / (double)G) ++g;
         }
-        // snake deal to CTAs
-        std::vector<std::vector<int32_t>> cta_groups(n_cta);
-        for (int64_t gi = 0; gi < G; ++gi) {
-            if (groups[gi].empty()) continue;
-            const int64_t r = gi / n_cta, k = gi % n_cta;
-            cta_groups[(r % 2 == 0) ? k : n_cta - 1 - k].push_back((int32_t)gi);
+        for (size_t k = cut; k < small.size(); ++k) pool.push_back(small[k]);
+        const uint32_t pool_fp = pool.empty() ? 0u : fp[pool.front()];
+        // slots: every non-empty queue, plus pool-only slots (at most one per pool molecule)
+        std::vector<int64_t> slots;
+        for (int64_t gi = 0, po = 0; gi < G; ++gi) {
+            if (!groups[gi].empty()) slots.push_back(gi);
+            else if (po < (int64_t)pool.size()) {
+                slots.push_back(gi);
+                ++po;
+            }
+        }
+        auto slice_of = [&](int64_t gi) { return groups[gi].empty() ? pool_fp : fp[groups[gi].front()]; };
+        std::vector<std::vector<int64_t>> cta_groups(n_cta);
+        for (size_t si = 0; si < slots.size(); ++si) {
+            const int64_t r = (int64_t)si / n_cta, k = (int64_t)si % n_cta;
+            cta_groups[(r % 2 == 0) ? k : n_cta - 1 - k].push_back(slots[si]);
         }
         bool fits = true;
         for (int32_t c = 0; c < n_cta && fits; ++c) {
             uint64_t used = 0;
-            for (int32_t g : cta_groups[c]) used += fp[groups[g].front()];
-            fits = used <= (uint64_t)arena;
+            for (int64_t gi : cta_groups[c]) used += slice_of(gi);
+            fits = used <= (uint64_t)arena && cta_groups[c].size() <= 16;
         }
         if (!fits && w > 1) continue;
         S.n_cta = n_cta;
@@ -657,12 +687,15 @@ void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, i
         S.slot_ptr.assign(1, 0);
         S.slot_mol.clear();
         S.slot_off.clear();
+        S.slot_bytes.clear();
+        S.pool_mol = pool;
         for (int32_t c = 0; c < n_cta; ++c) {
             uint32_t off = 0;
-            for (int32_t g : cta_groups[c]) {
+            for (int64_t gi : cta_groups[c]) {
                 S.slot_off.push_back((int32_t)off);
-                off += fp[groups[g].front()];
-                for (int32_t m : groups[g]) S.slot_mol.push_back(m);
+                S.slot_bytes.push_back((int32_t)slice_of(gi));
+                off += slice_of(gi);
+                for (int32_t m : groups[gi]) S.slot_mol.push_back(m);
                 S.slot_ptr.push_back((int32_t)S.slot_mol.size());
             }
             S.cta_slot_ptr.push_back((int32_t)S.slot_off.size());

@@ -28,17 +28,25 @@ struct Program;  // topology.cpp
 // Persistent schedule of the warp-per-molecule kernel: CTA c owns warp slots
 // [cta_slot_ptr[c], cta_slot_ptr[c+1]); slot s has a fixed shared-memory slice at byte
 // offset slot_off[s] and solves molecules slot_mol[slot_ptr[s] .. slot_ptr[s+1]) in order.
+// Warp-slot schedule of the batched kernel: slot s (warp s - cta_slot_ptr[c] of CTA c)
+// owns the shared-memory slice at slot_off[s] and solves slot_mol[slot_ptr[s] ..
+// slot_ptr[s + 1]) in order, then takes molecules from the shared pool (pool_mol, one
+// atomic ticket each) until it is empty.  Pool molecules are the smallest ones and fit
+// every slice.
 struct HostSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
-    std::vector<int32_t> cta_slot_ptr, slot_ptr, slot_mol, slot_off;
+    std::vector<int32_t> cta_slot_ptr, slot_ptr, slot_mol, slot_off, slot_bytes, pool_mol;
 };
 
 struct DeviceSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
+    int32_t n_slots = 0, pool_n = 0;
     int32_t* cta_slot_ptr = nullptr;
     int32_t* slot_ptr = nullptr;
     int32_t* slot_mol = nullptr;  // index into the small-molecule descriptor array
     int32_t* slot_off = nullptr;
+    int32_t* pool_mol = nullptr;
+    uint32_t* pool_ctr = nullptr;  // {next ticket, slots done}; zero between launches
 };
 
 }  // namespace ilves

@@ -192,3 +192,29 @@ def test_symbolic_factorisation_benzene_rings():
     assert t.n_molecules == 3 and t.n_fill > 0
     for m in range(3):
         _check_molecule(t, s, m, rng)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("n_mol,n_cta", [(600, 152), (37, 152), (1, 152), (300, 4)])
+def test_warp_slot_schedule(prec, n_mol, n_cta):
+    """Every warp-path molecule is queued exactly once (a slot or the pool), fits its
+    slot's slice, pool molecules fit every slice, and each CTA's slices fit the arena."""
+    arena = 232448
+    s = wl.tree_batch(n_mol=n_mol, seed=11)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
+    sc = t.schedule(prec, n_cta=n_cta, arena_bytes=arena)
+    ms, mb = sc["mol_slot"], sc["mol_bytes"]
+    ns = len(sc["slot_cta"])
+    assert ns >= 1 and np.all(mb > 0)
+    queued = ms >= 0
+    assert np.array_equal(np.bincount(ms[queued], minlength=ns), sc["slot_queue"])
+    assert int((ms == -1).sum()) == sc["pool_n"]
+    assert np.all(mb[queued] <= sc["slot_bytes"][ms[queued]])
+    if sc["pool_n"]:
+        assert mb[ms == -1].max() <= sc["slot_bytes"].min()
+        # the pool holds the smallest molecules
+        assert mb[ms == -1].max() <= mb[queued].min() if queued.any() else True
+    per_cta = np.bincount(sc["slot_cta"], weights=sc["slot_bytes"], minlength=n_cta)
+    assert per_cta.max() <= arena
+    assert np.bincount(sc["slot_cta"], minlength=n_cta).max() <= 16
+    assert np.all(np.diff(sc["slot_cta"]) >= 0)  # slots are numbered CTA by CTA
