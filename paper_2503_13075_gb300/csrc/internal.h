@@ -34,9 +34,14 @@ constexpr uint32_t kNoAtom32 = 0xFFFFFFFFu;
 
 // Program words.  IdxT is uint16_t for molecules run by one warp (compact, staged in
 // shared memory) and uint32_t for large molecules run by a whole CTA.
-//   Task: row, col of the target entry; atomsign = (shared atom << 1) | (sign
-//         product < 0), all-ones for fill entries and diagonals; tstart = first term.
-//         Task t's terms are [tstart_t, tstart_{t+1}); a sentinel task ends the list.
+//   Task (large molecules): row, col of the target entry; atomsign = (shared atom << 1) |
+//         (sign product < 0), the dummy atom for fill entries, unused for DIAG tasks;
+//         tstart = first term.  Task t's terms are [tstart_t, tstart_{t+1}); a sentinel
+//         task ends the list.
+//   Task word (warp molecules): 32 bits, see TaskWord; no term pointer: in every level
+//         lane r of the warp owns tasks t0 + r, t0 + r + 32, ..., and the terms are
+//         stored lane by lane (lane r's terms of level 0, then of level 1, ...), starting
+//         at lane_term[r]; a lane walks its terms with a running offset.
 //   Term: l = slot of Lt[row, m], u = slot of U[m, col], m = the earlier pivot.
 //   Piv:  diag = first slot of the pivot's U row (its L column follows), nup = |N+(pivot)|.
 //   ConA: local atom ids (i, j) of the constraint at position p.
@@ -45,12 +50,27 @@ template <class IdxT> struct Task { IdxT row, col, atomsign, tstart; };
 template <class IdxT> struct ConA { IdxT i, j; };
 template <class IdxT> struct Piv { IdxT diag, nup; };
 
+// Compact task word: row (8) | col (8) << 8 | shared atom (9) << 16 | negative sign
+// product (1) << 25 | number of terms (6) << 26.
+struct TaskWord {
+    static constexpr uint32_t kMaxTerms = 63, kMaxAtom = 511;
+    static ILVES_HD uint32_t row(uint32_t w) { return w & 0xFFu; }
+    static ILVES_HD uint32_t col(uint32_t w) { return (w >> 8) & 0xFFu; }
+    static ILVES_HD uint32_t atom(uint32_t w) { return (w >> 16) & 0x1FFu; }
+    static ILVES_HD uint32_t neg(uint32_t w) { return (w >> 25) & 1u; }
+    static ILVES_HD uint32_t nterm(uint32_t w) { return w >> 26; }
+    static ILVES_HD uint32_t make(uint32_t row, uint32_t col, uint32_t atom, uint32_t neg, uint32_t nterm) {
+        return row | (col << 8) | (atom << 16) | (neg << 25) | (nterm << 26);
+    }
+};
+
 // Term words.  Warp-sized molecules (fewer than 256 constraints and 4096 slots) pack a
 // term in 32 bits: l (12) | u (12) << 12 | m (8) << 24.  Large molecules use 4 x 32 bits.
 struct TermWide { uint32_t l, u, m, pad; };
 template <class IdxT> struct TermOf;
 template <> struct TermOf<uint16_t> {
     using T = uint32_t;
+    using TaskT = uint32_t;
     static ILVES_HD uint32_t l(T t) { return t & 0xFFFu; }
     static ILVES_HD uint32_t u(T t) { return (t >> 12) & 0xFFFu; }
     static ILVES_HD uint32_t m(T t) { return t >> 24; }
@@ -58,17 +78,20 @@ template <> struct TermOf<uint16_t> {
 };
 template <> struct TermOf<uint32_t> {
     using T = TermWide;
+    using TaskT = Task<uint32_t>;
     static ILVES_HD uint32_t l(T t) { return t.l; }
     static ILVES_HD uint32_t u(T t) { return t.u; }
     static ILVES_HD uint32_t m(T t) { return t.m; }
     static ILVES_HD T make(uint32_t l, uint32_t u, uint32_t m) { return TermWide{l, u, m, 0u}; }
 };
-constexpr uint32_t kCompactMaxConstraints = 256, kCompactMaxSlots = 4096;
+constexpr uint32_t kCompactMaxConstraints = 256, kCompactMaxSlots = 4096, kCompactMaxTerms = 65000;
 
 ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 
+// `staged` = bytes a warp copies into shared memory (everything but con_gid, which is
+// read from the global copy of the blob); `bytes` = the whole blob.
 struct ProgLayout {
-    uint32_t seg, con_atoms, con_gid, piv, lvl_task, lvl_piv, inc_ptr, inc, tasks, terms, bytes;
+    uint32_t seg, con_atoms, piv, lvl_task, lvl_piv, lane_term, inc_ptr, inc, tasks, terms, staged, con_gid, bytes;
 };
 
 // Segment table (n_seg + 1 rows of {first position, first level-table entry, first atom}):
@@ -81,34 +104,38 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
                                 uint32_t nlevel, uint32_t n_seg = 1) {
     ProgLayout L;
     const uint32_t ix = (uint32_t)sizeof(IdxT);
+    const bool compact = ix == 2u;
     uint32_t o = 0;
     L.seg = o;       o = align16(o + 12u * (n_seg + 1));
     L.con_atoms = o; o = align16(o + 2u * ix * nc);
-    L.con_gid = o;   o = align16(o + 4u * nc);
     L.piv = o;       o = align16(o + 2u * ix * nc);
     L.lvl_task = o;  o = align16(o + ix * (nlevel + 1));
     L.lvl_piv = o;   o = align16(o + ix * (nlevel + 1));
+    L.lane_term = o; o = align16(o + (compact ? ix * 32u : 0u));
     L.inc_ptr = o;   o = align16(o + ix * (na + 1));
     L.inc = o;       o = align16(o + ix * 2u * nc);
-    L.tasks = o;     o = align16(o + 4u * ix * (ntask + 1));
+    L.tasks = o;     o = align16(o + (compact ? 4u * ntask : 4u * ix * (ntask + 1)));
     L.terms = o;     o = align16(o + (uint32_t)sizeof(typename TermOf<IdxT>::T) * nterm);
+    L.staged = o;
+    L.con_gid = o;   o = align16(o + 4u * nc);
     L.bytes = o;
     return L;
 }
 
 // Numerical state of one molecule (after its program).  Float64-class values (float64,
 // or float-float pairs of the same size) take 8 bytes; lp_bytes is the factor element
-// size (4 for float32, 8 for float64); 3-vectors of the factor precision are padded to 4
-// elements.  Atom arrays have na + 1 entries: the extra atom has zero weight and is what
-// fill entries of the pattern point at.  The factor-precision weight array `wl` continues
-// with one entry per constraint, w_i + w_j, which DIAG tasks use as their "shared atom".
-// With `disp` the state keeps displacements x - x_unc and the per-constraint differences
-// s_k = x_unc,i - x_unc,j.
+// size (4 for float32, 8 for float64); 3-vectors of the factor precision take 4
+// elements and use the fourth: rhof[p].w holds w_i + w_j (the weight of a DIAG entry),
+// rf[p].w holds 1 / pivot p of the current factor.  Atom arrays have na + 1 entries:
+// the extra atom has zero weight and is what fill entries of the pattern point at.
+// With `disp` (float-float mode) the state keeps displacements x - x_unc and the
+// per-constraint differences s_k = x_unc,i - x_unc,j, and rho keeps only the low
+// float parts of rho (the high parts are rhof.xyz).
 // `stage` (= rf, up to the end) is free until the first violation pass: the warp path
 // gathers x_old there (AoS, 24 B per atom) while it sets the molecule up; the region is
 // extended when the arrays after rf are smaller than that.
 struct StateLayout {
-    uint32_t x, w, wl, rho, s, d2, lam, rhof, y, rf, inv, vals, stage, bytes;
+    uint32_t x, w, wl, rho, s, d2, lam, rhof, y, rf, vals, stage, bytes;
 };
 
 ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t lp_bytes, bool disp) {
@@ -117,15 +144,14 @@ ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint
     uint32_t o = 0;
     S.x = o;      o = align16(o + 24u * na);             // SoA: x[0..na), y[..], z[..]
     S.w = o;      o = align16(o + 8u * (na + 1));
-    S.wl = o;     o = align16(o + lp_bytes * (na + 1 + nc));
-    S.rho = o;    o = align16(o + 24u * nc);             // SoA
+    S.wl = o;     o = align16(o + lp_bytes * (na + 1));
+    S.rho = o;    o = align16(o + (disp ? 12u : 24u) * nc);  // SoA
     S.s = o;      o = align16(o + (disp ? 24u * nc : 0u));
     S.d2 = o;     o = align16(o + 8u * nc);
     S.lam = o;    o = align16(o + 8u * nc);
     S.rhof = o;   o = align16(o + vp * nc);
     S.y = o;      o = align16(o + (lp_bytes > 4u ? lp_bytes : 4u) * nc);
     S.rf = o;     o = align16(o + vp * nc);
-    S.inv = o;    o = align16(o + lp_bytes * nc);
     S.vals = o;   o = align16(o + lp_bytes * ntask);
     S.stage = S.rf;
     const uint32_t stage_end = align16(S.stage + 24u * na);

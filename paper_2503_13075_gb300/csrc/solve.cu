@@ -240,7 +240,9 @@ struct MolView {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
     using TO = TermOf<IdxT>;
+    using TaskT = typename TO::TaskT;
     static constexpr bool DF = Mode::df;
+    static constexpr bool kCompact = sizeof(IdxT) == 2;
     int na, nc;
     const SegRow* seg;
     const ConA<IdxT>* con;
@@ -248,18 +250,23 @@ struct MolView {
     const Piv<IdxT>* piv;
     const IdxT* lvl_task;
     const IdxT* lvl_piv;
+    const IdxT* lane_term;
     const IdxT* inc_ptr;
     const IdxT* inc;
-    const Task<IdxT>* tasks;
+    const TaskT* tasks;
     const typename TO::T* terms;
     double *X, *W, *RHO, *SK, *D2, *LAM;
-    LP *WL, *INV, *Y, *V;
-    V4 *RHOF, *RF;
+    float* RHOL;  // float-float mode: low parts of rho (SoA); the high parts are RHOF.xyz
+    LP *WL, *Y, *V;
+    V4 *RHOF, *RF;  // RHOF[p].w = w_i + w_j, RF[p].w = 1 / pivot p
     double* STG;  // x_old gathered AoS (warp path set-up only; aliases RF and later arrays)
     const MolDesc* D;
     const SolveArgs* A;
 
-    __device__ __forceinline__ void init(const MolDesc& d, const uint8_t* prog, uint8_t* st, const SolveArgs& a) {
+    // prog: the program (in shared memory for warp molecules); gprog: its global copy,
+    // which alone holds con_gid
+    __device__ __forceinline__ void init(const MolDesc& d, const uint8_t* prog, uint8_t* st, const SolveArgs& a,
+                                         const uint8_t* gprog) {
         D = &d;
         A = &a;
         na = d.na;
@@ -268,24 +275,25 @@ struct MolView {
         const StateLayout SL = state_layout(na, nc, d.ntask, sizeof(LP), DF);
         seg = reinterpret_cast<const SegRow*>(prog + PL.seg);
         con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
-        con_gid = reinterpret_cast<const int32_t*>(prog + PL.con_gid);
+        con_gid = reinterpret_cast<const int32_t*>(gprog + PL.con_gid);
         piv = reinterpret_cast<const Piv<IdxT>*>(prog + PL.piv);
         lvl_task = reinterpret_cast<const IdxT*>(prog + PL.lvl_task);
         lvl_piv = reinterpret_cast<const IdxT*>(prog + PL.lvl_piv);
+        lane_term = reinterpret_cast<const IdxT*>(prog + PL.lane_term);
         inc_ptr = reinterpret_cast<const IdxT*>(prog + PL.inc_ptr);
         inc = reinterpret_cast<const IdxT*>(prog + PL.inc);
-        tasks = reinterpret_cast<const Task<IdxT>*>(prog + PL.tasks);
+        tasks = reinterpret_cast<const TaskT*>(prog + PL.tasks);
         terms = reinterpret_cast<const typename TO::T*>(prog + PL.terms);
         X = reinterpret_cast<double*>(st + SL.x);
         W = reinterpret_cast<double*>(st + SL.w);
         WL = reinterpret_cast<LP*>(st + SL.wl);
         RHO = reinterpret_cast<double*>(st + SL.rho);
+        RHOL = reinterpret_cast<float*>(st + SL.rho);
         SK = reinterpret_cast<double*>(st + SL.s);
         D2 = reinterpret_cast<double*>(st + SL.d2);
         LAM = reinterpret_cast<double*>(st + SL.lam);
         RHOF = reinterpret_cast<V4*>(st + SL.rhof);
         RF = reinterpret_cast<V4*>(st + SL.rf);
-        INV = reinterpret_cast<LP*>(st + SL.inv);
         Y = reinterpret_cast<LP*>(st + SL.y);
         V = reinterpret_cast<LP*>(st + SL.vals);
         STG = reinterpret_cast<double*>(st + SL.stage);
@@ -294,6 +302,9 @@ struct MolView {
         return D->atom_base >= 0 ? (int64_t)D->atom_base + a : (int64_t)A->atom_gid[D->gid_off + a];
     }
     __device__ __forceinline__ ConA<IdxT> cons(int p) const { return ldp<kCoh>(con + p); }
+    __device__ __forceinline__ int32_t gid_of_con(int p) const { return __ldg(con_gid + p); }
+    __device__ __forceinline__ LP* inv_ptr(int p) const { return reinterpret_cast<LP*>(RF + p) + 3; }
+    __device__ __forceinline__ LP inv(int p) const { return lds<kCoh>(inv_ptr(p)); }
 
     // ---- S1
     // weights of atom a; with stage_ref, x_old is staged in X for s1_constraint
@@ -331,14 +342,14 @@ struct MolView {
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
         v.z = to_lp<LP>(rz);
-        v.w = LP(0);
+        v.w = to_lp<LP>(A->inv_mass[gi]) + to_lp<LP>(A->inv_mass[gj]);
         RHOF[p] = v;
-        const int32_t g = ldp<kCoh>(con_gid + p);
+        const int32_t g = gid_of_con(p);
         const double dd = A->d[g];
         if constexpr (DF) {
-            RHO[p] = as_bits(df_split(rx));
-            RHO[nc + p] = as_bits(df_split(ry));
-            RHO[2 * nc + p] = as_bits(df_split(rz));
+            RHOL[p] = df_split(rx).lo;
+            RHOL[nc + p] = df_split(ry).lo;
+            RHOL[2 * nc + p] = df_split(rz).lo;
             D2[p] = as_bits(df_split(dd * dd));
             SK[p] = as_bits(df_split(A->x_unc[3 * gi] - A->x_unc[3 * gj]));
             SK[nc + p] = as_bits(df_split(A->x_unc[3 * gi + 1] - A->x_unc[3 * gj + 1]));
@@ -349,7 +360,6 @@ struct MolView {
             RHO[2 * nc + p] = rz;
             D2[p] = dd * dd;
         }
-        WL[na + 1 + p] = to_lp<LP>(A->inv_mass[gi]) + to_lp<LP>(A->inv_mass[gj]);
         const float l0 = A->lambda0 ? A->lambda0[g] : 0.0f;
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         Y[p] = (LP)l0;
@@ -379,7 +389,7 @@ struct MolView {
         }
         for (int a = r0; a < na; a += ts) cp_async8(W + a, A->inv_mass + gid(a));
         for (int p = r0; p < nc; p += ts) {
-            const int32_t g = ldp<kCoh>(con_gid + p);
+            const int32_t g = gid_of_con(p);
             cp_async8(D2 + p, A->d + g);
             if (A->lambda0) cp_async4(reinterpret_cast<float*>(Y + p), A->lambda0 + g);
         }
@@ -400,13 +410,13 @@ struct MolView {
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
         v.z = to_lp<LP>(rz);
-        v.w = LP(0);
+        v.w = lds<kCoh>(WL + i) + lds<kCoh>(WL + j);
         RHOF[p] = v;
         const double dd = lds<kCoh>(D2 + p);
         if constexpr (DF) {
-            RHO[p] = as_bits(df_split(rx));
-            RHO[nc + p] = as_bits(df_split(ry));
-            RHO[2 * nc + p] = as_bits(df_split(rz));
+            RHOL[p] = df_split(rx).lo;
+            RHOL[nc + p] = df_split(ry).lo;
+            RHOL[2 * nc + p] = df_split(rz).lo;
             D2[p] = as_bits(df_split(dd * dd));
             SK[p] = as_bits(df_split(lds<kCoh>(X + 3 * i) - lds<kCoh>(X + 3 * j)));
             SK[nc + p] = as_bits(df_split(lds<kCoh>(X + 3 * i + 1) - lds<kCoh>(X + 3 * j + 1)));
@@ -417,7 +427,6 @@ struct MolView {
             RHO[2 * nc + p] = rz;
             D2[p] = dd * dd;
         }
-        WL[na + 1 + p] = lds<kCoh>(WL + i) + lds<kCoh>(WL + j);
         const float l0 = A->lambda0 ? lds<kCoh>(reinterpret_cast<const float*>(Y + p)) : 0.0f;
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         Y[p] = (LP)l0;
@@ -433,9 +442,10 @@ struct MolView {
                 const int p = (int)(v >> 1);
                 const float dl = (float)lds<kCoh>(Y + p);
                 const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
-                ax = df_add(ax, df_mul_f(as_df(lds<kCoh>(RHO + p)), c));
-                ay = df_add(ay, df_mul_f(as_df(lds<kCoh>(RHO + nc + p)), c));
-                az = df_add(az, df_mul_f(as_df(lds<kCoh>(RHO + 2 * nc + p)), c));
+                const V4 hi = lds<kCoh>(RHOF + p);
+                ax = df_add(ax, df_mul_f(dfloat{hi.x, lds<kCoh>(RHOL + p)}, c));
+                ay = df_add(ay, df_mul_f(dfloat{hi.y, lds<kCoh>(RHOL + nc + p)}, c));
+                az = df_add(az, df_mul_f(dfloat{hi.z, lds<kCoh>(RHOL + 2 * nc + p)}, c));
             }
             const dfloat w = as_df(lds<kCoh>(W + a));
             X[a] = as_bits(df_sub(as_df(lds<kCoh>(X + a)), df_mul(w, ax)));
@@ -460,7 +470,9 @@ struct MolView {
     }
 
     // ---- S2: violation of constraint p (float64 class), Jacobian row, right-hand side
-    __device__ __forceinline__ void violation(int p, bool& conv, bool& bad) {
+    // rows = false keeps RF (ILVES-F after its first iteration: RF.w holds the stored
+    // factor's reciprocal pivots and the Jacobian rows are not needed)
+    __device__ __forceinline__ void violation(int p, bool& conv, bool& bad, bool rows = true) {
         const ConA<IdxT> cc = cons(p);
         const int i = cc.i, j = cc.j;
         V4 v;
@@ -505,57 +517,75 @@ struct MolView {
             Y[p] = to_lp<LP>(sg);
         }
         v.w = LP(0);
-        RF[p] = v;
+        if (rows) RF[p] = v;
     }
 
-    // ---- S3 + S4 + forward S5: one task; DIAG tasks (diag = true) also produce 1/pivot and
-    //      the forward-solve entry.  Every entry is a - sum_m Lt[row,m] inv_m U[m,col].
-    __device__ __forceinline__ void task(int t, bool diag, bool& singular) {
-        const Task<IdxT> tk = ldp<kCoh>(tasks + t);
-        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
-        const V4 rr = lds<kCoh>(RF + tk.row), pp = lds<kCoh>(RHOF + tk.col);
-        const LP wv = lds<kCoh>(WL + (tk.atomsign >> 1));
-        const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
+    // ---- S3 + S4 + forward S5: one task writing value slot t, with terms [e0, e1);
+    //      DIAG tasks (diag = true) also produce 1/pivot and the forward-solve entry.
+    //      Every entry is a - sum_m Lt[row,m] inv_m U[m,col], a = 4 s s' w_atom r_row . rho_col
+    //      (for DIAG entries w_atom = w_i + w_j, kept in RHOF[row].w).
+    __device__ __forceinline__ void task_core(int t, int row, int col, int atom, bool neg, int e0, int e1, bool diag,
+                                              bool& singular) {
+        const V4 rr = lds<kCoh>(RF + row), pp = lds<kCoh>(RHOF + col);
+        const LP wv = diag ? pp.w : lds<kCoh>(WL + atom);
+        const LP c = neg ? LP(-4) * wv : LP(4) * wv;
         const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
         LP sacc = a, yv = LP(0);
 #pragma unroll 2
-        for (int e = tk.tstart; e < e1; ++e) {
+        for (int e = e0; e < e1; ++e) {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
-            const LP li = lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(INV + m);
+            const LP li = lds<kCoh>(V + TO::l(tr)) * inv(m);
             sacc -= li * lds<kCoh>(V + TO::u(tr));
-            yv += li * lds<kCoh>(Y + m);
+            if (diag) yv += li * lds<kCoh>(Y + m);
         }
         V[t] = sacc;
         if (diag) {
             singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
-            INV[tk.row] = lp_rcp(sacc);
-            Y[tk.row] = lds<kCoh>(Y + tk.row) - yv;
+            *inv_ptr(row) = lp_rcp(sacc);
+            Y[row] = lds<kCoh>(Y + row) - yv;
         }
+    }
+    // large molecules: task records with term pointers
+    __device__ __forceinline__ void task(int t, bool diag, bool& singular) {
+        const TaskT tk = ldp<kCoh>(tasks + t);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        task_core(t, tk.row, tk.col, tk.atomsign >> 1, tk.atomsign & 1, tk.tstart, e1, diag, singular);
+    }
+    // warp molecules: task word w, terms from e0
+    __device__ __forceinline__ void task_word(int t, uint32_t w, int e0, bool diag, bool& singular) {
+        task_core(t, TaskWord::row(w), TaskWord::col(w), TaskWord::atom(w), TaskWord::neg(w), e0,
+                  e0 + (int)TaskWord::nterm(w), diag, singular);
     }
 
     // ---- forward S5 alone (ILVES-F iterations after the first): y_p -= sum_m L[p,m] y_m,
-    //      with the terms of pivot p's DIAG task t
-    __device__ __forceinline__ void forward(int t, int p) {
-        const int e0 = ldp<kCoh>(tasks + t).tstart, e1 = ldp<kCoh>(tasks + t + 1).tstart;
+    //      with the terms [e0, e1) of pivot p's DIAG task
+    __device__ __forceinline__ void forward_terms(int p, int e0, int e1) {
         LP yv = LP(0);
         for (int e = e0; e < e1; ++e) {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
-            yv += lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(INV + m) * lds<kCoh>(Y + m);
+            yv += lds<kCoh>(V + TO::l(tr)) * inv(m) * lds<kCoh>(Y + m);
         }
         Y[p] = lds<kCoh>(Y + p) - yv;
+    }
+    __device__ __forceinline__ void forward(int t, int p) {
+        forward_terms(p, ldp<kCoh>(tasks + t).tstart, ldp<kCoh>(tasks + t + 1).tstart);
     }
     // ILVES-F assembles A(x_old, x_old): the Jacobian rows are the reference bonds
     __device__ __forceinline__ void chord_rows(int p) { RF[p] = lds<kCoh>(RHOF + p); }
 
     // ---- backward S5 for pivot p: delta_p = inv_p (y_p - sum_q U[p,q] delta_q)
+    __device__ __forceinline__ int task_col(int t) const {
+        if constexpr (kCompact) return (int)TaskWord::col(ldp<kCoh>(tasks + t));
+        else return (int)ldp<kCoh>(tasks + t).col;
+    }
     __device__ __forceinline__ void backward(int p) {
         const Piv<IdxT> pv = ldp<kCoh>(piv + p);
         const int us = pv.diag, nu = pv.nup;
         LP dl = lds<kCoh>(Y + p);
-        for (int k = 0; k < nu; ++k) dl -= lds<kCoh>(V + us + k) * lds<kCoh>(Y + ldp<kCoh>(tasks + us + k).col);
-        Y[p] = dl * lds<kCoh>(INV + p);
+        for (int k = 0; k < nu; ++k) dl -= lds<kCoh>(V + us + k) * lds<kCoh>(Y + task_col(us + k));
+        Y[p] = dl * inv(p);
     }
 
     __device__ __forceinline__ void lambda_acc(int p) {
@@ -578,7 +608,7 @@ struct MolView {
     }
     __device__ __forceinline__ void out_lambda(int p) {
         const double l = lds<kCoh>(LAM + p);
-        A->lambda_out[ldp<kCoh>(con_gid + p)] = DF ? df_join(as_df(l)) : l;
+        A->lambda_out[gid_of_con(p)] = DF ? df_join(as_df(l)) : l;
     }
 };
 
@@ -588,9 +618,10 @@ struct MolView {
 // ------------------------------------------------------------------------------------
 template <class Mode, class IdxT, class Team>
 __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
-                               const SolveArgs& A) {
+                               const SolveArgs& A, const uint8_t* gprog) {
+    constexpr bool kCompact = sizeof(IdxT) == 2;  // warp molecules (Team = WarpTeam)
     MolView<Mode, IdxT, false> M;
-    M.init(D, prog, st, A);
+    M.init(D, prog, st, A, gprog);
     const int na = D.na, nc = D.nc;
     const int r0 = tm.rank(), ts = tm.size();
     // ---- S1
@@ -622,7 +653,7 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
     int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
     for (int it = 0;; ++it) {
         bool conv = true, bad = false;
-        for (int p = r0; p < nc; p += ts) M.violation(p, conv, bad);
+        for (int p = r0; p < nc; p += ts) M.violation(p, conv, bad, !A.chord || it == 0);
         if (tm.any(bad)) {
             status = ILVES_MOL_NONFINITE;
             iters = it;
@@ -640,12 +671,22 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
                 for (int p = r0; p < nc; p += ts) M.chord_rows(p);
                 tm.sync();
             }
-            // one pass per level; the first np tasks of a level are its DIAG tasks
+            // one pass per level; the first np tasks of a level are its DIAG tasks; a warp
+            // lane walks its terms with a running offset
             bool singular = false;
+            int e = kCompact ? (int)M.lane_term[r0] : 0;
             for (int l = 0; l < D.nlevel; ++l) {
                 const int p0 = M.lvl_piv[l], np = M.lvl_piv[l + 1] - p0;
                 const int t0 = M.lvl_task[l], t1 = M.lvl_task[l + 1];
-                for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                if constexpr (kCompact) {
+                    for (int t = t0 + r0; t < t1; t += ts) {
+                        const uint32_t w = M.tasks[t];
+                        M.task_word(t, w, e, t < t0 + np, singular);
+                        e += (int)TaskWord::nterm(w);
+                    }
+                } else {
+                    for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                }
                 tm.sync();
             }
             if (tm.any(singular)) {
@@ -654,9 +695,19 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
                 break;
             }
         } else {  // ILVES-F: forward substitution with the stored factor
+            int e = kCompact ? (int)M.lane_term[r0] : 0;
             for (int l = 0; l < D.nlevel; ++l) {
                 const int p0 = M.lvl_piv[l], p1 = M.lvl_piv[l + 1], t0 = M.lvl_task[l];
-                for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
+                if constexpr (kCompact) {  // DIAG tasks: t0 + (p - p0); skip the others' terms
+                    const int t1 = M.lvl_task[l + 1];
+                    for (int t = t0 + r0; t < t1; t += ts) {
+                        const int n = (int)TaskWord::nterm(M.tasks[t]);
+                        if (t < t0 + (p1 - p0)) M.forward_terms(p0 + (t - t0), e, e + n);
+                        e += n;
+                    }
+                } else {
+                    for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
+                }
                 tm.sync();
             }
         }
@@ -723,7 +774,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                SolveArgs A) {
     const MolDesc D = *desc;
     MolView<Mode, uint32_t, true> M;
-    M.init(D, blob + D.blob_off, work + D.work_off, A);
+    M.init(D, blob + D.blob_off, work + D.work_off, A, blob + D.blob_off);
     const int n_parts = D.n_seg - 1;
     const SegRow* seg = M.seg;
     const int sep0 = __ldg(&seg[n_parts].piv), nsep = D.nc - sep0;
@@ -764,7 +815,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         const int slot = it & 3;
         // ---- violations of owned constraints, global vote
         bool conv = true, bad = false;
-        for_owned([&](int p) { M.violation(p, conv, bad); });
+        for_owned([&](int p) { M.violation(p, conv, bad, !A.chord || it == 0); });
         const int nconv_block = __syncthreads_count(!conv);
         const int bad_block = __syncthreads_or(bad);
         if (r0 == 0) {
@@ -908,7 +959,7 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
         const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg);
         const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
         uint4* dst = reinterpret_cast<uint4*>(slice);
-        const int n16 = (int)(PL.bytes >> 4);
+        const int n16 = (int)(PL.staged >> 4);
         for (int k = lane; k < n16; k += 32) cp_async16(dst + k, src + k);  // all in flight
         if (q + 1 < q1) {  // the next queued molecule's program and atom inputs into L2 meanwhile
             const MolDesc Dn = desc[S.slot_mol[q + 1]];
@@ -928,7 +979,7 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
         }
         cp_async_wait_all();
         __syncwarp();
-        solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.bytes, A);
+        solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.staged, A, blob + D.blob_off);
         __syncwarp();
         ++q;
         mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S) : -1);
@@ -951,7 +1002,7 @@ k_solve_large(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
               SolveArgs A) {
     const BlockTeam tm;
     const MolDesc D = desc[blockIdx.x];
-    solve_molecule<Mode, uint32_t, BlockTeam>(tm, D, blob + D.blob_off, work + D.work_off, A);
+    solve_molecule<Mode, uint32_t, BlockTeam>(tm, D, blob + D.blob_off, work + D.work_off, A, blob + D.blob_off);
 }
 
 __global__ void k_copy_free(const int32_t* __restrict__ idx, int n, const double* __restrict__ x_unc,

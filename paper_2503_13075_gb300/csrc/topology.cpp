@@ -247,8 +247,8 @@ static Program compile(int32_t nc, const Elimination& E, const std::vector<int32
     std::vector<std::vector<TermW>> tterms(t);
     for (int32_t p = 0; p < nc; ++p) {
         const int32_t td = P.diag_task[p];
-        // DIAG: a_pp = 4 (w_i + w_j) r_p . rho_p; the pseudo-atom na + 1 + p carries w_i + w_j
-        P.tasks[td] = {(uint32_t)p, (uint32_t)p, (uint32_t)(na_dummy + 1 + p) << 1, 0u};
+        // DIAG: a_pp = 4 (w_i + w_j) r_p . rho_p; the kernels keep w_i + w_j next to rho_p
+        P.tasks[td] = {(uint32_t)p, (uint32_t)p, (uint32_t)na_dummy << 1, 0u};
         for (int32_t m : dn[p]) tterms[td].push_back({(uint32_t)slot_L(p, m), (uint32_t)slot_U(m, p), (uint32_t)m, 0u});
         const int32_t nu = (int32_t)P.up[p].size();
         for (int32_t k = 0; k < nu; ++k) {
@@ -356,6 +356,7 @@ static ProgLayout layout_for(const MolHost& M) {
 
 template <class IdxT>
 static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
+    constexpr bool kCompact = sizeof(IdxT) == 2;
     const ProgLayout L = layout_for<IdxT>(M);
     std::memset(dst, 0, L.bytes);
     auto* seg = reinterpret_cast<SegRow*>(dst + L.seg);
@@ -367,7 +368,6 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
     auto* lvl_piv = reinterpret_cast<IdxT*>(dst + L.lvl_piv);
     auto* inc_ptr = reinterpret_cast<IdxT*>(dst + L.inc_ptr);
     auto* inc = reinterpret_cast<IdxT*>(dst + L.inc);
-    auto* tasks = reinterpret_cast<Task<IdxT>*>(dst + L.tasks);
     auto* terms = reinterpret_cast<typename TermOf<IdxT>::T*>(dst + L.terms);
     const int32_t nc = (int32_t)M.cons.size(), na = (int32_t)M.atoms.size();
     for (int32_t p = 0; p < nc; ++p) {
@@ -394,17 +394,49 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
         inc[fillp[con[p].i]++] = (IdxT)((uint32_t)p << 1);
         inc[fillp[con[p].j]++] = (IdxT)(((uint32_t)p << 1) | 1u);
     }
-    const IdxT no_atom = (IdxT)~(IdxT)0;
-    for (size_t t = 0; t < P.tasks.size(); ++t) {
-        const TaskW& w = P.tasks[t];
-        tasks[t].row = (IdxT)w.row;
-        tasks[t].col = (IdxT)w.col;
-        tasks[t].atomsign = w.atomsign == kNoAtom32 ? no_atom : (IdxT)w.atomsign;  // DIAG / sentinel
-        tasks[t].tstart = (IdxT)w.tstart;
+    auto term_of = [&](size_t k) { return TermOf<IdxT>::make(P.terms[k].l, P.terms[k].u, P.terms[k].m); };
+    if constexpr (kCompact) {
+        // task words; terms lane by lane (lane r owns t0 + r + 32 k of every level), each
+        // lane's terms in level order
+        auto* tasks = reinterpret_cast<uint32_t*>(dst + L.tasks);
+        auto* lane_term = reinterpret_cast<IdxT*>(dst + L.lane_term);
+        const int32_t ntask = (int32_t)P.tasks.size() - 1;
+        for (int32_t t = 0; t < ntask; ++t) {
+            const TaskW& w = P.tasks[t];
+            const uint32_t nt = P.tasks[t + 1].tstart - w.tstart;
+            tasks[t] = TaskWord::make(w.row, w.col, w.atomsign >> 1, w.atomsign & 1u, nt);
+        }
+        size_t o = 0;
+        const int32_t nl = (int32_t)P.lvl_task.size() - 1;
+        for (int32_t r = 0; r < 32; ++r) {
+            lane_term[r] = (IdxT)o;
+            for (int32_t l = 0; l < nl; ++l) {
+                const int32_t t0 = P.lvl_task[l], t1 = P.lvl_task[l + 1];
+                for (int32_t t = t0 + r; t < t1; t += 32)
+                    for (uint32_t k = P.tasks[t].tstart; k < P.tasks[t + 1].tstart; ++k) terms[o++] = term_of(k);
+            }
+        }
+    } else {
+        auto* tasks = reinterpret_cast<Task<IdxT>*>(dst + L.tasks);
+        const IdxT no_atom = (IdxT)~(IdxT)0;
+        for (size_t t = 0; t < P.tasks.size(); ++t) {
+            const TaskW& w = P.tasks[t];
+            tasks[t].row = (IdxT)w.row;
+            tasks[t].col = (IdxT)w.col;
+            tasks[t].atomsign = w.atomsign == kNoAtom32 ? no_atom : (IdxT)w.atomsign;  // sentinel
+            tasks[t].tstart = (IdxT)w.tstart;
+        }
+        for (size_t k = 0; k < P.terms.size(); ++k) terms[k] = term_of(k);
     }
-    for (size_t k = 0; k < P.terms.size(); ++k) {
-        terms[k] = TermOf<IdxT>::make(P.terms[k].l, P.terms[k].u, P.terms[k].m);
-    }
+}
+
+// true if a program fits the compact (warp) encoding: task words hold at most
+// TaskWord::kMaxTerms terms, term and slot indices fit their fields
+static bool fits_compact(const Program& P) {
+    if (P.tasks.size() >= kCompactMaxSlots || P.terms.size() > kCompactMaxTerms) return false;
+    for (size_t t = 0; t + 1 < P.tasks.size(); ++t)
+        if (P.tasks[t + 1].tstart - P.tasks[t].tstart > TaskWord::kMaxTerms) return false;
+    return true;
 }
 
 // ------------------------------------------------------------------------------------
@@ -509,7 +541,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             std::sort(v.begin(), v.end());
             v.erase(std::unique(v.begin(), v.end()), v.end());
         }
-        M.large = nc > warp_limit || nc >= (int32_t)kCompactMaxConstraints || na + 1 + nc > 32000;
+        M.large = nc > warp_limit || nc >= (int32_t)kCompactMaxConstraints || na > (int32_t)TaskWord::kMaxAtom;
         const int32_t part_min = o.partition_min_constraints > 0 ? o.partition_min_constraints : 4096;
         if (nc >= part_min) {
             // partitioned: parts of ~part_size constraints eliminated first, separators last
@@ -542,7 +574,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             continue;
         }
         Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : 32));
-        if (!M.large && (P->tasks.size() >= kCompactMaxSlots || P->terms.size() > 65000)) {
+        if (!M.large && !fits_compact(*P)) {
             M.large = true;
             *P = choose_order(nc, na, adj, M.ci, M.cj, o, 1024);
         }
@@ -598,7 +630,7 @@ uint32_t footprint(const MolHost& M, int mode) {
     const ProgLayout L = layout_for<uint16_t>(M);
     const StateLayout S = state_layout((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(), (uint32_t)M.ntask,
                                        lp, mode == ILVES_PREC_MIXED_DF);
-    return L.bytes + S.bytes;
+    return L.staged + S.bytes;
 }
 
 // Warp-slot schedule.  Warp-sized molecules are sorted by shared-memory footprint
