@@ -262,6 +262,7 @@ struct MolView {
     double* STG;  // x_old gathered AoS (warp path set-up only; aliases RF and later arrays)
     const MolDesc* D;
     const SolveArgs* A;
+    float tolf;  // tol in float (float-float convergence test)
 
     // prog: the program (in shared memory for warp molecules); gprog: its global copy,
     // which alone holds con_gid
@@ -269,6 +270,7 @@ struct MolView {
                                          const uint8_t* gprog) {
         D = &d;
         A = &a;
+        tolf = (float)a.tol;
         na = d.na;
         nc = d.nc;
         const ProgLayout PL = prog_layout<IdxT>(na, nc, d.ntask, d.nterm, d.nlevel, d.n_seg);
@@ -432,8 +434,11 @@ struct MolView {
         Y[p] = (LP)l0;
     }
 
-    // ---- S6: x_a -= w_a sum_k s_k(a) 2 Y_k rho_k   (Y holds delta, or lambda0)
-    __device__ __forceinline__ void update_atom(int a) {
+    // ---- S6: x_a -= w_a sum_k s_k(a) 2 Y_k rho_k   (Y holds delta, or lambda0).
+    //      upd_eval computes the new coordinates (float64 class, as bit patterns),
+    //      upd_store writes them.
+    struct Upd { double x, y, z; };
+    __device__ __forceinline__ Upd upd_eval(int a) const {
         const int e1 = ldp<kCoh>(inc_ptr + a + 1);
         if constexpr (DF) {
             dfloat ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
@@ -448,9 +453,9 @@ struct MolView {
                 az = df_add(az, df_mul_f(dfloat{hi.z, lds<kCoh>(RHOL + 2 * nc + p)}, c));
             }
             const dfloat w = as_df(lds<kCoh>(W + a));
-            X[a] = as_bits(df_sub(as_df(lds<kCoh>(X + a)), df_mul(w, ax)));
-            X[na + a] = as_bits(df_sub(as_df(lds<kCoh>(X + na + a)), df_mul(w, ay)));
-            X[2 * na + a] = as_bits(df_sub(as_df(lds<kCoh>(X + 2 * na + a)), df_mul(w, az)));
+            return {as_bits(df_sub(as_df(lds<kCoh>(X + a)), df_mul(w, ax))),
+                    as_bits(df_sub(as_df(lds<kCoh>(X + na + a)), df_mul(w, ay))),
+                    as_bits(df_sub(as_df(lds<kCoh>(X + 2 * na + a)), df_mul(w, az)))};
         } else {
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
@@ -463,19 +468,26 @@ struct MolView {
                 az = fma(c, lds<kCoh>(RHO + 2 * nc + p), az);
             }
             const double w = lds<kCoh>(W + a);
-            X[a] = fma(-w, ax, lds<kCoh>(X + a));
-            X[na + a] = fma(-w, ay, lds<kCoh>(X + na + a));
-            X[2 * na + a] = fma(-w, az, lds<kCoh>(X + 2 * na + a));
+            return {fma(-w, ax, lds<kCoh>(X + a)), fma(-w, ay, lds<kCoh>(X + na + a)),
+                    fma(-w, az, lds<kCoh>(X + 2 * na + a))};
         }
     }
+    __device__ __forceinline__ void upd_store(int a, const Upd& u) {
+        X[a] = u.x;
+        X[na + a] = u.y;
+        X[2 * na + a] = u.z;
+    }
+    __device__ __forceinline__ void update_atom(int a) { upd_store(a, upd_eval(a)); }
 
-    // ---- S2: violation of constraint p (float64 class), Jacobian row, right-hand side
-    // rows = false keeps RF (ILVES-F after its first iteration: RF.w holds the stored
-    // factor's reciprocal pivots and the Jacobian rows are not needed)
-    __device__ __forceinline__ void violation(int p, bool& conv, bool& bad, bool rows = true) {
+    // ---- S2: violation of constraint p (float64 class), Jacobian row, right-hand side.
+    //      viol_eval computes, viol_store writes (rows = false keeps RF: ILVES-F after its
+    //      first iteration, where RF.w holds the stored factor's reciprocal pivots and the
+    //      Jacobian rows are not needed).
+    struct Viol { V4 v; LP y; bool conv, bad; };
+    __device__ __forceinline__ Viol viol_eval(int p) const {
         const ConA<IdxT> cc = cons(p);
         const int i = cc.i, j = cc.j;
-        V4 v;
+        Viol o;
         if constexpr (DF) {
             const dfloat rx = df_add(as_df(lds<kCoh>(SK + p)), df_sub(as_df(lds<kCoh>(X + i)), as_df(lds<kCoh>(X + j))));
             const dfloat ry = df_add(as_df(lds<kCoh>(SK + nc + p)),
@@ -497,39 +509,55 @@ struct MolView {
             cross = __fmaf_rn(rz.hi, rz.lo, cross);
             const float tail = ((ex + ey) + (ez + e1)) + ((e2 + e3) - d2.lo) + (cross + cross);
             const float sg = s3 + tail;
-            conv = conv && fabsf(sg) <= (float)A->tol * d2.hi;
-            bad = bad || nonfinite(sg);
-            v.x = rx.hi;
-            v.y = ry.hi;
-            v.z = rz.hi;
-            Y[p] = sg;
+            o.conv = fabsf(sg) <= tolf * d2.hi;
+            o.bad = nonfinite(sg);
+            o.v.x = rx.hi;
+            o.v.y = ry.hi;
+            o.v.z = rz.hi;
+            o.y = sg;
         } else {
             const double rx = lds<kCoh>(X + i) - lds<kCoh>(X + j);
             const double ry = lds<kCoh>(X + na + i) - lds<kCoh>(X + na + j);
             const double rz = lds<kCoh>(X + 2 * na + i) - lds<kCoh>(X + 2 * na + j);
             const double d2 = lds<kCoh>(D2 + p);
             const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
-            conv = conv && abs_le(sg, A->tol * d2);
-            bad = bad || nonfinite(sg);
-            v.x = to_lp<LP>(rx);
-            v.y = to_lp<LP>(ry);
-            v.z = to_lp<LP>(rz);
-            Y[p] = to_lp<LP>(sg);
+            o.conv = abs_le(sg, A->tol * d2);
+            o.bad = nonfinite(sg);
+            o.v.x = to_lp<LP>(rx);
+            o.v.y = to_lp<LP>(ry);
+            o.v.z = to_lp<LP>(rz);
+            o.y = to_lp<LP>(sg);
         }
-        v.w = LP(0);
-        if (rows) RF[p] = v;
+        o.v.w = LP(0);
+        return o;
+    }
+    __device__ __forceinline__ void viol_store(int p, const Viol& o, bool rows) {
+        Y[p] = o.y;
+        if (rows) RF[p] = o.v;
+    }
+    __device__ __forceinline__ void violation(int p, bool& conv, bool& bad, bool rows = true) {
+        const Viol o = viol_eval(p);
+        conv = conv && o.conv;
+        bad = bad || o.bad;
+        viol_store(p, o, rows);
     }
 
     // ---- S3 + S4 + forward S5: one task writing value slot t, with terms [e0, e1);
     //      DIAG tasks (diag = true) also produce 1/pivot and the forward-solve entry.
     //      Every entry is a - sum_m Lt[row,m] inv_m U[m,col], a = 4 s s' w_atom r_row . rho_col
     //      (for DIAG entries w_atom = w_i + w_j, kept in RHOF[row].w).
-    __device__ __forceinline__ void task_core(int t, int row, int col, int atom, bool neg, int e0, int e1, bool diag,
-                                              bool& singular) {
+    __device__ __forceinline__ LP assemble(int row, int col, int atom, bool neg, bool diag) const {
         const V4 rr = lds<kCoh>(RF + row), pp = lds<kCoh>(RHOF + col);
         const LP wv = diag ? pp.w : lds<kCoh>(WL + atom);
         const LP c = neg ? LP(-4) * wv : LP(4) * wv;
-        const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+        return c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+    }
+    __device__ __forceinline__ void task_core(int t, int row, int col, int atom, bool neg, int e0, int e1, bool diag,
+                                              bool& singular) {
+        finish(t, row, assemble(row, col, atom, neg, diag), e0, e1, diag, singular);
+    }
+    // a - sum over terms [e0, e1) -> value slot t (and, for DIAG, 1/pivot and y_row)
+    __device__ __forceinline__ void finish(int t, int row, LP a, int e0, int e1, bool diag, bool& singular) {
         LP sacc = a, yv = LP(0);
 #pragma unroll 2
         for (int e = e0; e < e1; ++e) {
@@ -552,10 +580,18 @@ struct MolView {
         const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
         task_core(t, tk.row, tk.col, tk.atomsign >> 1, tk.atomsign & 1, tk.tstart, e1, diag, singular);
     }
-    // warp molecules: task word w, terms from e0
-    __device__ __forceinline__ void task_word(int t, uint32_t w, int e0, bool diag, bool& singular) {
-        task_core(t, TaskWord::row(w), TaskWord::col(w), TaskWord::atom(w), TaskWord::neg(w), e0,
-                  e0 + (int)TaskWord::nterm(w), diag, singular);
+    // warp molecules: one level's tasks t0 + lane + 32 k; the lane walks its terms from
+    //      offset e
+    __device__ __forceinline__ void level_tasks(int t0, int t1, int np, int lane, int& e, bool& singular) {
+        for (int t = t0 + lane; t < t1; t += 32) {
+            const uint32_t w = lds<kCoh>(tasks + t);
+            const int n = (int)TaskWord::nterm(w);
+            const bool diag = t < t0 + np;
+            finish(t, TaskWord::row(w),
+                   assemble(TaskWord::row(w), TaskWord::col(w), TaskWord::atom(w), TaskWord::neg(w), diag), e, e + n,
+                   diag, singular);
+            e += n;
+        }
     }
 
     // ---- forward S5 alone (ILVES-F iterations after the first): y_p -= sum_m L[p,m] y_m,
@@ -587,7 +623,6 @@ struct MolView {
         for (int k = 0; k < nu; ++k) dl -= lds<kCoh>(V + us + k) * lds<kCoh>(Y + task_col(us + k));
         Y[p] = dl * inv(p);
     }
-
     __device__ __forceinline__ void lambda_acc(int p) {
         if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(lds<kCoh>(LAM + p)), (float)lds<kCoh>(Y + p)));
         else LAM[p] = lds<kCoh>(LAM + p) + to_hp(lds<kCoh>(Y + p));
@@ -679,11 +714,7 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
                 const int p0 = M.lvl_piv[l], np = M.lvl_piv[l + 1] - p0;
                 const int t0 = M.lvl_task[l], t1 = M.lvl_task[l + 1];
                 if constexpr (kCompact) {
-                    for (int t = t0 + r0; t < t1; t += ts) {
-                        const uint32_t w = M.tasks[t];
-                        M.task_word(t, w, e, t < t0 + np, singular);
-                        e += (int)TaskWord::nterm(w);
-                    }
+                    M.level_tasks(t0, t1, np, r0, e, singular);
                 } else {
                     for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
                 }
