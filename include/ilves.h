@@ -221,6 +221,11 @@ typedef struct ilves_mlp ilves_mlp; /* opaque: parameters, Adam state, activatio
 /* Number of float32 parameters (ILVES_MLP_PARAMS). */
 int64_t ilves_mlp_param_count(void);
 
+/* Synchronises and reports how many tensor-core waits of this network's kernels gave up
+ * (bounded waits; the affected launch stops early, frees its tensor memory and leaves
+ * its outputs incomplete).  ILVES_OK if none, ILVES_ERR_TIMEOUT otherwise. */
+ilves_status ilves_mlp_check(const ilves_mlp* mlp, int32_t* waits_given_up);
+
 /* Creates a network on the current device with He-uniform weights drawn from `seed` and
  * activation buffers for up to max_batch training rows (allocates device memory). */
 ilves_status ilves_mlp_create(int32_t max_batch, uint64_t seed, ilves_mlp** out);
@@ -236,7 +241,9 @@ ilves_status ilves_mlp_features(const ilves_topology* topo, const double* x_old,
                                 const double* inv_mass, const double* d, float* features, float* scale,
                                 void* stream);
 
-/* Inference on n feature rows (DEVICE): y (n floats). */
+/* Inference on n feature rows (DEVICE, row-major n x 16, 16-byte aligned): y (n
+ * floats).  Runs on the tensor cores (tcgen05); ILVES_ERR_INVALID_ARG if features is
+ * not 16-byte aligned. */
 ilves_status ilves_mlp_forward(const ilves_mlp* mlp, const float* features, int32_t n, float* y, void* stream);
 
 /* One fused kernel computing features, the network and lambda_0 = y / scale for every
@@ -247,7 +254,8 @@ ilves_status ilves_warm_start(const ilves_mlp* mlp, const ilves_topology* topo, 
                               void* stream);
 
 /* Mean-squared-error gradient (DEVICE float32, ILVES_MLP_PARAMS values, may be NULL)
- * and loss (DEVICE float, may be NULL) on n <= max_batch rows; parameters unchanged. */
+ * and loss (DEVICE float, may be NULL) on n <= max_batch rows (features 16-byte
+ * aligned); parameters unchanged. */
 ilves_status ilves_mlp_gradient(ilves_mlp* mlp, const float* features, const float* target, int32_t n,
                                 float* grad, float* loss, void* stream);
 

@@ -83,6 +83,8 @@ def lib():
     L.ilves_topology_device_bytes.restype = I64
     L.ilves_mlp_param_count.argtypes = []
     L.ilves_mlp_param_count.restype = I64
+    L.ilves_mlp_check.argtypes = [P, pi32]
+    L.ilves_mlp_check.restype = I32
     L.ilves_mlp_create.argtypes = [I32, ctypes.c_uint64, ctypes.POINTER(P)]
     L.ilves_mlp_create.restype = I32
     L.ilves_mlp_destroy.argtypes = [P]
@@ -296,6 +298,12 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+    def check(self):
+        """Number of tensor-core waits that gave up (synchronises; 0 in a healthy run)."""
+        n = ctypes.c_int32()
+        lib().ilves_mlp_check(self._h, ctypes.byref(n))
+        return n.value
 
     def get_params(self):
         out = np.zeros(self.n_params, np.float32)

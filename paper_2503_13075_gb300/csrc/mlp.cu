@@ -7,9 +7,10 @@
 //   features  16 per constraint (own violation / alignment / masses, 4 line-graph
 //             neighbour slots with their violation, coupling cosine and shared mass)
 //   network   16 -> 128 -> ReLU -> 128 -> ReLU -> 1, bfloat16 weights and inputs,
-//             float32 accumulation, on the tensor cores (mma.sync m16n8k16): the first
-//             layer's accumulators are rounded to bfloat16 and reused in registers as the
-//             second layer's A operand, the third layer is a quad-shuffle dot product
+//             float32 accumulation, on the 5th-generation tensor cores (tcgen05.mma,
+//             operands in shared memory, accumulators in tensor memory): per 128-row tile
+//             one MMA for layer 1, its epilogue writes the bfloat16 A tile of layer 2
+//             (eight MMAs), whose epilogue does the third layer as a per-row dot product
 //   target    y = lambda * scale, scale = 4 (w_i + w_j) s.rho / d^2  -> lambda_0 = y / scale
 //   training  forward on the tensor cores storing activations, backward on the float32
 //             pipes (one thread per hidden unit, register accumulators, one atomic flush
@@ -35,9 +36,7 @@ constexpr int NF = ILVES_MLP_FEATURES, NH = ILVES_MLP_HIDDEN;
 constexpr int P_W1 = 0, P_B1 = P_W1 + NH * NF, P_W2 = P_B1 + NH, P_B2 = P_W2 + NH * NH, P_W3 = P_B2 + NH,
               P_B3 = P_W3 + NH, P_N = P_B3 + 1;
 static_assert(P_N == ILVES_MLP_PARAMS, "parameter count");
-constexpr int W1_LD = NF + 8;   // padded shared-memory row (bf16) -> conflict-free B fragments
-constexpr int W2_LD = NH + 8;
-constexpr int FWD_WARPS = 4;
+constexpr int TILE = 128;  // rows per tensor-core tile (M of the MMA), one thread per row
 
 // ------------------------------------------------------------------------------------
 // features
@@ -143,20 +142,11 @@ __global__ void k_diag_guess(FeatArgs F, float* __restrict__ lambda0) {
 }
 
 // ------------------------------------------------------------------------------------
-// tensor-core forward
+// tensor-core forward (tcgen05: operands in shared memory, accumulators in tensor memory)
 // ------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float& d0, float& d1, float& d2, float& d3, uint32_t a0, uint32_t a1,
-                                         uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 struct MlpWeights {
@@ -165,141 +155,248 @@ struct MlpWeights {
     const float* params;      // float32 master parameters (biases, w3, b3 read from here)
 };
 
-// Input rows come either from a feature matrix (training / explicit inference) or are
-// computed on the fly from the topology (fused warm start, output = lambda_0).
-template <bool kFused, bool kTrain>
-__global__ void __launch_bounds__(FWD_WARPS * 32)
-k_mlp_forward(MlpWeights Wt, const float* __restrict__ X, int n, FeatArgs F, float* __restrict__ out,
-              __nv_bfloat16* __restrict__ h1_out, float* __restrict__ h2_out) {
-    __shared__ __align__(16) __nv_bfloat16 w1s[NH * W1_LD];
-    __shared__ __align__(16) __nv_bfloat16 w2s[NH * W2_LD];
-    __shared__ float b1s[NH], b2s[NH], w3s[NH];
-    __shared__ float fs[FWD_WARPS][16][NF + 1];
-    __shared__ float scs[FWD_WARPS][16];
-    {  // stage the bfloat16 weights with 16-byte loads (8 values), all loads issued before the stores
-        const uint4* g1 = reinterpret_cast<const uint4*>(Wt.w1);
-        const uint4* g2 = reinterpret_cast<const uint4*>(Wt.w2);
-        constexpr int N1 = NH * NF / 8, N2 = NH * NH / 8, PER = N2 / (FWD_WARPS * 32);
-        uint4 v[PER];
-#pragma unroll
-        for (int u = 0; u < PER; ++u) v[u] = __ldg(g2 + threadIdx.x + u * FWD_WARPS * 32);
-        for (int e = threadIdx.x; e < N1; e += blockDim.x) {
-            const int row = (e * 8) / NF, col = (e * 8) % NF;
-            *reinterpret_cast<uint4*>(w1s + row * W1_LD + col) = __ldg(g1 + e);
-        }
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int e = threadIdx.x + u * FWD_WARPS * 32;
-            const int row = (e * 8) / NH, col = (e * 8) % NH;
-            *reinterpret_cast<uint4*>(w2s + row * W2_LD + col) = v[u];
-        }
+// Operand tiles use the tensor cores' canonical K-major layout without swizzling: the
+// tile is cut into core matrices of 8 rows x 16 bytes (8 bfloat16 of K), each stored as
+// 128 contiguous bytes; core (row group g, K chunk c) sits at g * SBO + c * 128.
+__device__ __forceinline__ uint32_t core_offset(int row, int kchunk, int kchunks) {
+    return (uint32_t)((row >> 3) * (kchunks * 128) + kchunk * 128 + (row & 7) * 16);
+}
+// shared-memory matrix descriptor: start >> 4, leading (K) byte offset >> 4, stride (row
+// group) byte offset >> 4, descriptor version 1 (bits 46-47), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: f32 accumulator (bits 4-5 = 1), bf16 A and B (bits
+// 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
+                                ((uint32_t)(TILE >> 4) << 24);
+// one 128-column accumulator: layer 2 reuses the columns once layer 1's epilogue has
+// moved them to shared memory
+constexpr uint32_t kTmemCols = NH;
+
+__device__ __forceinline__ uint32_t saddr_of(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+// bounded wait for the mbarrier phase of the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(64);
     }
-    for (int e = threadIdx.x; e < NH; e += blockDim.x) {
+    return false;
+}
+// 32 consecutive accumulator columns of this thread's row (warp w reads lanes 32w..32w+31)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// shared-memory plan of the forward kernel (bytes from a 128-byte aligned base); about
+// 74 KB, so at most three CTAs share an SM and their tensor memory (3 x 128 of 512
+// columns) always fits
+constexpr uint32_t SM_W1 = 0, SM_W2 = SM_W1 + NH * NF * 2, SM_A1 = SM_W2 + NH * NH * 2,
+                   SM_A2 = SM_A1 + TILE * NF * 2, SM_B = SM_A2 + TILE * NH * 2, SM_BAR = SM_B + 3 * NH * 4,
+                   SM_USED = SM_BAR + 16;
+constexpr uint32_t SM_REQUEST = SM_USED + 128;
+static_assert(4 * (SM_REQUEST + 1024) > 228 * 1024 && kTmemCols * 3 <= 512, "at most three CTAs per SM");
+
+// Persistent forward over 128-row tiles.  Per tile: rows -> bfloat16 A tile; one MMA
+// (K = 16) into the 128 tensor-memory columns; epilogue (+b1, ReLU, bfloat16) writes the
+// second A tile; eight MMAs (K = 128) into the same columns; epilogue (+b2, ReLU, dot
+// with w3, +b3) gives y.  One thread per row: thread t of warp w owns row 32 w + t, which
+// is tensor-memory lane 32 w + t.  Input rows come from a feature matrix or, fused, are
+// built from the topology (output lambda_0 = y / scale); in training mode the hidden
+// activations are stored for the backward pass.  A wait that gives up counts in *err and
+// ends the kernel after freeing its tensor memory.
+template <bool kFused, bool kTrain>
+__global__ void __launch_bounds__(TILE)
+k_mlp_forward(MlpWeights Wt, const float* __restrict__ X, int n, FeatArgs F, float* __restrict__ out,
+              __nv_bfloat16* __restrict__ h1_out, float* __restrict__ h2_out, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    float* b1s = reinterpret_cast<float*>(sm + SM_B);
+    float* b2s = b1s + NH;
+    float* w3s = b2s + NH;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + SM_BAR);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_BAR + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar = saddr_of(bar);
+    if (warp == 0) {  // 256 tensor-memory columns for this CTA
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr_of(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // weights into the canonical layout: 16-byte chunks of 8 K values
+    for (int e = tid; e < NH * NF / 8; e += TILE) {
+        const int row = e / (NF / 8), kc = e % (NF / 8);
+        *reinterpret_cast<uint4*>(sm + SM_W1 + core_offset(row, kc, NF / 8)) =
+            __ldg(reinterpret_cast<const uint4*>(Wt.w1) + e);
+    }
+    for (int e = tid; e < NH * NH / 8; e += TILE) {
+        const int row = e / (NH / 8), kc = e % (NH / 8);
+        *reinterpret_cast<uint4*>(sm + SM_W2 + core_offset(row, kc, NH / 8)) =
+            __ldg(reinterpret_cast<const uint4*>(Wt.w2) + e);
+    }
+    for (int e = tid; e < NH; e += TILE) {
         b1s[e] = Wt.params[P_B1 + e];
         b2s[e] = Wt.params[P_B2 + e];
         w3s[e] = Wt.params[P_W3 + e];
     }
     const float b3 = Wt.params[P_B3];
+    async_proxy_fence();
+    tc_fence_before();
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, q = lane & 3;
-    const int n_tiles = (n + 15) / 16;
-    for (int tile = blockIdx.x * FWD_WARPS + warp; tile < n_tiles; tile += gridDim.x * FWD_WARPS) {
-        const int r0 = tile * 16;
-        // ---- input rows into shared memory; in the fused mode two lanes build each row's
-        //      features from the warm-start workspace (lane r: own terms + slots 0-1,
-        //      lane r + 16: slots 2-3)
-        {
-            const int rl = lane & 15, half = lane >> 4, row = r0 + rl;
-            float f[NF], sc = 0.f;
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_lane = (uint32_t)(32 * warp) << 16;
+    const uint64_t dA1 = smem_desc(saddr_of(sm + SM_A1), 128, (NF / 8) * 128);
+    const uint64_t dW1 = smem_desc(saddr_of(sm + SM_W1), 128, (NF / 8) * 128);
+    const uint64_t dA2 = smem_desc(saddr_of(sm + SM_A2), 128, (NH / 8) * 128);
+    const uint64_t dW2 = smem_desc(saddr_of(sm + SM_W2), 128, (NH / 8) * 128);
+    uint32_t parity = 0;
+    bool ok = true;
+    const int n_tiles = (n + TILE - 1) / TILE;
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int row = tile * TILE + tid;
+        // ---- input row -> bfloat16 A tile
+        float f[NF], sc = 0.f;
 #pragma unroll
-            for (int c = 0; c < NF; ++c) f[c] = 0.f;
-            if (row < n) {
-                if constexpr (kFused) {
-                    ws_features(F, row, half, f, sc);
-                } else if (half == 0) {
+        for (int c = 0; c < NF; ++c) f[c] = 0.f;
+        if (row < n) {
+            if constexpr (kFused) {
+                ws_features(F, row, 0, f, sc);
+                ws_features(F, row, 1, f, sc);
+            } else {
+                const float4* xr = reinterpret_cast<const float4*>(X + (int64_t)row * NF);
 #pragma unroll
-                    for (int c = 0; c < NF; ++c) f[c] = X[(int64_t)row * NF + c];
-                }
-            }
-            if (half == 0) {
-#pragma unroll
-                for (int c = 0; c < 10; ++c) fs[warp][rl][c] = f[c];
-                scs[warp][rl] = sc;
-            }
-            if (kFused ? half == 1 : half == 0) {
-#pragma unroll
-                for (int c = 10; c < NF; ++c) fs[warp][rl][c] = f[c];
-            }
-        }
-        __syncwarp();
-        const uint32_t a0 = pack_bf16(fs[warp][g][2 * q], fs[warp][g][2 * q + 1]);
-        const uint32_t a1 = pack_bf16(fs[warp][g + 8][2 * q], fs[warp][g + 8][2 * q + 1]);
-        const uint32_t a2 = pack_bf16(fs[warp][g][2 * q + 8], fs[warp][g][2 * q + 9]);
-        const uint32_t a3 = pack_bf16(fs[warp][g + 8][2 * q + 8], fs[warp][g + 8][2 * q + 9]);
-        // ---- layer 1: 16 n-tiles of 8 hidden units; ReLU; bfloat16 A operand of layer 2
-        uint32_t h[NH / 16][4];
-#pragma unroll
-        for (int nt = 0; nt < NH / 8; ++nt) {
-            const __nv_bfloat16* wrow = w1s + (8 * nt + g) * W1_LD;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 2 * q);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 2 * q + 8);
-            const int c = 8 * nt + 2 * q;
-            float d0 = b1s[c], d1 = b1s[c + 1], d2 = b1s[c], d3 = b1s[c + 1];
-            mma_bf16(d0, d1, d2, d3, a0, a1, a2, a3, b0, b1);
-            const uint32_t lo = pack_bf16(fmaxf(d0, 0.f), fmaxf(d1, 0.f));
-            const uint32_t hi = pack_bf16(fmaxf(d2, 0.f), fmaxf(d3, 0.f));
-            h[nt >> 1][(nt & 1) * 2 + 0] = lo;  // a0 / a2 of k-tile nt/2
-            h[nt >> 1][(nt & 1) * 2 + 1] = hi;  // a1 / a3
-            if constexpr (kTrain) {
-                if (r0 + g < n) *reinterpret_cast<uint32_t*>(h1_out + (int64_t)(r0 + g) * NH + c) = lo;
-                if (r0 + g + 8 < n) *reinterpret_cast<uint32_t*>(h1_out + (int64_t)(r0 + g + 8) * NH + c) = hi;
-            }
-        }
-        // ---- layer 2 + layer 3
-        float y_lo = 0.f, y_hi = 0.f;
-#pragma unroll 4
-        for (int nt = 0; nt < NH / 8; ++nt) {
-            const int c = 8 * nt + 2 * q;
-            float d0 = b2s[c], d1 = b2s[c + 1], d2 = b2s[c], d3 = b2s[c + 1];
-            const __nv_bfloat16* wrow = w2s + (8 * nt + g) * W2_LD;
-#pragma unroll
-            for (int kt = 0; kt < NH / 16; ++kt) {
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 16 * kt + 2 * q);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 16 * kt + 2 * q + 8);
-                mma_bf16(d0, d1, d2, d3, h[kt][0], h[kt][1], h[kt][2], h[kt][3], b0, b1);
-            }
-            d0 = fmaxf(d0, 0.f);
-            d1 = fmaxf(d1, 0.f);
-            d2 = fmaxf(d2, 0.f);
-            d3 = fmaxf(d3, 0.f);
-            y_lo = fmaf(d0, w3s[c], fmaf(d1, w3s[c + 1], y_lo));
-            y_hi = fmaf(d2, w3s[c], fmaf(d3, w3s[c + 1], y_hi));
-            if constexpr (kTrain) {
-                if (r0 + g < n) *reinterpret_cast<float2*>(h2_out + (int64_t)(r0 + g) * NH + c) = make_float2(d0, d1);
-                if (r0 + g + 8 < n) *reinterpret_cast<float2*>(h2_out + (int64_t)(r0 + g + 8) * NH + c) = make_float2(d2, d3);
-            }
-        }
-        y_lo += __shfl_xor_sync(0xFFFFFFFFu, y_lo, 1);
-        y_lo += __shfl_xor_sync(0xFFFFFFFFu, y_lo, 2);
-        y_hi += __shfl_xor_sync(0xFFFFFFFFu, y_hi, 1);
-        y_hi += __shfl_xor_sync(0xFFFFFFFFu, y_hi, 2);
-        if (q == 0) {
-            for (int half = 0; half < 2; ++half) {
-                const int rl = g + 8 * half, row = r0 + rl;
-                if (row >= n) continue;
-                const float y = (half ? y_hi : y_lo) + b3;
-                if constexpr (kFused) {
-                    const float sc = scs[warp][rl];
-                    const float l0 = y / sc;
-                    out[row] = (sc != 0.f && isfinite(l0)) ? l0 : 0.f;
-                } else {
-                    out[row] = y;
+                for (int c = 0; c < NF / 4; ++c) {
+                    const float4 v = __ldg(xr + c);
+                    f[4 * c] = v.x;
+                    f[4 * c + 1] = v.y;
+                    f[4 * c + 2] = v.z;
+                    f[4 * c + 3] = v.w;
                 }
             }
         }
-        __syncwarp();
+#pragma unroll
+        for (int kc = 0; kc < NF / 8; ++kc)
+            *reinterpret_cast<uint4*>(sm + SM_A1 + core_offset(tid, kc, NF / 8)) =
+                make_uint4(pack_bf16(f[8 * kc], f[8 * kc + 1]), pack_bf16(f[8 * kc + 2], f[8 * kc + 3]),
+                           pack_bf16(f[8 * kc + 4], f[8 * kc + 5]), pack_bf16(f[8 * kc + 6], f[8 * kc + 7]));
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- layer 1: one MMA, K = 16
+        if (tid == 0) {
+            tc_mma(tmem, dA1, dW1, 0u);
+            tc_commit(mbar);
+        }
+        ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;  // one decision for the whole CTA
+        parity ^= 1u;
+        tc_fence_after();
+        if (!ok) break;
+#pragma unroll 1
+        for (int ch = 0; ch < NH / 32; ++ch) {
+            float v[32];
+            tmem_ld32(tmem + t_lane + 32 * ch, v);
+            uint32_t hb[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                hb[j] = pack_bf16(fmaxf(v[2 * j] + b1s[32 * ch + 2 * j], 0.f),
+                                  fmaxf(v[2 * j + 1] + b1s[32 * ch + 2 * j + 1], 0.f));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 u = make_uint4(hb[4 * q], hb[4 * q + 1], hb[4 * q + 2], hb[4 * q + 3]);
+                *reinterpret_cast<uint4*>(sm + SM_A2 + core_offset(tid, 4 * ch + q, NH / 8)) = u;
+                if constexpr (kTrain) {
+                    if (row < n) reinterpret_cast<uint4*>(h1_out + (int64_t)row * NH + 32 * ch)[q] = u;
+                }
+            }
+        }
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- layer 2: eight MMAs along K = 128 (16 per step: two core matrices, 256 bytes)
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < NH / 16; ++k) tc_mma(tmem, dA2 + (uint64_t)(k * 16), dW2 + (uint64_t)(k * 16), k > 0);
+            tc_commit(mbar);
+        }
+        ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;
+        parity ^= 1u;
+        tc_fence_after();
+        if (!ok) break;
+        float y = 0.f;
+#pragma unroll 1
+        for (int ch = 0; ch < NH / 32; ++ch) {
+            float v[32];
+            tmem_ld32(tmem + t_lane + 32 * ch, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                v[j] = fmaxf(v[j] + b2s[32 * ch + j], 0.f);
+                y = fmaf(v[j], w3s[32 * ch + j], y);
+            }
+            if constexpr (kTrain) {
+                if (row < n) {
+                    float4* h2r = reinterpret_cast<float4*>(h2_out + (int64_t)row * NH + 32 * ch);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) h2r[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+        }
+        if (row < n) {
+            y += b3;
+            if constexpr (kFused) {
+                const float l0 = y / sc;
+                out[row] = (sc != 0.f && isfinite(l0)) ? l0 : 0.f;
+            } else {
+                out[row] = y;
+            }
+        }
+        tc_fence_before();
     }
+    if (!ok && tid == 0) atomicAdd(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                                : "memory");
 }
 
 // ------------------------------------------------------------------------------------
@@ -416,6 +513,7 @@ struct ilves_mlp {
     __nv_bfloat16* w2b = nullptr;
     __nv_bfloat16* h1 = nullptr;
     float* h2 = nullptr;
+    int* err = nullptr;  // tensor-core waits that gave up (see ilves_mlp_check)
 };
 
 static ilves_status mlp_status(cudaError_t e) {
@@ -441,15 +539,38 @@ static FeatArgs feat_args(const ilves_topology* T, const double* x_old, const do
     return F;
 }
 
-// one wave of persistent blocks (4 per SM fit the 47 KB of shared memory each)
-static int fwd_grid(int n) {
+// Launches the tensor-core forward: persistent CTAs, at most three per SM (the shared
+// memory request guarantees it), one 128-row tile at a time.
+template <bool kFused, bool kTrain>
+static cudaError_t launch_forward(const MlpWeights& Wt, const float* X, int n, const FeatArgs& F, float* out,
+                                  __nv_bfloat16* h1, float* h2, int* err, cudaStream_t s) {
+    static bool attr_set[64] = {};
     int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles = (n + 15) / 16;
-    return std::max(1, std::min((tiles + FWD_WARPS - 1) / FWD_WARPS, sms * 4));
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_mlp_forward<kFused, kTrain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SM_REQUEST);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    const int tiles = (n + TILE - 1) / TILE;
+    const int grid = std::max(1, std::min(tiles, 3 * sms));
+    k_mlp_forward<kFused, kTrain><<<grid, TILE, SM_REQUEST, s>>>(Wt, X, n, F, out, h1, h2, err);
+    return cudaGetLastError();
 }
 
 extern "C" int64_t ilves_mlp_param_count(void) { return P_N; }
+
+extern "C" ilves_status ilves_mlp_check(const ilves_mlp* M, int32_t* waits_given_up) {
+    if (!M || !waits_given_up) return ILVES_ERR_INVALID_ARG;
+    int v = 0;
+    const cudaError_t e = cudaMemcpy(&v, M->err, sizeof(int), cudaMemcpyDeviceToHost);
+    *waits_given_up = v;
+    if (e != cudaSuccess) return mlp_status(e);
+    return v ? ILVES_ERR_TIMEOUT : ILVES_OK;
+}
 
 extern "C" ilves_status ilves_mlp_create(int32_t max_batch, uint64_t seed, ilves_mlp** out) {
     if (!out || max_batch <= 0) return ILVES_ERR_INVALID_ARG;
@@ -471,6 +592,8 @@ extern "C" ilves_status ilves_mlp_create(int32_t max_batch, uint64_t seed, ilves
     alloc((void**)&M->w2b, NH * NH * sizeof(__nv_bfloat16));
     alloc((void**)&M->h1, (size_t)max_batch * NH * sizeof(__nv_bfloat16));
     alloc((void**)&M->h2, (size_t)max_batch * NH * sizeof(float));
+    alloc((void**)&M->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(M->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         ilves_mlp_destroy(M);
         return mlp_status(e);
@@ -494,7 +617,7 @@ extern "C" ilves_status ilves_mlp_create(int32_t max_batch, uint64_t seed, ilves
 extern "C" void ilves_mlp_destroy(ilves_mlp* M) {
     if (!M) return;
     for (void* p : {(void*)M->params, (void*)M->m, (void*)M->v, (void*)M->grad, (void*)M->loss, (void*)M->y,
-                    (void*)M->w1b, (void*)M->w2b, (void*)M->h1, (void*)M->h2})
+                    (void*)M->w1b, (void*)M->w2b, (void*)M->h1, (void*)M->h2, (void*)M->err})
         if (p) cudaFree(p);
     delete M;
 }
@@ -534,11 +657,11 @@ extern "C" ilves_status ilves_mlp_forward(const ilves_mlp* M, const float* featu
                                           void* stream) {
     if (!M || n < 0 || (n > 0 && (!features || !y))) return ILVES_ERR_INVALID_ARG;
     if (n == 0) return ILVES_OK;
+    if (reinterpret_cast<uintptr_t>(features) & 15u) return ILVES_ERR_INVALID_ARG;
     const MlpWeights Wt{M->w1b, M->w2b, M->params};
     FeatArgs F{};
-    k_mlp_forward<false, false><<<fwd_grid(n), FWD_WARPS * 32, 0, (cudaStream_t)stream>>>(Wt, features, n, F, y,
-                                                                                           nullptr, nullptr);
-    return mlp_status(cudaGetLastError());
+    return mlp_status(
+        launch_forward<false, false>(Wt, features, n, F, y, nullptr, nullptr, M->err, (cudaStream_t)stream));
 }
 
 extern "C" ilves_status ilves_warm_start(const ilves_mlp* M, const ilves_topology* T, const double* x_old,
@@ -554,8 +677,9 @@ extern "C" ilves_status ilves_warm_start(const ilves_mlp* M, const ilves_topolog
         const MlpWeights Wt{M->w1b, M->w2b, M->params};
         const int np = std::max(T->n_c, T->n_atoms);
         k_ws_prep<<<(np + 255) / 256, 256, 0, (cudaStream_t)stream>>>(F);
-        k_mlp_forward<true, false><<<fwd_grid(T->n_c), FWD_WARPS * 32, 0, (cudaStream_t)stream>>>(
-            Wt, nullptr, T->n_c, F, lambda0, nullptr, nullptr);
+        const cudaError_t e =
+            launch_forward<true, false>(Wt, nullptr, T->n_c, F, lambda0, nullptr, nullptr, M->err, (cudaStream_t)stream);
+        if (e != cudaSuccess) return mlp_status(e);
     }
     return mlp_status(cudaGetLastError());
 }
@@ -564,7 +688,9 @@ extern "C" ilves_status ilves_warm_start(const ilves_mlp* M, const ilves_topolog
 static ilves_status mlp_gradient(ilves_mlp* M, const float* X, const float* t, int32_t n, cudaStream_t s) {
     const MlpWeights Wt{M->w1b, M->w2b, M->params};
     FeatArgs F{};
-    k_mlp_forward<false, true><<<fwd_grid(n), FWD_WARPS * 32, 0, s>>>(Wt, X, n, F, M->y, M->h1, M->h2);
+    if (reinterpret_cast<uintptr_t>(X) & 15u) return ILVES_ERR_INVALID_ARG;
+    const cudaError_t e = launch_forward<false, true>(Wt, X, n, F, M->y, M->h1, M->h2, M->err, s);
+    if (e != cudaSuccess) return mlp_status(e);
     k_zero<<<(P_N + 255) / 256, 256, 0, s>>>(M->grad, P_N);
     k_zero<<<1, 32, 0, s>>>(M->loss, 1);
     k_mlp_backward<<<(n + BWD_ROWS - 1) / BWD_ROWS, NH, 0, s>>>(X, t, n, M->y, M->h1, M->h2, M->w2b, M->params,
