@@ -90,9 +90,21 @@ ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 
 // `staged` = bytes a warp copies into shared memory (everything but con_gid, which is
 // read from the global copy of the blob); `bytes` = the whole blob.
+// Partitioned molecules add the Schur-contribution tables (see SepInfo, Contrib).
 struct ProgLayout {
-    uint32_t seg, con_atoms, piv, lvl_task, lvl_piv, lane_term, inc_ptr, inc, tasks, terms, staged, con_gid, bytes;
+    uint32_t seg, con_atoms, piv, lvl_task, lvl_piv, lane_term, inc_ptr, inc, tasks, terms, sep_info, cptr, cent,
+        staged, con_gid, bytes;
 };
+
+// Partitioned molecules: the separator block's entries receive the terms of interior
+// pivots (the Schur complement contributions) from the parts that own those pivots.
+// Part q computes, for each Contrib entry of its list, the partial sums over terms
+// [e0, e1) of task `task` (all with the earlier pivot m inside part q):
+//   sum L[row,m] inv_m U[m,col]   and, for a DIAG task, sum L[row,m] inv_m y_m
+// into slot `slot` (0 or 1) of that task.  The separator phase then subtracts the
+// `ngroups` slots and the remaining terms [b_start, end) itself.
+struct SepInfo { uint32_t b_start, ngroups; };
+struct Contrib { uint32_t task, slot, e0, e1; };
 
 // Segment table (n_seg + 1 rows of {first position, first level-table entry, first atom}):
 // one segment for an ordinary molecule; for a partitioned molecule one per part, then the
@@ -101,7 +113,7 @@ struct SegRow { int32_t piv, lvl, atom; };
 
 template <class IdxT>
 ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t nterm,
-                                uint32_t nlevel, uint32_t n_seg = 1) {
+                                uint32_t nlevel, uint32_t n_seg = 1, uint32_t n_sept = 0, uint32_t n_cent = 0) {
     ProgLayout L;
     const uint32_t ix = (uint32_t)sizeof(IdxT);
     const bool compact = ix == 2u;
@@ -116,6 +128,10 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
     L.inc = o;       o = align16(o + ix * 2u * nc);
     L.tasks = o;     o = align16(o + (compact ? 4u * ntask : 4u * ix * (ntask + 1)));
     L.terms = o;     o = align16(o + (uint32_t)sizeof(typename TermOf<IdxT>::T) * nterm);
+    const bool parted = n_seg > 1;
+    L.sep_info = o;  o = align16(o + (parted ? 8u * n_sept : 0u));
+    L.cptr = o;      o = align16(o + (parted ? 4u * n_seg : 0u));  // n_parts + 1 = n_seg entries
+    L.cent = o;      o = align16(o + (parted ? 16u * n_cent : 0u));
     L.staged = o;
     L.con_gid = o;   o = align16(o + 4u * nc);
     L.bytes = o;
@@ -159,7 +175,7 @@ ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint
     return S;
 }
 
-// One molecule as the kernels see it (56 bytes).
+// One molecule as the kernels see it (64 bytes).
 struct MolDesc {
     int64_t blob_off;    // byte offset of the program blob in the blob buffer (16-B aligned)
     int64_t work_off;    // large path: byte offset of the numerical state in the workspace
@@ -171,6 +187,8 @@ struct MolDesc {
     int32_t na, nc;
     int32_t nlevel;  // level-table entries - 1 (for one segment: its number of levels)
     int32_t n_seg;   // 1, or parts + 1 for a partitioned molecule
+    int32_t n_sept;  // partitioned: tasks of the separator segment (they are the last ones)
+    int32_t n_cent;  // partitioned: Schur contribution entries over all parts
 };
 
 }  // namespace ilves

@@ -203,8 +203,9 @@ struct SolveArgs {
 // and S holds s_k = x_unc,i - x_unc,j, so that r_k = s_k + (dx_i - dx_j).
 //
 // kCoh: the state lives in global memory and other CTAs write parts of it (partitioned
-// molecules), so mutable state is read through L2 (ld.global.cg) and never from a
-// possibly stale L1 line; the program is read-only and read through the texture path.
+// molecules), so state another CTA may have written is read through L2 (ld.global.cg)
+// and never from a possibly stale L1 line (see ldf); the program is read-only and read
+// through the texture path.
 template <bool kCoh, class T>
 __device__ __forceinline__ T lds(const T* p) {
     if constexpr (kCoh) {
@@ -220,6 +221,16 @@ __device__ __forceinline__ T lds(const T* p) {
     } else {
         return *p;
     }
+}
+// State loads of a partitioned molecule: values written by another CTA ("foreign": the
+// separator block and its atoms) are read through L2; everything else -- the CTA's own
+// parts, and arrays fixed since set-up -- through L1.  Plain loads in the other modes.
+template <bool kCoh, class T>
+__device__ __forceinline__ T ldf(const T* p, bool foreign) {
+    if constexpr (kCoh) {
+        if (foreign) return lds<true>(p);
+    }
+    return *p;
 }
 template <bool kCoh, class T>
 __device__ __forceinline__ T ldp(const T* p) {
@@ -259,6 +270,15 @@ struct MolView {
     float* RHOL;  // float-float mode: low parts of rho (SoA); the high parts are RHOF.xyz
     LP *WL, *Y, *V;
     V4 *RHOF, *RF;  // RHOF[p].w = w_i + w_j, RF[p].w = 1 / pivot p
+    // partitioned molecules: Schur contribution tables and their values (4 per separator
+    // task: two partial sums of L inv U, two of L inv y), in the workspace after the state
+    const SepInfo* sep_info;
+    const int32_t* cptr;
+    const Contrib* cent;
+    LP* CT;
+    int sep_t0;
+    int sep_p0;    // first separator position (nc if not partitioned)
+    bool cohall;   // every state load is foreign (the separator phase)
     double* STG;  // x_old gathered AoS (warp path set-up only; aliases RF and later arrays)
     const MolDesc* D;
     const SolveArgs* A;
@@ -273,7 +293,7 @@ struct MolView {
         tolf = (float)a.tol;
         na = d.na;
         nc = d.nc;
-        const ProgLayout PL = prog_layout<IdxT>(na, nc, d.ntask, d.nterm, d.nlevel, d.n_seg);
+        const ProgLayout PL = prog_layout<IdxT>(na, nc, d.ntask, d.nterm, d.nlevel, d.n_seg, d.n_sept, d.n_cent);
         const StateLayout SL = state_layout(na, nc, d.ntask, sizeof(LP), DF);
         seg = reinterpret_cast<const SegRow*>(prog + PL.seg);
         con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
@@ -299,6 +319,13 @@ struct MolView {
         Y = reinterpret_cast<LP*>(st + SL.y);
         V = reinterpret_cast<LP*>(st + SL.vals);
         STG = reinterpret_cast<double*>(st + SL.stage);
+        sep_info = reinterpret_cast<const SepInfo*>(prog + PL.sep_info);
+        cptr = reinterpret_cast<const int32_t*>(prog + PL.cptr);
+        cent = reinterpret_cast<const Contrib*>(prog + PL.cent);
+        CT = reinterpret_cast<LP*>(st + SL.bytes);
+        sep_t0 = d.ntask - d.n_sept;
+        sep_p0 = d.n_seg > 1 ? ldp<kCoh>(&seg[d.n_seg - 1].piv) : nc;
+        cohall = false;
     }
     __device__ __forceinline__ int64_t gid(int a) const {
         return D->atom_base >= 0 ? (int64_t)D->atom_base + a : (int64_t)A->atom_gid[D->gid_off + a];
@@ -306,7 +333,8 @@ struct MolView {
     __device__ __forceinline__ ConA<IdxT> cons(int p) const { return ldp<kCoh>(con + p); }
     __device__ __forceinline__ int32_t gid_of_con(int p) const { return __ldg(con_gid + p); }
     __device__ __forceinline__ LP* inv_ptr(int p) const { return reinterpret_cast<LP*>(RF + p) + 3; }
-    __device__ __forceinline__ LP inv(int p) const { return lds<kCoh>(inv_ptr(p)); }
+    __device__ __forceinline__ bool foreign(int p) const { return cohall || p >= sep_p0; }
+    __device__ __forceinline__ LP inv(int p) const { return ldf<kCoh>(inv_ptr(p), foreign(p)); }
 
     // ---- S1
     // weights of atom a; with stage_ref, x_old is staged in X for s1_constraint
@@ -398,38 +426,38 @@ struct MolView {
         cp_async_wait_all();
     }
     __device__ __forceinline__ void s1_atom_local(int a) {
-        const double w = lds<kCoh>(W + a);
+        const double w = *(W + a);
         if constexpr (DF) W[a] = as_bits(df_split(w));
         WL[a] = to_lp<LP>(w);
     }
     __device__ __forceinline__ void s1_constraint_local(int p) {
         const ConA<IdxT> c = cons(p);
         const int i = c.i, j = c.j;
-        const double rx = lds<kCoh>(STG + 3 * i) - lds<kCoh>(STG + 3 * j);
-        const double ry = lds<kCoh>(STG + 3 * i + 1) - lds<kCoh>(STG + 3 * j + 1);
-        const double rz = lds<kCoh>(STG + 3 * i + 2) - lds<kCoh>(STG + 3 * j + 2);
+        const double rx = *(STG + 3 * i) - *(STG + 3 * j);
+        const double ry = *(STG + 3 * i + 1) - *(STG + 3 * j + 1);
+        const double rz = *(STG + 3 * i + 2) - *(STG + 3 * j + 2);
         V4 v;
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
         v.z = to_lp<LP>(rz);
-        v.w = lds<kCoh>(WL + i) + lds<kCoh>(WL + j);
+        v.w = *(WL + i) + *(WL + j);
         RHOF[p] = v;
-        const double dd = lds<kCoh>(D2 + p);
+        const double dd = *(D2 + p);
         if constexpr (DF) {
             RHOL[p] = df_split(rx).lo;
             RHOL[nc + p] = df_split(ry).lo;
             RHOL[2 * nc + p] = df_split(rz).lo;
             D2[p] = as_bits(df_split(dd * dd));
-            SK[p] = as_bits(df_split(lds<kCoh>(X + 3 * i) - lds<kCoh>(X + 3 * j)));
-            SK[nc + p] = as_bits(df_split(lds<kCoh>(X + 3 * i + 1) - lds<kCoh>(X + 3 * j + 1)));
-            SK[2 * nc + p] = as_bits(df_split(lds<kCoh>(X + 3 * i + 2) - lds<kCoh>(X + 3 * j + 2)));
+            SK[p] = as_bits(df_split(*(X + 3 * i) - *(X + 3 * j)));
+            SK[nc + p] = as_bits(df_split(*(X + 3 * i + 1) - *(X + 3 * j + 1)));
+            SK[2 * nc + p] = as_bits(df_split(*(X + 3 * i + 2) - *(X + 3 * j + 2)));
         } else {
             RHO[p] = rx;
             RHO[nc + p] = ry;
             RHO[2 * nc + p] = rz;
             D2[p] = dd * dd;
         }
-        const float l0 = A->lambda0 ? lds<kCoh>(reinterpret_cast<const float*>(Y + p)) : 0.0f;
+        const float l0 = A->lambda0 ? *(reinterpret_cast<const float*>(Y + p)) : 0.0f;
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         Y[p] = (LP)l0;
     }
@@ -445,31 +473,31 @@ struct MolView {
             for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
                 const unsigned v = ldp<kCoh>(inc + e);
                 const int p = (int)(v >> 1);
-                const float dl = (float)lds<kCoh>(Y + p);
+                const float dl = (float)ldf<kCoh>(Y + p, foreign(p));
                 const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
-                const V4 hi = lds<kCoh>(RHOF + p);
-                ax = df_add(ax, df_mul_f(dfloat{hi.x, lds<kCoh>(RHOL + p)}, c));
-                ay = df_add(ay, df_mul_f(dfloat{hi.y, lds<kCoh>(RHOL + nc + p)}, c));
-                az = df_add(az, df_mul_f(dfloat{hi.z, lds<kCoh>(RHOL + 2 * nc + p)}, c));
+                const V4 hi = *(RHOF + p);
+                ax = df_add(ax, df_mul_f(dfloat{hi.x, *(RHOL + p)}, c));
+                ay = df_add(ay, df_mul_f(dfloat{hi.y, *(RHOL + nc + p)}, c));
+                az = df_add(az, df_mul_f(dfloat{hi.z, *(RHOL + 2 * nc + p)}, c));
             }
-            const dfloat w = as_df(lds<kCoh>(W + a));
-            return {as_bits(df_sub(as_df(lds<kCoh>(X + a)), df_mul(w, ax))),
-                    as_bits(df_sub(as_df(lds<kCoh>(X + na + a)), df_mul(w, ay))),
-                    as_bits(df_sub(as_df(lds<kCoh>(X + 2 * na + a)), df_mul(w, az)))};
+            const dfloat w = as_df(*(W + a));
+            return {as_bits(df_sub(as_df(*(X + a)), df_mul(w, ax))),
+                    as_bits(df_sub(as_df(*(X + na + a)), df_mul(w, ay))),
+                    as_bits(df_sub(as_df(*(X + 2 * na + a)), df_mul(w, az)))};
         } else {
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
                 const unsigned v = ldp<kCoh>(inc + e);
                 const int p = (int)(v >> 1);
-                const LP dl = lds<kCoh>(Y + p);
+                const LP dl = ldf<kCoh>(Y + p, foreign(p));
                 const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
-                ax = fma(c, lds<kCoh>(RHO + p), ax);
-                ay = fma(c, lds<kCoh>(RHO + nc + p), ay);
-                az = fma(c, lds<kCoh>(RHO + 2 * nc + p), az);
+                ax = fma(c, *(RHO + p), ax);
+                ay = fma(c, *(RHO + nc + p), ay);
+                az = fma(c, *(RHO + 2 * nc + p), az);
             }
-            const double w = lds<kCoh>(W + a);
-            return {fma(-w, ax, lds<kCoh>(X + a)), fma(-w, ay, lds<kCoh>(X + na + a)),
-                    fma(-w, az, lds<kCoh>(X + 2 * na + a))};
+            const double w = *(W + a);
+            return {fma(-w, ax, *(X + a)), fma(-w, ay, *(X + na + a)),
+                    fma(-w, az, *(X + 2 * na + a))};
         }
     }
     __device__ __forceinline__ void upd_store(int a, const Upd& u) {
@@ -487,14 +515,15 @@ struct MolView {
     __device__ __forceinline__ Viol viol_eval(int p) const {
         const ConA<IdxT> cc = cons(p);
         const int i = cc.i, j = cc.j;
+        const bool fx = foreign(p);
         Viol o;
         if constexpr (DF) {
-            const dfloat rx = df_add(as_df(lds<kCoh>(SK + p)), df_sub(as_df(lds<kCoh>(X + i)), as_df(lds<kCoh>(X + j))));
-            const dfloat ry = df_add(as_df(lds<kCoh>(SK + nc + p)),
-                                     df_sub(as_df(lds<kCoh>(X + na + i)), as_df(lds<kCoh>(X + na + j))));
-            const dfloat rz = df_add(as_df(lds<kCoh>(SK + 2 * nc + p)),
-                                     df_sub(as_df(lds<kCoh>(X + 2 * na + i)), as_df(lds<kCoh>(X + 2 * na + j))));
-            const dfloat d2 = as_df(lds<kCoh>(D2 + p));
+            const dfloat rx = df_add(as_df(*(SK + p)), df_sub(as_df(ldf<kCoh>(X + i, fx)), as_df(ldf<kCoh>(X + j, fx))));
+            const dfloat ry = df_add(as_df(*(SK + nc + p)),
+                                     df_sub(as_df(ldf<kCoh>(X + na + i, fx)), as_df(ldf<kCoh>(X + na + j, fx))));
+            const dfloat rz = df_add(as_df(*(SK + 2 * nc + p)),
+                                     df_sub(as_df(ldf<kCoh>(X + 2 * na + i, fx)), as_df(ldf<kCoh>(X + 2 * na + j, fx))));
+            const dfloat d2 = as_df(*(D2 + p));
             // |r|^2 - d^2: exact products of the high words, two-sums of the big terms,
             // every rounding error collected in a small tail
             const float px = __fmul_rn(rx.hi, rx.hi), ex = __fmaf_rn(rx.hi, rx.hi, -px);
@@ -516,10 +545,10 @@ struct MolView {
             o.v.z = rz.hi;
             o.y = sg;
         } else {
-            const double rx = lds<kCoh>(X + i) - lds<kCoh>(X + j);
-            const double ry = lds<kCoh>(X + na + i) - lds<kCoh>(X + na + j);
-            const double rz = lds<kCoh>(X + 2 * na + i) - lds<kCoh>(X + 2 * na + j);
-            const double d2 = lds<kCoh>(D2 + p);
+            const double rx = ldf<kCoh>(X + i, fx) - ldf<kCoh>(X + j, fx);
+            const double ry = ldf<kCoh>(X + na + i, fx) - ldf<kCoh>(X + na + j, fx);
+            const double rz = ldf<kCoh>(X + 2 * na + i, fx) - ldf<kCoh>(X + 2 * na + j, fx);
+            const double d2 = *(D2 + p);
             const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
             o.conv = abs_le(sg, A->tol * d2);
             o.bad = nonfinite(sg);
@@ -547,8 +576,8 @@ struct MolView {
     //      Every entry is a - sum_m Lt[row,m] inv_m U[m,col], a = 4 s s' w_atom r_row . rho_col
     //      (for DIAG entries w_atom = w_i + w_j, kept in RHOF[row].w).
     __device__ __forceinline__ LP assemble(int row, int col, int atom, bool neg, bool diag) const {
-        const V4 rr = lds<kCoh>(RF + row), pp = lds<kCoh>(RHOF + col);
-        const LP wv = diag ? pp.w : lds<kCoh>(WL + atom);
+        const V4 rr = ldf<kCoh>(RF + row, foreign(row)), pp = *(RHOF + col);
+        const LP wv = diag ? pp.w : *(WL + atom);
         const LP c = neg ? LP(-4) * wv : LP(4) * wv;
         return c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
     }
@@ -563,15 +592,16 @@ struct MolView {
         for (int e = e0; e < e1; ++e) {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
-            const LP li = lds<kCoh>(V + TO::l(tr)) * inv(m);
-            sacc -= li * lds<kCoh>(V + TO::u(tr));
-            if (diag) yv += li * lds<kCoh>(Y + m);
+            const bool fm = foreign(m);
+            const LP li = ldf<kCoh>(V + TO::l(tr), fm) * inv(m);
+            sacc -= li * ldf<kCoh>(V + TO::u(tr), fm);
+            if (diag) yv += li * ldf<kCoh>(Y + m, fm);
         }
         V[t] = sacc;
         if (diag) {
             singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
             *inv_ptr(row) = lp_rcp(sacc);
-            Y[row] = lds<kCoh>(Y + row) - yv;
+            Y[row] = ldf<kCoh>(Y + row, foreign(row)) - yv;
         }
     }
     // large molecules: task records with term pointers
@@ -601,15 +631,16 @@ struct MolView {
         for (int e = e0; e < e1; ++e) {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
-            yv += lds<kCoh>(V + TO::l(tr)) * inv(m) * lds<kCoh>(Y + m);
+            const bool fm = foreign(m);
+            yv += ldf<kCoh>(V + TO::l(tr), fm) * inv(m) * ldf<kCoh>(Y + m, fm);
         }
-        Y[p] = lds<kCoh>(Y + p) - yv;
+        Y[p] = ldf<kCoh>(Y + p, foreign(p)) - yv;
     }
     __device__ __forceinline__ void forward(int t, int p) {
         forward_terms(p, ldp<kCoh>(tasks + t).tstart, ldp<kCoh>(tasks + t + 1).tstart);
     }
     // ILVES-F assembles A(x_old, x_old): the Jacobian rows are the reference bonds
-    __device__ __forceinline__ void chord_rows(int p) { RF[p] = lds<kCoh>(RHOF + p); }
+    __device__ __forceinline__ void chord_rows(int p) { RF[p] = *(RHOF + p); }
 
     // ---- backward S5 for pivot p: delta_p = inv_p (y_p - sum_q U[p,q] delta_q)
     __device__ __forceinline__ int task_col(int t) const {
@@ -619,30 +650,95 @@ struct MolView {
     __device__ __forceinline__ void backward(int p) {
         const Piv<IdxT> pv = ldp<kCoh>(piv + p);
         const int us = pv.diag, nu = pv.nup;
-        LP dl = lds<kCoh>(Y + p);
-        for (int k = 0; k < nu; ++k) dl -= lds<kCoh>(V + us + k) * lds<kCoh>(Y + task_col(us + k));
+        const bool fp = foreign(p);
+        LP dl = ldf<kCoh>(Y + p, fp);
+        for (int k = 0; k < nu; ++k) {
+            const int q = task_col(us + k);
+            dl -= ldf<kCoh>(V + us + k, fp) * ldf<kCoh>(Y + q, foreign(q));
+        }
         Y[p] = dl * inv(p);
     }
+    // ---- partitioned molecules: part-side Schur contribution entry c (factor: the L inv U
+    //      sum as well; DIAG tasks: the L inv y sum of the forward solve)
+    __device__ __forceinline__ void contrib(int c, bool factor) {
+        const Contrib E = ldp<kCoh>(cent + c);
+        const TaskT tk = ldp<kCoh>(tasks + E.task);
+        const bool diag = tk.row == tk.col;
+        LP sv = LP(0), sy = LP(0);
+        for (uint32_t e = E.e0; e < E.e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            const bool fm = foreign(m);
+            const LP li = ldf<kCoh>(V + TO::l(tr), fm) * inv(m);
+            if (factor) sv += li * ldf<kCoh>(V + TO::u(tr), fm);
+            if (diag) sy += li * ldf<kCoh>(Y + m, fm);
+        }
+        LP* ct = CT + 4 * (E.task - sep_t0);
+        if (factor) ct[E.slot] = sv;
+        if (diag) ct[2 + E.slot] = sy;
+    }
+    // separator task t: the parts' contributions, then its remaining terms
+    __device__ __forceinline__ void task_sep(int t, bool diag, bool& singular) {
+        const TaskT tk = ldp<kCoh>(tasks + t);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        const SepInfo si = ldp<kCoh>(sep_info + (t - sep_t0));
+        const LP a = assemble(tk.row, tk.col, tk.atomsign >> 1, tk.atomsign & 1, diag);
+        const LP* ct = CT + 4 * (t - sep_t0);
+        LP sacc = a, yv = LP(0);
+        for (uint32_t g = 0; g < si.ngroups; ++g) {
+            sacc -= lds<kCoh>(ct + g);
+            if (diag) yv += lds<kCoh>(ct + 2 + g);
+        }
+        for (int e = (int)si.b_start; e < e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            const LP li = lds<kCoh>(V + TO::l(tr)) * inv(m);
+            sacc -= li * lds<kCoh>(V + TO::u(tr));
+            if (diag) yv += li * lds<kCoh>(Y + m);
+        }
+        V[t] = sacc;
+        if (diag) {
+            singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+            *inv_ptr(tk.row) = lp_rcp(sacc);
+            Y[tk.row] = lds<kCoh>(Y + tk.row) - yv;
+        }
+    }
+    // forward solve alone for separator pivot p (DIAG task t)
+    __device__ __forceinline__ void forward_sep(int t, int p) {
+        const SepInfo si = ldp<kCoh>(sep_info + (t - sep_t0));
+        const LP* ct = CT + 4 * (t - sep_t0);
+        LP yv = LP(0);
+        for (uint32_t g = 0; g < si.ngroups; ++g) yv += lds<kCoh>(ct + 2 + g);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        for (int e = (int)si.b_start; e < e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            yv += lds<kCoh>(V + TO::l(tr)) * inv(m) * lds<kCoh>(Y + m);
+        }
+        Y[p] = lds<kCoh>(Y + p) - yv;
+    }
+
     __device__ __forceinline__ void lambda_acc(int p) {
-        if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(lds<kCoh>(LAM + p)), (float)lds<kCoh>(Y + p)));
-        else LAM[p] = lds<kCoh>(LAM + p) + to_hp(lds<kCoh>(Y + p));
+        const LP dl = ldf<kCoh>(Y + p, foreign(p));
+        if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(*(LAM + p)), (float)dl));
+        else LAM[p] = *(LAM + p) + to_hp(dl);
     }
 
     // ---- S7
     __device__ __forceinline__ void out_atom(int a) {
         const int64_t g = gid(a);
         if constexpr (DF) {
-            A->x_out[3 * g] = A->x_unc[3 * g] + df_join(as_df(lds<kCoh>(X + a)));
-            A->x_out[3 * g + 1] = A->x_unc[3 * g + 1] + df_join(as_df(lds<kCoh>(X + na + a)));
-            A->x_out[3 * g + 2] = A->x_unc[3 * g + 2] + df_join(as_df(lds<kCoh>(X + 2 * na + a)));
+            A->x_out[3 * g] = A->x_unc[3 * g] + df_join(as_df(*(X + a)));
+            A->x_out[3 * g + 1] = A->x_unc[3 * g + 1] + df_join(as_df(*(X + na + a)));
+            A->x_out[3 * g + 2] = A->x_unc[3 * g + 2] + df_join(as_df(*(X + 2 * na + a)));
         } else {
-            A->x_out[3 * g] = lds<kCoh>(X + a);
-            A->x_out[3 * g + 1] = lds<kCoh>(X + na + a);
-            A->x_out[3 * g + 2] = lds<kCoh>(X + 2 * na + a);
+            A->x_out[3 * g] = *(X + a);
+            A->x_out[3 * g + 1] = *(X + na + a);
+            A->x_out[3 * g + 2] = *(X + 2 * na + a);
         }
     }
     __device__ __forceinline__ void out_lambda(int p) {
-        const double l = lds<kCoh>(LAM + p);
+        const double l = *(LAM + p);
         A->lambda_out[gid_of_con(p)] = DF ? df_join(as_df(l)) : l;
     }
 };
@@ -800,7 +896,7 @@ struct PartSync {
 };
 
 template <class Mode>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, uint8_t* work, PartSync* sync,
                SolveArgs A) {
     const MolDesc D = *desc;
@@ -890,21 +986,25 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                     for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
                 __syncthreads();
             }
+            // this part's contributions to the separator block (Schur complement)
+            const int c1 = __ldg(M.cptr + q + 1);
+            for (int c = __ldg(M.cptr + q) + r0; c < c1; c += ts) M.contrib(c, factor);
         }
         if (__syncthreads_or(singular) && r0 == 0) atomicOr(&sync->singular[slot], 1);
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
         // ---- phase B: CTA 0 factorises the separator block (the Schur complement) and
         //      solves it forward and backward
         if (b == 0) {
+            M.cohall = true;  // the separator block: every value may come from another CTA
             bool sing = false;
             const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
             for (int l = l0; l < l1; ++l) {
                 const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
                 const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
                 if (factor)
-                    for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, sing);
+                    for (int t = t0 + r0; t < t1; t += ts) M.task_sep(t, t < t0 + np, sing);
                 else
-                    for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
+                    for (int p = p0 + r0; p < p1; p += ts) M.forward_sep(t0 + (p - p0), p);
                 __syncthreads();
             }
             if (__syncthreads_or(sing) && r0 == 0) atomicOr(&sync->singular[slot], 1);
@@ -913,6 +1013,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                 for (int p = __ldg(M.lvl_piv + l) + r0; p < p1; p += ts) M.backward(p);
                 __syncthreads();
             }
+            M.cohall = false;
         }
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
         if (__ldcg(&sync->singular[slot])) {
@@ -1165,10 +1266,14 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         D.nc = (int32_t)M.cons.size();
         D.nlevel = M.nlevel;
         D.n_seg = M.n_seg;
+        D.n_sept = M.n_sept;
+        D.n_cent = M.n_cent;
         D.work_off = 0;
-        if (M.large) {
+        if (M.large) {  // state, then (partitioned) 4 contribution values per separator task
             D.work_off = woff;
-            woff += (std::max(state_layout(na, D.nc, M.ntask, 8, false).bytes, state_layout(na, D.nc, M.ntask, 4, true).bytes) + 255) & ~int64_t(255);
+            const int64_t st = std::max(state_layout(na, D.nc, M.ntask, 8, false).bytes,
+                                        state_layout(na, D.nc, M.ntask, 4, true).bytes);
+            woff += (st + 4 * 8 * (int64_t)M.n_sept + 255) & ~int64_t(255);
         }
     }
     std::vector<uint8_t> blob((size_t)std::max<int64_t>(boff, 16), 0);

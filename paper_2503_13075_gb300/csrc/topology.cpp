@@ -143,6 +143,11 @@ struct Program {
     std::vector<int32_t> seg_piv, seg_lvl, seg_atom;  // n_seg + 1 each
     int64_t passes_factor = 0, passes_solve = 0;
     int64_t n_fill = 0;
+    // partitioned: Schur contributions of the parts to the separator tasks
+    int32_t sep_t0 = 0;                        // first task of the separator segment
+    std::vector<SepInfo> sep_info;             // per separator task
+    std::vector<int32_t> cptr;                 // per part: [cptr[q], cptr[q+1]) into cent
+    std::vector<Contrib> cent;
 };
 
 // seg (optional): segment of every local constraint (a part, or n_seg - 1 for the
@@ -266,6 +271,38 @@ static Program compile(int32_t nc, const Elimination& E, const std::vector<int32
         P.terms.insert(P.terms.end(), tterms[k].begin(), tterms[k].end());
     }
     P.tasks[t] = {0u, 0u, kNoAtom32, (uint32_t)P.terms.size()};  // sentinel
+    if (n_seg > 1) {
+        // Schur contributions: the terms of a separator task are in ascending pivot
+        // position, so the interior pivots come first, grouped by part; the first two
+        // groups are summed by their parts, the rest (and the separator pivots) by the
+        // separator phase itself
+        const int32_t sep_seg = n_seg - 1, sep_p0 = P.seg_piv[sep_seg];
+        P.sep_t0 = P.lvl_task[P.seg_lvl[sep_seg]];
+        std::vector<int32_t> seg_of(nc, sep_seg);
+        for (int32_t g = 0; g < sep_seg; ++g)
+            for (int32_t p = P.seg_piv[g]; p < P.seg_piv[g + 1]; ++p) seg_of[p] = g;
+        std::vector<std::vector<Contrib>> per_part(sep_seg);
+        P.sep_info.assign(t - P.sep_t0, SepInfo{0u, 0u});
+        for (int32_t k = P.sep_t0; k < t; ++k) {
+            const uint32_t e0 = P.tasks[k].tstart, e1 = P.tasks[k + 1].tstart;
+            uint32_t e = e0, ng = 0;
+            while (e < e1 && (int32_t)P.terms[e].m < sep_p0 && ng < 2) {
+                const int32_t q = seg_of[P.terms[e].m];
+                uint32_t f = e;
+                while (f < e1 && (int32_t)P.terms[f].m < sep_p0 && seg_of[P.terms[f].m] == q) ++f;
+                per_part[q].push_back(Contrib{(uint32_t)k, ng, e, f});
+                ++ng;
+                e = f;
+            }
+            P.sep_info[k - P.sep_t0] = SepInfo{e, ng};
+        }
+        P.cptr.assign(sep_seg + 1, 0);
+        for (int32_t q = 0; q < sep_seg; ++q) {
+            P.cptr[q] = (int32_t)P.cent.size();
+            P.cent.insert(P.cent.end(), per_part[q].begin(), per_part[q].end());
+        }
+        P.cptr[sep_seg] = (int32_t)P.cent.size();
+    }
     for (int32_t g = 0; g < n_seg; ++g) {
         const int32_t b = P.seg_lvl[g];
         for (int32_t l = 0; l < seg_nlev[g]; ++l) {
@@ -351,7 +388,8 @@ static Program choose_order(int32_t nc, int32_t na, const std::vector<std::vecto
 template <class IdxT>
 static ProgLayout layout_for(const MolHost& M) {
     return prog_layout<IdxT>((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(), (uint32_t)M.ntask,
-                             (uint32_t)M.nterm, (uint32_t)M.nlevel, (uint32_t)M.n_seg);
+                             (uint32_t)M.nterm, (uint32_t)M.nlevel, (uint32_t)M.n_seg, (uint32_t)M.n_sept,
+                             (uint32_t)M.n_cent);
 }
 
 template <class IdxT>
@@ -427,6 +465,11 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
             tasks[t].tstart = (IdxT)w.tstart;
         }
         for (size_t k = 0; k < P.terms.size(); ++k) terms[k] = term_of(k);
+        if (P.n_seg > 1) {
+            std::memcpy(dst + L.sep_info, P.sep_info.data(), P.sep_info.size() * sizeof(SepInfo));
+            std::memcpy(dst + L.cptr, P.cptr.data(), P.cptr.size() * sizeof(int32_t));
+            std::memcpy(dst + L.cent, P.cent.data(), P.cent.size() * sizeof(Contrib));
+        }
     }
 }
 
@@ -565,6 +608,8 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             Elimination E = eliminate_rounds(nc, adj, 2, false, &stage);
             Program* P = new Program(compile(nc, E, M.ci, M.cj, 256, na, &seg, np + 1, &seg_atom));
             M.n_seg = np + 1;
+            M.n_sept = (int32_t)P->sep_info.size();
+            M.n_cent = (int32_t)P->cent.size();
             M.nlevel = P->nlevel;
             M.ntask = (int32_t)P->tasks.size() - 1;
             M.nterm = (int32_t)P->terms.size();

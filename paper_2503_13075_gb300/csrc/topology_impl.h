@@ -20,14 +20,12 @@ struct MolHost {
     bool parted = false;  // partitioned: solved by a cooperative multi-CTA launch
     int32_t n_seg = 1;
     int32_t nlevel = 0, ntask = 0, nterm = 0, n_fill = 0;
+    int32_t n_sept = 0, n_cent = 0;  // partitioned: separator tasks, Schur contribution entries
     int64_t passes = 0;
 };
 
 struct Program;  // topology.cpp
 
-// Persistent schedule of the warp-per-molecule kernel: CTA c owns warp slots
-// [cta_slot_ptr[c], cta_slot_ptr[c+1]); slot s has a fixed shared-memory slice at byte
-// offset slot_off[s] and solves molecules slot_mol[slot_ptr[s] .. slot_ptr[s+1]) in order.
 // Warp-slot schedule of the batched kernel: slot s (warp s - cta_slot_ptr[c] of CTA c)
 // owns the shared-memory slice at slot_off[s] and solves slot_mol[slot_ptr[s] ..
 // slot_ptr[s + 1]) in order, then takes molecules from the shared pool (pool_mol, one

@@ -222,3 +222,16 @@ def test_chord_method_ilves_f(prec, case):
     assert np.abs(x - ref.x).max() <= X_TOL
     assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL
     assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("part", [24, 64])
+def test_partitioned_small_parts(prec, part):
+    """Many small parts: most constraints couple to the separator block, whose entries
+    receive the parts' Schur contributions (two per entry) plus in-line terms."""
+    s = wl.protein_like(n_atoms=3000, seed=1010)
+    ref = orc.solve_system(s, tol=TOL)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=500, part_constraints=part)
+    assert t.n_large == 1
+    _, x, lam, it, st = run(s, prec, topo=t)
+    compare(s, ref, x, lam, it, st)
