@@ -718,6 +718,83 @@ struct MolView {
         Y[p] = lds<kCoh>(Y + p) - yv;
     }
 
+    // ---- the separator phase in shared memory (one CTA): SV = values of the separator
+    //      tasks, SRF = Jacobian rows of the separators (.w = 1 / pivot), SY = their
+    //      right-hand side / solution; indices local to the separator block.  Terms of
+    //      interior pivots beyond the parts' contributions read the global state.
+    __device__ __forceinline__ void sep_task_smem(int t, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY) const {
+        const TaskT tk = ldp<kCoh>(tasks + t);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        const int tl = t - sep_t0, row = tk.row - sep_p0, col = tk.col - sep_p0;
+        const SepInfo si = ldp<kCoh>(sep_info + tl);
+        const V4 rr = SRF[row], pp = *(RHOF + tk.col);
+        const LP wv = diag ? pp.w : *(WL + (tk.atomsign >> 1));
+        const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
+        const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+        LP sacc = a + SV[tl], yv = LP(0);  // SV, SY hold minus the parts' contributions
+        for (int e = (int)si.b_start; e < e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            LP li, u, ym;
+            if (m >= sep_p0) {
+                li = SV[TO::l(tr) - sep_t0] * reinterpret_cast<const LP*>(SRF + (m - sep_p0))[3];
+                u = SV[TO::u(tr) - sep_t0];
+                ym = SY[m - sep_p0];
+            } else {  // an interior pivot past the parts' two contribution slots
+                li = lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(inv_ptr(m));
+                u = lds<kCoh>(V + TO::u(tr));
+                ym = lds<kCoh>(Y + m);
+            }
+            sacc -= li * u;
+            if (diag) yv += li * ym;
+        }
+        SV[tl] = sacc;
+        if (diag) {
+            singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+            reinterpret_cast<LP*>(SRF + row)[3] = lp_rcp(sacc);
+            SY[row] -= yv;
+        }
+        (void)col;
+    }
+    __device__ __forceinline__ void sep_forward_smem(int t, int p, const LP* SV, const V4* SRF, LP* SY) const {
+        const int tl = t - sep_t0;
+        const SepInfo si = ldp<kCoh>(sep_info + tl);
+        LP yv = LP(0);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        for (int e = (int)si.b_start; e < e1; ++e) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            if (m >= sep_p0)
+                yv += SV[TO::l(tr) - sep_t0] * reinterpret_cast<const LP*>(SRF + (m - sep_p0))[3] * SY[m - sep_p0];
+            else
+                yv += lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(inv_ptr(m)) * lds<kCoh>(Y + m);
+        }
+        SY[p - sep_p0] -= yv;
+    }
+    // staging of separator task t: the parts' contributions, summed, go into SV[t] (as
+    //      its negative start value, factor iterations only) and, for a DIAG task, into
+    //      the right-hand side SY of its pivot
+    __device__ __forceinline__ void sep_stage_smem(int t, bool factor, LP* SV, LP* SY) const {
+        const int tl = t - sep_t0;
+        const SepInfo si = ldp<kCoh>(sep_info + tl);
+        const TaskT tk = ldp<kCoh>(tasks + t);
+        const LP* ct = CT + 4 * tl;
+        LP cv = LP(0), cy = LP(0);
+        for (uint32_t g = 0; g < si.ngroups; ++g) {
+            cv += lds<kCoh>(ct + g);
+            cy += lds<kCoh>(ct + 2 + g);
+        }
+        if (factor) SV[tl] = -cv;
+        if (tk.row == tk.col) SY[tk.row - sep_p0] -= cy;
+    }
+    __device__ __forceinline__ void sep_backward_smem(int p, const LP* SV, const V4* SRF, LP* SY) const {
+        const Piv<IdxT> pv = ldp<kCoh>(piv + p);
+        const int us = pv.diag, nu = pv.nup, pl = p - sep_p0;
+        LP dl = SY[pl];
+        for (int k = 0; k < nu; ++k) dl -= SV[us + k - sep_t0] * SY[task_col(us + k) - sep_p0];
+        SY[pl] = dl * reinterpret_cast<const LP*>(SRF + pl)[3];
+    }
+
     __device__ __forceinline__ void lambda_acc(int p) {
         const LP dl = ldf<kCoh>(Y + p, foreign(p));
         if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(*(LAM + p)), (float)dl));
@@ -887,6 +964,17 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* ctr, unsigned n_bl
     return ok != 0;
 }
 
+// Shared memory of the separator phase: rows (V4) and right-hand sides of the
+// separators, values of the separator tasks.  Used when it fits kSepSmemMax.
+constexpr uint32_t kSepSmemMax = 48 * 1024;
+template <class Mode>
+__host__ __device__ inline uint32_t sep_smem_bytes(int nsep, int n_sept) {
+    using LP = typename Mode::LP;
+    using V4 = typename Mode::V4;
+    return align16((uint32_t)sizeof(V4) * nsep) + align16((uint32_t)sizeof(LP) * nsep) +
+           align16((uint32_t)sizeof(LP) * n_sept);
+}
+
 struct PartSync {
     unsigned long long barrier;
     int notconv[4];
@@ -899,12 +987,21 @@ template <class Mode>
 __global__ void __launch_bounds__(256, 3)
 k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, uint8_t* work, PartSync* sync,
                SolveArgs A) {
+    using LP = typename Mode::LP;
+    using V4 = typename Mode::V4;
+    extern __shared__ __align__(16) uint8_t sep_smem[];
     const MolDesc D = *desc;
     MolView<Mode, uint32_t, true> M;
     M.init(D, blob + D.blob_off, work + D.work_off, A, blob + D.blob_off);
     const int n_parts = D.n_seg - 1;
     const SegRow* seg = M.seg;
     const int sep0 = __ldg(&seg[n_parts].piv), nsep = D.nc - sep0;
+    // separator block in shared memory when it fits (the host sized the launch alike)
+    const bool sep_in_smem = sep_smem_bytes<Mode>(nsep, D.n_sept) <= kSepSmemMax;
+    V4* SRF = reinterpret_cast<V4*>(sep_smem);
+    LP* SY = reinterpret_cast<LP*>(sep_smem + align16((uint32_t)sizeof(V4) * nsep));
+    LP* SV = reinterpret_cast<LP*>(sep_smem + align16((uint32_t)sizeof(V4) * nsep) +
+                                   align16((uint32_t)sizeof(LP) * nsep));
     const int G = gridDim.x, b = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
     const unsigned nb = gridDim.x;
     long long budget = kSpinBudget;
@@ -994,7 +1091,36 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
         // ---- phase B: CTA 0 factorises the separator block (the Schur complement) and
         //      solves it forward and backward
-        if (b == 0) {
+        if (b == 0 && sep_in_smem) {
+            // stage the separator rows (their factor's reciprocal pivots stay in SRF.w
+            // across ILVES-F iterations) and right-hand sides, solve in shared memory,
+            // publish the solution
+            for (int k = r0; k < nsep; k += ts) {
+                if (factor) SRF[k] = lds<true>(M.RF + sep0 + k);
+                SY[k] = lds<true>(M.Y + sep0 + k);
+            }
+            __syncthreads();
+            for (int t = M.sep_t0 + r0; t < D.ntask; t += ts) M.sep_stage_smem(t, factor, SV, SY);
+            __syncthreads();
+            bool sing = false;
+            const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
+            for (int l = l0; l < l1; ++l) {
+                const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
+                const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
+                if (factor)
+                    for (int t = t0 + r0; t < t1; t += ts) M.sep_task_smem(t, t < t0 + np, sing, SV, SRF, SY);
+                else
+                    for (int p = p0 + r0; p < p1; p += ts) M.sep_forward_smem(t0 + (p - p0), p, SV, SRF, SY);
+                __syncthreads();
+            }
+            if (__syncthreads_or(sing) && r0 == 0) atomicOr(&sync->singular[slot], 1);
+            for (int l = l1 - 1; l >= l0; --l) {
+                const int p1 = __ldg(M.lvl_piv + l + 1);
+                for (int p = __ldg(M.lvl_piv + l) + r0; p < p1; p += ts) M.sep_backward_smem(p, SV, SRF, SY);
+                __syncthreads();
+            }
+            for (int k = r0; k < nsep; k += ts) M.Y[sep0 + k] = SY[k];
+        } else if (b == 0) {
             M.cohall = true;  // the separator block: every value may come from another CTA
             bool sing = false;
             const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
@@ -1364,21 +1490,24 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
             ++launches;
         }
         if (!T->parted_desc.empty()) {
-            int per_sm = 0;
-            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>, T->parted_threads, 0)) !=
-                cudaSuccess)
-                return to_status(e);
-            const int max_grid = std::max(1, per_sm * T->n_sm);
             if ((e = cudaMemsetAsync(sync, 0, T->sync_bytes, side)) != cudaSuccess) return to_status(e);
             for (size_t k = 0; k < T->parted_desc.size(); ++k) {
                 const int32_t di = T->parted_desc[k];
-                const int n_parts = T->mols[T->desc_mol[di]].n_seg - 1;
+                const MolHost& MH = T->mols[T->desc_mol[di]];
+                const int n_parts = MH.n_seg - 1;
+                const uint32_t need = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
+                const size_t dyn = need <= kSepSmemMax ? need : 0;
+                int per_sm = 0;
+                if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>, T->parted_threads,
+                                                                       dyn)) != cudaSuccess)
+                    return to_status(e);
+                const int max_grid = std::max(1, per_sm * T->n_sm);
                 const MolDesc* dptr = T->d_desc + di;
                 PartSync* sp = reinterpret_cast<PartSync*>(sync) + k;
                 SolveArgs Aa = A;
                 void* args[] = {(void*)&dptr, (void*)&T->d_blob, (void*)&work, (void*)&sp, (void*)&Aa};
                 const dim3 grid(std::min(n_parts, max_grid)), block(T->parted_threads);
-                if ((e = cudaLaunchCooperativeKernel((const void*)k_solve_parted<Mode>, grid, block, args, 0, side)) !=
+                if ((e = cudaLaunchCooperativeKernel((const void*)k_solve_parted<Mode>, grid, block, args, dyn, side)) !=
                     cudaSuccess)
                     return to_status(e);
                 ++launches;

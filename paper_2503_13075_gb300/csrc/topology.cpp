@@ -609,6 +609,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             Program* P = new Program(compile(nc, E, M.ci, M.cj, 256, na, &seg, np + 1, &seg_atom));
             M.n_seg = np + 1;
             M.n_sept = (int32_t)P->sep_info.size();
+            M.n_sep = nc - P->seg_piv[np];
             M.n_cent = (int32_t)P->cent.size();
             M.nlevel = P->nlevel;
             M.ntask = (int32_t)P->tasks.size() - 1;

@@ -21,6 +21,7 @@ struct MolHost {
     int32_t n_seg = 1;
     int32_t nlevel = 0, ntask = 0, nterm = 0, n_fill = 0;
     int32_t n_sept = 0, n_cent = 0;  // partitioned: separator tasks, Schur contribution entries
+    int32_t n_sep = 0;               // partitioned: separator constraints
     int64_t passes = 0;
 };
 
