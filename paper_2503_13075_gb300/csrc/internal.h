@@ -39,9 +39,10 @@ constexpr uint32_t kNoAtom32 = 0xFFFFFFFFu;
 //         tstart = first term.  Task t's terms are [tstart_t, tstart_{t+1}); a sentinel
 //         task ends the list.
 //   Task word (warp molecules): 32 bits, see TaskWord; no term pointer: in every level
-//         lane r of the warp owns tasks t0 + r, t0 + r + 32, ..., and the terms are
-//         stored lane by lane (lane r's terms of level 0, then of level 1, ...), starting
-//         at lane_term[r]; a lane walks its terms with a running offset.
+//         thread r of the molecule's team (kSlotThreads threads) owns tasks t0 + r,
+//         t0 + r + kSlotThreads, ..., and the terms are stored thread by thread (thread
+//         r's terms of level 0, then of level 1, ...), starting at lane_term[r]; a thread
+//         walks its terms with a running offset.
 //   Term: l = slot of Lt[row, m], u = slot of U[m, col], m = the earlier pivot.
 //   Piv:  diag = first slot of the pivot's U row (its L column follows), nup = |N+(pivot)|.
 //   ConA: local atom ids (i, j) of the constraint at position p.
@@ -85,6 +86,14 @@ template <> struct TermOf<uint32_t> {
     static ILVES_HD T make(uint32_t l, uint32_t u, uint32_t m) { return TermWide{l, u, m, 0u}; }
 };
 constexpr uint32_t kCompactMaxConstraints = 256, kCompactMaxSlots = 4096, kCompactMaxTerms = 65000;
+// Threads of the team that solves one molecule of the batched kernel (one or two warps;
+// two halve the passes of wide levels at no cost in residency, which shared memory
+// limits), and molecule slots per CTA of that kernel.
+#ifndef ILVES_SLOT_THREADS
+#define ILVES_SLOT_THREADS 64
+#endif
+constexpr int kSlotThreads = ILVES_SLOT_THREADS;
+constexpr int kMaxSlotsPerCta = 512 / kSlotThreads;
 
 ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 
@@ -123,7 +132,7 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
     L.piv = o;       o = align16(o + 2u * ix * nc);
     L.lvl_task = o;  o = align16(o + ix * (nlevel + 1));
     L.lvl_piv = o;   o = align16(o + ix * (nlevel + 1));
-    L.lane_term = o; o = align16(o + (compact ? ix * 32u : 0u));
+    L.lane_term = o; o = align16(o + (compact ? ix * (uint32_t)kSlotThreads : 0u));
     L.inc_ptr = o;   o = align16(o + ix * (na + 1));
     L.inc = o;       o = align16(o + ix * 2u * nc);
     L.tasks = o;     o = align16(o + (compact ? 4u * ntask : 4u * ix * (ntask + 1)));

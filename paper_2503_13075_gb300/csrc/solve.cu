@@ -144,12 +144,42 @@ __device__ __forceinline__ double as_bits(dfloat v) { return *reinterpret_cast<d
 // ------------------------------------------------------------------------------------
 // teams
 // ------------------------------------------------------------------------------------
-struct WarpTeam {
-    __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
-    __device__ __forceinline__ int size() const { return 32; }
-    __device__ __forceinline__ void sync() const { __syncwarp(); }
-    __device__ __forceinline__ bool all(bool p) const { return __all_sync(0xFFFFFFFFu, p); }
-    __device__ __forceinline__ bool any(bool p) const { return __any_sync(0xFFFFFFFFu, p); }
+// The kSlotThreads threads (one or two whole warps) of a batched-kernel slot; two warps
+// synchronise on named barrier 1 + slot (barrier 0 is the CTA's).
+struct SlotTeam {
+    __device__ __forceinline__ int rank() const { return threadIdx.x % kSlotThreads; }
+    __device__ __forceinline__ int size() const { return kSlotThreads; }
+    __device__ __forceinline__ int id() const { return threadIdx.x / kSlotThreads; }
+    __device__ __forceinline__ void sync() const {
+        if constexpr (kSlotThreads == 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id() + 1), "n"(kSlotThreads) : "memory");
+    }
+    __device__ __forceinline__ bool all(bool p) const {
+        if constexpr (kSlotThreads == 32) {
+            return __all_sync(0xFFFFFFFFu, p);
+        } else {
+            unsigned r;
+            asm volatile("{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.and.pred po, %2, %3, pi;\n"
+                         "selp.u32 %0, 1, 0, po;\n}\n"
+                         : "=r"(r)
+                         : "r"((unsigned)p), "r"(id() + 1), "n"(kSlotThreads)
+                         : "memory");
+            return r != 0;
+        }
+    }
+    __device__ __forceinline__ bool any(bool p) const {
+        if constexpr (kSlotThreads == 32) {
+            return __any_sync(0xFFFFFFFFu, p);
+        } else {
+            unsigned r;
+            asm volatile("{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, %2, %3, pi;\n"
+                         "selp.u32 %0, 1, 0, po;\n}\n"
+                         : "=r"(r)
+                         : "r"((unsigned)p), "r"(id() + 1), "n"(kSlotThreads)
+                         : "memory");
+            return r != 0;
+        }
+    }
 };
 struct BlockTeam {
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
@@ -613,7 +643,7 @@ struct MolView {
     // warp molecules: one level's tasks t0 + lane + 32 k; the lane walks its terms from
     //      offset e
     __device__ __forceinline__ void level_tasks(int t0, int t1, int np, int lane, int& e, bool& singular) {
-        for (int t = t0 + lane; t < t1; t += 32) {
+        for (int t = t0 + lane; t < t1; t += kSlotThreads) {
             const uint32_t w = lds<kCoh>(tasks + t);
             const int n = (int)TaskWord::nterm(w);
             const bool diag = t < t0 + np;
@@ -827,13 +857,13 @@ struct MolView {
 template <class Mode, class IdxT, class Team>
 __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
                                const SolveArgs& A, const uint8_t* gprog) {
-    constexpr bool kCompact = sizeof(IdxT) == 2;  // warp molecules (Team = WarpTeam)
+    constexpr bool kCompact = sizeof(IdxT) == 2;  // batched-kernel molecules (Team = SlotTeam)
     MolView<Mode, IdxT, false> M;
     M.init(D, prog, st, A, gprog);
     const int na = D.na, nc = D.nc;
     const int r0 = tm.rank(), ts = tm.size();
     // ---- S1
-    if constexpr (std::is_same<Team, WarpTeam>::value) {
+    if constexpr (std::is_same<Team, SlotTeam>::value) {
         M.s1_gather(r0, ts);
         tm.sync();
         for (int a = r0; a < na; a += ts) M.s1_atom_local(a);
@@ -1175,6 +1205,9 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
 // ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
+constexpr int kStaticSlotSmem = 64;  // bytes: the pool-ticket words of the slots of a CTA
+static_assert(kStaticSlotSmem >= (int)(kMaxSlotsPerCta * sizeof(unsigned)), "ticket words");
+
 struct SmallSched {
     const int32_t* cta_slot_ptr;
     const int32_t* slot_ptr;
@@ -1192,10 +1225,11 @@ struct SmallSched {
 // asynchronous 16-byte copies, and the next queued molecule's program and atom inputs
 // are prefetched into L2 while the current one is solved.  The last warp to finish
 // resets the pool counters for the next launch.
-__device__ __forceinline__ int pool_ticket(const SmallSched& S) {
-    unsigned t = 0;
-    if ((threadIdx.x & 31) == 0) t = atomicAdd(S.pool_ctr, 1u);
-    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+__device__ __forceinline__ int pool_ticket(const SmallSched& S, const SlotTeam& tm, unsigned* box) {
+    if (tm.rank() == 0) *box = atomicAdd(S.pool_ctr, 1u);
+    tm.sync();
+    const unsigned t = *box;
+    tm.sync();  // every thread has read the box before the next ticket is written
     return t < (unsigned)S.pool_n ? __ldg(S.pool_mol + t) : -1;
 }
 
@@ -1204,43 +1238,46 @@ __global__ void __launch_bounds__(512, 1)
 k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
               SolveArgs A) {
     extern __shared__ __align__(16) uint8_t arena[];
-    const WarpTeam tm;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = S.cta_slot_ptr[blockIdx.x] + warp;
+    __shared__ __align__(16) unsigned ticket_box[kStaticSlotSmem / sizeof(unsigned)];
+    const SlotTeam tm;
+    const int lane = tm.rank();
+    const int slot = S.cta_slot_ptr[blockIdx.x] + tm.id();
     if (slot >= S.cta_slot_ptr[blockIdx.x + 1]) return;
+    unsigned* box = ticket_box + tm.id();
     uint8_t* slice = arena + S.slot_off[slot];
     const int q1 = S.slot_ptr[slot + 1];
     int q = S.slot_ptr[slot];
-    int mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S) : -1);
+    int mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S, tm, box) : -1);
     while (mol >= 0) {
         const MolDesc D = desc[mol];
         const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg);
         const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
         uint4* dst = reinterpret_cast<uint4*>(slice);
         const int n16 = (int)(PL.staged >> 4);
-        for (int k = lane; k < n16; k += 32) cp_async16(dst + k, src + k);  // all in flight
+        for (int k = lane; k < n16; k += kSlotThreads) cp_async16(dst + k, src + k);  // all in flight
         if (q + 1 < q1) {  // the next queued molecule's program and atom inputs into L2 meanwhile
             const MolDesc Dn = desc[S.slot_mol[q + 1]];
             const uint32_t nb = prog_layout<uint16_t>(Dn.na, Dn.nc, Dn.ntask, Dn.nterm, Dn.nlevel, Dn.n_seg).bytes;
             const uint8_t* pb = blob + Dn.blob_off;
-            for (uint32_t o = 128u * lane; o < nb; o += 4096u) prefetch_l2(pb + o);
+            constexpr uint32_t kStep = 128u * kSlotThreads;
+            for (uint32_t o = 128u * lane; o < nb; o += kStep) prefetch_l2(pb + o);
             if (Dn.atom_base >= 0) {
                 const uint8_t* xo = reinterpret_cast<const uint8_t*>(A.x_old + 3 * (int64_t)Dn.atom_base);
                 const uint8_t* xu = reinterpret_cast<const uint8_t*>(A.x_unc + 3 * (int64_t)Dn.atom_base);
                 const uint8_t* wm = reinterpret_cast<const uint8_t*>(A.inv_mass + Dn.atom_base);
-                for (uint32_t o = 128u * lane; o < 24u * (uint32_t)Dn.na; o += 4096u) {
+                for (uint32_t o = 128u * lane; o < 24u * (uint32_t)Dn.na; o += kStep) {
                     prefetch_l2(xo + o);
                     prefetch_l2(xu + o);
                 }
-                for (uint32_t o = 128u * lane; o < 8u * (uint32_t)Dn.na; o += 4096u) prefetch_l2(wm + o);
+                for (uint32_t o = 128u * lane; o < 8u * (uint32_t)Dn.na; o += kStep) prefetch_l2(wm + o);
             }
         }
         cp_async_wait_all();
-        __syncwarp();
-        solve_molecule<Mode, uint16_t, WarpTeam>(tm, D, slice, slice + PL.staged, A, blob + D.blob_off);
-        __syncwarp();
+        tm.sync();
+        solve_molecule<Mode, uint16_t, SlotTeam>(tm, D, slice, slice + PL.staged, A, blob + D.blob_off);
+        tm.sync();
         ++q;
-        mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S) : -1);
+        mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S, tm, box) : -1);
     }
     if (S.pool_n > 0 && lane == 0) {
         __threadfence();  // this warp's last ticket is ordered before its "done"
@@ -1351,7 +1388,9 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     T->n_sm = n_sm;
     const int ctas_per_sm = o.ctas_per_sm > 0 ? std::min(o.ctas_per_sm, 4) : 1;
-    const int arena = std::min(smem_optin, smem_sm / ctas_per_sm - 1024) & ~15;
+    // the batched kernel's dynamic arena; its static shared memory (one pool-ticket word
+    // per slot) comes off the per-block limit
+    const int arena = std::min(smem_optin - kStaticSlotSmem, smem_sm / ctas_per_sm - 1024) & ~15;
     // molecules whose slice does not fit an arena take the CTA-per-molecule path
     for (auto& M : T->mols)
         if (!M.large && footprint(M, ILVES_PREC_FP64) > (uint32_t)arena) M.large = true;
@@ -1429,8 +1468,8 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         for (int32_t m = 0; m < T->n_mol; ++m)
             if (!T->mols[m].large) fps.push_back(footprint(T->mols[m], mode));
         // auto: the largest warp count per CTA whose slices fit the arena (searched downwards)
-        int warps = o.warps_per_cta > 0 ? o.warps_per_cta : 16;
-        warps = std::max(1, std::min(16, warps));
+        int warps = o.warps_per_cta > 0 ? o.warps_per_cta : kMaxSlotsPerCta;
+        warps = std::max(1, std::min(kMaxSlotsPerCta, warps));
         HostSchedule HS;
         build_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
         for (auto& km : HS.slot_mol) km = desc_index[km];
@@ -1518,7 +1557,7 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
     if (T->n_small > 0) {
         SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off, DS.pool_mol, DS.pool_ctr,
                      DS.pool_n, DS.n_slots};
-        k_solve_small<Mode><<<DS.n_cta, DS.warps * 32, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
+        k_solve_small<Mode><<<DS.n_cta, DS.warps * kSlotThreads, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;
     }

@@ -434,8 +434,8 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
     }
     auto term_of = [&](size_t k) { return TermOf<IdxT>::make(P.terms[k].l, P.terms[k].u, P.terms[k].m); };
     if constexpr (kCompact) {
-        // task words; terms lane by lane (lane r owns t0 + r + 32 k of every level), each
-        // lane's terms in level order
+        // task words; terms thread by thread (team thread r owns t0 + r + kSlotThreads k of
+        // every level), each thread's terms in level order
         auto* tasks = reinterpret_cast<uint32_t*>(dst + L.tasks);
         auto* lane_term = reinterpret_cast<IdxT*>(dst + L.lane_term);
         const int32_t ntask = (int32_t)P.tasks.size() - 1;
@@ -446,11 +446,11 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
         }
         size_t o = 0;
         const int32_t nl = (int32_t)P.lvl_task.size() - 1;
-        for (int32_t r = 0; r < 32; ++r) {
+        for (int32_t r = 0; r < kSlotThreads; ++r) {
             lane_term[r] = (IdxT)o;
             for (int32_t l = 0; l < nl; ++l) {
                 const int32_t t0 = P.lvl_task[l], t1 = P.lvl_task[l + 1];
-                for (int32_t t = t0 + r; t < t1; t += 32)
+                for (int32_t t = t0 + r; t < t1; t += kSlotThreads)
                     for (uint32_t k = P.tasks[t].tstart; k < P.tasks[t + 1].tstart; ++k) terms[o++] = term_of(k);
             }
         }
@@ -619,7 +619,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             T->progs[m] = P;
             continue;
         }
-        Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : 32));
+        Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : kSlotThreads));
         if (!M.large && !fits_compact(*P)) {
             M.large = true;
             *P = choose_order(nc, na, adj, M.ci, M.cj, o, 1024);
@@ -713,23 +713,27 @@ void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, i
     double pool_cost = 0.0;
     while (cut > 0 && pool_cost + cost[small[cut - 1]] <= kPoolShare * total) pool_cost += cost[small[--cut]];
     const double head_cost = total - pool_cost;
-    for (int32_t w = std::max(1, std::min(16, warps)); w >= 1; --w) {
+    for (int32_t w = std::max(1, std::min(kMaxSlotsPerCta, warps)); w >= 1; --w) {
         const int64_t G = (int64_t)n_cta * w;
         const double target = head_cost / (double)G * kQueueSlack;
         std::vector<std::vector<int32_t>> groups(G);
         std::vector<int32_t> pool;
         int64_t g = 0;
         double acc = 0.0;
+        bool full = false;  // every queue closed: the rest joins the pool (it stays the smallest)
         for (size_t k = 0; k < cut; ++k) {
             const int32_t m = small[k];
-            if (!groups[g].empty() && acc + cost[m] > target) {
+            if (!full && !groups[g].empty() && acc + cost[m] > target) {
                 if (g + 1 < G) {
                     ++g;
                     acc = 0.0;
                 } else {
-                    pool.push_back(m);
-                    continue;
+                    full = true;
                 }
+            }
+            if (full) {
+                pool.push_back(m);
+                continue;
             }
             groups[g].push_back(m);
             acc += cost[m];
@@ -755,7 +759,7 @@ void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, i
         for (int32_t c = 0; c < n_cta && fits; ++c) {
             uint64_t used = 0;
             for (int64_t gi : cta_groups[c]) used += slice_of(gi);
-            fits = used <= (uint64_t)arena && cta_groups[c].size() <= 16;
+            fits = used <= (uint64_t)arena && cta_groups[c].size() <= (size_t)kMaxSlotsPerCta;
         }
         if (!fits && w > 1) continue;
         S.n_cta = n_cta;
