@@ -100,7 +100,7 @@ typedef struct {
     int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;
                                 2 = rounds of independent low-degree pivots with `degree_slack` */
     int32_t degree_slack;    /* ordering 2: admit pivots up to min degree + slack per round */
-    int32_t warps_per_cta;   /* 0 = autotuned; else 1..8 molecule slots (64-thread teams) per persistent CTA */
+    int32_t warps_per_cta;   /* 0 = autotuned; else 1..8 molecule slots (96-thread teams) per persistent CTA */
     int32_t ctas_per_sm;     /* 0 = autotuned; else 1..4 */
     int32_t device;          /* CUDA device ordinal the topology lives on (-1 = current device,
                                 -2 = plan on the host only: no CUDA call, ilves_solve refused) */

@@ -144,8 +144,8 @@ __device__ __forceinline__ double as_bits(dfloat v) { return *reinterpret_cast<d
 // ------------------------------------------------------------------------------------
 // teams
 // ------------------------------------------------------------------------------------
-// The kSlotThreads threads (one or two whole warps) of a batched-kernel slot; two warps
-// synchronise on named barrier 1 + slot (barrier 0 is the CTA's).
+// The kSlotThreads threads (whole warps) of a batched-kernel slot; more than one warp
+// synchronises on named barrier 1 + slot (barrier 0 is the CTA's).
 struct SlotTeam {
     __device__ __forceinline__ int rank() const { return threadIdx.x % kSlotThreads; }
     __device__ __forceinline__ int size() const { return kSlotThreads; }
@@ -1234,7 +1234,7 @@ __device__ __forceinline__ int pool_ticket(const SmallSched& S, const SlotTeam& 
 }
 
 template <class Mode>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(kSlotCtaThreads, 1)
 k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
               SolveArgs A) {
     extern __shared__ __align__(16) uint8_t arena[];
