@@ -492,7 +492,7 @@ def run_ilves(args):
             "tol": args.tol,
             "l2": "flushed (256 MiB write) before every timed step",
             "schedule": ("cooperative CTAs over partitions + separator (Schur) block" if s.name == "protein_like"
-                         else "persistent CTAs, one warp per molecule"),
+                         else "persistent CTAs, one 96-thread team per molecule"),
         },
         "valid": valid,
         "max_rel_violation": viol,
