@@ -752,15 +752,16 @@ struct MolView {
     //      tasks, SRF = Jacobian rows of the separators (.w = 1 / pivot), SY = their
     //      right-hand side / solution; indices local to the separator block.  Terms of
     //      interior pivots beyond the parts' contributions read the global state.
-    __device__ __forceinline__ void sep_task_smem(int t, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY) const {
+    //      SP = the separators' reference rows, SC = each task's assembly coefficient
+    //      (4 s s' w), both fixed for the whole solve.
+    __device__ __forceinline__ void sep_task_smem(int t, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
+                                                  const V4* SP, const LP* SC) const {
         const TaskT tk = ldp<kCoh>(tasks + t);
         const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
         const int tl = t - sep_t0, row = tk.row - sep_p0, col = tk.col - sep_p0;
         const SepInfo si = ldp<kCoh>(sep_info + tl);
-        const V4 rr = SRF[row], pp = *(RHOF + tk.col);
-        const LP wv = diag ? pp.w : *(WL + (tk.atomsign >> 1));
-        const LP c = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
-        const LP a = c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+        const V4 rr = SRF[row], pp = SP[col];
+        const LP a = SC[tl] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
         LP sacc = a + SV[tl], yv = LP(0);  // SV, SY hold minus the parts' contributions
         for (int e = (int)si.b_start; e < e1; ++e) {
             const auto tr = ldp<kCoh>(terms + e);
@@ -786,6 +787,48 @@ struct MolView {
         }
         (void)col;
     }
+    // the same with one warp per task, its lanes splitting the terms (the narrow last
+    //      levels, where few pivots carry many terms)
+    __device__ __forceinline__ void sep_task_smem_warp(int t, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
+                                                       const V4* SP, const LP* SC, int lane) const {
+        const TaskT tk = ldp<kCoh>(tasks + t);
+        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
+        const int tl = t - sep_t0, row = tk.row - sep_p0, col = tk.col - sep_p0;
+        const SepInfo si = ldp<kCoh>(sep_info + tl);
+        LP ps = LP(0), py = LP(0);
+        for (int e = (int)si.b_start + lane; e < e1; e += 32) {
+            const auto tr = ldp<kCoh>(terms + e);
+            const int m = TO::m(tr);
+            LP li, u, ym;
+            if (m >= sep_p0) {
+                li = SV[TO::l(tr) - sep_t0] * reinterpret_cast<const LP*>(SRF + (m - sep_p0))[3];
+                u = SV[TO::u(tr) - sep_t0];
+                ym = SY[m - sep_p0];
+            } else {
+                li = lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(inv_ptr(m));
+                u = lds<kCoh>(V + TO::u(tr));
+                ym = lds<kCoh>(Y + m);
+            }
+            ps += li * u;
+            if (diag) py += li * ym;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ps += __shfl_xor_sync(0xFFFFFFFFu, ps, o);
+            py += __shfl_xor_sync(0xFFFFFFFFu, py, o);
+        }
+        if (lane == 0) {
+            const V4 rr = SRF[row], pp = SP[col];
+            const LP a = SC[tl] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+            const LP sacc = a + SV[tl] - ps;
+            SV[tl] = sacc;
+            if (diag) {
+                singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+                reinterpret_cast<LP*>(SRF + row)[3] = lp_rcp(sacc);
+                SY[row] -= py;
+            }
+        }
+    }
     __device__ __forceinline__ void sep_forward_smem(int t, int p, const LP* SV, const V4* SRF, LP* SY) const {
         const int tl = t - sep_t0;
         const SepInfo si = ldp<kCoh>(sep_info + tl);
@@ -804,10 +847,14 @@ struct MolView {
     // staging of separator task t: the parts' contributions, summed, go into SV[t] (as
     //      its negative start value, factor iterations only) and, for a DIAG task, into
     //      the right-hand side SY of its pivot
-    __device__ __forceinline__ void sep_stage_smem(int t, bool factor, LP* SV, LP* SY) const {
+    __device__ __forceinline__ void sep_stage_smem(int t, bool factor, bool first, LP* SV, LP* SY, LP* SC) const {
         const int tl = t - sep_t0;
         const SepInfo si = ldp<kCoh>(sep_info + tl);
         const TaskT tk = ldp<kCoh>(tasks + t);
+        if (first) {  // 4 s s' w of the entry (w_i + w_j for a pivot)
+            const LP wv = tk.row == tk.col ? (RHOF + tk.row)->w : *(WL + (tk.atomsign >> 1));
+            SC[tl] = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
+        }
         const LP* ct = CT + 4 * tl;
         LP cv = LP(0), cy = LP(0);
         for (uint32_t g = 0; g < si.ngroups; ++g) {
@@ -995,14 +1042,15 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* ctr, unsigned n_bl
 }
 
 // Shared memory of the separator phase: rows (V4) and right-hand sides of the
-// separators, values of the separator tasks.  Used when it fits kSepSmemMax.
-constexpr uint32_t kSepSmemMax = 48 * 1024;
+// separators, values of the separator tasks; the separators' reference rows and the
+// tasks' assembly coefficients.  Used when it fits kSepSmemMax.
+constexpr uint32_t kSepSmemMax = 64 * 1024;
 template <class Mode>
 __host__ __device__ inline uint32_t sep_smem_bytes(int nsep, int n_sept) {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
-    return align16((uint32_t)sizeof(V4) * nsep) + align16((uint32_t)sizeof(LP) * nsep) +
-           align16((uint32_t)sizeof(LP) * n_sept);
+    return 2 * align16((uint32_t)sizeof(V4) * nsep) + align16((uint32_t)sizeof(LP) * nsep) +
+           2 * align16((uint32_t)sizeof(LP) * n_sept);
 }
 
 struct PartSync {
@@ -1032,6 +1080,9 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
     LP* SY = reinterpret_cast<LP*>(sep_smem + align16((uint32_t)sizeof(V4) * nsep));
     LP* SV = reinterpret_cast<LP*>(sep_smem + align16((uint32_t)sizeof(V4) * nsep) +
                                    align16((uint32_t)sizeof(LP) * nsep));
+    V4* SP = reinterpret_cast<V4*>(reinterpret_cast<uint8_t*>(SV) + align16((uint32_t)sizeof(LP) * D.n_sept));
+    LP* SC = reinterpret_cast<LP*>(reinterpret_cast<uint8_t*>(SP) + align16((uint32_t)sizeof(V4) * nsep));
+    bool sep_fixed_staged = false;
     const int G = gridDim.x, b = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
     const unsigned nb = gridDim.x;
     long long budget = kSpinBudget;
@@ -1128,17 +1179,23 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             for (int k = r0; k < nsep; k += ts) {
                 if (factor) SRF[k] = lds<true>(M.RF + sep0 + k);
                 SY[k] = lds<true>(M.Y + sep0 + k);
+                if (!sep_fixed_staged) SP[k] = *(M.RHOF + sep0 + k);
             }
             __syncthreads();
-            for (int t = M.sep_t0 + r0; t < D.ntask; t += ts) M.sep_stage_smem(t, factor, SV, SY);
+            for (int t = M.sep_t0 + r0; t < D.ntask; t += ts)
+                M.sep_stage_smem(t, factor, !sep_fixed_staged, SV, SY, SC);
+            sep_fixed_staged = true;
             __syncthreads();
             bool sing = false;
             const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
             for (int l = l0; l < l1; ++l) {
                 const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
                 const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
-                if (factor)
-                    for (int t = t0 + r0; t < t1; t += ts) M.sep_task_smem(t, t < t0 + np, sing, SV, SRF, SY);
+                if (factor && t1 - t0 <= 8 * (ts >> 5)) {  // narrow level: a warp per task
+                    for (int t = t0 + (r0 >> 5); t < t1; t += ts >> 5)
+                        M.sep_task_smem_warp(t, t < t0 + np, sing, SV, SRF, SY, SP, SC, r0 & 31);
+                } else if (factor)
+                    for (int t = t0 + r0; t < t1; t += ts) M.sep_task_smem(t, t < t0 + np, sing, SV, SRF, SY, SP, SC);
                 else
                     for (int p = p0 + r0; p < p1; p += ts) M.sep_forward_smem(t0 + (p - p0), p, SV, SRF, SY);
                 __syncthreads();
@@ -1536,6 +1593,10 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 const int n_parts = MH.n_seg - 1;
                 const uint32_t need = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
                 const size_t dyn = need <= kSepSmemMax ? need : 0;
+                if (dyn > 48 * 1024 &&
+                    (e = cudaFuncSetAttribute(k_solve_parted<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kSepSmemMax)) != cudaSuccess)
+                    return to_status(e);
                 int per_sm = 0;
                 if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>, T->parted_threads,
                                                                        dyn)) != cudaSuccess)
