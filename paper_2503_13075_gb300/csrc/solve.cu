@@ -364,7 +364,60 @@ struct MolView {
     __device__ __forceinline__ int32_t gid_of_con(int p) const { return __ldg(con_gid + p); }
     __device__ __forceinline__ LP* inv_ptr(int p) const { return reinterpret_cast<LP*>(RF + p) + 3; }
     __device__ __forceinline__ bool foreign(int p) const { return cohall || p >= sep_p0; }
-    __device__ __forceinline__ LP inv(int p) const { return ldf<kCoh>(inv_ptr(p), foreign(p)); }
+
+    // ---- partitioned molecules with one part per CTA: shared-memory copies of the CTA's
+    //      own part (positions [P0, P1), atoms [A0, A1), tasks [T0, T1)) of the values it
+    //      writes and reads back within a phase -- Y, RF (with 1/pivot), V, X.  Stores
+    //      go to both copies, so other CTAs keep reading the global state; loads of the
+    //      own part come from shared memory.  Off (XS == nullptr) in the other modes.
+    int P0 = 0, P1 = 0, A0 = 0, A1 = 0, T0 = 0, T1 = 0;
+    double* XS = nullptr;  // SoA with stride A1 - A0
+    LP* YS = nullptr;
+    V4* RFS = nullptr;
+    LP* VS = nullptr;
+    __device__ __forceinline__ bool in_p(int p) const {
+        if constexpr (kCoh) return XS != nullptr && p >= P0 && p < P1;
+        else return false;
+    }
+    __device__ __forceinline__ bool in_a(int a) const {
+        if constexpr (kCoh) return XS != nullptr && a >= A0 && a < A1;
+        else return false;
+    }
+    __device__ __forceinline__ bool in_t(int t) const {
+        if constexpr (kCoh) return XS != nullptr && t >= T0 && t < T1;
+        else return false;
+    }
+    __device__ __forceinline__ LP y_ld(int p) const { return in_p(p) ? YS[p - P0] : ldf<kCoh>(Y + p, foreign(p)); }
+    __device__ __forceinline__ void y_st(int p, LP v) {
+        Y[p] = v;
+        if (in_p(p)) YS[p - P0] = v;
+    }
+    __device__ __forceinline__ V4 rf_ld(int p) const { return in_p(p) ? RFS[p - P0] : ldf<kCoh>(RF + p, foreign(p)); }
+    __device__ __forceinline__ void rf_st(int p, const V4& v) {
+        RF[p] = v;
+        if (in_p(p)) RFS[p - P0] = v;
+    }
+    __device__ __forceinline__ LP inv(int p) const {
+        return in_p(p) ? reinterpret_cast<const LP*>(RFS + (p - P0))[3] : ldf<kCoh>(inv_ptr(p), foreign(p));
+    }
+    __device__ __forceinline__ void inv_st(int p, LP v) {
+        *inv_ptr(p) = v;
+        if (in_p(p)) reinterpret_cast<LP*>(RFS + (p - P0))[3] = v;
+    }
+    // task values: slots of tasks of pivot m are foreign when m is
+    __device__ __forceinline__ LP v_ld(int t, bool fgn) const { return in_t(t) ? VS[t - T0] : ldf<kCoh>(V + t, fgn); }
+    __device__ __forceinline__ void v_st(int t, LP v) {
+        V[t] = v;
+        if (in_t(t)) VS[t - T0] = v;
+    }
+    // coordinate c of atom a (float64 class)
+    __device__ __forceinline__ double x_ld(int c, int a, bool fgn) const {
+        return in_a(a) ? XS[c * (A1 - A0) + (a - A0)] : ldf<kCoh>(X + c * na + a, fgn);
+    }
+    __device__ __forceinline__ void x_st(int c, int a, double v) {
+        X[c * na + a] = v;
+        if (in_a(a)) XS[c * (A1 - A0) + (a - A0)] = v;
+    }
 
     // ---- S1
     // weights of atom a; with stage_ref, x_old is staged in X for s1_constraint
@@ -422,18 +475,18 @@ struct MolView {
         }
         const float l0 = A->lambda0 ? A->lambda0[g] : 0.0f;
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
-        Y[p] = (LP)l0;
+        y_st(p, (LP)l0);
     }
     __device__ __forceinline__ void s1_atom_unc(int a) {
         if constexpr (DF) {  // displacements start at zero
-            X[a] = 0.0;
-            X[na + a] = 0.0;
-            X[2 * na + a] = 0.0;
+            x_st(0, a, 0.0);
+            x_st(1, a, 0.0);
+            x_st(2, a, 0.0);
         } else {
             const int64_t g = gid(a);
-            X[a] = A->x_unc[3 * g];
-            X[na + a] = A->x_unc[3 * g + 1];
-            X[2 * na + a] = A->x_unc[3 * g + 2];
+            x_st(0, a, A->x_unc[3 * g]);
+            x_st(1, a, A->x_unc[3 * g + 1]);
+            x_st(2, a, A->x_unc[3 * g + 2]);
         }
     }
 
@@ -503,7 +556,7 @@ struct MolView {
             for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
                 const unsigned v = ldp<kCoh>(inc + e);
                 const int p = (int)(v >> 1);
-                const float dl = (float)ldf<kCoh>(Y + p, foreign(p));
+                const float dl = (float)y_ld(p);
                 const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
                 const V4 hi = *(RHOF + p);
                 ax = df_add(ax, df_mul_f(dfloat{hi.x, *(RHOL + p)}, c));
@@ -511,29 +564,28 @@ struct MolView {
                 az = df_add(az, df_mul_f(dfloat{hi.z, *(RHOL + 2 * nc + p)}, c));
             }
             const dfloat w = as_df(*(W + a));
-            return {as_bits(df_sub(as_df(*(X + a)), df_mul(w, ax))),
-                    as_bits(df_sub(as_df(*(X + na + a)), df_mul(w, ay))),
-                    as_bits(df_sub(as_df(*(X + 2 * na + a)), df_mul(w, az)))};
+            return {as_bits(df_sub(as_df(x_ld(0, a, false)), df_mul(w, ax))),
+                    as_bits(df_sub(as_df(x_ld(1, a, false)), df_mul(w, ay))),
+                    as_bits(df_sub(as_df(x_ld(2, a, false)), df_mul(w, az)))};
         } else {
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int e = ldp<kCoh>(inc_ptr + a); e < e1; ++e) {
                 const unsigned v = ldp<kCoh>(inc + e);
                 const int p = (int)(v >> 1);
-                const LP dl = ldf<kCoh>(Y + p, foreign(p));
+                const LP dl = y_ld(p);
                 const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
                 ax = fma(c, *(RHO + p), ax);
                 ay = fma(c, *(RHO + nc + p), ay);
                 az = fma(c, *(RHO + 2 * nc + p), az);
             }
             const double w = *(W + a);
-            return {fma(-w, ax, *(X + a)), fma(-w, ay, *(X + na + a)),
-                    fma(-w, az, *(X + 2 * na + a))};
+            return {fma(-w, ax, x_ld(0, a, false)), fma(-w, ay, x_ld(1, a, false)), fma(-w, az, x_ld(2, a, false))};
         }
     }
     __device__ __forceinline__ void upd_store(int a, const Upd& u) {
-        X[a] = u.x;
-        X[na + a] = u.y;
-        X[2 * na + a] = u.z;
+        x_st(0, a, u.x);
+        x_st(1, a, u.y);
+        x_st(2, a, u.z);
     }
     __device__ __forceinline__ void update_atom(int a) { upd_store(a, upd_eval(a)); }
 
@@ -548,11 +600,11 @@ struct MolView {
         const bool fx = foreign(p);
         Viol o;
         if constexpr (DF) {
-            const dfloat rx = df_add(as_df(*(SK + p)), df_sub(as_df(ldf<kCoh>(X + i, fx)), as_df(ldf<kCoh>(X + j, fx))));
+            const dfloat rx = df_add(as_df(*(SK + p)), df_sub(as_df(x_ld(0, i, fx)), as_df(x_ld(0, j, fx))));
             const dfloat ry = df_add(as_df(*(SK + nc + p)),
-                                     df_sub(as_df(ldf<kCoh>(X + na + i, fx)), as_df(ldf<kCoh>(X + na + j, fx))));
+                                     df_sub(as_df(x_ld(1, i, fx)), as_df(x_ld(1, j, fx))));
             const dfloat rz = df_add(as_df(*(SK + 2 * nc + p)),
-                                     df_sub(as_df(ldf<kCoh>(X + 2 * na + i, fx)), as_df(ldf<kCoh>(X + 2 * na + j, fx))));
+                                     df_sub(as_df(x_ld(2, i, fx)), as_df(x_ld(2, j, fx))));
             const dfloat d2 = as_df(*(D2 + p));
             // |r|^2 - d^2: exact products of the high words, two-sums of the big terms,
             // every rounding error collected in a small tail
@@ -575,9 +627,9 @@ struct MolView {
             o.v.z = rz.hi;
             o.y = sg;
         } else {
-            const double rx = ldf<kCoh>(X + i, fx) - ldf<kCoh>(X + j, fx);
-            const double ry = ldf<kCoh>(X + na + i, fx) - ldf<kCoh>(X + na + j, fx);
-            const double rz = ldf<kCoh>(X + 2 * na + i, fx) - ldf<kCoh>(X + 2 * na + j, fx);
+            const double rx = x_ld(0, i, fx) - x_ld(0, j, fx);
+            const double ry = x_ld(1, i, fx) - x_ld(1, j, fx);
+            const double rz = x_ld(2, i, fx) - x_ld(2, j, fx);
             const double d2 = *(D2 + p);
             const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
             o.conv = abs_le(sg, A->tol * d2);
@@ -591,8 +643,8 @@ struct MolView {
         return o;
     }
     __device__ __forceinline__ void viol_store(int p, const Viol& o, bool rows) {
-        Y[p] = o.y;
-        if (rows) RF[p] = o.v;
+        y_st(p, o.y);
+        if (rows) rf_st(p, o.v);
     }
     __device__ __forceinline__ void violation(int p, bool& conv, bool& bad, bool rows = true) {
         const Viol o = viol_eval(p);
@@ -606,7 +658,7 @@ struct MolView {
     //      Every entry is a - sum_m Lt[row,m] inv_m U[m,col], a = 4 s s' w_atom r_row . rho_col
     //      (for DIAG entries w_atom = w_i + w_j, kept in RHOF[row].w).
     __device__ __forceinline__ LP assemble(int row, int col, int atom, bool neg, bool diag) const {
-        const V4 rr = ldf<kCoh>(RF + row, foreign(row)), pp = *(RHOF + col);
+        const V4 rr = rf_ld(row), pp = *(RHOF + col);
         const LP wv = diag ? pp.w : *(WL + atom);
         const LP c = neg ? LP(-4) * wv : LP(4) * wv;
         return c * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
@@ -623,15 +675,15 @@ struct MolView {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
             const bool fm = foreign(m);
-            const LP li = ldf<kCoh>(V + TO::l(tr), fm) * inv(m);
-            sacc -= li * ldf<kCoh>(V + TO::u(tr), fm);
-            if (diag) yv += li * ldf<kCoh>(Y + m, fm);
+            const LP li = v_ld(TO::l(tr), fm) * inv(m);
+            sacc -= li * v_ld(TO::u(tr), fm);
+            if (diag) yv += li * y_ld(m);
         }
-        V[t] = sacc;
+        v_st(t, sacc);
         if (diag) {
             singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
-            *inv_ptr(row) = lp_rcp(sacc);
-            Y[row] = ldf<kCoh>(Y + row, foreign(row)) - yv;
+            inv_st(row, lp_rcp(sacc));
+            y_st(row, y_ld(row) - yv);
         }
     }
     // large molecules: task records with term pointers
@@ -662,15 +714,15 @@ struct MolView {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
             const bool fm = foreign(m);
-            yv += ldf<kCoh>(V + TO::l(tr), fm) * inv(m) * ldf<kCoh>(Y + m, fm);
+            yv += v_ld(TO::l(tr), fm) * inv(m) * y_ld(m);
         }
-        Y[p] = ldf<kCoh>(Y + p, foreign(p)) - yv;
+        y_st(p, y_ld(p) - yv);
     }
     __device__ __forceinline__ void forward(int t, int p) {
         forward_terms(p, ldp<kCoh>(tasks + t).tstart, ldp<kCoh>(tasks + t + 1).tstart);
     }
     // ILVES-F assembles A(x_old, x_old): the Jacobian rows are the reference bonds
-    __device__ __forceinline__ void chord_rows(int p) { RF[p] = *(RHOF + p); }
+    __device__ __forceinline__ void chord_rows(int p) { rf_st(p, *(RHOF + p)); }
 
     // ---- backward S5 for pivot p: delta_p = inv_p (y_p - sum_q U[p,q] delta_q)
     __device__ __forceinline__ int task_col(int t) const {
@@ -681,12 +733,12 @@ struct MolView {
         const Piv<IdxT> pv = ldp<kCoh>(piv + p);
         const int us = pv.diag, nu = pv.nup;
         const bool fp = foreign(p);
-        LP dl = ldf<kCoh>(Y + p, fp);
+        LP dl = y_ld(p);
         for (int k = 0; k < nu; ++k) {
             const int q = task_col(us + k);
-            dl -= ldf<kCoh>(V + us + k, fp) * ldf<kCoh>(Y + q, foreign(q));
+            dl -= v_ld(us + k, fp) * y_ld(q);
         }
-        Y[p] = dl * inv(p);
+        y_st(p, dl * inv(p));
     }
     // ---- partitioned molecules: part-side Schur contribution entry c (factor: the L inv U
     //      sum as well; DIAG tasks: the L inv y sum of the forward solve)
@@ -699,9 +751,9 @@ struct MolView {
             const auto tr = ldp<kCoh>(terms + e);
             const int m = TO::m(tr);
             const bool fm = foreign(m);
-            const LP li = ldf<kCoh>(V + TO::l(tr), fm) * inv(m);
-            if (factor) sv += li * ldf<kCoh>(V + TO::u(tr), fm);
-            if (diag) sy += li * ldf<kCoh>(Y + m, fm);
+            const LP li = v_ld(TO::l(tr), fm) * inv(m);
+            if (factor) sv += li * v_ld(TO::u(tr), fm);
+            if (diag) sy += li * y_ld(m);
         }
         LP* ct = CT + 4 * (E.task - sep_t0);
         if (factor) ct[E.slot] = sv;
@@ -873,7 +925,7 @@ struct MolView {
     }
 
     __device__ __forceinline__ void lambda_acc(int p) {
-        const LP dl = ldf<kCoh>(Y + p, foreign(p));
+        const LP dl = y_ld(p);
         if constexpr (DF) LAM[p] = as_bits(df_add_f(as_df(*(LAM + p)), (float)dl));
         else LAM[p] = *(LAM + p) + to_hp(dl);
     }
@@ -1053,6 +1105,22 @@ __host__ __device__ inline uint32_t sep_smem_bytes(int nsep, int n_sept) {
            2 * align16((uint32_t)sizeof(LP) * n_sept);
 }
 
+// Shared memory of a part's own copies (X, Y, RF, V) for the largest part.
+template <class Mode>
+__host__ __device__ inline uint32_t part_smem_bytes(int na, int np, int nt) {
+    using LP = typename Mode::LP;
+    using V4 = typename Mode::V4;
+    return align16(24u * na) + align16((uint32_t)sizeof(LP) * np) + align16((uint32_t)sizeof(V4) * np) +
+           align16((uint32_t)sizeof(LP) * nt);
+}
+constexpr uint32_t kPartedSmemMax = 72 * 1024;  // three CTAs per SM still fit
+
+// Dynamic shared memory of a partitioned launch: the separator block (CTA 0; 0 = it stays
+// in global memory), then the part copies (0 = off; on only with one part per CTA).
+struct PartedSmem {
+    uint32_t sep_bytes, part_bytes;
+};
+
 struct PartSync {
     unsigned long long barrier;
     int notconv[4];
@@ -1064,7 +1132,7 @@ struct PartSync {
 template <class Mode>
 __global__ void __launch_bounds__(256, 3)
 k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, uint8_t* work, PartSync* sync,
-               SolveArgs A) {
+               SolveArgs A, PartedSmem cfg) {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
     extern __shared__ __align__(16) uint8_t sep_smem[];
@@ -1075,7 +1143,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
     const SegRow* seg = M.seg;
     const int sep0 = __ldg(&seg[n_parts].piv), nsep = D.nc - sep0;
     // separator block in shared memory when it fits (the host sized the launch alike)
-    const bool sep_in_smem = sep_smem_bytes<Mode>(nsep, D.n_sept) <= kSepSmemMax;
+    const bool sep_in_smem = cfg.sep_bytes > 0;
     V4* SRF = reinterpret_cast<V4*>(sep_smem);
     LP* SY = reinterpret_cast<LP*>(sep_smem + align16((uint32_t)sizeof(V4) * nsep));
     LP* SV = reinterpret_cast<LP*>(sep_smem + align16((uint32_t)sizeof(V4) * nsep) +
@@ -1083,6 +1151,25 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
     V4* SP = reinterpret_cast<V4*>(reinterpret_cast<uint8_t*>(SV) + align16((uint32_t)sizeof(LP) * D.n_sept));
     LP* SC = reinterpret_cast<LP*>(reinterpret_cast<uint8_t*>(SP) + align16((uint32_t)sizeof(V4) * nsep));
     bool sep_fixed_staged = false;
+    if (cfg.part_bytes > 0 && (int)blockIdx.x < n_parts) {  // this CTA's part, copied in shared memory
+        const int q = blockIdx.x;
+        const SegRow s0 = seg[q], s1 = seg[q + 1];
+        M.P0 = s0.piv;
+        M.P1 = s1.piv;
+        M.A0 = s0.atom;
+        M.A1 = s1.atom;
+        M.T0 = __ldg(M.lvl_task + s0.lvl);
+        M.T1 = __ldg(M.lvl_task + s1.lvl - 1);
+        uint8_t* pb = sep_smem + align16(cfg.sep_bytes);
+        const int pna = M.A1 - M.A0, pnp = M.P1 - M.P0;
+        M.XS = reinterpret_cast<double*>(pb);
+        pb += align16(24u * pna);
+        M.YS = reinterpret_cast<LP*>(pb);
+        pb += align16((uint32_t)sizeof(LP) * pnp);
+        M.RFS = reinterpret_cast<V4*>(pb);
+        pb += align16((uint32_t)sizeof(V4) * pnp);
+        M.VS = reinterpret_cast<LP*>(pb);
+    }
     const int G = gridDim.x, b = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
     const unsigned nb = gridDim.x;
     long long budget = kSpinBudget;
@@ -1591,21 +1678,31 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 const int32_t di = T->parted_desc[k];
                 const MolHost& MH = T->mols[T->desc_mol[di]];
                 const int n_parts = MH.n_seg - 1;
-                const uint32_t need = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
-                const size_t dyn = need <= kSepSmemMax ? need : 0;
-                if (dyn > 48 * 1024 &&
-                    (e = cudaFuncSetAttribute(k_solve_parted<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kSepSmemMax)) != cudaSuccess)
+                // shared memory: the separator block if it fits, then the parts' copies if
+                // every part gets a CTA of its own at that size
+                const uint32_t need_sep = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
+                PartedSmem cfg{need_sep <= kSepSmemMax ? need_sep : 0u, 0u};
+                const uint32_t need_part = part_smem_bytes<Mode>(MH.part_na, MH.part_np, MH.part_nt);
+                if ((e = cudaFuncSetAttribute(k_solve_parted<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kPartedSmemMax)) != cudaSuccess)
                     return to_status(e);
-                int per_sm = 0;
-                if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>, T->parted_threads,
-                                                                       dyn)) != cudaSuccess)
-                    return to_status(e);
-                const int max_grid = std::max(1, per_sm * T->n_sm);
+                int per_sm = 0, max_grid = 1;
+                for (int attempt = 0; attempt < 2; ++attempt) {
+                    cfg.part_bytes = attempt == 0 ? need_part : 0u;
+                    const size_t dyn = cfg.sep_bytes + cfg.part_bytes + (cfg.sep_bytes ? 16 : 0);
+                    if (dyn > kPartedSmemMax) continue;
+                    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>,
+                                                                           T->parted_threads, dyn)) != cudaSuccess)
+                        return to_status(e);
+                    max_grid = std::max(1, per_sm * T->n_sm);
+                    if (cfg.part_bytes == 0 || max_grid >= n_parts) break;
+                }
+                if (cfg.part_bytes > 0 && max_grid < n_parts) cfg.part_bytes = 0;
+                const size_t dyn = cfg.sep_bytes + cfg.part_bytes + (cfg.sep_bytes ? 16 : 0);
                 const MolDesc* dptr = T->d_desc + di;
                 PartSync* sp = reinterpret_cast<PartSync*>(sync) + k;
                 SolveArgs Aa = A;
-                void* args[] = {(void*)&dptr, (void*)&T->d_blob, (void*)&work, (void*)&sp, (void*)&Aa};
+                void* args[] = {(void*)&dptr, (void*)&T->d_blob, (void*)&work, (void*)&sp, (void*)&Aa, (void*)&cfg};
                 const dim3 grid(std::min(n_parts, max_grid)), block(T->parted_threads);
                 if ((e = cudaLaunchCooperativeKernel((const void*)k_solve_parted<Mode>, grid, block, args, dyn, side)) !=
                     cudaSuccess)

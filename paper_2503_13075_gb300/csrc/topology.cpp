@@ -610,6 +610,11 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             M.n_seg = np + 1;
             M.n_sept = (int32_t)P->sep_info.size();
             M.n_sep = nc - P->seg_piv[np];
+            for (int32_t q = 0; q < np; ++q) {
+                M.part_na = std::max(M.part_na, P->seg_atom[q + 1] - P->seg_atom[q]);
+                M.part_np = std::max(M.part_np, P->seg_piv[q + 1] - P->seg_piv[q]);
+                M.part_nt = std::max(M.part_nt, P->lvl_task[P->seg_lvl[q + 1] - 1] - P->lvl_task[P->seg_lvl[q]]);
+            }
             M.n_cent = (int32_t)P->cent.size();
             M.nlevel = P->nlevel;
             M.ntask = (int32_t)P->tasks.size() - 1;

@@ -22,6 +22,7 @@ struct MolHost {
     int32_t nlevel = 0, ntask = 0, nterm = 0, n_fill = 0;
     int32_t n_sept = 0, n_cent = 0;  // partitioned: separator tasks, Schur contribution entries
     int32_t n_sep = 0;               // partitioned: separator constraints
+    int32_t part_na = 0, part_np = 0, part_nt = 0;  // partitioned: largest part (atoms, pivots, tasks)
     int64_t passes = 0;
 };
 
