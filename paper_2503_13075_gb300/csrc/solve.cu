@@ -1115,10 +1115,14 @@ __host__ __device__ inline uint32_t part_smem_bytes(int na, int np, int nt) {
 }
 constexpr uint32_t kPartedSmemMax = 72 * 1024;  // three CTAs per SM still fit
 
-// Dynamic shared memory of a partitioned launch: the separator block (CTA 0; 0 = it stays
-// in global memory), then the part copies (0 = off; on only with one part per CTA).
+// Dynamic shared memory of a partitioned launch: the separator block (0 = it stays in
+// global memory) of CTA sep_cta, and the part copies (0 = off; on only with one part per
+// CTA).  With a CTA of its own for the separator block (sep_cta == number of parts) both
+// regions start at offset 0 of their CTAs and a launch needs only the larger one, which
+// leaves more of each SM's L1 to the parts' programs; otherwise CTA 0 holds both.
 struct PartedSmem {
     uint32_t sep_bytes, part_bytes;
+    int32_t sep_cta;
 };
 
 struct PartSync {
@@ -1160,7 +1164,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         M.A1 = s1.atom;
         M.T0 = __ldg(M.lvl_task + s0.lvl);
         M.T1 = __ldg(M.lvl_task + s1.lvl - 1);
-        uint8_t* pb = sep_smem + align16(cfg.sep_bytes);
+        uint8_t* pb = sep_smem + (cfg.sep_cta == 0 ? align16(cfg.sep_bytes) : 0u);
         const int pna = M.A1 - M.A0, pnp = M.P1 - M.P0;
         M.XS = reinterpret_cast<double*>(pb);
         pb += align16(24u * pna);
@@ -1259,7 +1263,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
         // ---- phase B: CTA 0 factorises the separator block (the Schur complement) and
         //      solves it forward and backward
-        if (b == 0 && sep_in_smem) {
+        if (b == cfg.sep_cta && sep_in_smem) {
             // stage the separator rows (their factor's reciprocal pivots stay in SRF.w
             // across ILVES-F iterations) and right-hand sides, solve in shared memory,
             // publish the solution
@@ -1294,7 +1298,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                 __syncthreads();
             }
             for (int k = r0; k < nsep; k += ts) M.Y[sep0 + k] = SY[k];
-        } else if (b == 0) {
+        } else if (b == cfg.sep_cta) {
             M.cohall = true;  // the separator block: every value may come from another CTA
             bool sing = false;
             const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
@@ -1681,29 +1685,39 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 // shared memory: the separator block if it fits, then the parts' copies if
                 // every part gets a CTA of its own at that size
                 const uint32_t need_sep = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
-                PartedSmem cfg{need_sep <= kSepSmemMax ? need_sep : 0u, 0u};
+                const uint32_t sep_b = need_sep <= kSepSmemMax ? need_sep : 0u;
                 const uint32_t need_part = part_smem_bytes<Mode>(MH.part_na, MH.part_np, MH.part_nt);
                 if ((e = cudaFuncSetAttribute(k_solve_parted<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)kPartedSmemMax)) != cudaSuccess)
                     return to_status(e);
-                int per_sm = 0, max_grid = 1;
-                for (int attempt = 0; attempt < 2; ++attempt) {
-                    cfg.part_bytes = attempt == 0 ? need_part : 0u;
-                    const size_t dyn = cfg.sep_bytes + cfg.part_bytes + (cfg.sep_bytes ? 16 : 0);
-                    if (dyn > kPartedSmemMax) continue;
+                // configurations, best first: separator CTA of its own + part copies; CTA 0
+                // with both; CTA 0 with the separator block only
+                const PartedSmem cands[3] = {{sep_b, need_part, n_parts}, {sep_b, need_part, 0}, {sep_b, 0u, 0}};
+                PartedSmem cfg = cands[2];
+                size_t dyn = sep_b;
+                int max_grid = 1;
+                for (const PartedSmem& c : cands) {
+                    const size_t d = c.sep_cta == 0 ? align16(c.sep_bytes) + c.part_bytes
+                                                     : std::max<size_t>(c.sep_bytes, c.part_bytes);
+                    if (d > kPartedSmemMax) continue;
+                    int per_sm = 0;
                     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_parted<Mode>,
-                                                                           T->parted_threads, dyn)) != cudaSuccess)
+                                                                           T->parted_threads, d)) != cudaSuccess)
                         return to_status(e);
-                    max_grid = std::max(1, per_sm * T->n_sm);
-                    if (cfg.part_bytes == 0 || max_grid >= n_parts) break;
+                    const int mg = std::max(1, per_sm * T->n_sm);
+                    const int needed = c.sep_cta > 0 ? n_parts + 1 : (c.part_bytes > 0 ? n_parts : 1);
+                    if (mg >= needed || &c == &cands[2]) {
+                        cfg = c;
+                        dyn = d;
+                        max_grid = mg;
+                        break;
+                    }
                 }
-                if (cfg.part_bytes > 0 && max_grid < n_parts) cfg.part_bytes = 0;
-                const size_t dyn = cfg.sep_bytes + cfg.part_bytes + (cfg.sep_bytes ? 16 : 0);
                 const MolDesc* dptr = T->d_desc + di;
                 PartSync* sp = reinterpret_cast<PartSync*>(sync) + k;
                 SolveArgs Aa = A;
                 void* args[] = {(void*)&dptr, (void*)&T->d_blob, (void*)&work, (void*)&sp, (void*)&Aa, (void*)&cfg};
-                const dim3 grid(std::min(n_parts, max_grid)), block(T->parted_threads);
+                const dim3 grid(cfg.sep_cta > 0 ? n_parts + 1 : std::min(n_parts, max_grid)), block(T->parted_threads);
                 if ((e = cudaLaunchCooperativeKernel((const void*)k_solve_parted<Mode>, grid, block, args, dyn, side)) !=
                     cudaSuccess)
                     return to_status(e);
