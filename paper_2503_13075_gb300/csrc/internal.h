@@ -105,7 +105,7 @@ ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 // Partitioned molecules add the Schur-contribution tables (see SepInfo, Contrib).
 struct ProgLayout {
     uint32_t seg, con_atoms, piv, lvl_task, lvl_piv, lane_term, inc_ptr, inc, tasks, terms, sep_info, cptr, cent,
-        staged, con_gid, bytes;
+        pprog_off, pprog, staged, con_gid, bytes;
 };
 
 // Partitioned molecules: the separator block's entries receive the terms of interior
@@ -118,6 +118,38 @@ struct ProgLayout {
 struct SepInfo { uint32_t b_start, ngroups; };
 struct Contrib { uint32_t task, slot, e0, e1; };
 
+// Part programs (partitioned molecules): each part's factorisation and back substitution
+// again, in 16-bit part-local indices, small enough to stage in the shared memory of the
+// part's CTA.  Positions, task slots and atoms count from the part's first; a row or
+// column that is a separator is coded 0x8000 | k, k indexing the part's separator table
+// (global positions); a fill entry's atom is 0xFFFF.  Terms are stored thread by thread
+// for a team of kPartThreads, like the warp programs.  Layout (16-byte aligned sections):
+//   header    PartProgHeader
+//   lvl_piv   uint16 x (nlev + 1)       local positions of each level
+//   lvl_task  uint16 x (nlev + 1)       local task slots of each level
+//   septab    int32  x nsep             global positions of the separators referenced
+//   lane_term uint32 x kPartThreads     first term of each team thread
+//   piv       uint32 x np               U-row slot | (number of U-row entries << 16)
+//   tasks     uint2  x nt               (row | col << 16, atom | neg << 16 | nterm << 24)
+//   terms     uint2  x nterm            (l | u << 16, m)
+constexpr int kPartThreads = 256;
+constexpr uint32_t kPartSep = 0x8000u, kPartNoAtom = 0xFFFFu;
+struct PartProgHeader { uint32_t np, nt, na, nlev, nsep, nterm, pad0, pad1; };
+struct PartProgLayout { uint32_t lvl_piv, lvl_task, septab, lane_term, piv, tasks, terms, bytes; };
+ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t nlev, uint32_t nsep, uint32_t nterm) {
+    PartProgLayout L;
+    uint32_t o = (uint32_t)sizeof(PartProgHeader);
+    L.lvl_piv = o;   o = align16(o + 2u * (nlev + 1));
+    L.lvl_task = o;  o = align16(o + 2u * (nlev + 1));
+    L.septab = o;    o = align16(o + 4u * nsep);
+    L.lane_term = o; o = align16(o + 4u * (uint32_t)kPartThreads);
+    L.piv = o;       o = align16(o + 4u * np);
+    L.tasks = o;     o = align16(o + 8u * nt);
+    L.terms = o;     o = align16(o + 8u * nterm);
+    L.bytes = o;
+    return L;
+}
+
 // Segment table (n_seg + 1 rows of {first position, first level-table entry, first atom}):
 // one segment for an ordinary molecule; for a partitioned molecule one per part, then the
 // separators (constraints between parts), whose atom range is empty.
@@ -125,7 +157,8 @@ struct SegRow { int32_t piv, lvl, atom; };
 
 template <class IdxT>
 ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32_t nterm,
-                                uint32_t nlevel, uint32_t n_seg = 1, uint32_t n_sept = 0, uint32_t n_cent = 0) {
+                                uint32_t nlevel, uint32_t n_seg = 1, uint32_t n_sept = 0, uint32_t n_cent = 0,
+                                uint32_t pprog_bytes = 0) {
     ProgLayout L;
     const uint32_t ix = (uint32_t)sizeof(IdxT);
     const bool compact = ix == 2u;
@@ -144,6 +177,8 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
     L.sep_info = o;  o = align16(o + (parted ? 8u * n_sept : 0u));
     L.cptr = o;      o = align16(o + (parted ? 4u * n_seg : 0u));  // n_parts + 1 = n_seg entries
     L.cent = o;      o = align16(o + (parted ? 16u * n_cent : 0u));
+    L.pprog_off = o; o = align16(o + (pprog_bytes ? 4u * n_seg : 0u));  // n_parts + 1 entries
+    L.pprog = o;     o = align16(o + pprog_bytes);
     L.staged = o;
     L.con_gid = o;   o = align16(o + 4u * nc);
     L.bytes = o;
@@ -187,7 +222,7 @@ ILVES_HD StateLayout state_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint
     return S;
 }
 
-// One molecule as the kernels see it (64 bytes).
+// One molecule as the kernels see it (72 bytes).
 struct MolDesc {
     int64_t blob_off;    // byte offset of the program blob in the blob buffer (16-B aligned)
     int64_t work_off;    // large path: byte offset of the numerical state in the workspace
@@ -201,6 +236,8 @@ struct MolDesc {
     int32_t n_seg;   // 1, or parts + 1 for a partitioned molecule
     int32_t n_sept;  // partitioned: tasks of the separator segment (they are the last ones)
     int32_t n_cent;  // partitioned: Schur contribution entries over all parts
+    int32_t pprog_bytes;  // partitioned: bytes of all part programs (0 = none)
+    int32_t pad_;
 };
 
 }  // namespace ilves

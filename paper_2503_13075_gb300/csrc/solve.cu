@@ -323,7 +323,8 @@ struct MolView {
         tolf = (float)a.tol;
         na = d.na;
         nc = d.nc;
-        const ProgLayout PL = prog_layout<IdxT>(na, nc, d.ntask, d.nterm, d.nlevel, d.n_seg, d.n_sept, d.n_cent);
+        const ProgLayout PL =
+            prog_layout<IdxT>(na, nc, d.ntask, d.nterm, d.nlevel, d.n_seg, d.n_sept, d.n_cent, d.pprog_bytes);
         const StateLayout SL = state_layout(na, nc, d.ntask, sizeof(LP), DF);
         seg = reinterpret_cast<const SegRow*>(prog + PL.seg);
         con = reinterpret_cast<const ConA<IdxT>*>(prog + PL.con_atoms);
@@ -417,6 +418,105 @@ struct MolView {
     __device__ __forceinline__ void x_st(int c, int a, double v) {
         X[c * na + a] = v;
         if (in_a(a)) XS[c * (A1 - A0) + (a - A0)] = v;
+    }
+
+    // ---- partitioned molecules, one part per CTA, with the part's program staged in
+    //      shared memory (PartProgHeader): 16-bit part-local task words, terms and pivot
+    //      records; a position code c is the part position P0 + c, or, with kPartSep
+    //      set, the separator PST[c & ~kPartSep].  RHS and WLS hold the part's reference
+    //      rows and weights (fixed for the solve).  Off (PH == nullptr) otherwise.
+    const PartProgHeader* PH = nullptr;
+    const uint16_t *PLP = nullptr, *PLT = nullptr;
+    const int32_t* PST = nullptr;
+    const uint32_t *PLANE = nullptr, *PPIV = nullptr;
+    const uint2 *PTK = nullptr, *PTM = nullptr;
+    V4* RHS = nullptr;
+    LP* WLS = nullptr;
+    __device__ __forceinline__ void part_prog_bind(const uint8_t* sp) {
+        PH = reinterpret_cast<const PartProgHeader*>(sp);
+        const PartProgLayout L = part_prog_layout(PH->np, PH->nt, PH->nlev, PH->nsep, PH->nterm);
+        PLP = reinterpret_cast<const uint16_t*>(sp + L.lvl_piv);
+        PLT = reinterpret_cast<const uint16_t*>(sp + L.lvl_task);
+        PST = reinterpret_cast<const int32_t*>(sp + L.septab);
+        PLANE = reinterpret_cast<const uint32_t*>(sp + L.lane_term);
+        PPIV = reinterpret_cast<const uint32_t*>(sp + L.piv);
+        PTK = reinterpret_cast<const uint2*>(sp + L.tasks);
+        PTM = reinterpret_cast<const uint2*>(sp + L.terms);
+    }
+    // current Jacobian row / reference row of the constraint with position code c
+    __device__ __forceinline__ V4 prow(uint32_t c) const {
+        return (c & kPartSep) ? lds<kCoh>(RF + PST[c & ~kPartSep]) : RFS[c];
+    }
+    __device__ __forceinline__ V4 pref(uint32_t c) const {
+        return (c & kPartSep) ? *(RHOF + PST[c & ~kPartSep]) : RHS[c];
+    }
+    // one level of the part's factorisation: local tasks t0 + r + kPartThreads k, DIAG
+    //      tasks first (np of them, pivots p0 + ...); thread r walks its terms from offset e
+    __device__ __forceinline__ void part_level(int t0, int t1, int np, int r, int& e, bool& singular) {
+        for (int t = t0 + r; t < t1; t += kPartThreads) {
+            const uint2 w = PTK[t];
+            const uint32_t rc = w.x & 0xFFFFu, cc = w.x >> 16, ac = w.y & 0xFFFFu;
+            const int n = (int)(w.y >> 24);
+            const bool diag = t < t0 + np;
+            const V4 rr = prow(rc), pp = pref(cc);
+            const LP wv = diag ? pp.w : (ac == kPartNoAtom ? LP(0) : WLS[ac]);
+            const LP cf = ((w.y >> 16) & 1u) ? LP(-4) * wv : LP(4) * wv;
+            const LP a = cf * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+            LP sacc = a, yv = LP(0);
+#pragma unroll 2
+            for (int k = e; k < e + n; ++k) {
+                const uint2 tr = PTM[k];
+                const uint32_t m = tr.y;
+                const LP li = VS[tr.x & 0xFFFFu] * reinterpret_cast<const LP*>(RFS + m)[3];
+                sacc -= li * VS[tr.x >> 16];
+                if (diag) yv += li * YS[m];
+            }
+            e += n;
+            VS[t] = sacc;
+            V[T0 + t] = sacc;
+            if (diag) {  // rc is a part position
+                singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+                const LP ri = lp_rcp(sacc);
+                reinterpret_cast<LP*>(RFS + rc)[3] = ri;
+                *inv_ptr(P0 + (int)rc) = ri;
+                const LP ny = YS[rc] - yv;
+                YS[rc] = ny;
+                Y[P0 + (int)rc] = ny;
+            }
+        }
+    }
+    // forward substitution alone (ILVES-F with its stored factor): the DIAG tasks of a level
+    __device__ __forceinline__ void part_forward_level(int t0, int t1, int p0, int np, int r, int& e) {
+        for (int t = t0 + r; t < t1; t += kPartThreads) {
+            const int n = (int)(PTK[t].y >> 24);
+            if (t < t0 + np) {
+                const int pl = p0 + (t - t0);
+                LP yv = LP(0);
+                for (int k = e; k < e + n; ++k) {
+                    const uint2 tr = PTM[k];
+                    const uint32_t m = tr.y;
+                    yv += VS[tr.x & 0xFFFFu] * reinterpret_cast<const LP*>(RFS + m)[3] * YS[m];
+                }
+                const LP ny = YS[pl] - yv;
+                YS[pl] = ny;
+                Y[P0 + pl] = ny;
+            }
+            e += n;
+        }
+    }
+    // backward substitution for part pivot pl (local position)
+    __device__ __forceinline__ void part_backward(int pl) {
+        const uint32_t pv = PPIV[pl];
+        const int us = (int)(pv & 0xFFFFu), nu = (int)(pv >> 16);
+        LP dl = YS[pl];
+        for (int k = 0; k < nu; ++k) {
+            const uint32_t q = PTK[us + k].x >> 16;
+            const LP yq = (q & kPartSep) ? lds<kCoh>(Y + PST[q & ~kPartSep]) : YS[q];
+            dl -= VS[us + k] * yq;
+        }
+        const LP r = dl * reinterpret_cast<const LP*>(RFS + pl)[3];
+        YS[pl] = r;
+        Y[P0 + pl] = r;
     }
 
     // ---- S1
@@ -1113,6 +1213,15 @@ __host__ __device__ inline uint32_t part_smem_bytes(int na, int np, int nt) {
     return align16(24u * na) + align16((uint32_t)sizeof(LP) * np) + align16((uint32_t)sizeof(V4) * np) +
            align16((uint32_t)sizeof(LP) * nt);
 }
+// The same with the part program staged too: the part's reference rows and weights, then
+// the largest part program.
+template <class Mode>
+__host__ __device__ inline uint32_t part_prog_smem_bytes(int na, int np, int nt, int prog_max) {
+    using LP = typename Mode::LP;
+    using V4 = typename Mode::V4;
+    return part_smem_bytes<Mode>(na, np, nt) + align16((uint32_t)sizeof(V4) * np) +
+           align16((uint32_t)sizeof(LP) * na) + (uint32_t)prog_max;
+}
 constexpr uint32_t kPartedSmemMax = 72 * 1024;  // three CTAs per SM still fit
 
 // Dynamic shared memory of a partitioned launch: the separator block (0 = it stays in
@@ -1123,6 +1232,7 @@ constexpr uint32_t kPartedSmemMax = 72 * 1024;  // three CTAs per SM still fit
 struct PartedSmem {
     uint32_t sep_bytes, part_bytes;
     int32_t sep_cta;
+    uint32_t prog;  // nonzero: part programs staged too (part_bytes counts them)
 };
 
 struct PartSync {
@@ -1173,6 +1283,23 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         M.RFS = reinterpret_cast<V4*>(pb);
         pb += align16((uint32_t)sizeof(V4) * pnp);
         M.VS = reinterpret_cast<LP*>(pb);
+        if (cfg.prog) {
+            pb += align16((uint32_t)sizeof(LP) * (M.T1 - M.T0));
+            M.RHS = reinterpret_cast<V4*>(pb);
+            pb += align16((uint32_t)sizeof(V4) * pnp);
+            M.WLS = reinterpret_cast<LP*>(pb);
+            pb += align16((uint32_t)sizeof(LP) * pna);
+            const ProgLayout PL = prog_layout<uint32_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg, D.n_sept,
+                                                        D.n_cent, D.pprog_bytes);
+            const uint8_t* gp = blob + D.blob_off;
+            const uint32_t o0 = __ldg(reinterpret_cast<const uint32_t*>(gp + PL.pprog_off) + q);
+            const uint32_t o1 = __ldg(reinterpret_cast<const uint32_t*>(gp + PL.pprog_off) + q + 1);
+            for (uint32_t o = 16u * threadIdx.x; o < o1 - o0; o += 16u * blockDim.x)
+                cp_async16(pb + o, gp + PL.pprog + o0 + o);
+            cp_async_wait_all();
+            __syncthreads();
+            M.part_prog_bind(pb);
+        }
     }
     const int G = gridDim.x, b = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
     const unsigned nb = gridDim.x;
@@ -1202,6 +1329,11 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
     for_owned([&](int p) { M.s1_constraint(p, false); });
     for_my_atoms([&](int a) { M.s1_atom_unc(a); });
     bool alive = grid_sync(&sync->barrier, nb, budget);
+    if (M.PH) {  // the part's reference rows and weights (written by this CTA in S1)
+        for (int k = r0; k < M.P1 - M.P0; k += ts) M.RHS[k] = *(M.RHOF + M.P0 + k);
+        for (int a = r0; a < M.A1 - M.A0; a += ts) M.WLS[a] = *(M.WL + M.A0 + a);
+        __syncthreads();
+    }
     if (alive && A.lambda0) {
         for_my_atoms([&](int a) { M.update_atom(a); });
         alive = grid_sync(&sync->barrier, nb, budget);
@@ -1245,15 +1377,26 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         //      the separators) level by level; ILVES-F iterations only substitute forward
         bool singular = false;
         for (int q = b; q < n_parts; q += G) {
-            const int l0 = __ldg(&seg[q].lvl), l1 = __ldg(&seg[q + 1].lvl) - 1;
-            for (int l = l0; l < l1; ++l) {
-                const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
-                const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
-                if (factor)
-                    for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
-                else
-                    for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
-                __syncthreads();
+            if (M.PH) {  // the part program in shared memory (one part per CTA)
+                const int nl = (int)M.PH->nlev;
+                int e = (int)M.PLANE[r0];
+                for (int l = 0; l < nl; ++l) {
+                    const int p0 = M.PLP[l], np = M.PLP[l + 1] - p0, t0 = M.PLT[l], t1 = M.PLT[l + 1];
+                    if (factor) M.part_level(t0, t1, np, r0, e, singular);
+                    else M.part_forward_level(t0, t1, p0, np, r0, e);
+                    __syncthreads();
+                }
+            } else {
+                const int l0 = __ldg(&seg[q].lvl), l1 = __ldg(&seg[q + 1].lvl) - 1;
+                for (int l = l0; l < l1; ++l) {
+                    const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
+                    const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
+                    if (factor)
+                        for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
+                    else
+                        for (int p = p0 + r0; p < p1; p += ts) M.forward(t0 + (p - p0), p);
+                    __syncthreads();
+                }
             }
             // this part's contributions to the separator block (Schur complement)
             const int c1 = __ldg(M.cptr + q + 1);
@@ -1327,6 +1470,14 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         }
         // ---- phase D: back substitution inside every part, multipliers, positions
         for (int q = b; q < n_parts; q += G) {
+            if (M.PH) {
+                for (int l = (int)M.PH->nlev - 1; l >= 0; --l) {
+                    const int p1 = M.PLP[l + 1];
+                    for (int p = M.PLP[l] + r0; p < p1; p += ts) M.part_backward(p);
+                    __syncthreads();
+                }
+                continue;
+            }
             const int l0 = __ldg(&seg[q].lvl), l1 = __ldg(&seg[q + 1].lvl) - 1;
             for (int l = l1 - 1; l >= l0; --l) {
                 const int p1 = __ldg(M.lvl_piv + l + 1);
@@ -1581,6 +1732,7 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         D.n_seg = M.n_seg;
         D.n_sept = M.n_sept;
         D.n_cent = M.n_cent;
+        D.pprog_bytes = M.pprog_bytes;
         D.work_off = 0;
         if (M.large) {  // state, then (partitioned) 4 contribution values per separator task
             D.work_off = woff;
@@ -1687,16 +1839,28 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 const uint32_t need_sep = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
                 const uint32_t sep_b = need_sep <= kSepSmemMax ? need_sep : 0u;
                 const uint32_t need_part = part_smem_bytes<Mode>(MH.part_na, MH.part_np, MH.part_nt);
+                // part programs in shared memory: 256-thread CTAs (their terms are laid out
+                // thread by thread for kPartThreads threads)
+                const uint32_t pp = MH.pprog_bytes > 0 && T->parted_threads == kPartThreads ? 1u : 0u;
+                const uint32_t need_pp =
+                    pp ? part_prog_smem_bytes<Mode>(MH.part_na, MH.part_np, MH.part_nt, MH.pprog_max) : 0u;
                 if ((e = cudaFuncSetAttribute(k_solve_parted<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)kPartedSmemMax)) != cudaSuccess)
                     return to_status(e);
-                // configurations, best first: separator CTA of its own + part copies; CTA 0
-                // with both; CTA 0 with the separator block only
-                const PartedSmem cands[3] = {{sep_b, need_part, n_parts}, {sep_b, need_part, 0}, {sep_b, 0u, 0}};
-                PartedSmem cfg = cands[2];
+                // configurations, best first: separator CTA of its own + part copies and
+                // programs; the same without programs; CTA 0 with the separator block and the
+                // part copies (with, then without programs); CTA 0 with the separator block only
+                constexpr int kCands = 5;
+                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u},
+                                                  {sep_b, need_part, n_parts, 0u},
+                                                  {sep_b, need_pp, 0, 1u},
+                                                  {sep_b, need_part, 0, 0u},
+                                                  {sep_b, 0u, 0, 0u}};
+                PartedSmem cfg = cands[kCands - 1];
                 size_t dyn = sep_b;
                 int max_grid = 1;
                 for (const PartedSmem& c : cands) {
+                    if (c.prog && !pp) continue;
                     const size_t d = c.sep_cta == 0 ? align16(c.sep_bytes) + c.part_bytes
                                                      : std::max<size_t>(c.sep_bytes, c.part_bytes);
                     if (d > kPartedSmemMax) continue;
@@ -1706,7 +1870,7 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                         return to_status(e);
                     const int mg = std::max(1, per_sm * T->n_sm);
                     const int needed = c.sep_cta > 0 ? n_parts + 1 : (c.part_bytes > 0 ? n_parts : 1);
-                    if (mg >= needed || &c == &cands[2]) {
+                    if (mg >= needed || &c == &cands[kCands - 1]) {
                         cfg = c;
                         dyn = d;
                         max_grid = mg;

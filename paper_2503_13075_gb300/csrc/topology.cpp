@@ -148,7 +148,107 @@ struct Program {
     std::vector<SepInfo> sep_info;             // per separator task
     std::vector<int32_t> cptr;                 // per part: [cptr[q], cptr[q+1]) into cent
     std::vector<Contrib> cent;
+    // partitioned: part programs (see PartProgHeader), empty if a part does not fit them
+    std::vector<uint8_t> pprog;
+    std::vector<uint32_t> pprog_off;  // per part, then the total
+    uint32_t pprog_max = 0;           // largest part program (bytes)
 };
+
+// Part programs of a partitioned molecule (16-bit part-local encoding of the part's
+// tasks, terms and pivots); false if some part exceeds the encoding's ranges.
+static bool build_part_programs(Program& P, int32_t nc, int32_t na_dummy) {
+    const int32_t n_parts = P.n_seg - 1;
+    const int32_t sep_p0 = P.seg_piv[n_parts];
+    P.pprog.clear();
+    P.pprog_off.assign(n_parts + 1, 0);
+    P.pprog_max = 0;
+    for (int32_t g = 0; g < n_parts; ++g) {
+        const int32_t P0 = P.seg_piv[g], P1 = P.seg_piv[g + 1], np = P1 - P0;
+        const int32_t lv0 = P.seg_lvl[g], nlev = P.seg_lvl[g + 1] - 1 - lv0;
+        const int32_t T0 = P.lvl_task[lv0], T1 = P.lvl_task[lv0 + nlev], nt = T1 - T0;
+        const int32_t A0 = P.seg_atom[g], A1 = P.seg_atom[g + 1];
+        if (np >= (int32_t)kPartSep || nt >= 65536 || A1 - A0 >= (int32_t)kPartNoAtom) return false;
+        std::vector<int32_t> septab;
+        auto code = [&](int32_t pos, uint32_t& c) {
+            if (pos >= P0 && pos < P1) {
+                c = (uint32_t)(pos - P0);
+                return true;
+            }
+            if (pos < sep_p0) return false;  // another part: not expected in this part's tasks
+            auto it = std::lower_bound(septab.begin(), septab.end(), pos);
+            c = kPartSep | (uint32_t)(it - septab.begin());
+            return true;
+        };
+        for (int32_t t = T0; t < T1; ++t)
+            for (int32_t pos : {(int32_t)P.tasks[t].row, (int32_t)P.tasks[t].col})
+                if (pos >= sep_p0) septab.push_back(pos);
+        std::sort(septab.begin(), septab.end());
+        septab.erase(std::unique(septab.begin(), septab.end()), septab.end());
+        if (septab.size() >= kPartSep) return false;
+        // terms, thread by thread over the part's levels
+        std::vector<uint32_t> lane_term(kPartThreads);
+        std::vector<uint32_t> terms;
+        for (int32_t r = 0; r < kPartThreads; ++r) {
+            lane_term[r] = (uint32_t)(terms.size() / 2);
+            for (int32_t l = 0; l < nlev; ++l)
+                for (int32_t t = P.lvl_task[lv0 + l] + r; t < P.lvl_task[lv0 + l + 1]; t += kPartThreads)
+                    for (uint32_t k = P.tasks[t].tstart; k < P.tasks[t + 1].tstart; ++k) {
+                        const TermW& tr = P.terms[k];
+                        const int32_t l_ = (int32_t)tr.l - T0, u_ = (int32_t)tr.u - T0, m_ = (int32_t)tr.m - P0;
+                        if (l_ < 0 || l_ >= nt || u_ < 0 || u_ >= nt || m_ < 0 || m_ >= np) return false;
+                        terms.push_back((uint32_t)l_ | ((uint32_t)u_ << 16));
+                        terms.push_back((uint32_t)m_);
+                    }
+        }
+        const uint32_t nterm = (uint32_t)(terms.size() / 2);
+        const PartProgLayout L = part_prog_layout(np, nt, nlev, (uint32_t)septab.size(), nterm);
+        const size_t base = P.pprog.size();
+        P.pprog_off[g] = (uint32_t)base;
+        P.pprog.resize(base + L.bytes, 0);
+        uint8_t* d = P.pprog.data() + base;
+        const PartProgHeader H{(uint32_t)np, (uint32_t)nt, (uint32_t)(A1 - A0), (uint32_t)nlev,
+                               (uint32_t)septab.size(), nterm, 0u, 0u};
+        std::memcpy(d, &H, sizeof(H));
+        auto* lp = reinterpret_cast<uint16_t*>(d + L.lvl_piv);
+        auto* lt = reinterpret_cast<uint16_t*>(d + L.lvl_task);
+        for (int32_t l = 0; l <= nlev; ++l) {
+            lp[l] = (uint16_t)(P.lvl_piv[lv0 + l] - P0);
+            lt[l] = (uint16_t)(P.lvl_task[lv0 + l] - T0);
+        }
+        std::memcpy(d + L.septab, septab.data(), septab.size() * 4);
+        std::memcpy(d + L.lane_term, lane_term.data(), lane_term.size() * 4);
+        auto* pv = reinterpret_cast<uint32_t*>(d + L.piv);
+        for (int32_t p = P0; p < P1; ++p) {
+            const int32_t us = P.ustart[p] - T0, nu = (int32_t)P.up[p].size();
+            if (us < 0 || us + nu > nt) return false;
+            pv[p - P0] = (uint32_t)us | ((uint32_t)nu << 16);
+        }
+        auto* tw = reinterpret_cast<uint32_t*>(d + L.tasks);
+        for (int32_t t = T0; t < T1; ++t) {
+            const TaskW& w = P.tasks[t];
+            uint32_t rc, cc;
+            if (!code((int32_t)w.row, rc) || !code((int32_t)w.col, cc)) return false;
+            const uint32_t nterm_t = P.tasks[t + 1].tstart - w.tstart;
+            if (nterm_t > 255u) return false;
+            // the shared atom of an off-diagonal entry is an atom of the part's constraint
+            const int32_t a = (int32_t)(w.atomsign >> 1);
+            uint32_t ac = kPartNoAtom;
+            if (w.row != w.col && a != na_dummy) {
+                if (a < A0 || a >= A1) return false;
+                ac = (uint32_t)(a - A0);
+            }
+            tw[2 * (t - T0)] = rc | (cc << 16);
+            tw[2 * (t - T0) + 1] = ac | ((w.atomsign & 1u) << 16) | (nterm_t << 24);
+        }
+        std::memcpy(d + L.terms, terms.data(), terms.size() * 4);
+        P.pprog_max = std::max(P.pprog_max, L.bytes);
+        // keep each part program 16-byte aligned
+        P.pprog.resize((P.pprog.size() + 15) & ~size_t(15), 0);
+    }
+    P.pprog_off[n_parts] = (uint32_t)P.pprog.size();
+    (void)nc;
+    return true;
+}
 
 // seg (optional): segment of every local constraint (a part, or n_seg - 1 for the
 // separators); positions are ordered by segment, then level; levels count only
@@ -389,7 +489,7 @@ template <class IdxT>
 static ProgLayout layout_for(const MolHost& M) {
     return prog_layout<IdxT>((uint32_t)M.atoms.size(), (uint32_t)M.cons.size(), (uint32_t)M.ntask,
                              (uint32_t)M.nterm, (uint32_t)M.nlevel, (uint32_t)M.n_seg, (uint32_t)M.n_sept,
-                             (uint32_t)M.n_cent);
+                             (uint32_t)M.n_cent, sizeof(IdxT) == 4 ? (uint32_t)M.pprog_bytes : 0u);
 }
 
 template <class IdxT>
@@ -469,6 +569,10 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
             std::memcpy(dst + L.sep_info, P.sep_info.data(), P.sep_info.size() * sizeof(SepInfo));
             std::memcpy(dst + L.cptr, P.cptr.data(), P.cptr.size() * sizeof(int32_t));
             std::memcpy(dst + L.cent, P.cent.data(), P.cent.size() * sizeof(Contrib));
+            if (M.pprog_bytes > 0) {
+                std::memcpy(dst + L.pprog_off, P.pprog_off.data(), P.pprog_off.size() * sizeof(uint32_t));
+                std::memcpy(dst + L.pprog, P.pprog.data(), P.pprog.size());
+            }
         }
     }
 }
@@ -616,6 +720,13 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
                 M.part_nt = std::max(M.part_nt, P->lvl_task[P->seg_lvl[q + 1] - 1] - P->lvl_task[P->seg_lvl[q]]);
             }
             M.n_cent = (int32_t)P->cent.size();
+            if (build_part_programs(*P, nc, na)) {
+                M.pprog_bytes = (int32_t)P->pprog.size();
+                M.pprog_max = (int32_t)P->pprog_max;
+            } else {
+                P->pprog.clear();
+                P->pprog_off.clear();
+            }
             M.nlevel = P->nlevel;
             M.ntask = (int32_t)P->tasks.size() - 1;
             M.nterm = (int32_t)P->terms.size();
