@@ -132,10 +132,13 @@ struct Contrib { uint32_t task, slot, e0, e1; };
 //   piv       uint32 x np               U-row slot | (number of U-row entries << 16)
 //   tasks     uint2  x nt               (row | col << 16, atom | neg << 16 | nterm << 24)
 //   terms     uint2  x nterm            (l | u << 16, m)
+// followed, in shared memory only, by a scratch section (not in the blob) that holds the
+// separators' current and reference rows and solution values during a phase.
 constexpr int kPartThreads = 256;
 constexpr uint32_t kPartSep = 0x8000u, kPartNoAtom = 0xFFFFu;
 struct PartProgHeader { uint32_t np, nt, na, nlev, nsep, nterm, pad0, pad1; };
-struct PartProgLayout { uint32_t lvl_piv, lvl_task, septab, lane_term, piv, tasks, terms, bytes; };
+struct PartProgLayout { uint32_t lvl_piv, lvl_task, septab, lane_term, piv, tasks, terms, scratch, bytes; };
+constexpr uint32_t kPartSepScratch = 2u * 32u + 8u;  // per separator: two rows and a value (float64)
 ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t nlev, uint32_t nsep, uint32_t nterm) {
     PartProgLayout L;
     uint32_t o = (uint32_t)sizeof(PartProgHeader);
@@ -145,6 +148,33 @@ ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t nlev
     L.lane_term = o; o = align16(o + 4u * (uint32_t)kPartThreads);
     L.piv = o;       o = align16(o + 4u * np);
     L.tasks = o;     o = align16(o + 8u * nt);
+    L.terms = o;     o = align16(o + 8u * nterm);
+    L.scratch = o;   o = align16(o + kPartSepScratch * nsep);
+    L.bytes = o;
+    return L;
+}
+
+// Separator program (partitioned molecules): the separator block's factorisation in
+// indices local to the block (positions from the first separator, task slots from the
+// first separator task), staged in the shared memory of the CTA that solves the block.
+// A term whose eliminated pivot is a separator is (l | u << 16, m); one whose pivot is an
+// interior pivot (beyond the parts' contribution slots) is (0xFFFFFFFF, global term index).
+//   header    SepProgHeader
+//   lvl_piv   uint16 x (nlev + 1)
+//   lvl_task  uint16 x (nlev + 1)
+//   piv       uint32 x nsep             U-row slot | (number of U-row entries << 16)
+//   tasks     uint2  x (nt + 1)         (row | col << 16, first term | ngroups << 30), sentinel
+//   terms     uint2  x nterm
+struct SepProgHeader { uint32_t nsep, nt, nlev, nterm; };
+struct SepProgLayout { uint32_t lvl_piv, lvl_task, piv, tasks, terms, bytes; };
+constexpr uint32_t kSepInterior = 0xFFFFFFFFu;
+ILVES_HD SepProgLayout sep_prog_layout(uint32_t nsep, uint32_t nt, uint32_t nlev, uint32_t nterm) {
+    SepProgLayout L;
+    uint32_t o = (uint32_t)sizeof(SepProgHeader);
+    L.lvl_piv = o;   o = align16(o + 2u * (nlev + 1));
+    L.lvl_task = o;  o = align16(o + 2u * (nlev + 1));
+    L.piv = o;       o = align16(o + 4u * nsep);
+    L.tasks = o;     o = align16(o + 8u * (nt + 1));
     L.terms = o;     o = align16(o + 8u * nterm);
     L.bytes = o;
     return L;
@@ -177,7 +207,7 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
     L.sep_info = o;  o = align16(o + (parted ? 8u * n_sept : 0u));
     L.cptr = o;      o = align16(o + (parted ? 4u * n_seg : 0u));  // n_parts + 1 = n_seg entries
     L.cent = o;      o = align16(o + (parted ? 16u * n_cent : 0u));
-    L.pprog_off = o; o = align16(o + (pprog_bytes ? 4u * n_seg : 0u));  // n_parts + 1 entries
+    L.pprog_off = o; o = align16(o + (pprog_bytes ? 4u * (n_seg + 1) : 0u));  // parts, separators, end
     L.pprog = o;     o = align16(o + pprog_bytes);
     L.staged = o;
     L.con_gid = o;   o = align16(o + 4u * nc);
@@ -236,7 +266,7 @@ struct MolDesc {
     int32_t n_seg;   // 1, or parts + 1 for a partitioned molecule
     int32_t n_sept;  // partitioned: tasks of the separator segment (they are the last ones)
     int32_t n_cent;  // partitioned: Schur contribution entries over all parts
-    int32_t pprog_bytes;  // partitioned: bytes of all part programs (0 = none)
+    int32_t pprog_bytes;  // partitioned: bytes of the segment programs (parts, then separators)
     int32_t pad_;
 };
 

@@ -432,6 +432,8 @@ struct MolView {
     const uint2 *PTK = nullptr, *PTM = nullptr;
     V4* RHS = nullptr;
     LP* WLS = nullptr;
+    V4 *SEPRF = nullptr, *SEPREF = nullptr;  // the separators' current and reference rows
+    LP* SEPY = nullptr;                      // and solution values (scratch after the program)
     __device__ __forceinline__ void part_prog_bind(const uint8_t* sp) {
         PH = reinterpret_cast<const PartProgHeader*>(sp);
         const PartProgLayout L = part_prog_layout(PH->np, PH->nt, PH->nlev, PH->nsep, PH->nterm);
@@ -442,14 +444,14 @@ struct MolView {
         PPIV = reinterpret_cast<const uint32_t*>(sp + L.piv);
         PTK = reinterpret_cast<const uint2*>(sp + L.tasks);
         PTM = reinterpret_cast<const uint2*>(sp + L.terms);
+        uint8_t* sc = const_cast<uint8_t*>(sp) + L.scratch;
+        SEPRF = reinterpret_cast<V4*>(sc);
+        SEPREF = SEPRF + PH->nsep;
+        SEPY = reinterpret_cast<LP*>(SEPREF + PH->nsep);
     }
     // current Jacobian row / reference row of the constraint with position code c
-    __device__ __forceinline__ V4 prow(uint32_t c) const {
-        return (c & kPartSep) ? lds<kCoh>(RF + PST[c & ~kPartSep]) : RFS[c];
-    }
-    __device__ __forceinline__ V4 pref(uint32_t c) const {
-        return (c & kPartSep) ? *(RHOF + PST[c & ~kPartSep]) : RHS[c];
-    }
+    __device__ __forceinline__ V4 prow(uint32_t c) const { return (c & kPartSep) ? SEPRF[c & ~kPartSep] : RFS[c]; }
+    __device__ __forceinline__ V4 pref(uint32_t c) const { return (c & kPartSep) ? SEPREF[c & ~kPartSep] : RHS[c]; }
     // one level of the part's factorisation: local tasks t0 + r + kPartThreads k, DIAG
     //      tasks first (np of them, pivots p0 + ...); thread r walks its terms from offset e
     __device__ __forceinline__ void part_level(int t0, int t1, int np, int r, int& e, bool& singular) {
@@ -511,7 +513,7 @@ struct MolView {
         LP dl = YS[pl];
         for (int k = 0; k < nu; ++k) {
             const uint32_t q = PTK[us + k].x >> 16;
-            const LP yq = (q & kPartSep) ? lds<kCoh>(Y + PST[q & ~kPartSep]) : YS[q];
+            const LP yq = (q & kPartSep) ? SEPY[q & ~kPartSep] : YS[q];
             dl -= VS[us + k] * yq;
         }
         const LP r = dl * reinterpret_cast<const LP*>(RFS + pl)[3];
@@ -900,34 +902,54 @@ struct MolView {
         Y[p] = lds<kCoh>(Y + p) - yv;
     }
 
-    // ---- the separator phase in shared memory (one CTA): SV = values of the separator
-    //      tasks, SRF = Jacobian rows of the separators (.w = 1 / pivot), SY = their
-    //      right-hand side / solution; indices local to the separator block.  Terms of
-    //      interior pivots beyond the parts' contributions read the global state.
+    // ---- the separator phase in shared memory (one CTA), from the separator program
+    //      (SepProgHeader; SLP .. STM point into its shared-memory copy): SV = values of
+    //      the separator tasks, SRF = Jacobian rows of the separators (.w = 1 / pivot), SY
+    //      = their right-hand side / solution; indices local to the separator block.
+    //      Terms of interior pivots beyond the parts' contributions read the global state.
     //      SP = the separators' reference rows, SC = each task's assembly coefficient
     //      (4 s s' w), both fixed for the whole solve.
-    __device__ __forceinline__ void sep_task_smem(int t, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
+    const uint16_t *SLP = nullptr, *SLT = nullptr;
+    const uint32_t* SPV = nullptr;
+    const uint2 *STK = nullptr, *STM = nullptr;
+    __device__ __forceinline__ void sep_prog_bind(const uint8_t* sp) {
+        const SepProgHeader* h = reinterpret_cast<const SepProgHeader*>(sp);
+        const SepProgLayout L = sep_prog_layout(h->nsep, h->nt, h->nlev, h->nterm);
+        SLP = reinterpret_cast<const uint16_t*>(sp + L.lvl_piv);
+        SLT = reinterpret_cast<const uint16_t*>(sp + L.lvl_task);
+        SPV = reinterpret_cast<const uint32_t*>(sp + L.piv);
+        STK = reinterpret_cast<const uint2*>(sp + L.tasks);
+        STM = reinterpret_cast<const uint2*>(sp + L.terms);
+    }
+    // the factors of one term: L[row,m] inv_m, U[m,col] and y_m
+    __device__ __forceinline__ void sep_term(const uint2 tr, const LP* SV, const V4* SRF, const LP* SY, LP& li, LP& u,
+                                             LP& ym) const {
+        if (tr.x != kSepInterior) {
+            const uint32_t m = tr.y;
+            li = SV[tr.x & 0xFFFFu] * reinterpret_cast<const LP*>(SRF + m)[3];
+            u = SV[tr.x >> 16];
+            ym = SY[m];
+        } else {  // an interior pivot past the parts' two contribution slots
+            const auto g = ldp<kCoh>(terms + tr.y);
+            const int m = TO::m(g);
+            li = lds<kCoh>(V + TO::l(g)) * lds<kCoh>(inv_ptr(m));
+            u = lds<kCoh>(V + TO::u(g));
+            ym = lds<kCoh>(Y + m);
+        }
+    }
+    __device__ __forceinline__ static int sep_e(const uint2 w) { return (int)(w.y & 0x3FFFFFFFu); }
+    // separator task tl (local), one thread
+    __device__ __forceinline__ void sep_task_smem(int tl, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
                                                   const V4* SP, const LP* SC) const {
-        const TaskT tk = ldp<kCoh>(tasks + t);
-        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
-        const int tl = t - sep_t0, row = tk.row - sep_p0, col = tk.col - sep_p0;
-        const SepInfo si = ldp<kCoh>(sep_info + tl);
+        const uint2 w = STK[tl];
+        const int e1 = sep_e(STK[tl + 1]);
+        const int row = (int)(w.x & 0xFFFFu), col = (int)(w.x >> 16);
         const V4 rr = SRF[row], pp = SP[col];
         const LP a = SC[tl] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
         LP sacc = a + SV[tl], yv = LP(0);  // SV, SY hold minus the parts' contributions
-        for (int e = (int)si.b_start; e < e1; ++e) {
-            const auto tr = ldp<kCoh>(terms + e);
-            const int m = TO::m(tr);
+        for (int e = sep_e(w); e < e1; ++e) {
             LP li, u, ym;
-            if (m >= sep_p0) {
-                li = SV[TO::l(tr) - sep_t0] * reinterpret_cast<const LP*>(SRF + (m - sep_p0))[3];
-                u = SV[TO::u(tr) - sep_t0];
-                ym = SY[m - sep_p0];
-            } else {  // an interior pivot past the parts' two contribution slots
-                li = lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(inv_ptr(m));
-                u = lds<kCoh>(V + TO::u(tr));
-                ym = lds<kCoh>(Y + m);
-            }
+            sep_term(STM[e], SV, SRF, SY, li, u, ym);
             sacc -= li * u;
             if (diag) yv += li * ym;
         }
@@ -937,30 +959,17 @@ struct MolView {
             reinterpret_cast<LP*>(SRF + row)[3] = lp_rcp(sacc);
             SY[row] -= yv;
         }
-        (void)col;
     }
     // the same with one warp per task, its lanes splitting the terms (the narrow last
     //      levels, where few pivots carry many terms)
-    __device__ __forceinline__ void sep_task_smem_warp(int t, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
+    __device__ __forceinline__ void sep_task_smem_warp(int tl, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
                                                        const V4* SP, const LP* SC, int lane) const {
-        const TaskT tk = ldp<kCoh>(tasks + t);
-        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
-        const int tl = t - sep_t0, row = tk.row - sep_p0, col = tk.col - sep_p0;
-        const SepInfo si = ldp<kCoh>(sep_info + tl);
+        const uint2 w = STK[tl];
+        const int e1 = sep_e(STK[tl + 1]);
         LP ps = LP(0), py = LP(0);
-        for (int e = (int)si.b_start + lane; e < e1; e += 32) {
-            const auto tr = ldp<kCoh>(terms + e);
-            const int m = TO::m(tr);
+        for (int e = sep_e(w) + lane; e < e1; e += 32) {
             LP li, u, ym;
-            if (m >= sep_p0) {
-                li = SV[TO::l(tr) - sep_t0] * reinterpret_cast<const LP*>(SRF + (m - sep_p0))[3];
-                u = SV[TO::u(tr) - sep_t0];
-                ym = SY[m - sep_p0];
-            } else {
-                li = lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(inv_ptr(m));
-                u = lds<kCoh>(V + TO::u(tr));
-                ym = lds<kCoh>(Y + m);
-            }
+            sep_term(STM[e], SV, SRF, SY, li, u, ym);
             ps += li * u;
             if (diag) py += li * ym;
         }
@@ -970,6 +979,7 @@ struct MolView {
             py += __shfl_xor_sync(0xFFFFFFFFu, py, o);
         }
         if (lane == 0) {
+            const int row = (int)(w.x & 0xFFFFu), col = (int)(w.x >> 16);
             const V4 rr = SRF[row], pp = SP[col];
             const LP a = SC[tl] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
             const LP sacc = a + SV[tl] - ps;
@@ -981,46 +991,45 @@ struct MolView {
             }
         }
     }
-    __device__ __forceinline__ void sep_forward_smem(int t, int p, const LP* SV, const V4* SRF, LP* SY) const {
-        const int tl = t - sep_t0;
-        const SepInfo si = ldp<kCoh>(sep_info + tl);
+    // forward substitution alone for separator pivot pl (its DIAG task tl)
+    __device__ __forceinline__ void sep_forward_smem(int tl, int pl, const LP* SV, const V4* SRF, LP* SY) const {
         LP yv = LP(0);
-        const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
-        for (int e = (int)si.b_start; e < e1; ++e) {
-            const auto tr = ldp<kCoh>(terms + e);
-            const int m = TO::m(tr);
-            if (m >= sep_p0)
-                yv += SV[TO::l(tr) - sep_t0] * reinterpret_cast<const LP*>(SRF + (m - sep_p0))[3] * SY[m - sep_p0];
-            else
-                yv += lds<kCoh>(V + TO::l(tr)) * lds<kCoh>(inv_ptr(m)) * lds<kCoh>(Y + m);
+        const int e1 = sep_e(STK[tl + 1]);
+        for (int e = sep_e(STK[tl]); e < e1; ++e) {
+            LP li, u, ym;
+            sep_term(STM[e], SV, SRF, SY, li, u, ym);
+            yv += li * ym;
         }
-        SY[p - sep_p0] -= yv;
+        SY[pl] -= yv;
     }
-    // staging of separator task t: the parts' contributions, summed, go into SV[t] (as
-    //      its negative start value, factor iterations only) and, for a DIAG task, into
-    //      the right-hand side SY of its pivot
-    __device__ __forceinline__ void sep_stage_smem(int t, bool factor, bool first, LP* SV, LP* SY, LP* SC) const {
-        const int tl = t - sep_t0;
-        const SepInfo si = ldp<kCoh>(sep_info + tl);
-        const TaskT tk = ldp<kCoh>(tasks + t);
-        if (first) {  // 4 s s' w of the entry (w_i + w_j for a pivot)
-            const LP wv = tk.row == tk.col ? (RHOF + tk.row)->w : *(WL + (tk.atomsign >> 1));
-            SC[tl] = (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
-        }
-        const LP* ct = CT + 4 * tl;
+    // staging of separator task tl: the parts' contributions CS (4 per task: two partial
+    //      sums of L inv U, two of L inv y), summed, go into SV (as its negative start
+    //      value, factor iterations only) and, for a DIAG task, into the right-hand side
+    //      SY of its pivot
+    //      (CS in shared memory, or the global CT when cs_global)
+    __device__ __forceinline__ void sep_stage_smem(int tl, bool factor, const LP* CS, bool cs_global, LP* SV,
+                                                   LP* SY) const {
+        const uint2 w = STK[tl];
+        const uint32_t ng = w.y >> 30;
         LP cv = LP(0), cy = LP(0);
-        for (uint32_t g = 0; g < si.ngroups; ++g) {
-            cv += lds<kCoh>(ct + g);
-            cy += lds<kCoh>(ct + 2 + g);
+        for (uint32_t g = 0; g < ng; ++g) {
+            cv += cs_global ? lds<kCoh>(CS + 4 * tl + g) : CS[4 * tl + g];
+            cy += cs_global ? lds<kCoh>(CS + 4 * tl + 2 + g) : CS[4 * tl + 2 + g];
         }
         if (factor) SV[tl] = -cv;
-        if (tk.row == tk.col) SY[tk.row - sep_p0] -= cy;
+        if ((w.x & 0xFFFFu) == (w.x >> 16)) SY[w.x & 0xFFFFu] -= cy;
     }
-    __device__ __forceinline__ void sep_backward_smem(int p, const LP* SV, const V4* SRF, LP* SY) const {
-        const Piv<IdxT> pv = ldp<kCoh>(piv + p);
-        const int us = pv.diag, nu = pv.nup, pl = p - sep_p0;
+    // assembly coefficient 4 s s' w of separator task tl (w_i + w_j for a pivot)
+    __device__ __forceinline__ LP sep_coef(int tl) const {
+        const TaskT tk = ldp<kCoh>(tasks + sep_t0 + tl);
+        const LP wv = tk.row == tk.col ? lds<kCoh>(RHOF + tk.row).w : lds<kCoh>(WL + (tk.atomsign >> 1));
+        return (tk.atomsign & 1) ? LP(-4) * wv : LP(4) * wv;
+    }
+    __device__ __forceinline__ void sep_backward_smem(int pl, const LP* SV, const V4* SRF, LP* SY) const {
+        const uint32_t pv = SPV[pl];
+        const int us = (int)(pv & 0xFFFFu), nu = (int)(pv >> 16);
         LP dl = SY[pl];
-        for (int k = 0; k < nu; ++k) dl -= SV[us + k - sep_t0] * SY[task_col(us + k) - sep_p0];
+        for (int k = 0; k < nu; ++k) dl -= SV[us + k] * SY[STK[us + k].x >> 16];
         SY[pl] = dl * reinterpret_cast<const LP*>(SRF + pl)[3];
     }
 
@@ -1195,14 +1204,15 @@ __device__ __forceinline__ bool grid_sync(unsigned long long* ctr, unsigned n_bl
 
 // Shared memory of the separator phase: rows (V4) and right-hand sides of the
 // separators, values of the separator tasks; the separators' reference rows and the
-// tasks' assembly coefficients.  Used when it fits kSepSmemMax.
-constexpr uint32_t kSepSmemMax = 64 * 1024;
+// tasks' assembly coefficients; with stage_ct, a copy of the parts' contributions (4 per
+// task); the separator program.  Used when it fits kPartedSmemMax.
 template <class Mode>
-__host__ __device__ inline uint32_t sep_smem_bytes(int nsep, int n_sept) {
+__host__ __device__ inline uint32_t sep_smem_bytes(int nsep, int n_sept, int sprog_bytes, bool stage_ct) {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
     return 2 * align16((uint32_t)sizeof(V4) * nsep) + align16((uint32_t)sizeof(LP) * nsep) +
-           2 * align16((uint32_t)sizeof(LP) * n_sept);
+           2 * align16((uint32_t)sizeof(LP) * n_sept) + (stage_ct ? align16(4u * (uint32_t)sizeof(LP) * n_sept) : 0u) +
+           align16((uint32_t)sprog_bytes);
 }
 
 // Shared memory of a part's own copies (X, Y, RF, V) for the largest part.
@@ -1232,7 +1242,8 @@ constexpr uint32_t kPartedSmemMax = 72 * 1024;  // three CTAs per SM still fit
 struct PartedSmem {
     uint32_t sep_bytes, part_bytes;
     int32_t sep_cta;
-    uint32_t prog;  // nonzero: part programs staged too (part_bytes counts them)
+    uint32_t prog;    // nonzero: part programs staged too (part_bytes counts them)
+    uint32_t sep_ct;  // nonzero: the separator CTA stages the contributions (sep_bytes counts them)
 };
 
 struct PartSync {
@@ -1264,7 +1275,16 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                                    align16((uint32_t)sizeof(LP) * nsep));
     V4* SP = reinterpret_cast<V4*>(reinterpret_cast<uint8_t*>(SV) + align16((uint32_t)sizeof(LP) * D.n_sept));
     LP* SC = reinterpret_cast<LP*>(reinterpret_cast<uint8_t*>(SP) + align16((uint32_t)sizeof(V4) * nsep));
+    LP* CS = reinterpret_cast<LP*>(reinterpret_cast<uint8_t*>(SC) + align16((uint32_t)sizeof(LP) * D.n_sept));
+    uint8_t* SPROG =
+        reinterpret_cast<uint8_t*>(CS) + (cfg.sep_ct ? align16(4u * (uint32_t)sizeof(LP) * D.n_sept) : 0u);
     bool sep_fixed_staged = false;
+    // segment programs: part q's is [poff[q], poff[q + 1]) of the pprog section, the
+    // separator block's follows
+    const ProgLayout PL = prog_layout<uint32_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg, D.n_sept, D.n_cent,
+                                                D.pprog_bytes);
+    const uint8_t* gp = blob + D.blob_off;
+    const uint32_t* poff = reinterpret_cast<const uint32_t*>(gp + PL.pprog_off);
     if (cfg.part_bytes > 0 && (int)blockIdx.x < n_parts) {  // this CTA's part, copied in shared memory
         const int q = blockIdx.x;
         const SegRow s0 = seg[q], s1 = seg[q + 1];
@@ -1289,11 +1309,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             pb += align16((uint32_t)sizeof(V4) * pnp);
             M.WLS = reinterpret_cast<LP*>(pb);
             pb += align16((uint32_t)sizeof(LP) * pna);
-            const ProgLayout PL = prog_layout<uint32_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg, D.n_sept,
-                                                        D.n_cent, D.pprog_bytes);
-            const uint8_t* gp = blob + D.blob_off;
-            const uint32_t o0 = __ldg(reinterpret_cast<const uint32_t*>(gp + PL.pprog_off) + q);
-            const uint32_t o1 = __ldg(reinterpret_cast<const uint32_t*>(gp + PL.pprog_off) + q + 1);
+            const uint32_t o0 = __ldg(poff + q), o1 = __ldg(poff + q + 1);
             for (uint32_t o = 16u * threadIdx.x; o < o1 - o0; o += 16u * blockDim.x)
                 cp_async16(pb + o, gp + PL.pprog + o0 + o);
             cp_async_wait_all();
@@ -1329,9 +1345,11 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
     for_owned([&](int p) { M.s1_constraint(p, false); });
     for_my_atoms([&](int a) { M.s1_atom_unc(a); });
     bool alive = grid_sync(&sync->barrier, nb, budget);
-    if (M.PH) {  // the part's reference rows and weights (written by this CTA in S1)
+    if (M.PH) {  // the part's reference rows and weights (written by this CTA in S1), the
+                 // separators' reference rows (written by their owners)
         for (int k = r0; k < M.P1 - M.P0; k += ts) M.RHS[k] = *(M.RHOF + M.P0 + k);
         for (int a = r0; a < M.A1 - M.A0; a += ts) M.WLS[a] = *(M.WL + M.A0 + a);
+        for (int k = r0; k < (int)M.PH->nsep; k += ts) M.SEPREF[k] = lds<true>(M.RHOF + M.PST[k]);
         __syncthreads();
     }
     if (alive && A.lambda0) {
@@ -1378,6 +1396,10 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         bool singular = false;
         for (int q = b; q < n_parts; q += G) {
             if (M.PH) {  // the part program in shared memory (one part per CTA)
+                if (factor) {  // current rows of the separators the part's entries touch
+                    for (int k = r0; k < (int)M.PH->nsep; k += ts) M.SEPRF[k] = lds<true>(M.RF + M.PST[k]);
+                    __syncthreads();
+                }
                 const int nl = (int)M.PH->nlev;
                 int e = (int)M.PLANE[r0];
                 for (int l = 0; l < nl; ++l) {
@@ -1407,24 +1429,38 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         // ---- phase B: CTA 0 factorises the separator block (the Schur complement) and
         //      solves it forward and backward
         if (b == cfg.sep_cta && sep_in_smem) {
+            if (!sep_fixed_staged) {  // the separator program, reference rows, coefficients
+                const uint32_t o0 = __ldg(poff + n_parts), o1 = __ldg(poff + n_parts + 1);
+                for (uint32_t o = 16u * r0; o < o1 - o0; o += 16u * ts) cp_async16(SPROG + o, gp + PL.pprog + o0 + o);
+                for (int k = r0; k < nsep; k += ts) SP[k] = lds<true>(M.RHOF + sep0 + k);
+                for (int tl = r0; tl < D.n_sept; tl += ts) SC[tl] = M.sep_coef(tl);
+                cp_async_wait_all();
+                __syncthreads();
+                M.sep_prog_bind(SPROG);
+                sep_fixed_staged = true;
+            }
             // stage the separator rows (their factor's reciprocal pivots stay in SRF.w
-            // across ILVES-F iterations) and right-hand sides, solve in shared memory,
-            // publish the solution
+            // across ILVES-F iterations), right-hand sides and the parts' contributions,
+            // solve in shared memory, publish the solution
+            if (cfg.sep_ct) {
+                const int n16 = (int)(4u * (uint32_t)sizeof(LP) * D.n_sept / 16u);
+                for (int k = r0; k < n16; k += ts)
+                    cp_async16(reinterpret_cast<uint8_t*>(CS) + 16 * k, reinterpret_cast<const uint8_t*>(M.CT) + 16 * k);
+            }
             for (int k = r0; k < nsep; k += ts) {
                 if (factor) SRF[k] = lds<true>(M.RF + sep0 + k);
                 SY[k] = lds<true>(M.Y + sep0 + k);
-                if (!sep_fixed_staged) SP[k] = *(M.RHOF + sep0 + k);
             }
+            cp_async_wait_all();
             __syncthreads();
-            for (int t = M.sep_t0 + r0; t < D.ntask; t += ts)
-                M.sep_stage_smem(t, factor, !sep_fixed_staged, SV, SY, SC);
-            sep_fixed_staged = true;
+            for (int tl = r0; tl < D.n_sept; tl += ts)
+                M.sep_stage_smem(tl, factor, cfg.sep_ct ? CS : M.CT, !cfg.sep_ct, SV, SY);
             __syncthreads();
             bool sing = false;
-            const int l0 = __ldg(&seg[n_parts].lvl), l1 = __ldg(&seg[n_parts + 1].lvl) - 1;
-            for (int l = l0; l < l1; ++l) {
-                const int p0 = __ldg(M.lvl_piv + l), p1 = __ldg(M.lvl_piv + l + 1), np = p1 - p0;
-                const int t0 = __ldg(M.lvl_task + l), t1 = __ldg(M.lvl_task + l + 1);
+            const int nl = (int)reinterpret_cast<const SepProgHeader*>(SPROG)->nlev;
+            for (int l = 0; l < nl; ++l) {
+                const int p0 = M.SLP[l], p1 = M.SLP[l + 1], np = p1 - p0;
+                const int t0 = M.SLT[l], t1 = M.SLT[l + 1];
                 if (factor && t1 - t0 <= 8 * (ts >> 5)) {  // narrow level: a warp per task
                     for (int t = t0 + (r0 >> 5); t < t1; t += ts >> 5)
                         M.sep_task_smem_warp(t, t < t0 + np, sing, SV, SRF, SY, SP, SC, r0 & 31);
@@ -1435,9 +1471,9 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                 __syncthreads();
             }
             if (__syncthreads_or(sing) && r0 == 0) atomicOr(&sync->singular[slot], 1);
-            for (int l = l1 - 1; l >= l0; --l) {
-                const int p1 = __ldg(M.lvl_piv + l + 1);
-                for (int p = __ldg(M.lvl_piv + l) + r0; p < p1; p += ts) M.sep_backward_smem(p, SV, SRF, SY);
+            for (int l = nl - 1; l >= 0; --l) {
+                const int p1 = M.SLP[l + 1];
+                for (int p = M.SLP[l] + r0; p < p1; p += ts) M.sep_backward_smem(p, SV, SRF, SY);
                 __syncthreads();
             }
             for (int k = r0; k < nsep; k += ts) M.Y[sep0 + k] = SY[k];
@@ -1471,6 +1507,8 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         // ---- phase D: back substitution inside every part, multipliers, positions
         for (int q = b; q < n_parts; q += G) {
             if (M.PH) {
+                for (int k = r0; k < (int)M.PH->nsep; k += ts) M.SEPY[k] = lds<true>(M.Y + M.PST[k]);
+                __syncthreads();
                 for (int l = (int)M.PH->nlev - 1; l >= 0; --l) {
                     const int p1 = M.PLP[l + 1];
                     for (int p = M.PLP[l] + r0; p < p1; p += ts) M.part_backward(p);
@@ -1836,12 +1874,22 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 const int n_parts = MH.n_seg - 1;
                 // shared memory: the separator block if it fits, then the parts' copies if
                 // every part gets a CTA of its own at that size
-                const uint32_t need_sep = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept);
-                const uint32_t sep_b = need_sep <= kSepSmemMax ? need_sep : 0u;
+                // (with a staged copy of the contributions if that fits too)
+                uint32_t sep_b = 0, sep_ct = 0;
+                if (MH.sprog_bytes > 0) {
+                    const uint32_t with_ct = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept, MH.sprog_bytes, true);
+                    const uint32_t without = sep_smem_bytes<Mode>(MH.n_sep, MH.n_sept, MH.sprog_bytes, false);
+                    if (with_ct <= kPartedSmemMax) {
+                        sep_b = with_ct;
+                        sep_ct = 1;
+                    } else if (without <= kPartedSmemMax) {
+                        sep_b = without;
+                    }
+                }
                 const uint32_t need_part = part_smem_bytes<Mode>(MH.part_na, MH.part_np, MH.part_nt);
                 // part programs in shared memory: 256-thread CTAs (their terms are laid out
                 // thread by thread for kPartThreads threads)
-                const uint32_t pp = MH.pprog_bytes > 0 && T->parted_threads == kPartThreads ? 1u : 0u;
+                const uint32_t pp = MH.pprog_max > 0 && T->parted_threads == kPartThreads ? 1u : 0u;
                 const uint32_t need_pp =
                     pp ? part_prog_smem_bytes<Mode>(MH.part_na, MH.part_np, MH.part_nt, MH.pprog_max) : 0u;
                 if ((e = cudaFuncSetAttribute(k_solve_parted<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1851,11 +1899,11 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 // programs; the same without programs; CTA 0 with the separator block and the
                 // part copies (with, then without programs); CTA 0 with the separator block only
                 constexpr int kCands = 5;
-                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u},
-                                                  {sep_b, need_part, n_parts, 0u},
-                                                  {sep_b, need_pp, 0, 1u},
-                                                  {sep_b, need_part, 0, 0u},
-                                                  {sep_b, 0u, 0, 0u}};
+                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u, sep_ct},
+                                                  {sep_b, need_part, n_parts, 0u, sep_ct},
+                                                  {sep_b, need_pp, 0, 1u, sep_ct},
+                                                  {sep_b, need_part, 0, 0u, sep_ct},
+                                                  {sep_b, 0u, 0, 0u, sep_ct}};
                 PartedSmem cfg = cands[kCands - 1];
                 size_t dyn = sep_b;
                 int max_grid = 1;

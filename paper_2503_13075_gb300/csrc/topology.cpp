@@ -150,13 +150,14 @@ struct Program {
     std::vector<Contrib> cent;
     // partitioned: part programs (see PartProgHeader), empty if a part does not fit them
     std::vector<uint8_t> pprog;
-    std::vector<uint32_t> pprog_off;  // per part, then the total
+    std::vector<uint32_t> pprog_off;  // per part, the separator program, its end
     uint32_t pprog_max = 0;           // largest part program (bytes)
 };
 
 // Part programs of a partitioned molecule (16-bit part-local encoding of the part's
-// tasks, terms and pivots); false if some part exceeds the encoding's ranges.
-static bool build_part_programs(Program& P, int32_t nc, int32_t na_dummy) {
+// tasks, terms and pivots; see PartProgHeader); false if some part exceeds the
+// encoding's ranges.
+static bool build_part_programs(Program& P, int32_t na_dummy) {
     const int32_t n_parts = P.n_seg - 1;
     const int32_t sep_p0 = P.seg_piv[n_parts];
     P.pprog.clear();
@@ -204,7 +205,7 @@ static bool build_part_programs(Program& P, int32_t nc, int32_t na_dummy) {
         const PartProgLayout L = part_prog_layout(np, nt, nlev, (uint32_t)septab.size(), nterm);
         const size_t base = P.pprog.size();
         P.pprog_off[g] = (uint32_t)base;
-        P.pprog.resize(base + L.bytes, 0);
+        P.pprog.resize(base + L.scratch, 0);  // the scratch section exists in shared memory only
         uint8_t* d = P.pprog.data() + base;
         const PartProgHeader H{(uint32_t)np, (uint32_t)nt, (uint32_t)(A1 - A0), (uint32_t)nlev,
                                (uint32_t)septab.size(), nterm, 0u, 0u};
@@ -246,8 +247,57 @@ static bool build_part_programs(Program& P, int32_t nc, int32_t na_dummy) {
         P.pprog.resize((P.pprog.size() + 15) & ~size_t(15), 0);
     }
     P.pprog_off[n_parts] = (uint32_t)P.pprog.size();
-    (void)nc;
     return true;
+}
+
+// The separator block's program (see SepProgHeader), appended to the part programs;
+// pprog_off[n_parts] .. pprog_off[n_parts + 1] delimits it.
+static void build_sep_program(Program& P, int32_t nc) {
+    const int32_t n_parts = P.n_seg - 1;
+    const int32_t sep_p0 = P.seg_piv[n_parts], nsep = nc - sep_p0;
+    const int32_t lv0 = P.seg_lvl[n_parts], nlev = P.seg_lvl[n_parts + 1] - 1 - lv0;
+    const int32_t T0 = P.sep_t0, nt = (int32_t)P.tasks.size() - 1 - T0;
+    P.pprog_off.resize(n_parts + 2);
+    P.pprog_off[n_parts + 1] = P.pprog_off[n_parts] = (uint32_t)P.pprog.size();
+    if (nsep >= 65536 || nt >= 65536) return;  // no program: too large for shared memory anyway
+    std::vector<uint32_t> tw(2 * (nt + 1)), terms;
+    for (int32_t k = 0; k < nt; ++k) {
+        const int32_t t = T0 + k;
+        const SepInfo si = P.sep_info[k];
+        tw[2 * k] = (P.tasks[t].row - (uint32_t)sep_p0) | ((P.tasks[t].col - (uint32_t)sep_p0) << 16);
+        tw[2 * k + 1] = (uint32_t)(terms.size() / 2) | (si.ngroups << 30);
+        for (uint32_t e = si.b_start; e < P.tasks[t + 1].tstart; ++e) {
+            const TermW& tr = P.terms[e];
+            if ((int32_t)tr.m >= sep_p0) {
+                terms.push_back((tr.l - (uint32_t)T0) | ((tr.u - (uint32_t)T0) << 16));
+                terms.push_back(tr.m - (uint32_t)sep_p0);
+            } else {
+                terms.push_back(kSepInterior);
+                terms.push_back(e);
+            }
+        }
+    }
+    const uint32_t nterm = (uint32_t)(terms.size() / 2);
+    tw[2 * nt] = 0u;
+    tw[2 * nt + 1] = nterm;
+    const SepProgLayout L = sep_prog_layout((uint32_t)nsep, (uint32_t)nt, (uint32_t)nlev, nterm);
+    const size_t base = P.pprog.size();
+    P.pprog.resize(base + L.bytes, 0);
+    uint8_t* d = P.pprog.data() + base;
+    const SepProgHeader H{(uint32_t)nsep, (uint32_t)nt, (uint32_t)nlev, nterm};
+    std::memcpy(d, &H, sizeof(H));
+    auto* lp = reinterpret_cast<uint16_t*>(d + L.lvl_piv);
+    auto* lt = reinterpret_cast<uint16_t*>(d + L.lvl_task);
+    for (int32_t l = 0; l <= nlev; ++l) {
+        lp[l] = (uint16_t)(P.lvl_piv[lv0 + l] - sep_p0);
+        lt[l] = (uint16_t)(P.lvl_task[lv0 + l] - T0);
+    }
+    auto* pv = reinterpret_cast<uint32_t*>(d + L.piv);
+    for (int32_t p = sep_p0; p < nc; ++p)
+        pv[p - sep_p0] = (uint32_t)(P.ustart[p] - T0) | ((uint32_t)P.up[p].size() << 16);
+    std::memcpy(d + L.tasks, tw.data(), tw.size() * 4);
+    std::memcpy(d + L.terms, terms.data(), terms.size() * 4);
+    P.pprog_off[n_parts + 1] = (uint32_t)P.pprog.size();
 }
 
 // seg (optional): segment of every local constraint (a part, or n_seg - 1 for the
@@ -720,13 +770,16 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
                 M.part_nt = std::max(M.part_nt, P->lvl_task[P->seg_lvl[q + 1] - 1] - P->lvl_task[P->seg_lvl[q]]);
             }
             M.n_cent = (int32_t)P->cent.size();
-            if (build_part_programs(*P, nc, na)) {
-                M.pprog_bytes = (int32_t)P->pprog.size();
-                M.pprog_max = (int32_t)P->pprog_max;
-            } else {
+            // segment programs: the parts' (all or none), then the separator block's
+            if (!build_part_programs(*P, na)) {
                 P->pprog.clear();
-                P->pprog_off.clear();
+                P->pprog_off.assign(np + 1, 0u);
+                P->pprog_max = 0;
             }
+            build_sep_program(*P, nc);
+            M.pprog_bytes = (int32_t)P->pprog.size();
+            M.pprog_max = (int32_t)P->pprog_max;
+            M.sprog_bytes = (int32_t)(P->pprog_off[np + 1] - P->pprog_off[np]);
             M.nlevel = P->nlevel;
             M.ntask = (int32_t)P->tasks.size() - 1;
             M.nterm = (int32_t)P->terms.size();

@@ -23,8 +23,9 @@ struct MolHost {
     int32_t n_sept = 0, n_cent = 0;  // partitioned: separator tasks, Schur contribution entries
     int32_t n_sep = 0;               // partitioned: separator constraints
     int32_t part_na = 0, part_np = 0, part_nt = 0;  // partitioned: largest part (atoms, pivots, tasks)
-    int32_t pprog_bytes = 0;         // partitioned: bytes of the part programs (0 = none)
-    int32_t pprog_max = 0;           // partitioned: largest part program (bytes)
+    int32_t pprog_bytes = 0;         // partitioned: bytes of the segment programs
+    int32_t pprog_max = 0;           // partitioned: largest part program (bytes; 0 = none)
+    int32_t sprog_bytes = 0;         // partitioned: bytes of the separator program (0 = none)
     int64_t passes = 0;
 };
 
