@@ -1278,7 +1278,6 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
     LP* CS = reinterpret_cast<LP*>(reinterpret_cast<uint8_t*>(SC) + align16((uint32_t)sizeof(LP) * D.n_sept));
     uint8_t* SPROG =
         reinterpret_cast<uint8_t*>(CS) + (cfg.sep_ct ? align16(4u * (uint32_t)sizeof(LP) * D.n_sept) : 0u);
-    bool sep_fixed_staged = false;
     // segment programs: part q's is [poff[q], poff[q + 1]) of the pprog section, the
     // separator block's follows
     const ProgLayout PL = prog_layout<uint32_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg, D.n_sept, D.n_cent,
@@ -1352,6 +1351,15 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         for (int k = r0; k < (int)M.PH->nsep; k += ts) M.SEPREF[k] = lds<true>(M.RHOF + M.PST[k]);
         __syncthreads();
     }
+    if (b == cfg.sep_cta && sep_in_smem) {  // the separator program, reference rows, coefficients
+        const uint32_t o0 = __ldg(poff + n_parts), o1 = __ldg(poff + n_parts + 1);
+        for (uint32_t o = 16u * r0; o < o1 - o0; o += 16u * ts) cp_async16(SPROG + o, gp + PL.pprog + o0 + o);
+        for (int k = r0; k < nsep; k += ts) SP[k] = lds<true>(M.RHOF + sep0 + k);
+        for (int tl = r0; tl < D.n_sept; tl += ts) SC[tl] = M.sep_coef(tl);
+        cp_async_wait_all();
+        __syncthreads();
+        M.sep_prog_bind(SPROG);
+    }
     if (alive && A.lambda0) {
         for_my_atoms([&](int a) { M.update_atom(a); });
         alive = grid_sync(&sync->barrier, nb, budget);
@@ -1392,7 +1400,15 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
         }
         // ---- phase A: every part factorises its interior (and its rows/columns towards
-        //      the separators) level by level; ILVES-F iterations only substitute forward
+        //      the separators) level by level; ILVES-F iterations only substitute forward.
+        //      Meanwhile the separator CTA stages the separator rows (their factor's
+        //      reciprocal pivots stay in SRF.w across ILVES-F iterations) and right-hand
+        //      sides, which phase A does not change.
+        if (b == cfg.sep_cta && sep_in_smem)
+            for (int k = r0; k < nsep; k += ts) {
+                if (factor) SRF[k] = lds<true>(M.RF + sep0 + k);
+                SY[k] = lds<true>(M.Y + sep0 + k);
+            }
         bool singular = false;
         for (int q = b; q < n_parts; q += G) {
             if (M.PH) {  // the part program in shared memory (one part per CTA)
@@ -1429,27 +1445,12 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         // ---- phase B: CTA 0 factorises the separator block (the Schur complement) and
         //      solves it forward and backward
         if (b == cfg.sep_cta && sep_in_smem) {
-            if (!sep_fixed_staged) {  // the separator program, reference rows, coefficients
-                const uint32_t o0 = __ldg(poff + n_parts), o1 = __ldg(poff + n_parts + 1);
-                for (uint32_t o = 16u * r0; o < o1 - o0; o += 16u * ts) cp_async16(SPROG + o, gp + PL.pprog + o0 + o);
-                for (int k = r0; k < nsep; k += ts) SP[k] = lds<true>(M.RHOF + sep0 + k);
-                for (int tl = r0; tl < D.n_sept; tl += ts) SC[tl] = M.sep_coef(tl);
-                cp_async_wait_all();
-                __syncthreads();
-                M.sep_prog_bind(SPROG);
-                sep_fixed_staged = true;
-            }
-            // stage the separator rows (their factor's reciprocal pivots stay in SRF.w
-            // across ILVES-F iterations), right-hand sides and the parts' contributions,
-            // solve in shared memory, publish the solution
+            // the parts' contributions (the separator rows and right-hand sides were staged
+            // during phase A), then the solve in shared memory; publish the solution
             if (cfg.sep_ct) {
                 const int n16 = (int)(4u * (uint32_t)sizeof(LP) * D.n_sept / 16u);
                 for (int k = r0; k < n16; k += ts)
                     cp_async16(reinterpret_cast<uint8_t*>(CS) + 16 * k, reinterpret_cast<const uint8_t*>(M.CT) + 16 * k);
-            }
-            for (int k = r0; k < nsep; k += ts) {
-                if (factor) SRF[k] = lds<true>(M.RF + sep0 + k);
-                SY[k] = lds<true>(M.Y + sep0 + k);
             }
             cp_async_wait_all();
             __syncthreads();
