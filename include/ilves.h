@@ -96,6 +96,18 @@ typedef enum { ILVES_PREC_FP64 = 0, ILVES_PREC_MIXED = 1, ILVES_PREC_MIXED_DF = 
  *  iteration) to reach the same tolerance. */
 #define ILVES_CHORD 256
 
+/* Start flag, OR-ed into the precision argument of ilves_solve: the solve computes the
+ * diagonal (Jacobi) starting multipliers itself, in its set-up pass, instead of reading
+ * lambda0 (which must then be NULL):
+ *   lambda0_k = sigma_k(x_unc) / (4 (w_i + w_j) (s_k . r_k)),  s = x_unc,i - x_unc,j,
+ *   r = x_old,i - x_old,j,
+ * i.e. one Newton step (Sec. 2.3) on the diagonal of A(x_unc, x_old) alone, in float32
+ * arithmetic on coordinates rounded to float32; 0 where that quotient is not finite.  The
+ * values are the ones ilves_warm_start computes without a network, so the two routes
+ * give identical solves; the flag saves that separate pass over the inputs.  The paper
+ * starts from lambda0 = 0 (Sec. 2.3); the guess is this library's addition. */
+#define ILVES_START_DIAG 512
+
 typedef struct {
     int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;
                                 2 = rounds of independent low-degree pivots with `degree_slack` */
@@ -141,14 +153,16 @@ ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const 
  *  d         DEVICE float64 (n_constraints): target distances d_k > 0.
  *  tol       relative tolerance on |sigma_k| / d_k^2 (e.g. 1e-12).
  *  max_iter  maximum number of linear solves per molecule (>= 0).
- *  precision one of ilves_precision, optionally OR-ed with ILVES_CHORD.
- *  lambda0   DEVICE float32 (n_constraints) initial multipliers, or NULL for zero.
+ *  precision one of ilves_precision, optionally OR-ed with ILVES_CHORD and ILVES_START_DIAG.
+ *  lambda0   DEVICE float32 (n_constraints) initial multipliers, or NULL for zero (NULL
+ *            with ILVES_START_DIAG).
  *  x_out     DEVICE float64 (n_atoms, 3): constrained positions (may alias x_unc).
  *  lambda_out DEVICE float64 (n_constraints): multipliers, or NULL.
  *  iterations_out DEVICE int32 (n_molecules): linear solves per molecule, or NULL.
  *  mol_status_out DEVICE int32 (n_molecules): ilves_mol_status per molecule, or NULL.
  *  stream    cudaStream_t to enqueue on.
- * Errors: ILVES_ERR_INVALID_ARG (NULL required pointer, bad precision, max_iter < 0),
+ * Errors: ILVES_ERR_INVALID_ARG (NULL required pointer, bad precision, max_iter < 0,
+ *         lambda0 given with ILVES_START_DIAG),
  *         ILVES_ERR_CUDA (launch failure).  Allocates nothing.
  */
 ilves_status ilves_solve(ilves_topology* topo, const double* x_old, const double* x_unc,

@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ilves.h")
 
 FP64, MIXED, MIXED_DF = 0, 1, 2
 CHORD = 256  # ILVES-F flag
+START_DIAG = 512  # diagonal starting multipliers computed inside the solve
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_df": MIXED_DF}
 CONVERGED, MAX_ITER, SINGULAR_PIVOT, NONFINITE, WAIT_TIMEOUT = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "invalid topology", 3: "CUDA error", 4: "out of device memory",
@@ -228,8 +229,10 @@ class Topology:
 
     def solve(self, x_old, x_unc, inv_mass, d, tol=1e-12, max_iter=25, precision="mixed", lambda0=None,
               x_out=None, lambda_out=None, iterations_out=None, status_out=None, stream=None,
-              method="newton", _entry="ilves_solve"):
-        """One ``ilves_solve`` on device tensors; returns (x, lambda, iterations, status)."""
+              method="newton", start=None, _entry="ilves_solve"):
+        """One ``ilves_solve`` on device tensors; returns (x, lambda, iterations, status).
+        ``start="diag"`` computes the diagonal starting multipliers inside the solve
+        (``ILVES_START_DIAG``; lambda0 must then be None)."""
         import torch
 
         if self.plan_only:
@@ -255,6 +258,12 @@ class Topology:
             prec |= CHORD
         elif method != "newton":
             raise ValueError("method must be 'newton' (ILVES-M) or 'chord' (ILVES-F)")
+        if start == "diag":
+            if lambda0 is not None:
+                raise ValueError("start='diag' computes lambda0 itself; pass lambda0=None")
+            prec |= START_DIAG
+        elif start is not None:
+            raise ValueError("start must be None or 'diag'")
         fn = getattr(lib(), _entry)
         _check(fn(self._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), float(tol), int(max_iter),
                   prec, None if lambda0 is None else _ptr(lambda0), _ptr(x_out), _ptr(lambda_out),

@@ -221,8 +221,25 @@ struct SolveArgs {
     const int32_t* atom_gid;
     double tol;
     int32_t max_iter;
-    int32_t chord;  // ILVES-F: factorise A(x_old, x_old) once, reuse it every iteration
+    int32_t chord;       // ILVES-F: factorise A(x_old, x_old) once, reuse it every iteration
+    int32_t start_diag;  // lambda0 = the diagonal guess, computed in S1 (lambda0 is NULL)
+    __host__ __device__ bool has_start() const { return lambda0 != nullptr || start_diag != 0; }
 };
+
+// The diagonal (Jacobi) start of constraint k: lambda0_k = sigma_k(x_unc) / A_kk with
+// A_kk = 4 (w_i + w_j) (s_k . r_k), s = x_unc,i - x_unc,j, r = x_old,i - x_old,j (one
+// Newton step on the diagonal of A(x_unc, x_old)); float32 arithmetic on coordinates
+// rounded to float32, as the stand-alone warm start (ilves_warm_start without a network)
+// computes it, so both routes give the same lambda0.
+__device__ __forceinline__ float f32_of(float v) { return v; }
+__device__ __forceinline__ float f32_of(double v) { return narrow(v); }
+__device__ __forceinline__ float diag_start(float sx, float sy, float sz, float rx, float ry, float rz, float d,
+                                           float w_ij) {
+    const float d2 = d * d;
+    const float a = 4.0f * w_ij * (sx * rx + sy * ry + sz * rz);
+    const float l0 = ((sx * sx + sy * sy + sz * sz) - d2) / a;
+    return (a != 0.f && isfinite(l0)) ? l0 : 0.f;
+}
 
 // ------------------------------------------------------------------------------------
 // per-item operations on one molecule's program and state
@@ -575,7 +592,17 @@ struct MolView {
             RHO[2 * nc + p] = rz;
             D2[p] = dd * dd;
         }
-        const float l0 = A->lambda0 ? A->lambda0[g] : 0.0f;
+        float l0 = A->lambda0 ? A->lambda0[g] : 0.0f;
+        if (A->start_diag) {
+            float o[6];  // x_old,i - x_old,j and x_unc,i - x_unc,j, per coordinate rounded first
+            for (int c = 0; c < 3; ++c) {
+                o[c] = ref_staged ? narrow(X[c * na + i]) - narrow(X[c * na + j])
+                                  : narrow(A->x_old[3 * gi + c]) - narrow(A->x_old[3 * gj + c]);
+                o[3 + c] = narrow(A->x_unc[3 * gi + c]) - narrow(A->x_unc[3 * gj + c]);
+            }
+            l0 = diag_start(o[3], o[4], o[5], o[0], o[1], o[2], narrow(dd),
+                            narrow(A->inv_mass[gi]) + narrow(A->inv_mass[gj]));
+        }
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         y_st(p, (LP)l0);
     }
@@ -606,7 +633,7 @@ struct MolView {
         for (int p = r0; p < nc; p += ts) {
             const int32_t g = gid_of_con(p);
             cp_async8(D2 + p, A->d + g);
-            if (A->lambda0) cp_async4(reinterpret_cast<float*>(Y + p), A->lambda0 + g);
+            if (A->lambda0 && !A->start_diag) cp_async4(reinterpret_cast<float*>(Y + p), A->lambda0 + g);
         }
         cp_async_wait_all();
     }
@@ -642,7 +669,17 @@ struct MolView {
             RHO[2 * nc + p] = rz;
             D2[p] = dd * dd;
         }
-        const float l0 = A->lambda0 ? *(reinterpret_cast<const float*>(Y + p)) : 0.0f;
+        float l0 = A->lambda0 ? *(reinterpret_cast<const float*>(Y + p)) : 0.0f;
+        if (A->start_diag) {  // x_unc is in X (AoS in the float-float mode, else SoA)
+            float u[3];
+            for (int c = 0; c < 3; ++c)
+                u[c] = DF ? narrow(*(X + 3 * i + c)) - narrow(*(X + 3 * j + c))
+                          : narrow(*(X + c * na + i)) - narrow(*(X + c * na + j));
+            l0 = diag_start(u[0], u[1], u[2], narrow(*(STG + 3 * i)) - narrow(*(STG + 3 * j)),
+                            narrow(*(STG + 3 * i + 1)) - narrow(*(STG + 3 * j + 1)),
+                            narrow(*(STG + 3 * i + 2)) - narrow(*(STG + 3 * j + 2)), narrow(dd),
+                            f32_of(*(WL + i)) + f32_of(*(WL + j)));
+        }
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         Y[p] = (LP)l0;
     }
@@ -1092,7 +1129,7 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
         for (int a = r0; a < na; a += ts) M.s1_atom_unc(a);
         tm.sync();
     }
-    if (A.lambda0) {  // x = x_unc - M^-1 G(x_old)^T lambda0
+    if (A.has_start()) {  // x = x_unc - M^-1 G(x_old)^T lambda0
         for (int a = r0; a < na; a += ts) M.update_atom(a);
         tm.sync();
     }
@@ -1360,7 +1397,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         __syncthreads();
         M.sep_prog_bind(SPROG);
     }
-    if (alive && A.lambda0) {
+    if (alive && A.has_start()) {
         for_my_atoms([&](int a) { M.update_atom(a); });
         alive = grid_sync(&sync->barrier, nb, budget);
     }
@@ -2058,9 +2095,11 @@ extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, cons
     A.tol = tol;
     A.max_iter = max_iter;
     A.chord = (precision & ILVES_CHORD) ? 1 : 0;
+    A.start_diag = (precision & ILVES_START_DIAG) ? 1 : 0;
+    if (A.start_diag && lambda0) return ILVES_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
-    switch (precision & ~ILVES_CHORD) {
+    switch (precision & ~(ILVES_CHORD | ILVES_START_DIAG)) {
         case ILVES_PREC_FP64: return launch_mode<ModeFP64>(T, A, s);
         case ILVES_PREC_MIXED: return launch_mode<ModeMixed>(T, A, s);
         case ILVES_PREC_MIXED_DF: return launch_mode<ModeMixedDF>(T, A, s);
@@ -2077,7 +2116,8 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     if (max_iter < 0 || !(tol >= 0.0)) return ILVES_ERR_INVALID_ARG;
     if (T->n_atoms > 0 && (!x_old || !x_unc || !inv_mass || !x_out)) return ILVES_ERR_INVALID_ARG;
     if (T->n_c > 0 && !d) return ILVES_ERR_INVALID_ARG;
-    const int32_t prec_mode = precision & ~ILVES_CHORD;
+    const int32_t prec_mode = precision & ~(ILVES_CHORD | ILVES_START_DIAG);
+    if ((precision & ILVES_START_DIAG) && lambda0) return ILVES_ERR_INVALID_ARG;
     if (prec_mode < ILVES_PREC_FP64 || prec_mode > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
     const uint64_t work_aligned = ((uint64_t)T->work_bytes + 255) & ~uint64_t(255);
     if (work_aligned + (uint64_t)T->sync_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
@@ -2101,6 +2141,7 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     A.tol = tol;
     A.max_iter = max_iter;
     A.chord = (precision & ILVES_CHORD) ? 1 : 0;
+    A.start_diag = (precision & ILVES_START_DIAG) ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
     uint8_t* sync = scratch + work_aligned;

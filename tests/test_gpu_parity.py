@@ -235,3 +235,41 @@ def test_partitioned_small_parts(prec, part):
     assert t.n_large == 1
     _, x, lam, it, st = run(s, prec, topo=t)
     compare(s, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["trees", "cta_path", "protein_parted"])
+def test_diag_start_inside_the_solve(prec, case):
+    """ILVES_START_DIAG: the set-up pass computes the diagonal starting multipliers itself.
+    With max_iter = 0 the solve returns them unchanged (lambda_out) with the positions
+    they give, which must equal, bit for bit, a solve started from ilves_warm_start's
+    diagonal guess; the converged solve meets the oracle bounds."""
+    if case == "trees":
+        s = wl.tree_batch(n_mol=128, seed=1003)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    elif case == "cta_path":
+        s = wl.tree_batch(n_mol=20, seed=78)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, max_warp_constraints=10)
+        assert t.n_large > 0
+    else:
+        s = wl.protein_like(n_atoms=12000, seed=1002)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000)
+        assert t.n_large == 1
+    xo, xu, w, d = to_dev(s)
+    lam0 = B.warm_start(None, t, xo, xu, w, d)
+    a = [v.cpu().numpy() for v in t.solve(xo, xu, w, d, precision=prec, lambda0=lam0, max_iter=0)]
+    b = [v.cpu().numpy() for v in t.solve(xo, xu, w, d, precision=prec, start="diag", max_iter=0)]
+    assert np.array_equal(b[1], lam0.cpu().numpy().astype(np.float64))
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    ref = orc.solve_system(s, tol=TOL)
+    x, lam, it, st = [v.cpu().numpy() for v in t.solve(xo, xu, w, d, precision=prec, start="diag")]
+    compare(s, ref, x, lam, it, st, it_slack=2)
+    with pytest.raises(ValueError):
+        t.solve(xo, xu, w, d, precision=prec, lambda0=lam0, start="diag")
+    # the C ABI refuses a lambda0 together with the flag
+    P = lambda v: v.data_ptr()
+    xs = torch.empty_like(xu)
+    code = B.lib().ilves_solve(t._h, P(xo), P(xu), P(w), P(d), 1e-12, 25, B.PRECISIONS[prec] | B.START_DIAG,
+                               P(lam0), P(xs), None, None, None, None)
+    assert code == 1  # ILVES_ERR_INVALID_ARG
