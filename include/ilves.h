@@ -161,6 +161,12 @@ ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const 
  *  iterations_out DEVICE int32 (n_molecules): linear solves per molecule, or NULL.
  *  mol_status_out DEVICE int32 (n_molecules): ilves_mol_status per molecule, or NULL.
  *  stream    cudaStream_t to enqueue on.
+ * Every array argument may instead be page-locked HOST memory allocated or registered
+ * through CUDA (cudaHostAlloc, cudaMallocHost, cudaHostRegister), whose host address is
+ * also its device address: the kernels then read the inputs and write the outputs in
+ * place over the host link, overlapped with the solve, with no staging copies (the
+ * caller synchronises the stream before reading the outputs).  Pageable host memory is
+ * not supported.  The caller owns every buffer; none is retained after the call.
  * Errors: ILVES_ERR_INVALID_ARG (NULL required pointer, bad precision, max_iter < 0,
  *         lambda0 given with ILVES_START_DIAG),
  *         ILVES_ERR_CUDA (launch failure).  Allocates nothing.

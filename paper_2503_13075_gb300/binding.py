@@ -152,6 +152,7 @@ class Topology:
         self.n_atoms = int(n_atoms)
         self.n_constraints = int(ai.size)
         self.plan_only = plan_only
+        self._device_index = None if device is None else int(device)
         n = ctypes.c_int32()
         nnz = ctypes.c_int64()
         ml = ctypes.c_int32()
@@ -230,28 +231,49 @@ class Topology:
     def solve(self, x_old, x_unc, inv_mass, d, tol=1e-12, max_iter=25, precision="mixed", lambda0=None,
               x_out=None, lambda_out=None, iterations_out=None, status_out=None, stream=None,
               method="newton", start=None, _entry="ilves_solve"):
-        """One ``ilves_solve`` on device tensors; returns (x, lambda, iterations, status).
+        """One ``ilves_solve``; returns (x, lambda, iterations, status).  Every tensor is a
+        CUDA tensor on the topology's device or a page-locked (pinned) host tensor, which the
+        kernels read or write in place; outputs not given are allocated like ``x_unc``.
         ``start="diag"`` computes the diagonal starting multipliers inside the solve
         (``ILVES_START_DIAG``; lambda0 must then be None)."""
         import torch
 
         if self.plan_only:
             raise RuntimeError("topology was planned on the host only")
-        dev = x_unc.device
-        if dev.type != "cuda":
-            raise ValueError("ilves_solve takes CUDA tensors")
+        given = [t for t in (x_old, x_unc, inv_mass, d, lambda0, x_out, lambda_out, iterations_out, status_out)
+                 if t is not None]
+        dev = next((t.device for t in given if t.is_cuda), None)
+        if dev is None:
+            dev = torch.device("cuda", self._device_index if self._device_index is not None
+                               else torch.cuda.current_device())
+
+        def placed(t):  # on the solve's device, or page-locked host memory
+            return t.device == dev or (t.device.type == "cpu" and t.is_pinned())
+
         for name, t, shape in (("x_old", x_old, (self.n_atoms, 3)), ("x_unc", x_unc, (self.n_atoms, 3)),
                                ("inv_mass", inv_mass, (self.n_atoms,)), ("d", d, (self.n_constraints,))):
-            if t.dtype != torch.float64 or tuple(t.shape) != shape or not t.is_contiguous() or t.device != dev:
-                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape {shape}")
+            if t.dtype != torch.float64 or tuple(t.shape) != shape or not t.is_contiguous() or not placed(t):
+                raise ValueError(f"{name} must be a contiguous float64 tensor of shape {shape}, "
+                                 "on the CUDA device or in pinned host memory")
         if lambda0 is not None and (lambda0.dtype != torch.float32 or lambda0.numel() != self.n_constraints
-                                    or not lambda0.is_contiguous()):
+                                    or not lambda0.is_contiguous() or not placed(lambda0)):
             raise ValueError("lambda0 must be a contiguous float32 tensor of n_constraints entries")
-        x_out = torch.empty_like(x_unc) if x_out is None else x_out
-        lambda_out = torch.empty(self.n_constraints, dtype=torch.float64, device=dev) if lambda_out is None else lambda_out
-        iterations_out = (torch.empty(self.n_molecules, dtype=torch.int32, device=dev)
-                          if iterations_out is None else iterations_out)
-        status_out = torch.empty(self.n_molecules, dtype=torch.int32, device=dev) if status_out is None else status_out
+        host = x_unc.device.type == "cpu"
+
+        def alloc(n, dtype):
+            return torch.empty(n, dtype=dtype, pin_memory=True) if host else torch.empty(n, dtype=dtype, device=dev)
+
+        x_out = alloc((self.n_atoms, 3), torch.float64) if x_out is None else x_out
+        lambda_out = alloc(self.n_constraints, torch.float64) if lambda_out is None else lambda_out
+        iterations_out = alloc(self.n_molecules, torch.int32) if iterations_out is None else iterations_out
+        status_out = alloc(self.n_molecules, torch.int32) if status_out is None else status_out
+        for name, t, dtype, n in (("x_out", x_out, torch.float64, 3 * self.n_atoms),
+                                  ("lambda_out", lambda_out, torch.float64, self.n_constraints),
+                                  ("iterations_out", iterations_out, torch.int32, self.n_molecules),
+                                  ("status_out", status_out, torch.int32, self.n_molecules)):
+            if t.dtype != dtype or t.numel() != n or not t.is_contiguous() or not placed(t):
+                raise ValueError(f"{name} must be a contiguous {dtype} tensor of {n} entries, "
+                                 "on the CUDA device or in pinned host memory")
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream.cuda_stream
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         if method == "chord":

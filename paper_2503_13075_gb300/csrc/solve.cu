@@ -555,11 +555,17 @@ struct MolView {
         W[na] = 0.0;
         WL[na] = LP(0);
     }
-    // rho, assembly data, lambda0 of constraint p; ref_staged: x_old staged in X (else global)
-    __device__ __forceinline__ void s1_constraint(int p, bool ref_staged) {
+    // rho, assembly data, lambda0 of constraint p; ref_staged: x_old staged in X (else
+    // global); part_staged (partitioned, both atoms in the CTA's part): x_old in X, x_unc
+    // in the part copy XS, weights in WL, so the inputs are read once per atom, in order
+    __device__ __forceinline__ void s1_constraint(int p, bool ref_staged, bool part_staged = false) {
         const ConA<IdxT> c = cons(p);
         const int i = c.i, j = c.j;
         const int64_t gi = gid(i), gj = gid(j);
+        ref_staged = ref_staged || part_staged;
+        auto unc = [&](int cc, int a, int64_t ga) {
+            return part_staged ? XS[cc * (A1 - A0) + (a - A0)] : A->x_unc[3 * ga + cc];
+        };
         double rx, ry, rz;
         if (ref_staged) {
             rx = X[i] - X[j];
@@ -574,7 +580,7 @@ struct MolView {
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
         v.z = to_lp<LP>(rz);
-        v.w = to_lp<LP>(A->inv_mass[gi]) + to_lp<LP>(A->inv_mass[gj]);
+        v.w = part_staged ? *(WL + i) + *(WL + j) : to_lp<LP>(A->inv_mass[gi]) + to_lp<LP>(A->inv_mass[gj]);
         RHOF[p] = v;
         const int32_t g = gid_of_con(p);
         const double dd = A->d[g];
@@ -583,9 +589,9 @@ struct MolView {
             RHOL[nc + p] = df_split(ry).lo;
             RHOL[2 * nc + p] = df_split(rz).lo;
             D2[p] = as_bits(df_split(dd * dd));
-            SK[p] = as_bits(df_split(A->x_unc[3 * gi] - A->x_unc[3 * gj]));
-            SK[nc + p] = as_bits(df_split(A->x_unc[3 * gi + 1] - A->x_unc[3 * gj + 1]));
-            SK[2 * nc + p] = as_bits(df_split(A->x_unc[3 * gi + 2] - A->x_unc[3 * gj + 2]));
+            SK[p] = as_bits(df_split(unc(0, i, gi) - unc(0, j, gj)));
+            SK[nc + p] = as_bits(df_split(unc(1, i, gi) - unc(1, j, gj)));
+            SK[2 * nc + p] = as_bits(df_split(unc(2, i, gi) - unc(2, j, gj)));
         } else {
             RHO[p] = rx;
             RHO[nc + p] = ry;
@@ -598,13 +604,23 @@ struct MolView {
             for (int c = 0; c < 3; ++c) {
                 o[c] = ref_staged ? narrow(X[c * na + i]) - narrow(X[c * na + j])
                                   : narrow(A->x_old[3 * gi + c]) - narrow(A->x_old[3 * gj + c]);
-                o[3 + c] = narrow(A->x_unc[3 * gi + c]) - narrow(A->x_unc[3 * gj + c]);
+                o[3 + c] = narrow(unc(c, i, gi)) - narrow(unc(c, j, gj));
             }
             l0 = diag_start(o[3], o[4], o[5], o[0], o[1], o[2], narrow(dd),
-                            narrow(A->inv_mass[gi]) + narrow(A->inv_mass[gj]));
+                            part_staged ? f32_of(*(WL + i)) + f32_of(*(WL + j))
+                                        : narrow(A->inv_mass[gi]) + narrow(A->inv_mass[gj]));
         }
         LAM[p] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         y_st(p, (LP)l0);
+    }
+    // partitioned S1 with part copies: x_unc of atom a into the part copy XS only (raw
+    // values, every mode), then, after the constraints, into X (s1_atom_unc_staged)
+    __device__ __forceinline__ void s1_stage_unc(int a) {
+        const int64_t g = gid(a);
+        for (int c = 0; c < 3; ++c) XS[c * (A1 - A0) + (a - A0)] = A->x_unc[3 * g + c];
+    }
+    __device__ __forceinline__ void s1_atom_unc_staged(int a) {
+        for (int c = 0; c < 3; ++c) x_st(c, a, DF ? 0.0 : XS[c * (A1 - A0) + (a - A0)]);
     }
     __device__ __forceinline__ void s1_atom_unc(int a) {
         if constexpr (DF) {  // displacements start at zero
@@ -1375,11 +1391,25 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             for (int a = a0 + r0; a < a1; a += ts) f(a);
         }
     };
-    // ---- S1 (reference geometry straight from global x_old: separators span parts)
-    for_my_atoms([&](int a) { M.s1_atom(a, false); });
-    if (b == 0 && r0 == 0) M.s1_dummy();
-    for_owned([&](int p) { M.s1_constraint(p, false); });
-    for_my_atoms([&](int a) { M.s1_atom_unc(a); });
+    // ---- S1.  With part copies the inputs of the part's atoms are read once each, in
+    //      order (x_old into X, x_unc into XS), and the part's constraints built from
+    //      them; separators (atoms of two parts) read the inputs directly.
+    if (M.XS) {
+        for_my_atoms([&](int a) {
+            M.s1_atom(a, true);
+            M.s1_stage_unc(a);
+        });
+        if (b == 0 && r0 == 0) M.s1_dummy();
+        __syncthreads();
+        for_owned([&](int p) { M.s1_constraint(p, false, p < sep0); });
+        __syncthreads();
+        for_my_atoms([&](int a) { M.s1_atom_unc_staged(a); });
+    } else {
+        for_my_atoms([&](int a) { M.s1_atom(a, false); });
+        if (b == 0 && r0 == 0) M.s1_dummy();
+        for_owned([&](int p) { M.s1_constraint(p, false); });
+        for_my_atoms([&](int a) { M.s1_atom_unc(a); });
+    }
     bool alive = grid_sync(&sync->barrier, nb, budget);
     if (M.PH) {  // the part's reference rows and weights (written by this CTA in S1), the
                  // separators' reference rows (written by their owners)

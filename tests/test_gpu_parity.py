@@ -273,3 +273,31 @@ def test_diag_start_inside_the_solve(prec, case):
     code = B.lib().ilves_solve(t._h, P(xo), P(xu), P(w), P(d), 1e-12, 25, B.PRECISIONS[prec] | B.START_DIAG,
                                P(lam0), P(xs), None, None, None, None)
     assert code == 1  # ILVES_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["trees", "cta_path", "protein_parted"])
+def test_pinned_host_buffers(prec, case):
+    """ilves_solve on page-locked host buffers (read and written in place by the kernels)
+    gives bit for bit the results of the same solve on device buffers."""
+    if case == "trees":
+        s = wl.tree_batch(n_mol=128, seed=1004)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    elif case == "cta_path":
+        s = wl.tree_batch(n_mol=20, seed=79)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, max_warp_constraints=10)
+        assert t.n_large > 0
+    else:
+        s = wl.protein_like(n_atoms=12000, seed=1005)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000)
+        assert t.n_large == 1
+    dev_out = [v.cpu().numpy() for v in t.solve(*to_dev(s), precision=prec, start="diag")]
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (s.x_old, s.x_unc, s.inv_mass, s.d)]
+    outs = t.solve(*host, precision=prec, start="diag")
+    torch.cuda.synchronize()
+    assert all(o.device.type == "cpu" and o.is_pinned() for o in outs)
+    for u, v in zip(dev_out, outs):
+        assert np.array_equal(u, v.numpy())
+    assert np.all(dev_out[3] == B.CONVERGED)
+    with pytest.raises(ValueError):  # pageable host memory is refused
+        t.solve(*[torch.from_numpy(np.ascontiguousarray(a)) for a in (s.x_old, s.x_unc, s.inv_mass, s.d)])
