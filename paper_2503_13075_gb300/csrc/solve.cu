@@ -406,27 +406,46 @@ struct MolView {
         else return false;
     }
     __device__ __forceinline__ LP y_ld(int p) const { return in_p(p) ? YS[p - P0] : ldf<kCoh>(Y + p, foreign(p)); }
+    // wt: the part's values must also reach global memory (another CTA reads them: the
+    //     separator phase's terms of interior pivots beyond the contribution slots)
+    bool wt = true;
     __device__ __forceinline__ void y_st(int p, LP v) {
-        Y[p] = v;
-        if (in_p(p)) YS[p - P0] = v;
+        if (!in_p(p)) {
+            Y[p] = v;
+            return;
+        }
+        if (wt) Y[p] = v;
+        YS[p - P0] = v;
     }
     __device__ __forceinline__ V4 rf_ld(int p) const { return in_p(p) ? RFS[p - P0] : ldf<kCoh>(RF + p, foreign(p)); }
     __device__ __forceinline__ void rf_st(int p, const V4& v) {
-        RF[p] = v;
-        if (in_p(p)) RFS[p - P0] = v;
+        if (!in_p(p)) {
+            RF[p] = v;
+            return;
+        }
+        if (wt) RF[p] = v;
+        RFS[p - P0] = v;
     }
     __device__ __forceinline__ LP inv(int p) const {
         return in_p(p) ? reinterpret_cast<const LP*>(RFS + (p - P0))[3] : ldf<kCoh>(inv_ptr(p), foreign(p));
     }
     __device__ __forceinline__ void inv_st(int p, LP v) {
-        *inv_ptr(p) = v;
-        if (in_p(p)) reinterpret_cast<LP*>(RFS + (p - P0))[3] = v;
+        if (!in_p(p)) {
+            *inv_ptr(p) = v;
+            return;
+        }
+        if (wt) *inv_ptr(p) = v;
+        reinterpret_cast<LP*>(RFS + (p - P0))[3] = v;
     }
     // task values: slots of tasks of pivot m are foreign when m is
     __device__ __forceinline__ LP v_ld(int t, bool fgn) const { return in_t(t) ? VS[t - T0] : ldf<kCoh>(V + t, fgn); }
     __device__ __forceinline__ void v_st(int t, LP v) {
-        V[t] = v;
-        if (in_t(t)) VS[t - T0] = v;
+        if (!in_t(t)) {
+            V[t] = v;
+            return;
+        }
+        if (wt) V[t] = v;
+        VS[t - T0] = v;
     }
     // coordinate c of atom a (float64 class)
     __device__ __forceinline__ double x_ld(int c, int a, bool fgn) const {
@@ -492,15 +511,17 @@ struct MolView {
             }
             e += n;
             VS[t] = sacc;
-            V[T0 + t] = sacc;
+            if (wt) V[T0 + t] = sacc;
             if (diag) {  // rc is a part position
                 singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
                 const LP ri = lp_rcp(sacc);
                 reinterpret_cast<LP*>(RFS + rc)[3] = ri;
-                *inv_ptr(P0 + (int)rc) = ri;
                 const LP ny = YS[rc] - yv;
                 YS[rc] = ny;
-                Y[P0 + (int)rc] = ny;
+                if (wt) {
+                    *inv_ptr(P0 + (int)rc) = ri;
+                    Y[P0 + (int)rc] = ny;
+                }
             }
         }
     }
@@ -518,7 +539,7 @@ struct MolView {
                 }
                 const LP ny = YS[pl] - yv;
                 YS[pl] = ny;
-                Y[P0 + pl] = ny;
+                if (wt) Y[P0 + pl] = ny;
             }
             e += n;
         }
@@ -535,7 +556,7 @@ struct MolView {
         }
         const LP r = dl * reinterpret_cast<const LP*>(RFS + pl)[3];
         YS[pl] = r;
-        Y[P0 + pl] = r;
+        if (wt) Y[P0 + pl] = r;
     }
 
     // ---- S1
@@ -1297,6 +1318,8 @@ struct PartedSmem {
     int32_t sep_cta;
     uint32_t prog;    // nonzero: part programs staged too (part_bytes counts them)
     uint32_t sep_ct;  // nonzero: the separator CTA stages the contributions (sep_bytes counts them)
+    uint32_t wt;      // nonzero: parts write their factor values, reciprocal pivots, rows and
+                      // solve vector through to global memory (the separator phase reads some)
 };
 
 struct PartSync {
@@ -1355,6 +1378,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         M.RFS = reinterpret_cast<V4*>(pb);
         pb += align16((uint32_t)sizeof(V4) * pnp);
         M.VS = reinterpret_cast<LP*>(pb);
+        M.wt = cfg.wt != 0;
         if (cfg.prog) {
             pb += align16((uint32_t)sizeof(LP) * (M.T1 - M.T0));
             M.RHS = reinterpret_cast<V4*>(pb);
@@ -1967,11 +1991,14 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 // programs; the same without programs; CTA 0 with the separator block and the
                 // part copies (with, then without programs); CTA 0 with the separator block only
                 constexpr int kCands = 5;
-                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u, sep_ct},
-                                                  {sep_b, need_part, n_parts, 0u, sep_ct},
-                                                  {sep_b, need_pp, 0, 1u, sep_ct},
-                                                  {sep_b, need_part, 0, 0u, sep_ct},
-                                                  {sep_b, 0u, 0, 0u, sep_ct}};
+                // the parts' values go through to global memory only if the separator phase
+                // reads interior pivots' values (terms beyond the two contribution slots)
+                const uint32_t wt = MH.sprog_bytes == 0 || MH.sep_interior > 0 ? 1u : 0u;
+                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u, sep_ct, wt},
+                                                  {sep_b, need_part, n_parts, 0u, sep_ct, wt},
+                                                  {sep_b, need_pp, 0, 1u, sep_ct, wt},
+                                                  {sep_b, need_part, 0, 0u, sep_ct, wt},
+                                                  {sep_b, 0u, 0, 0u, sep_ct, wt}};
                 PartedSmem cfg = cands[kCands - 1];
                 size_t dyn = sep_b;
                 int max_grid = 1;

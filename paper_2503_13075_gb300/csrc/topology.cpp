@@ -152,6 +152,7 @@ struct Program {
     std::vector<uint8_t> pprog;
     std::vector<uint32_t> pprog_off;  // per part, the separator program, its end
     uint32_t pprog_max = 0;           // largest part program (bytes)
+    int32_t sep_interior = 0;         // separator-program terms on interior pivots
 };
 
 // Part programs of a partitioned molecule (16-bit part-local encoding of the part's
@@ -259,6 +260,7 @@ static void build_sep_program(Program& P, int32_t nc) {
     const int32_t T0 = P.sep_t0, nt = (int32_t)P.tasks.size() - 1 - T0;
     P.pprog_off.resize(n_parts + 2);
     P.pprog_off[n_parts + 1] = P.pprog_off[n_parts] = (uint32_t)P.pprog.size();
+    P.sep_interior = 0;
     if (nsep >= 65536 || nt >= 65536) return;  // no program: too large for shared memory anyway
     std::vector<uint32_t> tw(2 * (nt + 1)), terms;
     for (int32_t k = 0; k < nt; ++k) {
@@ -274,6 +276,7 @@ static void build_sep_program(Program& P, int32_t nc) {
             } else {
                 terms.push_back(kSepInterior);
                 terms.push_back(e);
+                ++P.sep_interior;
             }
         }
     }
@@ -780,6 +783,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             M.pprog_bytes = (int32_t)P->pprog.size();
             M.pprog_max = (int32_t)P->pprog_max;
             M.sprog_bytes = (int32_t)(P->pprog_off[np + 1] - P->pprog_off[np]);
+            M.sep_interior = P->sep_interior;
             M.nlevel = P->nlevel;
             M.ntask = (int32_t)P->tasks.size() - 1;
             M.nterm = (int32_t)P->terms.size();

@@ -26,6 +26,7 @@ struct MolHost {
     int32_t pprog_bytes = 0;         // partitioned: bytes of the segment programs
     int32_t pprog_max = 0;           // partitioned: largest part program (bytes; 0 = none)
     int32_t sprog_bytes = 0;         // partitioned: bytes of the separator program (0 = none)
+    int32_t sep_interior = 0;        // partitioned: separator terms on interior pivots (read from global)
     int64_t passes = 0;
 };
 
