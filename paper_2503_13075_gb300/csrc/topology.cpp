@@ -762,8 +762,24 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             }
             std::vector<int32_t> seg_atom(bounds);
             seg_atom.push_back(na);  // the separator segment owns no atoms
-            Elimination E = eliminate_rounds(nc, adj, 2, false, &stage);
-            Program* P = new Program(compile(nc, E, M.ci, M.cj, 256, na, &seg, np + 1, &seg_atom));
+            // elimination order: rounds of independent pivots of near-minimum degree; the
+            // degree slack is tuned per molecule for the fewest levels in the deepest part
+            // (every level of a part costs a CTA barrier and a dependent chain, twice per
+            // iteration), then the fewest terms
+            Program* P = nullptr;
+            int64_t best_key = 0;
+            for (int32_t slack : {2, 3, 4, 6}) {
+                Program C = compile(nc, eliminate_rounds(nc, adj, slack, false, &stage), M.ci, M.cj, 256, na, &seg,
+                                    np + 1, &seg_atom);
+                int32_t deepest = 0;
+                for (int32_t q = 0; q < np; ++q) deepest = std::max(deepest, C.seg_lvl[q + 1] - 1 - C.seg_lvl[q]);
+                const int64_t key = ((int64_t)deepest << 40) + (int64_t)C.terms.size();
+                if (!P || key < best_key) {
+                    delete P;
+                    P = new Program(std::move(C));
+                    best_key = key;
+                }
+            }
             M.n_seg = np + 1;
             M.n_sept = (int32_t)P->sep_info.size();
             M.n_sep = nc - P->seg_piv[np];
