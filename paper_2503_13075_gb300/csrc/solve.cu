@@ -1034,34 +1034,46 @@ struct MolView {
             SY[row] -= yv;
         }
     }
-    // the same with one warp per task, its lanes splitting the terms (the narrow last
-    //      levels, where few pivots carry many terms)
-    __device__ __forceinline__ void sep_task_smem_warp(int tl, bool diag, bool& singular, LP* SV, V4* SRF, LP* SY,
-                                                       const V4* SP, const LP* SC, int lane) const {
-        const uint2 w = STK[tl];
-        const int e1 = sep_e(STK[tl + 1]);
-        LP ps = LP(0), py = LP(0);
-        for (int e = sep_e(w) + lane; e < e1; e += 32) {
-            LP li, u, ym;
-            sep_term(STM[e], SV, SRF, SY, li, u, ym);
-            ps += li * u;
-            if (diag) py += li * ym;
-        }
+    // one level with g lanes per task (g a power of two up to 32; the narrow last levels,
+    //      where few pivots carry many terms): the lanes of a group split the task's
+    //      terms and reduce them with shuffles within the group.  Every thread runs the
+    //      same number of passes, so the shuffles see whole warps.
+    __device__ __forceinline__ void sep_level_groups(int t0, int t1, int np, int g, int r0, int ts, bool& singular,
+                                                     LP* SV, V4* SRF, LP* SY, const V4* SP, const LP* SC) const {
+        const int sub = r0 & (g - 1), per_pass = ts / g;
+        for (int tb = t0; tb < t1; tb += per_pass) {
+            const int tl = tb + r0 / g;
+            const bool act = tl < t1, diag = tl < t0 + np;
+            LP ps = LP(0), py = LP(0);
+            uint2 w = make_uint2(0u, 0u);
+            if (act) {
+                w = STK[tl];
+                const int e1 = sep_e(STK[tl + 1]);
+                for (int e = sep_e(w) + sub; e < e1; e += g) {
+                    LP li, u, ym;
+                    sep_term(STM[e], SV, SRF, SY, li, u, ym);
+                    ps += li * u;
+                    if (diag) py += li * ym;
+                }
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ps += __shfl_xor_sync(0xFFFFFFFFu, ps, o);
-            py += __shfl_xor_sync(0xFFFFFFFFu, py, o);
-        }
-        if (lane == 0) {
-            const int row = (int)(w.x & 0xFFFFu), col = (int)(w.x >> 16);
-            const V4 rr = SRF[row], pp = SP[col];
-            const LP a = SC[tl] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
-            const LP sacc = a + SV[tl] - ps;
-            SV[tl] = sacc;
-            if (diag) {
-                singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
-                reinterpret_cast<LP*>(SRF + row)[3] = lp_rcp(sacc);
-                SY[row] -= py;
+            for (int o = 16; o > 0; o >>= 1) {
+                if (o < g) {  // uniform over the warp
+                    ps += __shfl_xor_sync(0xFFFFFFFFu, ps, o);
+                    py += __shfl_xor_sync(0xFFFFFFFFu, py, o);
+                }
+            }
+            if (act && sub == 0) {
+                const int row = (int)(w.x & 0xFFFFu), col = (int)(w.x >> 16);
+                const V4 rr = SRF[row], pp = SP[col];
+                const LP a = SC[tl] * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+                const LP sacc = a + SV[tl] - ps;
+                SV[tl] = sacc;
+                if (diag) {
+                    singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+                    reinterpret_cast<LP*>(SRF + row)[3] = lp_rcp(sacc);
+                    SY[row] -= py;
+                }
             }
         }
     }
@@ -1553,9 +1565,10 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             for (int l = 0; l < nl; ++l) {
                 const int p0 = M.SLP[l], p1 = M.SLP[l + 1], np = p1 - p0;
                 const int t0 = M.SLT[l], t1 = M.SLT[l + 1];
-                if (factor && t1 - t0 <= 8 * (ts >> 5)) {  // narrow level: a warp per task
-                    for (int t = t0 + (r0 >> 5); t < t1; t += ts >> 5)
-                        M.sep_task_smem_warp(t, t < t0 + np, sing, SV, SRF, SY, SP, SC, r0 & 31);
+                int g = 1;  // narrow level: g >= 4 lanes per task, one pass
+                while (g < 32 && 2 * g * (t1 - t0) <= ts) g *= 2;
+                if (factor && g >= 4) {
+                    M.sep_level_groups(t0, t1, np, g, r0, ts, sing, SV, SRF, SY, SP, SC);
                 } else if (factor)
                     for (int t = t0 + r0; t < t1; t += ts) M.sep_task_smem(t, t < t0 + np, sing, SV, SRF, SY, SP, SC);
                 else
