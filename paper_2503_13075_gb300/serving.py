@@ -7,13 +7,14 @@ A request carries one molecule topology (constrained atom pairs) and its coordin
 * keeps set-up topologies (programs, schedules, workspaces) resident on the device in an
   LRU cache bounded by an HBM budget; a topology is planned and uploaded on its first
   request (``ilves_setup_topology``) and reused afterwards,
-* admits a request only if its topology and its input/output buffers fit the budget
+* admits a request only if its topology and its input/output footprint fit the budget
   (otherwise it is rejected with a reason, never queued forever),
 * batches requests as they arrive: a batch closes after ``max_wait_s`` or ``max_batch``
-  requests; all solves of a batch are enqueued back to back on a pool of CUDA streams
-  (host->device copies, warm start, ilves_solve, device->host copies), one stream per
-  topology so that solves sharing a topology's workspace stay ordered, and the batch
-  completes when every stream has finished,
+  requests; all solves of a batch are enqueued back to back on a pool of CUDA streams,
+  one stream per topology so that solves sharing a topology's workspace stay ordered,
+  and the batch completes when every stream has finished.  Each ilves_solve reads the
+  request's page-locked host inputs and writes its page-locked host outputs in place
+  (no staging copies) and computes the diagonal start itself,
 * records per-request latency (arrival -> results on the host), iterations and status;
   ``max_relative_violation`` reports the accuracy of returned positions.
 """
@@ -147,14 +148,16 @@ class Engine:
         self.cache.hits = self.cache.misses = 0
 
     def pin(self, req):
-        """Pinned host buffers of a request (done when the request is created)."""
+        """Pinned host buffers of a request (done when the request is created): inputs
+        x_old, x_unc, inv_mass, d; outputs x, iterations, status, lambda."""
         torch = self.torch
         req.host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                     for a in (req.x_old, req.x_unc, req.inv_mass, req.d)]
         n_mol_max = max(1, len(req.d))
         req.host += [torch.empty(req.n_atoms, 3, dtype=torch.float64).pin_memory(),
                      torch.empty(n_mol_max, dtype=torch.int32).pin_memory(),
-                     torch.empty(n_mol_max, dtype=torch.int32).pin_memory()]
+                     torch.empty(n_mol_max, dtype=torch.int32).pin_memory(),
+                     torch.empty(max(1, len(req.d)), dtype=torch.float64).pin_memory()]
 
     def _run_batch(self, batch):
         torch = self.torch
@@ -169,20 +172,17 @@ class Engine:
             # one stream per topology: solves of one topology share its workspace and must be
             # stream-ordered; different topologies overlap on different streams
             s = self.streams[int(req.key[:8], 16) % len(self.streams)]
-            with torch.cuda.stream(s):
-                dev = [h.to(self.dev, non_blocking=True) for h in req.host[:4]]
-                l0 = None
-                if self.warm_start == "diag":
-                    l0 = B.warm_start(None, topo, *dev, stream=s)
-                x, lam, it, st = topo.solve(*dev, tol=self.tol, precision=self.precision, lambda0=l0, stream=s)
-                hx, hi, hs = req.host[4], req.host[5][: topo.n_molecules], req.host[6][: topo.n_molecules]
-                hx.copy_(x, non_blocking=True)
-                hi.copy_(it, non_blocking=True)
-                hs.copy_(st, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(s)
-            jobs.append((req, ev, hx, hi, hs, dev, x))
-        for req, ev, hx, hi, hs, dev, x in jobs:
+            # the kernels read the request's pinned inputs and write its pinned outputs in
+            # place (no staging copies); the diagonal start is computed inside the solve
+            hx, hi, hs = req.host[4], req.host[5][: topo.n_molecules], req.host[6][: topo.n_molecules]
+            hl = req.host[7][: topo.n_constraints]
+            topo.solve(*req.host[:4], tol=self.tol, precision=self.precision, x_out=hx, lambda_out=hl,
+                       iterations_out=hi, status_out=hs, stream=s,
+                       start="diag" if self.warm_start == "diag" else None)
+            ev = torch.cuda.Event()
+            ev.record(s)
+            jobs.append((req, ev, hx, hi, hs))
+        for req, ev, hx, hi, hs in jobs:
             ev.synchronize()
             req.done = self.now()
             req.x, req.iterations, req.mol_status = hx.numpy().copy(), hi.numpy().copy(), hs.numpy().copy()
