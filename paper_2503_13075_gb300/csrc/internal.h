@@ -104,8 +104,8 @@ ILVES_HD uint32_t align16(uint32_t b) { return (b + 15u) & ~15u; }
 // read from the global copy of the blob); `bytes` = the whole blob.
 // Partitioned molecules add the Schur-contribution tables (see SepInfo, Contrib).
 struct ProgLayout {
-    uint32_t seg, con_atoms, piv, lvl_task, lvl_piv, lane_term, inc_ptr, inc, tasks, terms, sep_info, cptr, cent,
-        pprog_off, pprog, staged, con_gid, bytes;
+    uint32_t seg, con_atoms, piv, lvl_task, lvl_piv, lane_term, inc_ptr, inc, atom_off, tasks, terms, sep_info,
+        cptr, cent, pprog_off, pprog, staged, con_gid, bytes;
 };
 
 // Partitioned molecules: the separator block's entries receive the terms of interior
@@ -201,6 +201,7 @@ ILVES_HD ProgLayout prog_layout(uint32_t na, uint32_t nc, uint32_t ntask, uint32
     L.lane_term = o; o = align16(o + (compact ? ix * (uint32_t)kSlotThreads : 0u));
     L.inc_ptr = o;   o = align16(o + ix * (na + 1));
     L.inc = o;       o = align16(o + ix * 2u * nc);
+    L.atom_off = o;  o = align16(o + (compact ? ix * na : 0u));  // atom slot -> local atom
     L.tasks = o;     o = align16(o + (compact ? 4u * ntask : 4u * ix * (ntask + 1)));
     L.terms = o;     o = align16(o + (uint32_t)sizeof(typename TermOf<IdxT>::T) * nterm);
     const bool parted = n_seg > 1;

@@ -311,6 +311,7 @@ struct MolView {
     const IdxT* lane_term;
     const IdxT* inc_ptr;
     const IdxT* inc;
+    const IdxT* aslot;  // batched molecules: local atom of each atom slot
     const TaskT* tasks;
     const typename TO::T* terms;
     double *X, *W, *RHO, *SK, *D2, *LAM;
@@ -352,6 +353,7 @@ struct MolView {
         lane_term = reinterpret_cast<const IdxT*>(prog + PL.lane_term);
         inc_ptr = reinterpret_cast<const IdxT*>(prog + PL.inc_ptr);
         inc = reinterpret_cast<const IdxT*>(prog + PL.inc);
+        aslot = reinterpret_cast<const IdxT*>(prog + PL.atom_off);
         tasks = reinterpret_cast<const TaskT*>(prog + PL.tasks);
         terms = reinterpret_cast<const typename TO::T*>(prog + PL.terms);
         X = reinterpret_cast<double*>(st + SL.x);
@@ -375,8 +377,15 @@ struct MolView {
         sep_p0 = d.n_seg > 1 ? ldp<kCoh>(&seg[d.n_seg - 1].piv) : nc;
         cohall = false;
     }
+    // global atom of atom slot o (the molecule's atoms in ascending global order); in
+    //      large molecules local atom a sits in slot a, in batched molecules in the slot
+    //      whose entry of aslot is a (their local atoms are ordered by degree)
+    __device__ __forceinline__ int64_t slot_gid(int o) const {
+        return D->atom_base >= 0 ? (int64_t)D->atom_base + o : (int64_t)A->atom_gid[D->gid_off + o];
+    }
     __device__ __forceinline__ int64_t gid(int a) const {
-        return D->atom_base >= 0 ? (int64_t)D->atom_base + a : (int64_t)A->atom_gid[D->gid_off + a];
+        static_assert(!kCompact, "batched molecules address their atoms by slot");
+        return slot_gid(a);
     }
     __device__ __forceinline__ ConA<IdxT> cons(int p) const { return ldp<kCoh>(con + p); }
     __device__ __forceinline__ int32_t gid_of_con(int p) const { return __ldg(con_gid + p); }
@@ -659,14 +668,15 @@ struct MolView {
     // ---- S1, shared-memory state: one batch of asynchronous gathers, then local passes.
     // x_old -> STG (AoS); x_unc -> X (SoA; AoS in the float-float mode, where X is free
     // until the displacements start); inv_mass -> W, d -> D2, lambda0 -> Y as raw values.
+    //      The reads run over atom slots, so consecutive lanes read consecutive addresses.
     __device__ __forceinline__ void s1_gather(int r0, int ts) {
         for (int e = r0; e < 3 * na; e += ts) {
-            const int a = e / 3, c = e - 3 * a;
-            const int64_t g = 3 * gid(a) + c;
-            cp_async8(STG + e, A->x_old + g);
-            cp_async8(DF ? X + e : X + c * na + a, A->x_unc + g);
+            const int o = e / 3, c = e - 3 * o, a = (int)aslot[o];
+            const int64_t g = 3 * slot_gid(o) + c;
+            cp_async8(STG + 3 * a + c, A->x_old + g);
+            cp_async8(DF ? X + 3 * a + c : X + c * na + a, A->x_unc + g);
         }
-        for (int a = r0; a < na; a += ts) cp_async8(W + a, A->inv_mass + gid(a));
+        for (int o = r0; o < na; o += ts) cp_async8(W + aslot[o], A->inv_mass + slot_gid(o));
         for (int p = r0; p < nc; p += ts) {
             const int32_t g = gid_of_con(p);
             cp_async8(D2 + p, A->d + g);
@@ -1138,6 +1148,15 @@ struct MolView {
             A->x_out[3 * g + 2] = *(X + 2 * na + a);
         }
     }
+    // batched molecules: the positions, one coordinate per lane in global order
+    __device__ __forceinline__ void out_atoms_by_slot(int r0, int ts) {
+        for (int e = r0; e < 3 * na; e += ts) {
+            const int o = e / 3, c = e - 3 * o, a = (int)aslot[o];
+            const int64_t g = 3 * slot_gid(o) + c;
+            if constexpr (DF) A->x_out[g] = A->x_unc[g] + df_join(as_df(*(X + c * na + a)));
+            else A->x_out[g] = *(X + c * na + a);
+        }
+    }
     __device__ __forceinline__ void out_lambda(int p) {
         const double l = *(LAM + p);
         A->lambda_out[gid_of_con(p)] = DF ? df_join(as_df(l)) : l;
@@ -1248,7 +1267,9 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
         for (int a = r0; a < na; a += ts) M.update_atom(a);
         tm.sync();
     }
-    for (int a = r0; a < na; a += ts) M.out_atom(a);
+    if constexpr (kCompact) M.out_atoms_by_slot(r0, ts);
+    else
+        for (int a = r0; a < na; a += ts) M.out_atom(a);
     if (A.lambda_out)
         for (int p = r0; p < nc; p += ts) M.out_lambda(p);
     if (r0 == 0) {

@@ -585,6 +585,10 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
         inc[fillp[con[p].i]++] = (IdxT)((uint32_t)p << 1);
         inc[fillp[con[p].j]++] = (IdxT)(((uint32_t)p << 1) | 1u);
     }
+    if constexpr (kCompact) {  // the local atom of each atom slot (ascending global order)
+        auto* aslot = reinterpret_cast<IdxT*>(dst + L.atom_off);
+        for (int32_t a = 0; a < na; ++a) aslot[M.aperm.empty() ? a : M.aperm[a]] = (IdxT)a;
+    }
     auto term_of = [&](size_t k) { return TermOf<IdxT>::make(P.terms[k].l, P.terms[k].u, P.terms[k].m); };
     if constexpr (kCompact) {
         // task words; terms thread by thread (team thread r owns t0 + r + kSlotThreads k of
@@ -627,6 +631,32 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
                 std::memcpy(dst + L.pprog, P.pprog.data(), P.pprog.size());
             }
         }
+    }
+}
+
+// Batched molecules: relabel the local atoms in order of decreasing degree (number of
+// constraints; ties keep their order), so that the lanes of a warp update atoms with equal
+// incidence counts -- the position update's float64 loop then runs no longer than its
+// atoms need.  The program's shared atoms follow the new labels; aperm maps them back.
+static void relabel_atoms_by_degree(MolHost& M, Program& P) {
+    const int32_t na = (int32_t)M.atoms.size(), nc = (int32_t)M.ci.size();
+    std::vector<int32_t> deg(na, 0);
+    for (int32_t c = 0; c < nc; ++c) {
+        ++deg[M.ci[c]];
+        ++deg[M.cj[c]];
+    }
+    M.aperm.resize(na);
+    std::iota(M.aperm.begin(), M.aperm.end(), 0);
+    std::stable_sort(M.aperm.begin(), M.aperm.end(), [&](int32_t a, int32_t b) { return deg[a] > deg[b]; });
+    std::vector<int32_t> inv(na);
+    for (int32_t a = 0; a < na; ++a) inv[M.aperm[a]] = a;
+    for (int32_t c = 0; c < nc; ++c) {
+        M.ci[c] = inv[M.ci[c]];
+        M.cj[c] = inv[M.cj[c]];
+    }
+    for (TaskW& w : P.tasks) {
+        const uint32_t a = w.atomsign >> 1;
+        if (w.atomsign != kNoAtom32 && a < (uint32_t)na) w.atomsign = ((uint32_t)inv[a] << 1) | (w.atomsign & 1u);
     }
 }
 
@@ -813,6 +843,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             M.large = true;
             *P = choose_order(nc, na, adj, M.ci, M.cj, o, 1024);
         }
+        if (!M.large) relabel_atoms_by_degree(M, *P);
         M.nlevel = P->nlevel;
         M.ntask = (int32_t)P->tasks.size() - 1;
         M.nterm = (int32_t)P->terms.size();

@@ -16,6 +16,11 @@ struct MolHost {
     std::vector<int32_t> atoms;      // global atom ids, ascending
     std::vector<int32_t> cons;       // global constraint ids, ascending (local constraint id order)
     std::vector<int32_t> ci, cj;     // per local constraint: local atom ids
+    // batched (compact) molecules: local atom a is atoms[aperm[a]] (local atoms ordered by
+    // degree, so a warp's lanes update atoms with the same number of constraints; the
+    // kernels reach the inputs and outputs through the atom slots, in the order of atoms);
+    // empty = identity
+    std::vector<int32_t> aperm;
     bool large = false;
     bool parted = false;  // partitioned: solved by a cooperative multi-CTA launch
     int32_t n_seg = 1;
