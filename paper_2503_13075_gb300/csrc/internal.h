@@ -130,6 +130,7 @@ struct Contrib { uint32_t task, slot, e0, e1; };
 //   septab    int32  x nsep             global positions of the separators referenced
 //   lane_term uint32 x kPartThreads     first term of each team thread
 //   piv       uint32 x np               U-row slot | (number of U-row entries << 16)
+//   aorder    uint16 x na               the part's atoms in update order (decreasing degree)
 //   tasks     uint2  x nt               (row | col << 16, atom | neg << 16 | nterm << 24)
 //   terms     uint2  x nterm            (l | u << 16, m)
 // followed, in shared memory only, by a scratch section (not in the blob) that holds the
@@ -137,9 +138,10 @@ struct Contrib { uint32_t task, slot, e0, e1; };
 constexpr int kPartThreads = 256;
 constexpr uint32_t kPartSep = 0x8000u, kPartNoAtom = 0xFFFFu;
 struct PartProgHeader { uint32_t np, nt, na, nlev, nsep, nterm, pad0, pad1; };
-struct PartProgLayout { uint32_t lvl_piv, lvl_task, septab, lane_term, piv, tasks, terms, scratch, bytes; };
+struct PartProgLayout { uint32_t lvl_piv, lvl_task, septab, lane_term, piv, aorder, tasks, terms, scratch, bytes; };
 constexpr uint32_t kPartSepScratch = 2u * 32u + 8u;  // per separator: two rows and a value (float64)
-ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t nlev, uint32_t nsep, uint32_t nterm) {
+ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t na, uint32_t nlev, uint32_t nsep,
+                                         uint32_t nterm) {
     PartProgLayout L;
     uint32_t o = (uint32_t)sizeof(PartProgHeader);
     L.lvl_piv = o;   o = align16(o + 2u * (nlev + 1));
@@ -147,6 +149,7 @@ ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t nlev
     L.septab = o;    o = align16(o + 4u * nsep);
     L.lane_term = o; o = align16(o + 4u * (uint32_t)kPartThreads);
     L.piv = o;       o = align16(o + 4u * np);
+    L.aorder = o;    o = align16(o + 2u * na);
     L.tasks = o;     o = align16(o + 8u * nt);
     L.terms = o;     o = align16(o + 8u * nterm);
     L.scratch = o;   o = align16(o + kPartSepScratch * nsep);

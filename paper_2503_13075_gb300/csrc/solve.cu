@@ -474,6 +474,7 @@ struct MolView {
     const uint16_t *PLP = nullptr, *PLT = nullptr;
     const int32_t* PST = nullptr;
     const uint32_t *PLANE = nullptr, *PPIV = nullptr;
+    const uint16_t* PAORD = nullptr;  // the part's atoms in update order (offsets from A0)
     const uint2 *PTK = nullptr, *PTM = nullptr;
     V4* RHS = nullptr;
     LP* WLS = nullptr;
@@ -481,12 +482,13 @@ struct MolView {
     LP* SEPY = nullptr;                      // and solution values (scratch after the program)
     __device__ __forceinline__ void part_prog_bind(const uint8_t* sp) {
         PH = reinterpret_cast<const PartProgHeader*>(sp);
-        const PartProgLayout L = part_prog_layout(PH->np, PH->nt, PH->nlev, PH->nsep, PH->nterm);
+        const PartProgLayout L = part_prog_layout(PH->np, PH->nt, PH->na, PH->nlev, PH->nsep, PH->nterm);
         PLP = reinterpret_cast<const uint16_t*>(sp + L.lvl_piv);
         PLT = reinterpret_cast<const uint16_t*>(sp + L.lvl_task);
         PST = reinterpret_cast<const int32_t*>(sp + L.septab);
         PLANE = reinterpret_cast<const uint32_t*>(sp + L.lane_term);
         PPIV = reinterpret_cast<const uint32_t*>(sp + L.piv);
+        PAORD = reinterpret_cast<const uint16_t*>(sp + L.aorder);
         PTK = reinterpret_cast<const uint2*>(sp + L.tasks);
         PTM = reinterpret_cast<const uint2*>(sp + L.terms);
         uint8_t* sc = const_cast<uint8_t*>(sp) + L.scratch;
@@ -1448,6 +1450,15 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             for (int a = a0 + r0; a < a1; a += ts) f(a);
         }
     };
+    // the position updates, in the part program's order when there is one (atoms of equal
+    // degree side by side, so a warp's float64 incidence loops run equally long)
+    auto for_update_atoms = [&](auto&& f) {
+        if (M.PH) {
+            for (int k = r0; k < M.A1 - M.A0; k += ts) f(M.A0 + (int)M.PAORD[k]);
+        } else {
+            for_my_atoms(f);
+        }
+    };
     // ---- S1.  With part copies the inputs of the part's atoms are read once each, in
     //      order (x_old into X, x_unc into XS), and the part's constraints built from
     //      them; separators (atoms of two parts) read the inputs directly.
@@ -1485,7 +1496,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         M.sep_prog_bind(SPROG);
     }
     if (alive && A.has_start()) {
-        for_my_atoms([&](int a) { M.update_atom(a); });
+        for_update_atoms([&](int a) { M.update_atom(a); });
         alive = grid_sync(&sync->barrier, nb, budget);
     }
     int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
@@ -1650,7 +1661,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
             }
         }
         for_owned([&](int p) { M.lambda_acc(p); });
-        for_my_atoms([&](int a) { M.update_atom(a); });
+        for_update_atoms([&](int a) { M.update_atom(a); });
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
     }
     if (!alive) {

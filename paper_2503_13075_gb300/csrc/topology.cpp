@@ -158,7 +158,13 @@ struct Program {
 // Part programs of a partitioned molecule (16-bit part-local encoding of the part's
 // tasks, terms and pivots; see PartProgHeader); false if some part exceeds the
 // encoding's ranges.
-static bool build_part_programs(Program& P, int32_t na_dummy) {
+static bool build_part_programs(Program& P, int32_t na_dummy, const std::vector<int32_t>& ci,
+                                const std::vector<int32_t>& cj) {
+    std::vector<int32_t> deg(na_dummy, 0);
+    for (size_t c = 0; c < ci.size(); ++c) {
+        ++deg[ci[c]];
+        ++deg[cj[c]];
+    }
     const int32_t n_parts = P.n_seg - 1;
     const int32_t sep_p0 = P.seg_piv[n_parts];
     P.pprog.clear();
@@ -203,7 +209,7 @@ static bool build_part_programs(Program& P, int32_t na_dummy) {
                     }
         }
         const uint32_t nterm = (uint32_t)(terms.size() / 2);
-        const PartProgLayout L = part_prog_layout(np, nt, nlev, (uint32_t)septab.size(), nterm);
+        const PartProgLayout L = part_prog_layout(np, nt, A1 - A0, nlev, (uint32_t)septab.size(), nterm);
         const size_t base = P.pprog.size();
         P.pprog_off[g] = (uint32_t)base;
         P.pprog.resize(base + L.scratch, 0);  // the scratch section exists in shared memory only
@@ -219,6 +225,12 @@ static bool build_part_programs(Program& P, int32_t na_dummy) {
         }
         std::memcpy(d + L.septab, septab.data(), septab.size() * 4);
         std::memcpy(d + L.lane_term, lane_term.data(), lane_term.size() * 4);
+        // update order: decreasing degree, so a warp's lanes run equal incidence loops
+        std::vector<int32_t> ord(A1 - A0);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return deg[A0 + x] > deg[A0 + y]; });
+        auto* ao = reinterpret_cast<uint16_t*>(d + L.aorder);
+        for (int32_t k = 0; k < A1 - A0; ++k) ao[k] = (uint16_t)ord[k];
         auto* pv = reinterpret_cast<uint32_t*>(d + L.piv);
         for (int32_t p = P0; p < P1; ++p) {
             const int32_t us = P.ustart[p] - T0, nu = (int32_t)P.up[p].size();
@@ -820,7 +832,7 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             }
             M.n_cent = (int32_t)P->cent.size();
             // segment programs: the parts' (all or none), then the separator block's
-            if (!build_part_programs(*P, na)) {
+            if (!build_part_programs(*P, na, M.ci, M.cj)) {
                 P->pprog.clear();
                 P->pprog_off.assign(np + 1, 0u);
                 P->pprog_max = 0;
