@@ -306,6 +306,21 @@ ilves_status ilves_topology_molecules(const ilves_topology* topo, int32_t* atoms
 ilves_status ilves_topology_export_molecule(const ilves_topology* topo, int32_t mol, int32_t* pos_gid,
                                             int32_t* level, int32_t* up_ptr, int32_t* up_idx);
 
+/* Data layout of molecule `mol` as the kernels see it (HOST outputs, any may be NULL), for
+ * checking the planner:
+ *  atom_gid[a] (n_atoms of the molecule entries): global atom of local atom a -- batched
+ *    molecules order their local atoms by decreasing number of constraints;
+ *  n_parts: parts of a partitioned molecule (0 otherwise); per part (n_parts entries):
+ *    part_levels (elimination levels of the part) and part_prog_bytes (bytes of its
+ *    shared-memory program; 0 when the parts run from the global program);
+ *  sep_summary[4]: the separator block's levels, its program's bytes, the number of its
+ *    terms on interior pivots (read from the parts' global state), and the largest part
+ *    program with its scratch area (bytes).
+ * No counterpart in the paper: introspection of this library's planner. */
+ilves_status ilves_topology_export_layout(const ilves_topology* topo, int32_t mol, int32_t* atom_gid,
+                                          int32_t* n_parts, int32_t* part_levels, int32_t* part_prog_bytes,
+                                          int32_t* sep_summary);
+
 /* Host-side plan of the batched kernel's warp-slot schedule for one precision mode
  * (ILVES_PREC_*), as it would be built for a grid of n_cta CTAs with arena_bytes of
  * shared memory each; no device is needed (introspection and tests).  Outputs (any may

@@ -66,6 +66,8 @@ def lib():
     L.ilves_topology_molecules.restype = I32
     L.ilves_topology_export_molecule.argtypes = [P, I32, P, P, P, P]
     L.ilves_topology_export_molecule.restype = I32
+    L.ilves_topology_export_layout.argtypes = [P, I32, P, P, P, P, P]
+    L.ilves_topology_export_layout.restype = I32
     L.ilves_topology_schedule.argtypes = [P, I32, I32, I32, P, P, P, P, P, P, P]
     L.ilves_topology_schedule.restype = I32
     L.ilves_destroy_topology.argtypes = [P]
@@ -194,6 +196,28 @@ class Topology:
         idx = np.zeros(max(1, int(ptr[-1])), np.int32)
         _check(L.ilves_topology_export_molecule(self._h, int(mol), None, None, None, _ptr(idx)), "export")
         return pos, lev, ptr, idx[: ptr[-1]]
+
+    def export_layout(self, mol):
+        """``ilves_topology_export_layout``: dict with the global atom of each local atom
+        (``atom_gid``), and for a partitioned molecule the parts' levels and program bytes and
+        the separator block's levels, program bytes, interior terms and the largest part
+        program (bytes, with its scratch area)."""
+        atoms, _, _, _ = self.molecules()
+        L = lib()
+        na = int(atoms[mol])
+        gid = np.zeros(max(1, na), np.int32)
+        n_parts = ctypes.c_int32()
+        _check(L.ilves_topology_export_layout(self._h, int(mol), _ptr(gid), ctypes.byref(n_parts), None, None, None),
+               "export_layout")
+        npart = n_parts.value
+        lev = np.zeros(max(1, npart), np.int32)
+        pb = np.zeros(max(1, npart), np.int32)
+        sep = np.zeros(4, np.int32)
+        _check(L.ilves_topology_export_layout(self._h, int(mol), None, None, _ptr(lev), _ptr(pb), _ptr(sep)),
+               "export_layout")
+        return {"atom_gid": gid[:na], "n_parts": npart, "part_levels": lev[:npart], "part_prog_bytes": pb[:npart],
+                "sep_levels": int(sep[0]), "sep_prog_bytes": int(sep[1]), "sep_interior_terms": int(sep[2]),
+                "part_prog_max": int(sep[3])}
 
     def schedule(self, precision="mixed", n_cta=152, arena_bytes=232448):
         """Host plan of the batched kernel's warp slots (``ilves_topology_schedule``):

@@ -2310,6 +2310,14 @@ extern "C" ilves_status ilves_topology_export_molecule(const ilves_topology* T, 
     return ILVES_OK;
 }
 
+extern "C" ilves_status ilves_topology_export_layout(const ilves_topology* T, int32_t mol, int32_t* atom_gid,
+                                                     int32_t* n_parts, int32_t* part_levels,
+                                                     int32_t* part_prog_bytes, int32_t* sep_summary) {
+    if (!T || mol < 0 || mol >= T->n_mol) return ILVES_ERR_INVALID_ARG;
+    program_export_layout(T, mol, atom_gid, n_parts, part_levels, part_prog_bytes, sep_summary);
+    return ILVES_OK;
+}
+
 extern "C" ilves_status ilves_topology_schedule(const ilves_topology* T, int32_t precision, int32_t n_cta,
                                                 int32_t arena_bytes, int32_t* n_slots, int32_t* pool_n,
                                                 int32_t* slot_cta, int32_t* slot_bytes, int32_t* slot_queue,

@@ -897,6 +897,28 @@ void program_export(const ilves_topology* T, int32_t m, int32_t* pos_gid, int32_
     if (up_ptr) up_ptr[nc] = e;
 }
 
+void program_export_layout(const ilves_topology* T, int32_t m, int32_t* atom_gid, int32_t* n_parts,
+                           int32_t* part_levels, int32_t* part_prog_bytes, int32_t* sep_summary) {
+    const MolHost& M = T->mols[m];
+    const Program& P = *T->progs[m];
+    const int32_t na = (int32_t)M.atoms.size();
+    if (atom_gid)
+        for (int32_t a = 0; a < na; ++a) atom_gid[a] = M.atoms[M.aperm.empty() ? a : M.aperm[a]];
+    const int32_t np = M.parted ? P.n_seg - 1 : 0;
+    if (n_parts) *n_parts = np;
+    const bool have_parts = M.parted && P.pprog_max > 0;
+    for (int32_t q = 0; q < np; ++q) {
+        if (part_levels) part_levels[q] = P.seg_lvl[q + 1] - 1 - P.seg_lvl[q];
+        if (part_prog_bytes) part_prog_bytes[q] = have_parts ? (int32_t)(P.pprog_off[q + 1] - P.pprog_off[q]) : 0;
+    }
+    if (sep_summary) {
+        sep_summary[0] = M.parted ? P.seg_lvl[np + 1] - 1 - P.seg_lvl[np] : 0;
+        sep_summary[1] = M.parted ? M.sprog_bytes : 0;
+        sep_summary[2] = M.parted ? M.sep_interior : 0;
+        sep_summary[3] = M.parted ? M.pprog_max : 0;
+    }
+}
+
 void free_programs(ilves_topology* T) {
     for (Program* P : T->progs) delete P;
     T->progs.clear();

@@ -111,5 +111,7 @@ int64_t program_blob_bytes(const ilves_topology* T, int32_t m);
 void program_write_blob(const ilves_topology* T, int32_t m, uint8_t* dst);
 void program_export(const ilves_topology* T, int32_t m, int32_t* pos_gid, int32_t* level,
                     int32_t* up_ptr, int32_t* up_idx);
+void program_export_layout(const ilves_topology* T, int32_t m, int32_t* atom_gid, int32_t* n_parts,
+                           int32_t* part_levels, int32_t* part_prog_bytes, int32_t* sep_summary);
 void free_programs(ilves_topology* T);
 }  // namespace ilves

@@ -218,3 +218,50 @@ def test_warp_slot_schedule(prec, n_mol, n_cta):
     assert per_cta.max() <= arena
     assert np.bincount(sc["slot_cta"], minlength=n_cta).max() <= 16
     assert np.all(np.diff(sc["slot_cta"]) >= 0)  # slots are numbered CTA by CTA
+
+
+def test_batched_atoms_ordered_by_degree():
+    """Batched molecules order their local atoms by decreasing number of constraints (ties
+    in global order), as a permutation of the molecule's atoms; molecules on the
+    CTA-per-molecule path keep the global order."""
+    s = wl.tree_batch(n_mol=48, seed=31)
+    deg = np.bincount(np.concatenate([s.atom_i, s.atom_j]), minlength=s.n_atoms)
+    for forced_large in (False, True):
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True,
+                       max_warp_constraints=10 if forced_large else 0)
+        atoms, cons, _, first = t.molecules()
+        for m in range(t.n_molecules):
+            gid = t.export_layout(m)["atom_gid"]
+            assert sorted(gid.tolist()) == list(range(first[m], first[m] + atoms[m]))
+            if forced_large and cons[m] > 10:
+                assert np.all(np.diff(gid) > 0)
+                continue
+            d = deg[gid]
+            assert np.all(np.diff(d) <= 0)
+            ties = np.diff(d) == 0
+            assert np.all(np.diff(gid)[ties] > 0)
+
+
+def test_partitioned_programs_layout():
+    """A partitioned molecule gets a shared-memory program per part and one for the
+    separator block; the parts' level counts are those of the exported elimination; no
+    separator term reads an interior pivot (a separator constraint touches at most two
+    parts, whose contributions fill its two slots); the slack tuning keeps the deepest part
+    shallow."""
+    s = wl.protein_like(n_atoms=20000, seed=1002)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, partition_min_constraints=2000)
+    assert t.n_large == 1
+    atoms, cons, _, _ = t.molecules()
+    m = int(np.argmax(cons))
+    L = t.export_layout(m)
+    assert L["n_parts"] >= 50
+    assert np.all(L["part_prog_bytes"] > 0) and np.all(L["part_prog_bytes"] % 16 == 0)
+    assert L["part_prog_max"] > L["part_prog_bytes"].max()  # scratch behind the largest program
+    assert L["sep_prog_bytes"] > 0 and L["sep_interior_terms"] == 0
+    pos, level, _, _ = t.export_molecule(m)
+    starts = [0] + [p for p in range(1, pos.size) if level[p] < level[p - 1]] + [pos.size]
+    seg_levels = [int(level[a:b].max()) + 1 for a, b in zip(starts, starts[1:])]
+    assert seg_levels[:-1] == L["part_levels"].tolist()
+    assert seg_levels[-1] == L["sep_levels"]
+    assert L["part_levels"].max() <= 12
+    assert sorted(L["atom_gid"].tolist()) == list(range(s.n_atoms))
