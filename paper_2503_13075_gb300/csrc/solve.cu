@@ -468,7 +468,8 @@ struct MolView {
     // ---- partitioned molecules, one part per CTA, with the part's program staged in
     //      shared memory (PartProgHeader): 16-bit part-local task words, terms and pivot
     //      records; a position code c is the part position P0 + c, or, with kPartSep
-    //      set, the separator PST[c & ~kPartSep].  RHS and WLS hold the part's reference
+    //      set, the separator PST[c & ~kPartSep], whose rows and solution values are staged
+    //      in SEPRF / SEPREF / SEPY once per phase.  RHS and WLS hold the part's reference
     //      rows and weights (fixed for the solve).  Off (PH == nullptr) otherwise.
     const PartProgHeader* PH = nullptr;
     const uint16_t *PLP = nullptr, *PLT = nullptr;
