@@ -91,6 +91,24 @@ def algorithmic_bytes(s):
     return 80 * s.n_atoms + 24 * s.n_constraints + 8 * s.n_molecules
 
 
+FP64_PEAK_GFLOPS = 1250.0  # GB300 float64 (non-tensor) peak, nominal: 152 SMs x ~2 FMA/clk x 2 x 2.07 GHz
+
+
+def mixed_fp64_flops(mol_atoms, mol_cons, mol_iters, started):
+    """Algorithmic float64 flops of one mixed-precision solve (the steps the mixed mode keeps
+    in float64), summed over molecules with their own Newton solve counts I:
+      set-up: rho (3 per constraint) and d^2 (1);
+      I + 1 violation passes: r = x_i - x_j (3), |r|^2 - d^2 as three FMAs (6), tol d^2 (1);
+      I multiplier accumulations (1 per constraint);
+      I position updates, plus one from the starting multipliers when there are some:
+      three FMAs per atom-constraint incidence (2 per constraint) and three per atom."""
+    na = np.asarray(mol_atoms, np.float64)
+    nc = np.asarray(mol_cons, np.float64)
+    it = np.asarray(mol_iters, np.float64)
+    upd = it + (1.0 if started else 0.0)
+    return float(np.sum(4 * nc + 10 * nc * (it + 1) + nc * it + (12 * nc + 6 * na) * upd))
+
+
 KERNEL_SOURCES = ("solve.cu", "internal.h", "devmath.cuh", "topology.cpp", "topology_impl.h")
 
 
@@ -467,6 +485,15 @@ def run_ilves(args):
     solve_per = sum(solve_ms) / len(solve_ms)
     achieved = ab / (solve_per * 1e-3) / 1e9
     kname = "k_solve_parted" if s.name == "protein_like" else "k_solve_small"
+    fp64 = None
+    if args.precision == "mixed" and args.method == "newton":  # the float64 pipe, beside the HBM roofline
+        mol_atoms, mol_cons, _, _ = topo.molecules()
+        fl = mixed_fp64_flops(mol_atoms, mol_cons, iters, args.warm_start != "none")
+        got = fl / (solve_per * 1e-3) / 1e9
+        fp64 = {"achieved": got, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": got / FP64_PEAK_GFLOPS,
+                "peak_kind": "nominal", "flops_per_launch": fl,
+                "basis": "algorithmic float64 flops of the mixed mode (set-up, violations, multipliers, "
+                         "position updates) per launch / kernel time"}
     traffic, traffic_src = (None, None) if args.method != "newton" else measured_traffic(kname, args.precision, s.n_atoms)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -511,6 +538,7 @@ def run_ilves(args):
                      "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
                      "kernel": kname,
                      "kernel_ms": solve_per},
+        "fp64_alu": fp64,
         "e2e": {"value": e2e_value, "unit": "atoms*solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_per, "all_converged": e2e_ok,
                 "transfer": "ilves_solve on page-locked host buffers: the kernels read the inputs and write "
