@@ -301,3 +301,19 @@ def test_pinned_host_buffers(prec, case):
     assert np.all(dev_out[3] == B.CONVERGED)
     with pytest.raises(ValueError):  # pageable host memory is refused
         t.solve(*[torch.from_numpy(np.ascontiguousarray(a)) for a in (s.x_old, s.x_unc, s.inv_mass, s.d)])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_chord_with_diag_start(prec):
+    """ILVES-F from the diagonal start computed inside the solve: same root as the Newton
+    oracle, within the parity bounds, on the batched and the partitioned paths."""
+    for s, topo in ((wl.tree_batch(n_mol=96, seed=1006), None),
+                    (wl.protein_like(n_atoms=12000, seed=1007), "parted")):
+        t = (B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000) if topo
+             else B.Topology(s.n_atoms, s.atom_i, s.atom_j))
+        ref = orc.solve_system(s, tol=TOL)
+        _, x, lam, it, st = run(s, prec, topo=t, method="chord", max_iter=60, start="diag")
+        assert np.all(st == B.CONVERGED)
+        assert np.abs(x - ref.x).max() <= X_TOL
+        assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL
+        assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
