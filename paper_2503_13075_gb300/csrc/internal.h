@@ -133,15 +133,20 @@ struct Contrib { uint32_t task, slot, e0, e1; };
 //   aorder    uint16 x na               the part's atoms in update order (decreasing degree)
 //   tasks     uint2  x nt               (row | col << 16, atom | neg << 16 | nterm << 24)
 //   terms     uint2  x nterm            (l | u << 16, m)
+//   contribs  uint2  x ncontrib         the part's Schur contributions (see Contrib):
+//                                       (CT slot | DIAG << 31, first cterm | count << 16)
+//   cterms    uint2  x ncterm           their terms, (l | u << 16, m)
 // followed, in shared memory only, by a scratch section (not in the blob) that holds the
 // separators' current and reference rows and solution values during a phase.
 constexpr int kPartThreads = 256;
 constexpr uint32_t kPartSep = 0x8000u, kPartNoAtom = 0xFFFFu;
-struct PartProgHeader { uint32_t np, nt, na, nlev, nsep, nterm, pad0, pad1; };
-struct PartProgLayout { uint32_t lvl_piv, lvl_task, septab, lane_term, piv, aorder, tasks, terms, scratch, bytes; };
+struct PartProgHeader { uint32_t np, nt, na, nlev, nsep, nterm, ncontrib, ncterm; };
+struct PartProgLayout {
+    uint32_t lvl_piv, lvl_task, septab, lane_term, piv, aorder, tasks, terms, contribs, cterms, scratch, bytes;
+};
 constexpr uint32_t kPartSepScratch = 2u * 32u + 8u;  // per separator: two rows and a value (float64)
 ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t na, uint32_t nlev, uint32_t nsep,
-                                         uint32_t nterm) {
+                                         uint32_t nterm, uint32_t ncontrib, uint32_t ncterm) {
     PartProgLayout L;
     uint32_t o = (uint32_t)sizeof(PartProgHeader);
     L.lvl_piv = o;   o = align16(o + 2u * (nlev + 1));
@@ -152,6 +157,8 @@ ILVES_HD PartProgLayout part_prog_layout(uint32_t np, uint32_t nt, uint32_t na, 
     L.aorder = o;    o = align16(o + 2u * na);
     L.tasks = o;     o = align16(o + 8u * nt);
     L.terms = o;     o = align16(o + 8u * nterm);
+    L.contribs = o;  o = align16(o + 8u * ncontrib);
+    L.cterms = o;    o = align16(o + 8u * ncterm);
     L.scratch = o;   o = align16(o + kPartSepScratch * nsep);
     L.bytes = o;
     return L;

@@ -477,13 +477,15 @@ struct MolView {
     const uint32_t *PLANE = nullptr, *PPIV = nullptr;
     const uint16_t* PAORD = nullptr;  // the part's atoms in update order (offsets from A0)
     const uint2 *PTK = nullptr, *PTM = nullptr;
+    const uint2 *PCB = nullptr, *PCT = nullptr;  // the part's contributions and their terms
     V4* RHS = nullptr;
     LP* WLS = nullptr;
     V4 *SEPRF = nullptr, *SEPREF = nullptr;  // the separators' current and reference rows
     LP* SEPY = nullptr;                      // and solution values (scratch after the program)
     __device__ __forceinline__ void part_prog_bind(const uint8_t* sp) {
         PH = reinterpret_cast<const PartProgHeader*>(sp);
-        const PartProgLayout L = part_prog_layout(PH->np, PH->nt, PH->na, PH->nlev, PH->nsep, PH->nterm);
+        const PartProgLayout L =
+            part_prog_layout(PH->np, PH->nt, PH->na, PH->nlev, PH->nsep, PH->nterm, PH->ncontrib, PH->ncterm);
         PLP = reinterpret_cast<const uint16_t*>(sp + L.lvl_piv);
         PLT = reinterpret_cast<const uint16_t*>(sp + L.lvl_task);
         PST = reinterpret_cast<const int32_t*>(sp + L.septab);
@@ -492,6 +494,8 @@ struct MolView {
         PAORD = reinterpret_cast<const uint16_t*>(sp + L.aorder);
         PTK = reinterpret_cast<const uint2*>(sp + L.tasks);
         PTM = reinterpret_cast<const uint2*>(sp + L.terms);
+        PCB = reinterpret_cast<const uint2*>(sp + L.contribs);
+        PCT = reinterpret_cast<const uint2*>(sp + L.cterms);
         uint8_t* sc = const_cast<uint8_t*>(sp) + L.scratch;
         SEPRF = reinterpret_cast<V4*>(sc);
         SEPREF = SEPRF + PH->nsep;
@@ -536,6 +540,23 @@ struct MolView {
                 }
             }
         }
+    }
+    // contribution c of the part to the separator block (as contrib, from the part program)
+    __device__ __forceinline__ void part_contrib(int c, bool factor) {
+        const uint2 E = PCB[c];
+        const bool diag = (E.x >> 31) != 0u;
+        const int e0 = (int)(E.y & 0xFFFFu), e1 = e0 + (int)(E.y >> 16);
+        LP sv = LP(0), sy = LP(0);
+        for (int k = e0; k < e1; ++k) {
+            const uint2 tr = PCT[k];
+            const uint32_t m = tr.y;
+            const LP li = VS[tr.x & 0xFFFFu] * reinterpret_cast<const LP*>(RFS + m)[3];
+            if (factor) sv += li * VS[tr.x >> 16];
+            if (diag) sy += li * YS[m];
+        }
+        LP* ct = CT + (E.x & 0x7FFFFFFFu);
+        if (factor) ct[0] = sv;
+        if (diag) ct[2] = sy;
     }
     // forward substitution alone (ILVES-F with its stored factor): the DIAG tasks of a level
     __device__ __forceinline__ void part_forward_level(int t0, int t1, int p0, int np, int r, int& e) {
@@ -1573,8 +1594,12 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
                 }
             }
             // this part's contributions to the separator block (Schur complement)
-            const int c1 = __ldg(M.cptr + q + 1);
-            for (int c = __ldg(M.cptr + q) + r0; c < c1; c += ts) M.contrib(c, factor);
+            if (M.PH) {
+                for (int c = r0; c < (int)M.PH->ncontrib; c += ts) M.part_contrib(c, factor);
+            } else {
+                const int c1 = __ldg(M.cptr + q + 1);
+                for (int c = __ldg(M.cptr + q) + r0; c < c1; c += ts) M.contrib(c, factor);
+            }
         }
         if (__syncthreads_or(singular) && r0 == 0) atomicOr(&sync->singular[slot], 1);
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;

@@ -209,13 +209,34 @@ static bool build_part_programs(Program& P, int32_t na_dummy, const std::vector<
                     }
         }
         const uint32_t nterm = (uint32_t)(terms.size() / 2);
-        const PartProgLayout L = part_prog_layout(np, nt, A1 - A0, nlev, (uint32_t)septab.size(), nterm);
+        // the part's Schur contributions: separator task slot in the contribution table,
+        // DIAG flag, and their terms in part-local indices
+        std::vector<uint32_t> contribs, cterms;
+        for (int32_t c = P.cptr[g]; c < P.cptr[g + 1]; ++c) {
+            const Contrib& E = P.cent[c];
+            const TaskW& tk = P.tasks[E.task];
+            const uint32_t ct = 4u * (E.task - (uint32_t)P.sep_t0) + E.slot;
+            const uint32_t first = (uint32_t)(cterms.size() / 2), count = E.e1 - E.e0;
+            if (ct >= 0x80000000u || first + count >= 65536u) return false;
+            contribs.push_back(ct | (tk.row == tk.col ? 0x80000000u : 0u));
+            contribs.push_back(first | (count << 16));
+            for (uint32_t e = E.e0; e < E.e1; ++e) {
+                const TermW& tr = P.terms[e];
+                const int32_t l_ = (int32_t)tr.l - T0, u_ = (int32_t)tr.u - T0, m_ = (int32_t)tr.m - P0;
+                if (l_ < 0 || l_ >= nt || u_ < 0 || u_ >= nt || m_ < 0 || m_ >= np) return false;
+                cterms.push_back((uint32_t)l_ | ((uint32_t)u_ << 16));
+                cterms.push_back((uint32_t)m_);
+            }
+        }
+        const uint32_t ncontrib = (uint32_t)(contribs.size() / 2), ncterm = (uint32_t)(cterms.size() / 2);
+        const PartProgLayout L =
+            part_prog_layout(np, nt, A1 - A0, nlev, (uint32_t)septab.size(), nterm, ncontrib, ncterm);
         const size_t base = P.pprog.size();
         P.pprog_off[g] = (uint32_t)base;
         P.pprog.resize(base + L.scratch, 0);  // the scratch section exists in shared memory only
         uint8_t* d = P.pprog.data() + base;
-        const PartProgHeader H{(uint32_t)np, (uint32_t)nt, (uint32_t)(A1 - A0), (uint32_t)nlev,
-                               (uint32_t)septab.size(), nterm, 0u, 0u};
+        const PartProgHeader H{(uint32_t)np,    (uint32_t)nt, (uint32_t)(A1 - A0), (uint32_t)nlev,
+                               (uint32_t)septab.size(), nterm, ncontrib, ncterm};
         std::memcpy(d, &H, sizeof(H));
         auto* lp = reinterpret_cast<uint16_t*>(d + L.lvl_piv);
         auto* lt = reinterpret_cast<uint16_t*>(d + L.lvl_task);
@@ -255,6 +276,8 @@ static bool build_part_programs(Program& P, int32_t na_dummy, const std::vector<
             tw[2 * (t - T0) + 1] = ac | ((w.atomsign & 1u) << 16) | (nterm_t << 24);
         }
         std::memcpy(d + L.terms, terms.data(), terms.size() * 4);
+        std::memcpy(d + L.contribs, contribs.data(), contribs.size() * 4);
+        std::memcpy(d + L.cterms, cterms.data(), cterms.size() * 4);
         P.pprog_max = std::max(P.pprog_max, L.bytes);
         // keep each part program 16-byte aligned
         P.pprog.resize((P.pprog.size() + 15) & ~size_t(15), 0);
