@@ -317,3 +317,16 @@ def test_chord_with_diag_start(prec):
         assert np.abs(x - ref.x).max() <= X_TOL
         assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL
         assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_partitioned_more_parts_than_resident_ctas(prec):
+    """718 parts: more than three CTAs per SM can hold, so CTAs loop over several parts
+    without shared-memory part copies, and the separator block (too large for shared
+    memory) is solved from global memory by CTA 0 -- the fallback configuration."""
+    s = wl.protein_like(n_atoms=30000, seed=1011)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, part_constraints=48)
+    assert t.n_large == 1
+    ref = orc.solve_system(s, tol=TOL)
+    _, x, lam, it, st = run(s, prec, topo=t, start="diag")
+    compare(s, ref, x, lam, it, st, it_slack=2)
