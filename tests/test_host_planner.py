@@ -265,3 +265,23 @@ def test_partitioned_programs_layout():
     assert seg_levels[-1] == L["sep_levels"]
     assert L["part_levels"].max() <= 12
     assert sorted(L["atom_gid"].tolist()) == list(range(s.n_atoms))
+
+
+def test_partition_threshold_and_ring_atom_order():
+    """A tree of exactly the partition threshold (constraints) is partitioned, one
+    constraint fewer is not; benzene rings (fill in the factor) order their atoms carbons
+    first (three constraints each), hydrogens after."""
+    s = wl.tree_molecules_of_sizes([2001], seed=41)  # 2000 constraints
+    for thresh, parted in ((2000, True), (2001, False)):
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, partition_min_constraints=thresh,
+                       max_warp_constraints=0)
+        L = t.export_layout(0)
+        assert (L["n_parts"] > 1) == parted
+        if parted:
+            assert np.all(L["part_prog_bytes"] > 0) and L["sep_interior_terms"] == 0
+    b = wl.benzene_batch(n_mol=8, seed=42)
+    t = B.Topology(b.n_atoms, b.atom_i, b.atom_j, plan_only=True)
+    deg = np.bincount(np.concatenate([b.atom_i, b.atom_j]), minlength=b.n_atoms)
+    for m in range(t.n_molecules):
+        gid = t.export_layout(m)["atom_gid"]
+        assert gid.size == 12 and list(deg[gid]) == [3] * 6 + [1] * 6
