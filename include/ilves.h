@@ -167,6 +167,10 @@ ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const 
  * place over the host link, overlapped with the solve, with no staging copies (the
  * caller synchronises the stream before reading the outputs).  Pageable host memory is
  * not supported.  The caller owns every buffer; none is retained after the call.
+ * The call enqueues only kernel launches, an asynchronous memset and event fork/join
+ * between the stream and the topology's side stream, so it can be captured into a CUDA
+ * graph (stream capture) after one ordinary call has set the kernels' attributes; each
+ * replay solves the inputs then in the captured buffers.
  * Errors: ILVES_ERR_INVALID_ARG (NULL required pointer, bad precision, max_iter < 0,
  *         lambda0 given with ILVES_START_DIAG),
  *         ILVES_ERR_CUDA (launch failure).  Allocates nothing.
