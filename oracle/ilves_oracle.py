@@ -110,6 +110,12 @@ def newton_matrix(x, x_old, inv_mass, atom_i, atom_j):
     return (G @ Minv @ G0.T).tocsc()
 
 
+def chord_matrix(x_old, inv_mass, atom_i, atom_j):
+    """ILVES-F's constant matrix A(x_old, x_old) = G(x_old) M^-1 G(x_old)^T (supplement Sec. 3,
+    the approximation of A(phi_k(lambda), q_k) by A(q_k, q_k)); symmetric."""
+    return newton_matrix(x_old, x_old, inv_mass, atom_i, atom_j)
+
+
 def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lambda0=None, method="newton"):
     """ILVES-M exact Newton (or ILVES-F, method="chord") on every molecule; see the module docstring."""
     x_old = np.asarray(x_old, np.float64).reshape(-1, 3)
@@ -130,7 +136,7 @@ def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lam
     history = []
     chord_lu = None
     if method == "chord":  # A(x_old, x_old), factorised once
-        chord_lu = spla.splu(newton_matrix(x_old, x_old, inv_mass, atom_i, atom_j), permc_spec="COLAMD")
+        chord_lu = spla.splu(chord_matrix(x_old, inv_mass, atom_i, atom_j), permc_spec="COLAMD")
     elif method != "newton":
         raise ValueError(method)
     for it in range(max_iter + 1):

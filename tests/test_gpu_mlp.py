@@ -80,6 +80,20 @@ def test_training_reduces_loss_and_warm_start_keeps_parity():
             assert it.mean() <= it0.mean()
 
 
+def test_forward_on_hand_parameters():
+    """The tensor-core forward pass on the hand-worked parameter set of the oracle pins
+    (tests/test_mlp_oracle.py): every output is exact, across tile boundaries and a ragged
+    tail (the three rows repeated 100 times)."""
+    from tests.test_mlp_oracle import HAND_Y, hand_features, hand_params
+
+    mlp = B.Mlp(max_batch=512, seed=7)
+    mlp.set_params(hand_params().astype(np.float32))
+    X = np.tile(hand_features(), (100, 1)).astype(np.float32)
+    y = mlp.forward(torch.from_numpy(X).to(DEV)).cpu().numpy()
+    assert mlp.check() == 0
+    assert np.array_equal(y, np.tile(HAND_Y, 100).astype(np.float32))
+
+
 def test_params_round_trip_and_save(tmp_path):
     mlp = B.Mlp(max_batch=64, seed=2)
     th = mo.init_params(11).astype(np.float32)

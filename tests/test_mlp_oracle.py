@@ -86,3 +86,42 @@ def test_neighbour_slots_follow_constraint_order():
         for side in (0, 1):
             ls = [l for l in nbr[k, 2 * side:2 * side + 2] if l >= 0]
             assert ls == sorted(ls)
+
+
+# Hand-worked parameters: hidden unit h < 4 copies feature h, unit 4 copies -feature 0, b1[1] =
+# 0.5; the second layer is the identity on units 0..4 with b2[2] = -0.25 and b2[3] = 0.5; the
+# output weights are (1, 2, 1, -1, 0.5) and b3 = -1.  With H1 = relu(W1 x + b1) and
+# H2 = relu(W2 H1 + b2) the output y = w3 . H2 + b3 of each row below is worked out by hand:
+#   x = (1, -2, 0.5, -1):  H1 = (1, 0, 0.5, 0, 0),   H2 = (1, 0, 0.25, 0.5, 0),  y = -0.25
+#   x = (-1, 0.25, 0, 0):  H1 = (0, 0.75, 0, 0, 1),  H2 = (0, 0.75, 0, 0.5, 1),  y = 0.5
+#   x = (0.5, 1, 2, 0):    H1 = (0.5, 1.5, 2, 0, 0), H2 = (0.5, 1.5, 1.75, 0.5, 0), y = 3.75
+# A missing ReLU in either hidden layer, a ReLU on the output, or a bias added twice or not at
+# all changes at least one of them.  Every value is exact in bfloat16.
+HAND_X = np.array([[1.0, -2.0, 0.5, -1.0], [-1.0, 0.25, 0.0, 0.0], [0.5, 1.0, 2.0, 0.0]])
+HAND_Y = np.array([-0.25, 0.5, 3.75])
+
+
+def hand_params():
+    p = {name: np.zeros(shape) for name, shape in mo.SIZES}
+    for h in range(4):
+        p["W1"][h, h] = 1.0
+    p["W1"][4, 0] = -1.0
+    p["b1"][1] = 0.5
+    for h in range(5):
+        p["W2"][h, h] = 1.0
+    p["b2"][2], p["b2"][3] = -0.25, 0.5
+    p["w3"][:5] = [1.0, 2.0, 1.0, -1.0, 0.5]
+    p["b3"][0] = -1.0
+    return mo.pack(p)
+
+
+def hand_features():
+    X = np.zeros((len(HAND_X), mo.N_FEAT))
+    X[:, :4] = HAND_X
+    return X
+
+
+@pytest.mark.parametrize("bf16_mode", [False, True])
+def test_forward_pass_on_hand_parameters(bf16_mode):
+    y, _ = mo.forward(hand_params(), hand_features(), bf16_mode=bf16_mode)
+    assert np.array_equal(y, HAND_Y)

@@ -311,3 +311,67 @@ def test_chord_method_reaches_the_newton_root_linearly(maker):
         h = [e for e in chord.history if e > 1e-12]
         ratios = [b / a for a, b in zip(h, h[1:])]
         assert max(ratios[1:]) < 0.5
+
+
+@pytest.mark.parametrize("seed,n", [(41, 10), (42, 30)])
+def test_chord_matrix_is_the_reference_jacobian(seed, n):
+    """ILVES-F's constant matrix is A(x_old, x_old) (supplement Sec. 3): the Jacobian, negated,
+    of lambda -> sigma(x_old - M^-1 G(x_old)^T lambda) at lambda = 0.  The Jacobian comes from
+    central differences of this file's own loop evaluation (exact: the map is quadratic).  The
+    matrix is symmetric and differs from the first Newton matrix A(x_unc, x_old); and the
+    oracle's chord iterates are lambda_{l+1} = lambda_l + A0^-1 sigma(x(lambda_l)) with it."""
+    s = small_tree(seed, n)
+    ai, aj = s.atom_i.astype(np.int64), s.atom_j.astype(np.int64)
+    at_ref = wl.System("ref", s.x_old, s.x_old.copy(), s.inv_mass, s.atom_i, s.atom_j, s.d)
+    nc = len(s.d)
+    h = 1e-4
+    J = np.empty((nc, nc))
+    for l in range(nc):
+        e = np.zeros(nc)
+        e[l] = h
+        J[:, l] = (sigma_of_lambda(at_ref, e)[0] - sigma_of_lambda(at_ref, -e)[0]) / (2 * h)
+    A0 = orc.chord_matrix(s.x_old, s.inv_mass, ai, aj).toarray()
+    np.testing.assert_allclose(A0, -J, atol=1e-9 * np.abs(A0).max())
+    assert np.abs(A0 - A0.T).max() <= 1e-15 * np.abs(A0).max()
+    A_unc = orc.newton_matrix(s.x_unc, s.x_old, s.inv_mass, ai, aj).toarray()
+    assert np.abs(A_unc - A0).max() > 1e-3 * np.abs(A0).max()
+    lam = np.zeros(nc)
+    for k in (1, 2, 3):
+        sig, _ = sigma_of_lambda(s, lam)
+        lam = lam + np.linalg.solve(-J, sig)
+        got = orc.solve_system(s, tol=1e-30, max_iter=k, method="chord")
+        assert got.status[0] == orc.MAX_ITER and got.iterations[0] == k
+        np.testing.assert_allclose(got.lam, lam, rtol=1e-8, atol=1e-9 * np.abs(lam).max())
+
+
+def test_molecules_are_numbered_by_smallest_atom():
+    """Molecule ids follow the smallest atom of each component, whatever the constraint order:
+    {6, 7, 8} listed first is molecule 2, {0, 2} molecule 0, {3, 4, 5} molecule 1; atom 1 is
+    in no constraint.  Per-molecule outputs of the solve follow the same numbering."""
+    ai = np.array([8, 7, 4, 2, 3])
+    aj = np.array([7, 6, 5, 0, 4])
+    mol, n = orc.molecules(9, ai, aj)
+    assert n == 3 and mol.tolist() == [2, 2, 1, 0, 1]
+    # molecule 0 feasible (no solve), molecules 1 and 2 perturbed; atom 1 passes through
+    rng = np.random.default_rng(3)
+    x_old = np.cumsum(rng.normal(0.0, 0.1, (9, 3)), axis=0)
+    r = x_old[ai] - x_old[aj]
+    d = np.sqrt(np.einsum("ij,ij->i", r, r))
+    x_unc = x_old + rng.normal(0.0, 0.004, (9, 3))
+    x_unc[[0, 2]] = x_old[[0, 2]] + 0.01  # a rigid shift keeps {0, 2} feasible
+    res = orc.solve(x_old, x_unc, np.ones(9), ai, aj, d)
+    assert res.mol_of_constraint.tolist() == [2, 2, 1, 0, 1]
+    assert res.iterations[0] == 0 and res.iterations[1] > 0 and res.iterations[2] > 0
+    assert np.array_equal(res.x[1], x_unc[1])
+
+
+def test_average_relative_error_follows_the_paper_formula():
+    """Main text, Results: (1 / (2 n N_s)) sum_k sum_i |d_i^2 - |q_a - q_b|^2| / d_i^2.  Three bonds
+    (d = 1, 1, 2) at squared lengths 1.02, 0.99 and 4.04 in one step: (0.02 + 0.01 + 0.01) / 6."""
+    x = np.zeros((6, 3))
+    x[1, 0] = math.sqrt(1.02)
+    x[2, 0], x[3, 0] = 10.0, 10.0 + math.sqrt(0.99)
+    x[4, 0], x[5, 0] = 20.0, 20.0 + math.sqrt(4.04)
+    ai, aj, d = np.array([0, 2, 4]), np.array([1, 3, 5]), np.array([1.0, 1.0, 2.0])
+    assert orc.average_relative_error(x, ai, aj, d) == pytest.approx(0.04 / 6.0, rel=1e-12)
+    assert orc.max_relative_violation(x, ai, aj, d) == pytest.approx(0.02, rel=1e-12)
