@@ -13,8 +13,8 @@ buffers: ilves_solve's kernels read the inputs (x_old, x_unc, inv_mass, d) and
 write x, lambda, iterations and status in place over the host link, inside the
 timed region; the host then reads the statuses.
 
---impl reference times the FP64 CPU oracle (the deliberately plain reference) on
-a bounded sample of the same workload on the host cores.
+--impl reference times the FP64 CPU oracle (the deliberately plain reference) on the
+same workload, molecule-parallel over the host cores.
 """
 from __future__ import annotations
 
@@ -59,29 +59,34 @@ def parse():
     p.add_argument("--duration", type=float, default=1.0, help="serving: seconds of arrivals")
     p.add_argument("--method", default="newton", choices=["newton", "chord"],
                    help="ILVES-M (Newton) or ILVES-F (chord: A(x_old, x_old) factorised once)")
+    p.add_argument("--xoh", action="store_true",
+                   help="add X-O-H triangle-closing distances on every hydroxyl (main text, h-angles)")
     p.add_argument("--warm-start", default="diag", choices=["none", "diag", "mlp"],
                    help="initial multipliers: zero, diagonal (Jacobi) guess, or the learned network")
     return p.parse_args()
 
 
-def workload(name, n_mol, seed, n_atoms=100_000):
+def workload(name, n_mol, seed, n_atoms=100_000, xoh=False):
     from paper_2503_13075_gb300 import workloads as wl
 
     if name == "protein_like":
-        return wl.protein_like(n_atoms=n_atoms, seed=1002 + (seed - 1001))
+        return wl.protein_like(n_atoms=n_atoms, seed=1002 + (seed - 1001), xoh=xoh)
     if name == "chain64":
         return wl.chain64(seed=1000 + (seed - 1001))
-    return wl.tree_batch(n_mol=n_mol, seed=seed)
+    return wl.tree_batch(n_mol=n_mol, seed=seed, xoh=xoh)
 
 
 def workload_name(s):
     if s.name == "protein_like":
+        n_xoh = s.meta.get("n_xoh_constraints", 0)
         return (f"protein_like: one connected system of {s.n_atoms} atoms, {s.n_constraints} constraints "
-                f"({s.meta.get('n_angle_constraints', 0)} H-X-H angle distances), partitioned over CTAs")
+                f"({s.meta.get('n_angle_constraints', 0) - n_xoh} H-X-H" + (f" and {n_xoh} X-O-H" if n_xoh else "")
+                + " angle distances), partitioned over CTAs")
     if s.name == "chain64":
         return "chain64: one 64-carbon chain, 63 bonds, batch of 1 (latency)"
+    extra = "all bonds and X-O-H distances" if s.n_constraints > s.n_atoms - s.n_molecules else "all bonds"
     return (f"tree_batch: {s.n_molecules} tree molecules of U{{20..200}} atoms "
-            f"({s.n_atoms} atoms, {s.n_constraints} constraints), all bonds constrained")
+            f"({s.n_atoms} atoms, {s.n_constraints} constraints), {extra} constrained")
 
 
 def algorithmic_bytes(s):
@@ -227,61 +232,119 @@ def max_over_ranks(v, world, device=None):
     return mr.max_over_ranks(v, world, device)
 
 
-def cpu_oracle_rate(s_full, budget_s=12.0, seed=0):
-    """Times the oracle on whole molecules of the workload until ~budget_s of CPU work."""
+def _oracle_chunk(args):
+    """One worker task of the all-core oracle: a contiguous run of whole molecules."""
     from oracle import ilves_oracle as orc
-    from paper_2503_13075_gb300 import workloads as wl
 
-    ptr = s_full.mol_atom_ptr
-    n_take = min(s_full.n_molecules, 512)
-    a0, a1 = 0, int(ptr[n_take])
-    sel = (s_full.atom_i < a1)
-    sub = wl.System("sample", s_full.x_old[a0:a1], s_full.x_unc[a0:a1], s_full.inv_mass[a0:a1],
-                    s_full.atom_i[sel], s_full.atom_j[sel], s_full.d[sel])
-    atoms = 0
+    x_old, x_unc, w, ai, aj, d, tol = args
+    r = orc.solve(x_old, x_unc, w, ai, aj, d, tol=tol)
+    return r.x, r.lam, r.iterations, r.status
+
+
+def _noop(_):
+    return 0
+
+
+def molecule_chunks(s, n_chunks, tol):
+    """Contiguous runs of whole molecules (atoms and constraints of a molecule are
+    contiguous in every workload), as oracle tasks."""
+    ptr = np.asarray(s.mol_atom_ptr if s.mol_atom_ptr is not None else [0, s.n_atoms])
+    nm = len(ptr) - 1
+    cuts = np.unique(np.linspace(0, nm, min(nm, n_chunks) + 1).astype(np.int64))
+    tasks = []
+    for m0, m1 in zip(cuts[:-1], cuts[1:]):
+        a0, a1 = int(ptr[m0]), int(ptr[m1])
+        sel = (s.atom_i >= a0) & (s.atom_i < a1)
+        tasks.append((s.x_old[a0:a1], s.x_unc[a0:a1], s.inv_mass[a0:a1], s.atom_i[sel] - a0, s.atom_j[sel] - a0,
+                      s.d[sel], tol))
+    return tasks
+
+
+def cpu_oracle(s, tol, cores=None):
+    """The oracle (plain FP64 Newton + SuperLU) on the whole workload: once on one core (its
+    result is also the reference for the GPU's error report), then molecule-parallel over
+    all host cores (a spawn-started process pool; pool start-up is not timed).  A single
+    connected system has one molecule and gains nothing from the pool."""
+    import multiprocessing as mp
+
+    from oracle import ilves_oracle as orc
+
     t0 = time.perf_counter()
-    reps = 0
-    while True:
-        r = orc.solve_system(sub, tol=1e-12)
-        atoms += sub.n_atoms
-        reps += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    assert np.all(r.status == 0)
-    return atoms / dt, dt, f"first {n_take} molecules ({sub.n_atoms} atoms) of the workload, {reps} solves"
+    ref = orc.solve_system(s, tol=tol)
+    t1 = time.perf_counter()
+    single = {"value": s.n_atoms / (t1 - t0), "unit": "atoms*solves/s", "cores": 1, "kind": "oracle",
+              "sample": f"the whole workload ({s.n_atoms} atoms), one solve", "seconds": round(t1 - t0, 2)}
+    cores = cores or os.cpu_count() or 1
+    allc = None
+    if s.n_molecules > 1 and cores > 1:
+        tasks = molecule_chunks(s, 4 * cores, tol)
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_noop, range(4 * cores))  # workers started and numpy / scipy imported
+            pool.map(_oracle_chunk, tasks[:cores])
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_chunk, tasks, chunksize=1)
+            t1 = time.perf_counter()
+        assert all(np.all(r[3] == 0) for r in res)
+        allc = {"value": s.n_atoms / (t1 - t0), "unit": "atoms*solves/s", "cores": cores, "kind": "oracle",
+                "sample": f"the whole workload ({s.n_atoms} atoms), one solve, {len(tasks)} molecule "
+                          f"chunks over {cores} processes", "seconds": round(t1 - t0, 2)}
+    return ref, single, allc
+
+
+def oracle_error(ref, x, lam, it, st):
+    """Error of a GPU result against the FP64 oracle on the same inputs, with the parity
+    tests' bounds: |x - x_oracle| <= 1e-10 nm; |lambda - lambda_oracle| <= 1e-8 |lambda_oracle|
+    + 1e-10 max |lambda_oracle| (lambda_over_bound <= 1); iterations within +-1 (+-2 from a
+    warm start)."""
+    scale = float(np.abs(ref.lam).max(initial=0.0))
+    dl = np.abs(lam - ref.lam)
+    big = np.abs(ref.lam) >= 1e-3 * scale
+    return {"max_abs_x_nm": float(np.abs(x - ref.x).max(initial=0.0)),
+            "lambda_over_bound": float((dl / (1e-8 * np.abs(ref.lam) + 1e-10 * scale)).max(initial=0.0)),
+            "max_rel_lambda_above_1e-3_of_max": float((dl[big] / np.abs(ref.lam[big])).max(initial=0.0)),
+            "max_abs_iterations_diff": int(np.abs(it.astype(np.int64) - ref.iterations).max(initial=0)),
+            "statuses_equal": bool(np.array_equal(st, ref.status))}
 
 
 def run_reference(args):
+    """The oracle (plain FP64 Newton + SuperLU) as the reference arm: every step solves the
+    whole workload once, molecule-parallel over the host cores (spawn-started process pool;
+    a single connected system runs on one core).  Rank 0 only."""
+    import multiprocessing as mp
+
     rank, world, local = dist_setup(args)
     if rank != 0:
         return
-    s = workload(args.workload, args.n_mol, 1001, args.n_atoms)
-    from oracle import ilves_oracle as orc
-    from paper_2503_13075_gb300 import workloads as wl
-
-    ptr = s.mol_atom_ptr
-    n_take = min(s.n_molecules, 256)
-    a1 = int(ptr[n_take])
-    sel = s.atom_i < a1
-    sub = wl.System("sample", s.x_old[:a1], s.x_unc[:a1], s.inv_mass[:a1], s.atom_i[sel], s.atom_j[sel], s.d[sel])
-    for _ in range(args.warmup):
-        orc.solve_system(sub, tol=args.tol)
+    s = workload(args.workload, args.n_mol, 1001, args.n_atoms, args.xoh)
+    cores = os.cpu_count() or 1
+    tasks = molecule_chunks(s, 4 * cores, args.tol)
+    use_pool = len(tasks) > 1 and cores > 1
     times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = orc.solve_system(sub, tol=args.tol)
-        times.append(time.perf_counter() - t0)
-    assert np.all(r.status == 0)
+    pool = mp.get_context("spawn").Pool(cores) if use_pool else None
+    try:
+        if pool is not None:
+            pool.map(_noop, range(4 * cores))
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_chunk, tasks, chunksize=1) if pool is not None else [_oracle_chunk(t) for t in tasks]
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    assert all(np.all(r[3] == 0) for r in res)
     per_step = sum(times) / len(times)
-    value = sub.n_atoms / per_step
-    sample = f"first {n_take} molecules ({sub.n_atoms} atoms) of the workload per step"
+    value = s.n_atoms / per_step
+    used = cores if use_pool else 1
+    sample = (f"the whole workload ({s.n_atoms} atoms) per step, {len(tasks)} molecule chunks over {used} "
+              f"process(es)")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "atoms*solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(s), "tol": args.tol, "oracle": "FP64 Newton + SuperLU (scipy)"},
-        "cpu_baseline": {"value": value, "unit": "atoms*solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "atoms*solves/s", "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "atoms*solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -360,7 +423,7 @@ def run_ilves(args):
     dev = torch.device("cuda", local)
     from paper_2503_13075_gb300 import binding as B
 
-    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank, args.n_atoms)  # weak scaling: every rank its own batch
+    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank, args.n_atoms, args.xoh)  # weak scaling: own batch per rank
     topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
     f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     dev_in = (f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d))
@@ -490,16 +553,22 @@ def run_ilves(args):
         mol_atoms, mol_cons, _, _ = topo.molecules()
         fl = mixed_fp64_flops(mol_atoms, mol_cons, iters, args.warm_start != "none")
         got = fl / (solve_per * 1e-3) / 1e9
-        fp64 = {"achieved": got, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": got / FP64_PEAK_GFLOPS,
-                "peak_kind": "nominal", "flops_per_launch": fl,
+        peak64, kind64 = FP64_PEAK_GFLOPS, "nominal"
+        try:
+            peak64, kind64 = B.measure_fp64_fma(), "measured (ilves_measure_fp64_fma, this run)"
+        except Exception:
+            pass
+        fp64 = {"achieved": got, "peak": peak64, "unit": "GFLOP/s", "frac": got / peak64,
+                "peak_kind": kind64, "flops_per_launch": fl,
                 "basis": "algorithmic float64 flops of the mixed mode (set-up, violations, multipliers, "
                          "position updates) per launch / kernel time"}
     traffic, traffic_src = (None, None) if args.method != "newton" else measured_traffic(kname, args.precision, s.n_atoms)
-    cpu = None
+    cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, sample = cpu_oracle_rate(s)
-        cpu = {"value": rate, "unit": "atoms*solves/s", "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": round(dt, 2)}
+        ref, single, allc = cpu_oracle(s, args.tol)
+        cpu = dict(allc or single)
+        cpu["single_core"] = single
+        err = oracle_error(ref, x, out[1].cpu().numpy(), iters, out[3].cpu().numpy())
     if rank != 0:
         return
     res = {
@@ -532,8 +601,7 @@ def run_ilves(args):
         "plain_fp64": None if value64 is None else {"value": value64, "ms_per_step": per64,
                                                     "precision": "fp64", "warm_start": "none"},
         "speedup_vs_plain_fp64": None if value64 is None else value / value64,
-        "ablation": ablation,
-        "warm_start_training": mlp_info,
+        "oracle_error": err,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
                      "kernel": kname,
@@ -547,6 +615,8 @@ def run_ilves(args):
         "wall_s_timed_region": t_wall,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "warm_start_training": mlp_info,
+        "ablation": ablation,
     }
     print(json.dumps(res))
 

@@ -120,6 +120,10 @@ typedef struct {
     int32_t partition_min_constraints; /* molecules with at least this many constraints are
                                           partitioned over many CTAs (0 = 4096) */
     int32_t part_constraints;      /* target constraints per part of a partitioned molecule (0 = 256) */
+    int32_t wait_test;             /* testing only (0 in normal use): the grid barriers of partitioned
+                                      solves also wait for this many CTAs that do not exist, so every
+                                      bounded wait runs out and the molecule reports
+                                      ILVES_MOL_WAIT_TIMEOUT; the kernel then returns normally */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */
@@ -188,20 +192,26 @@ ilves_status ilves_solve(ilves_topology* topo, const double* x_old, const double
  * start-up, or code that must not call cudaMalloc / cudaFree because those may
  * synchronise the device in the middle of an asynchronous time-stepping pipeline.
  *
- * Semantics, arguments and results are those of ilves_solve.  The difference: molecules
- * too large for one warp (the CTA-per-molecule path) keep their solver state in one
- * file-scope device array of ilves_static_scratch_bytes() bytes (16 MiB) instead of the
- * topology's workspace.  Every GPU that loads the library holds that array until exit.
+ * Semantics, arguments and results are those of ilves_solve.  The difference: the solver
+ * state of every molecule that a whole CTA or a cooperative group of CTAs solves (molecules
+ * too large for one warp team, and partitioned molecules with their Schur contribution
+ * slots), and the grid-barrier areas of partitioned molecules, live in one file-scope
+ * device array of ilves_static_scratch_bytes() bytes (16 MiB) instead of the topology's
+ * workspace.  Every GPU that loads the library holds that array until exit.
  *  - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
- *  - The topology must have been set up on the CURRENT device.  The first call on a
- *    device looks up the array's device address (cudaGetSymbolAddress) and may load the
- *    library's device code; make that first call before any stream capture.
+ *    It clears the barrier area itself, with an asynchronous memset on the topology's
+ *    side stream (a memset, not an allocation).
+ *  - ilves_setup_topology still reserves the topology's own workspace (counted by
+ *    ilves_topology_device_bytes); this entry point leaves it unused.
+ *  - The topology must have been set up on the CURRENT device.  Every call looks up the
+ *    array's device address on that device (cudaGetSymbolAddress); the first call on a
+ *    device may also load the library's device code, so make it before any stream capture.
  *  - Returns ILVES_ERR_TOO_LARGE, without launching anything, when the topology's
- *    large-molecule state (ilves_topology_workspace_bytes) exceeds the static maximum.
- *  - All calls share the one array.  Each call writes every scratch location before it
- *    reads it, so nothing needs clearing between calls, but calls that overlap on the
- *    GPU (other streams, other threads, or ilves_solve_static_scratch on two topologies
- *    at once) race on the array: serialise them.
+ *    state and barrier areas (ilves_topology_workspace_bytes) exceed the static maximum.
+ *  - All calls share the one array.  Each call writes every state location before it
+ *    reads it and clears the barrier area, so results do not depend on what an earlier
+ *    call left there; but calls that overlap on the GPU (other streams, other threads, or
+ *    ilves_solve_static_scratch on two topologies at once) race on the array: serialise them.
  */
 ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_old, const double* x_unc,
                                         const double* inv_mass, const double* d, double tol,
@@ -249,6 +259,12 @@ int64_t ilves_mlp_param_count(void);
  * (bounded waits; the affected launch stops early, frees its tensor memory and leaves
  * its outputs incomplete).  ILVES_OK if none, ILVES_ERR_TIMEOUT otherwise. */
 ilves_status ilves_mlp_check(const ilves_mlp* mlp, int32_t* waits_given_up);
+
+/* Testing only: with on != 0 the network's forward kernels first wait on a tensor-core
+ * completion barrier that nothing signals (before any MMA is issued), so the bounded wait
+ * runs out, the kernel frees its tensor memory and returns, and ilves_mlp_check reports
+ * ILVES_ERR_TIMEOUT.  on = 0 restores normal operation. */
+ilves_status ilves_mlp_set_wait_test(ilves_mlp* mlp, int32_t on);
 
 /* Creates a network on the current device with He-uniform weights drawn from `seed` and
  * activation buffers for up to max_batch training rows (allocates device memory). */
@@ -340,6 +356,15 @@ ilves_status ilves_topology_schedule(const ilves_topology* topo, int32_t precisi
                                      int32_t arena_bytes, int32_t* n_slots, int32_t* pool_n,
                                      int32_t* slot_cta, int32_t* slot_bytes, int32_t* slot_queue,
                                      int32_t* mol_slot, int32_t* mol_bytes);
+
+/* Measures the float64 FMA rate of the current device (GFLOP/s, 2 flops per FMA) with
+ * a kernel of eight independent FMA chains per thread over every SM, timed with CUDA events
+ * on `stream` (synchronous; allocates and frees a small device buffer).  No counterpart in
+ * the paper: the mixed mode keeps violations, multiplier sums and position updates in
+ * float64 (supplement Sec. 2.3 quantities), and this rate is their ceiling beside HBM.
+ *  iters: FMAs per chain (e.g. 4096).  gflops: HOST output.
+ * Errors: ILVES_ERR_INVALID_ARG (NULL gflops, iters < 1), ILVES_ERR_OOM, ILVES_ERR_CUDA. */
+ilves_status ilves_measure_fp64_fma(int32_t iters, double* gflops, void* stream);
 
 /* Releases every device and host buffer of the topology (NULL is ignored). */
 void ilves_destroy_topology(ilves_topology* topo);

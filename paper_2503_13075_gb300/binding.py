@@ -36,7 +36,8 @@ class SetupOpts(ctypes.Structure):
     _fields_ = [("ordering", ctypes.c_int32), ("degree_slack", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_warp_constraints", ctypes.c_int32),
-                ("partition_min_constraints", ctypes.c_int32), ("part_constraints", ctypes.c_int32)]
+                ("partition_min_constraints", ctypes.c_int32), ("part_constraints", ctypes.c_int32),
+                ("wait_test", ctypes.c_int32)]
 
 
 _lib = None
@@ -84,10 +85,14 @@ def lib():
     L.ilves_topology_workspace_bytes.restype = I64
     L.ilves_topology_device_bytes.argtypes = [P]
     L.ilves_topology_device_bytes.restype = I64
+    L.ilves_measure_fp64_fma.argtypes = [I32, ctypes.POINTER(D), VP]
+    L.ilves_measure_fp64_fma.restype = I32
     L.ilves_mlp_param_count.argtypes = []
     L.ilves_mlp_param_count.restype = I64
     L.ilves_mlp_check.argtypes = [P, pi32]
     L.ilves_mlp_check.restype = I32
+    L.ilves_mlp_set_wait_test.argtypes = [P, I32]
+    L.ilves_mlp_set_wait_test.restype = I32
     L.ilves_mlp_create.argtypes = [I32, ctypes.c_uint64, ctypes.POINTER(P)]
     L.ilves_mlp_create.restype = I32
     L.ilves_mlp_destroy.argtypes = [P]
@@ -130,7 +135,7 @@ class Topology:
 
     def __init__(self, n_atoms, atom_i, atom_j, ordering=0, degree_slack=2, warps_per_cta=0,
                  ctas_per_sm=0, device=None, plan_only=False, max_warp_constraints=0,
-                 partition_min_constraints=0, part_constraints=0):
+                 partition_min_constraints=0, part_constraints=0, wait_test=0):
         L = lib()
         ai = np.ascontiguousarray(atom_i, dtype=np.int32)
         aj = np.ascontiguousarray(atom_j, dtype=np.int32)
@@ -143,6 +148,7 @@ class Topology:
         o.max_warp_constraints = max_warp_constraints
         o.partition_min_constraints = partition_min_constraints
         o.part_constraints = part_constraints
+        o.wait_test = wait_test
         if plan_only:
             o.device = -2
         elif device is not None:
@@ -317,6 +323,16 @@ class Topology:
         return x_out, lambda_out, iterations_out, status_out
 
 
+def measure_fp64_fma(iters=4096, stream=None, device=None):
+    """``ilves_measure_fp64_fma``: the float64 FMA rate of the current device, GFLOP/s."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    g = ctypes.c_double()
+    _check(lib().ilves_measure_fp64_fma(int(iters), ctypes.byref(g), _stream(dev, stream)), "ilves_measure_fp64_fma")
+    return g.value
+
+
 def _stream(dev, stream=None):
     import torch
 
@@ -359,6 +375,11 @@ class Mlp:
         n = ctypes.c_int32()
         lib().ilves_mlp_check(self._h, ctypes.byref(n))
         return n.value
+
+    def set_wait_test(self, on):
+        """Testing only (``ilves_mlp_set_wait_test``): forward kernels wait on a barrier nothing
+        signals, so the bounded wait runs out and ``check()`` reports it."""
+        _check(lib().ilves_mlp_set_wait_test(self._h, 1 if on else 0), "ilves_mlp_set_wait_test")
 
     def get_params(self):
         out = np.zeros(self.n_params, np.float32)

@@ -240,7 +240,8 @@ static_assert(4 * (SM_REQUEST + 1024) > 228 * 1024 && kTmemCols * 3 <= 512, "at 
 template <bool kFused, bool kTrain>
 __global__ void __launch_bounds__(TILE)
 k_mlp_forward(MlpWeights Wt, const float* __restrict__ X, int n, FeatArgs F, float* __restrict__ out,
-              __nv_bfloat16* __restrict__ h1_out, float* __restrict__ h2_out, int* __restrict__ err) {
+              __nv_bfloat16* __restrict__ h1_out, float* __restrict__ h2_out, int* __restrict__ err,
+              int wait_test) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float* b1s = reinterpret_cast<float*>(sm + SM_B);
@@ -290,6 +291,9 @@ k_mlp_forward(MlpWeights Wt, const float* __restrict__ X, int n, FeatArgs F, flo
     uint32_t parity = 0;
     bool ok = true;
     const int n_tiles = (n + TILE - 1) / TILE;
+    if (wait_test) {  // testing: wait on a phase nothing completes (no MMA in flight), so the wait runs out
+        ok = __syncthreads_and(mbar_wait(mbar, parity)) != 0;
+    }
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int row = tile * TILE + tid;
         // ---- input row -> bfloat16 A tile
@@ -514,6 +518,7 @@ struct ilves_mlp {
     __nv_bfloat16* h1 = nullptr;
     float* h2 = nullptr;
     int* err = nullptr;  // tensor-core waits that gave up (see ilves_mlp_check)
+    int32_t wait_test = 0;  // testing: forward kernels wait on a phase nothing completes
 };
 
 static ilves_status mlp_status(cudaError_t e) {
@@ -543,7 +548,7 @@ static FeatArgs feat_args(const ilves_topology* T, const double* x_old, const do
 // memory request guarantees it), one 128-row tile at a time.
 template <bool kFused, bool kTrain>
 static cudaError_t launch_forward(const MlpWeights& Wt, const float* X, int n, const FeatArgs& F, float* out,
-                                  __nv_bfloat16* h1, float* h2, int* err, cudaStream_t s) {
+                                  __nv_bfloat16* h1, float* h2, int* err, int wait_test, cudaStream_t s) {
     static bool attr_set[64] = {};
     int dev = 0, sms = 152;
     cudaError_t e = cudaGetDevice(&dev);
@@ -557,7 +562,7 @@ static cudaError_t launch_forward(const MlpWeights& Wt, const float* X, int n, c
     }
     const int tiles = (n + TILE - 1) / TILE;
     const int grid = std::max(1, std::min(tiles, 3 * sms));
-    k_mlp_forward<kFused, kTrain><<<grid, TILE, SM_REQUEST, s>>>(Wt, X, n, F, out, h1, h2, err);
+    k_mlp_forward<kFused, kTrain><<<grid, TILE, SM_REQUEST, s>>>(Wt, X, n, F, out, h1, h2, err, wait_test);
     return cudaGetLastError();
 }
 
@@ -570,6 +575,12 @@ extern "C" ilves_status ilves_mlp_check(const ilves_mlp* M, int32_t* waits_given
     *waits_given_up = v;
     if (e != cudaSuccess) return mlp_status(e);
     return v ? ILVES_ERR_TIMEOUT : ILVES_OK;
+}
+
+extern "C" ilves_status ilves_mlp_set_wait_test(ilves_mlp* M, int32_t on) {
+    if (!M) return ILVES_ERR_INVALID_ARG;
+    M->wait_test = on ? 1 : 0;
+    return ILVES_OK;
 }
 
 extern "C" ilves_status ilves_mlp_create(int32_t max_batch, uint64_t seed, ilves_mlp** out) {
@@ -661,7 +672,7 @@ extern "C" ilves_status ilves_mlp_forward(const ilves_mlp* M, const float* featu
     const MlpWeights Wt{M->w1b, M->w2b, M->params};
     FeatArgs F{};
     return mlp_status(
-        launch_forward<false, false>(Wt, features, n, F, y, nullptr, nullptr, M->err, (cudaStream_t)stream));
+        launch_forward<false, false>(Wt, features, n, F, y, nullptr, nullptr, M->err, M->wait_test, (cudaStream_t)stream));
 }
 
 extern "C" ilves_status ilves_warm_start(const ilves_mlp* M, const ilves_topology* T, const double* x_old,
@@ -678,7 +689,8 @@ extern "C" ilves_status ilves_warm_start(const ilves_mlp* M, const ilves_topolog
         const int np = std::max(T->n_c, T->n_atoms);
         k_ws_prep<<<(np + 255) / 256, 256, 0, (cudaStream_t)stream>>>(F);
         const cudaError_t e =
-            launch_forward<true, false>(Wt, nullptr, T->n_c, F, lambda0, nullptr, nullptr, M->err, (cudaStream_t)stream);
+            launch_forward<true, false>(Wt, nullptr, T->n_c, F, lambda0, nullptr, nullptr, M->err, M->wait_test,
+                                        (cudaStream_t)stream);
         if (e != cudaSuccess) return mlp_status(e);
     }
     return mlp_status(cudaGetLastError());
@@ -689,7 +701,7 @@ static ilves_status mlp_gradient(ilves_mlp* M, const float* X, const float* t, i
     const MlpWeights Wt{M->w1b, M->w2b, M->params};
     FeatArgs F{};
     if (reinterpret_cast<uintptr_t>(X) & 15u) return ILVES_ERR_INVALID_ARG;
-    const cudaError_t e = launch_forward<false, true>(Wt, X, n, F, M->y, M->h1, M->h2, M->err, s);
+    const cudaError_t e = launch_forward<false, true>(Wt, X, n, F, M->y, M->h1, M->h2, M->err, M->wait_test, s);
     if (e != cudaSuccess) return mlp_status(e);
     k_zero<<<(P_N + 255) / 256, 256, 0, s>>>(M->grad, P_N);
     k_zero<<<1, 32, 0, s>>>(M->loss, 1);

@@ -25,7 +25,6 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -1377,6 +1376,7 @@ struct PartedSmem {
     uint32_t sep_ct;  // nonzero: the separator CTA stages the contributions (sep_bytes counts them)
     uint32_t wt;      // nonzero: parts write their factor values, reciprocal pivots, rows and
                       // solve vector through to global memory (the separator phase reads some)
+    uint32_t phantom; // testing: CTAs the grid barriers wait for beyond the launch's (never arrive)
 };
 
 struct PartSync {
@@ -1451,7 +1451,7 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
         }
     }
     const int G = gridDim.x, b = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
-    const unsigned nb = gridDim.x;
+    const unsigned nb = gridDim.x + cfg.phantom;
     long long budget = kSpinBudget;
     auto part_atoms = [&](int q, int& a0, int& a1) {
         a0 = __ldg(&seg[q].atom);
@@ -2065,11 +2065,12 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
                 // the parts' values go through to global memory only if the separator phase
                 // reads interior pivots' values (terms beyond the two contribution slots)
                 const uint32_t wt = MH.sprog_bytes == 0 || MH.sep_interior > 0 ? 1u : 0u;
-                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u, sep_ct, wt},
-                                                  {sep_b, need_part, n_parts, 0u, sep_ct, wt},
-                                                  {sep_b, need_pp, 0, 1u, sep_ct, wt},
-                                                  {sep_b, need_part, 0, 0u, sep_ct, wt},
-                                                  {sep_b, 0u, 0, 0u, sep_ct, wt}};
+                const uint32_t ph = (uint32_t)T->wait_test;
+                const PartedSmem cands[kCands] = {{sep_b, need_pp, n_parts, 1u, sep_ct, wt, ph},
+                                                  {sep_b, need_part, n_parts, 0u, sep_ct, wt, ph},
+                                                  {sep_b, need_pp, 0, 1u, sep_ct, wt, ph},
+                                                  {sep_b, need_part, 0, 0u, sep_ct, wt, ph},
+                                                  {sep_b, 0u, 0, 0u, sep_ct, wt, ph}};
                 PartedSmem cfg = cands[kCands - 1];
                 size_t dyn = sep_b;
                 int max_grid = 1;
@@ -2131,28 +2132,23 @@ static ilves_status launch_mode(ilves_topology* T, const SolveArgs& A, cudaStrea
 
 // ------------------------------------------------------------------------------------
 // Allocation-free variant (see ilves_solve_static_scratch in ilves.h).  The state of
-// CTA-per-molecule solves lives in this file-scope device array instead of the
-// topology's workspace.  Host code must not pass the symbol itself to a kernel (in host
-// code it names a host-side stand-in); its device address is looked up once per device.
+// molecules solved by a CTA or a cooperative group of CTAs (large and partitioned
+// molecules, with the partitioned molecules' contribution slots) and the partitioned
+// molecules' grid-barrier areas live in this file-scope device array instead of the
+// topology's workspace; the solve clears the barrier areas with a memset on the side
+// stream.  Host code must not pass the symbol itself to a kernel (in host code it names a
+// host-side stand-in); its device address is looked up on every call, so a device reset
+// between calls cannot leave a stale address behind.
 // ------------------------------------------------------------------------------------
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_scratch_mutex;
-static void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up on first use).
-static ilves_status static_scratch_address(int dev, uint8_t** out) {
-    if (dev < 0 || dev >= kMaxDevices) return ILVES_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) return ILVES_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = reinterpret_cast<uint8_t*>(g_scratch_addr[dev]);
+// Device address of g_static_scratch on the current device.
+static ilves_status static_scratch_address(uint8_t** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return ILVES_ERR_CUDA;
+    *out = reinterpret_cast<uint8_t*>(p);
     return ILVES_OK;
 }
 
@@ -2173,6 +2169,7 @@ extern "C" void ilves_default_opts(ilves_setup_opts* o) {
     o->max_warp_constraints = 0;
     o->partition_min_constraints = 0;
     o->part_constraints = 0;
+    o->wait_test = 0;
 }
 
 extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const int32_t* atom_i,
@@ -2186,9 +2183,19 @@ extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constrai
     ilves_default_opts(&o);
     if (opts) o = *opts;
     if (o.ordering < 0 || o.ordering > 2 || o.degree_slack < 0 || o.warps_per_cta < 0 ||
-        o.warps_per_cta > 16 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4)
+        o.warps_per_cta > 16 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4 || o.wait_test < 0 || o.wait_test > 64)
         return ILVES_ERR_INVALID_ARG;
     ilves_topology* T = new ilves_topology();
+    T->wait_test = o.wait_test;
+    // the planner sizes partitioned molecules for the device's SM count (all parts of a
+    // cooperative launch must be resident at once); a host-only plan assumes 152 SMs
+    if (o.device != -2) {
+        int dev = o.device;
+        if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+        int n_sm = 0;
+        if (dev >= 0 && cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            T->n_sm = n_sm;
+    }
     ilves_status s = plan_topology(T, n_atoms, n_constraints, atom_i, atom_j, o);
     if (s == ILVES_OK && o.device != -2) s = upload_topology(T, o);
     if (s != ILVES_OK) {
@@ -2253,7 +2260,7 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     if (cudaGetDevice(&dev) != cudaSuccess) return ILVES_ERR_CUDA;
     if (dev != T->device) return ILVES_ERR_INVALID_ARG;
     uint8_t* scratch = nullptr;
-    ilves_status st = static_scratch_address(dev, &scratch);
+    ilves_status st = static_scratch_address(&scratch);
     if (st != ILVES_OK) return st;
     SolveArgs A;
     A.x_old = x_old;

@@ -811,7 +811,14 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
         if (nc >= part_min) {
             // partitioned: parts of ~part_size constraints eliminated first, separators last
             M.large = M.parted = true;
-            const int32_t part_size = o.part_constraints > 0 ? o.part_constraints : 256;
+            // automatic part size: about 256 constraints, but never more parts (plus the
+            // separator CTA) than three CTAs per SM can keep resident, since the parts of a
+            // cooperative launch run at once with their programs in shared memory
+            int32_t part_size = o.part_constraints > 0 ? o.part_constraints : 256;
+            if (o.part_constraints <= 0) {
+                const int32_t max_parts = 3 * (T->n_sm > 0 ? T->n_sm : 152) - 1;
+                part_size = std::max(part_size, (nc + max_parts - 1) / max_parts);
+            }
             const int32_t n_parts = std::max(2, std::min(8192, (nc + part_size - 1) / part_size));
             std::vector<int32_t> bounds = partition_atoms(na, M.ci, M.cj, n_parts);
             const int32_t np = (int32_t)bounds.size() - 1;

@@ -98,6 +98,7 @@ struct ilves_topology {
     int32_t parted_threads = 256;
     int32_t parted_max_ctas = 0;
     int32_t last_launches = 0;
+    int32_t wait_test = 0;                   // testing: phantom CTAs the partitioned grid barriers wait for
     bool smem_attr_set[3] = {false, false, false};
 };
 

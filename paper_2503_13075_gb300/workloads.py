@@ -258,6 +258,30 @@ def _renumber_dfs(b):
     return elem, bonds, pos
 
 
+def _xoh_pairs(elem, bonds):
+    """X-O-H triangle-closing pairs (main text, ``h-angles``): every oxygen bonded to exactly
+    one hydrogen H and one heavy atom X contributes the X...H distance."""
+    nb = [[] for _ in elem]
+    for p, c, _ in bonds:
+        nb[p].append(c)
+        nb[c].append(p)
+    out = []
+    for a, e in enumerate(elem):
+        if e != "O" or len(nb[a]) != 2:
+            continue
+        hs = [c for c in nb[a] if elem[c] == "H"]
+        xs = [c for c in nb[a] if elem[c] != "H"]
+        if len(hs) == 1 and len(xs) == 1:
+            out.append((min(xs[0], hs[0]), max(xs[0], hs[0])))
+    return out
+
+
+def _with_xoh(mol):
+    """A tree molecule (elements, bonds, positions) with its X-O-H distances appended."""
+    elem, bonds, pos = mol
+    return elem, list(bonds) + [(u, v, 0.0) for u, v in _xoh_pairs(elem, bonds)], pos
+
+
 def _assemble(name, mols, rng, sigma, seed, box):
     """Concatenate molecules, place them in a box, perturb, and build boundary arrays."""
     xs, ii, jj, dd, el, ptr = [], [], [], [], [], [0]
@@ -340,11 +364,14 @@ def chain_batch(n_chains: int, seed: int, sigma: float = 0.002, box: float = 20.
 
 
 def tree_batch(n_mol: int = 4096, lo: int = 20, hi: int = 200, seed: int = 1001,
-               sigma: float = 0.003, box: float | None = None) -> System:
-    """Batch of independent random tree molecules with U{lo..hi} atoms each."""
+               sigma: float = 0.003, box: float | None = None, xoh: bool = False) -> System:
+    """Batch of independent random tree molecules with U{lo..hi} atoms each; with ``xoh``
+    every hydroxyl adds its X-O-H triangle-closing distance (3-cycles in the graph)."""
     rng = np.random.default_rng(seed)
     sizes = rng.integers(lo, hi + 1, size=n_mol)
     mols = [_tree_molecule(rng, int(n)) for n in sizes]
+    if xoh:
+        mols = [_with_xoh(m) for m in mols]
     if box is None:  # ~100 atoms per nm^3, a condensed-phase density
         box = float(max(1.0, (sizes.sum() / 100.0) ** (1.0 / 3.0)))
     s = _assemble(f"tree_batch{n_mol}", mols, rng, sigma, seed, box)
@@ -358,13 +385,14 @@ def tree_molecules_of_sizes(sizes, seed: int, sigma: float = 0.003, box: float =
     return _exact_lengths(_assemble("trees", mols, rng, sigma, seed, box))
 
 
-def protein_like(n_atoms: int = 100_000, seed: int = 1002, sigma: float = 0.004) -> System:
+def protein_like(n_atoms: int = 100_000, seed: int = 1002, sigma: float = 0.004, xoh: bool = False) -> System:
     """One connected protein-like system: backbone + side chains + H-X-H distances.
 
     Residue pattern: N(-H) - CA(-HA)(side chain) - C(=O).  Side chains are random
     heavy-atom subtrees (elements C/N/O/S in the tree-batch proportions) saturated
     with hydrogens, so terminal carbons become CH3 and terminal nitrogens NH2/NH3.
     Each CH3 and NH3 adds the three H-H distances of its hydrogens, each NH2 adds one.
+    With ``xoh`` every hydroxyl (side-chain O with one H) also adds its X-O-H distance.
     """
     rng = np.random.default_rng(seed)
     b = _Builder(rng)
@@ -425,6 +453,9 @@ def protein_like(n_atoms: int = 100_000, seed: int = 1002, sigma: float = 0.004)
             for u in range(len(hs)):
                 for v in range(u + 1, len(hs)):
                     extra.append((hs[u], hs[v]))
+    n_hxh = len(extra)
+    if xoh:
+        extra += _xoh_pairs(elem, bonds)
     cons = [(p, c, ln) for p, c, ln in bonds]
     # interleave each angle distance after the bond of its later hydrogen (keeps bands narrow)
     by_child = {}
@@ -437,6 +468,7 @@ def protein_like(n_atoms: int = 100_000, seed: int = 1002, sigma: float = 0.004)
     s = _assemble("protein_like", [(elem, merged, pos)], rng, sigma, seed, box=0.0)
     s = _exact_lengths(s)
     s.meta["n_angle_constraints"] = len(extra)
+    s.meta["n_xoh_constraints"] = len(extra) - n_hxh
     return s
 
 

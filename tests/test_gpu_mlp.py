@@ -5,6 +5,8 @@ output within 1e-3 relative to max |y| of the oracle's bfloat16 emulation; gradi
 within 5e-3 of max |g| (float32 accumulation vs float64); a warm-started solve meets
 the same parity bounds as the zero start, in no more iterations after training.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -92,6 +94,25 @@ def test_forward_on_hand_parameters():
     y = mlp.forward(torch.from_numpy(X).to(DEV)).cpu().numpy()
     assert mlp.check() == 0
     assert np.array_equal(y, np.tile(HAND_Y, 100).astype(np.float32))
+
+
+def test_tensor_core_wait_runs_out():
+    """A bounded device wait that runs out: in wait-test mode the forward kernel waits on a
+    completion barrier nothing signals (no MMA in flight), gives up, frees its tensor memory
+    and returns; ilves_mlp_check reports it.  A fresh network afterwards computes normally."""
+    X = torch.zeros(128, 16, dtype=torch.float32, device=DEV)
+    mlp = B.Mlp(max_batch=256, seed=8)
+    mlp.set_wait_test(True)
+    mlp.forward(X)
+    assert mlp.check() >= 1
+    code = B.lib().ilves_mlp_check(mlp._h, ctypes.byref(ctypes.c_int32()))
+    assert code == 5  # ILVES_ERR_TIMEOUT
+    m2 = B.Mlp(max_batch=256, seed=9)
+    from tests.test_mlp_oracle import HAND_Y, hand_features, hand_params
+
+    m2.set_params(hand_params().astype(np.float32))
+    y = m2.forward(torch.from_numpy(hand_features().astype(np.float32)).to(DEV)).cpu().numpy()
+    assert m2.check() == 0 and np.array_equal(y, HAND_Y.astype(np.float32))
 
 
 def test_params_round_trip_and_save(tmp_path):

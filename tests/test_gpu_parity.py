@@ -330,3 +330,60 @@ def test_partitioned_more_parts_than_resident_ctas(prec):
     ref = orc.solve_system(s, tol=TOL)
     _, x, lam, it, st = run(s, prec, topo=t, start="diag")
     compare(s, ref, x, lam, it, st, it_slack=2)
+
+
+def test_partitioned_grid_barrier_wait_runs_out():
+    """A bounded device wait that runs out: with ``wait_test`` the partitioned solve's grid
+    barriers also count CTAs that never arrive.  Every CTA gives up after its spin budget,
+    the kernel returns normally, the molecule reports WAIT_TIMEOUT, and the context stays
+    usable for the next (ordinary) solve."""
+    import time
+
+    s = wl.protein_like(n_atoms=6000, seed=1020)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=1000, wait_test=1)
+    assert t.n_large == 1
+    t0 = time.perf_counter()
+    _, x, lam, it, st = run(s, "mixed", topo=t)
+    assert time.perf_counter() - t0 < 20.0
+    assert st.tolist() == [B.WAIT_TIMEOUT]
+    ref = orc.solve_system(s, tol=TOL)
+    t2 = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=1000)
+    _, x, lam, it, st = run(s, "mixed", topo=t2)
+    compare(s, ref, x, lam, it, st)
+
+
+@pytest.fixture(scope="module")
+def protein_full():
+    s = wl.protein_like()
+    return s, orc.solve_system(s, tol=TOL), B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("start", [None, "diag"])
+def test_protein_like_full_size(prec, start, protein_full):
+    """The 100,001-atom protein-like system (114,987 constraints) as benchmarked: one
+    partitioned cooperative solve, element by element against the oracle."""
+    s, ref, t = protein_full
+    assert t.n_large == 1 and t.n_molecules == 1
+    _, x, lam, it, st = run(s, prec, topo=t, start=start)
+    compare(s, ref, x, lam, it, st, it_slack=1 if start is None else 2)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["trees", "protein_parted"])
+def test_hydroxyl_angle_distances(prec, case):
+    """X-O-H triangle-closing distances (main text, h-angles) on top of all bonds (and the
+    H-X-H distances of the protein-like system): parity with the oracle, zero and diagonal
+    starts, on the batched and the partitioned paths."""
+    if case == "trees":
+        s = wl.tree_batch(n_mol=256, seed=1030, xoh=True)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    else:
+        s = wl.protein_like(n_atoms=12000, seed=1031, xoh=True)
+        assert s.meta["n_xoh_constraints"] > 0
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000)
+        assert t.n_large == 1
+    ref = orc.solve_system(s, tol=TOL)
+    for start in (None, "diag"):
+        _, x, lam, it, st = run(s, prec, topo=t, start=start)
+        compare(s, ref, x, lam, it, st, it_slack=1 if start is None else 2)

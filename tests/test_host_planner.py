@@ -38,6 +38,10 @@ def test_invalid_arguments():
     with pytest.raises(B.IlvesError) as e:
         B.Topology(4, [0], [1], ordering=7, plan_only=True)
     assert e.value.code == 1
+    with pytest.raises(B.IlvesError) as e:  # the wait-test knob is bounded
+        B.Topology(4, [0], [1], wait_test=65, plan_only=True)
+    assert e.value.code == 1
+    B.Topology(4, [0], [1], wait_test=1, plan_only=True)
 
 
 def _line_graph(ai, aj):
@@ -121,6 +125,22 @@ def test_symbolic_factorisation_rings_and_cliques():
     t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
     assert t.n_molecules == 1
     _check_molecule(t, s, 0, rng)
+
+
+def test_symbolic_factorisation_hydroxyl_triangles():
+    """X-O-H distances (main text, h-angles) close 3-cycles through hydroxyl oxygens: tree
+    molecules and a protein-like fragment with them keep a consistent symbolic LU."""
+    rng = np.random.default_rng(2)
+    s = wl.tree_batch(n_mol=24, seed=21, xoh=True)
+    assert s.n_constraints > s.n_atoms - s.n_molecules  # some molecules carry triangles
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
+    assert t.n_molecules == s.n_molecules
+    for m in range(t.n_molecules):
+        _check_molecule(t, s, m, rng)
+    p = wl.protein_like(n_atoms=800, seed=6, xoh=True)
+    assert p.meta["n_xoh_constraints"] > 0
+    t = B.Topology(p.n_atoms, p.atom_i, p.atom_j, plan_only=True)
+    _check_molecule(t, p, 0, rng)
 
 
 def test_level_counts_are_small():

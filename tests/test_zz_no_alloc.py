@@ -6,7 +6,8 @@ must not call cudaMalloc / cudaFree because they can synchronise the device) use
 ilves_solve_static_scratch.  It keeps the state of the CTA-per-molecule path in one
 static device array instead of the topology's workspace.  These tests check, through
 the C ABI, that two calls in a row give the results of ilves_solve within the parity
-tolerances used by the other GPU tests, and that an oversized topology is rejected.
+tolerances used by the other GPU tests -- after a solve of another topology has left its
+own state in the array -- and that an oversized topology is rejected.
 """
 import numpy as np
 import pytest
@@ -40,21 +41,30 @@ def _same(ref, got):
     assert np.all(np.abs(l1 - l0) <= LAM_RTOL * np.abs(l0) + 1e-10 * scale)
 
 
+def _case(case, seed):
+    if case == "protein_like":
+        s = wl.protein_like(n_atoms=20000 - 997 * (seed % 2), seed=seed)
+        return s, B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    # a batch where most molecules take the CTA-per-molecule path, some the warp path
+    s = wl.tree_batch(n_mol=24 + seed % 5, seed=seed)
+    return s, B.Topology(s.n_atoms, s.atom_i, s.atom_j, max_warp_constraints=40)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 @pytest.mark.parametrize("case", ["protein_like", "forced_large"])
 def test_static_scratch_matches_solve(case, prec):
-    if case == "protein_like":
-        s = wl.protein_like(n_atoms=20000, seed=1002)
-        topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
-    else:  # a batch where most molecules take the CTA-per-molecule path, some the warp path
-        s = wl.tree_batch(n_mol=24, seed=77)
-        topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j, max_warp_constraints=40)
+    s, topo = _case(case, 1002 if case == "protein_like" else 77)
     assert topo.n_large > 0
     assert 0 < topo.workspace_bytes() <= B.lib().ilves_static_scratch_bytes()
     dev_in = _dev(s)
     ref = _host(topo.solve(*dev_in, precision=prec))
     assert np.all(ref[3] == B.CONVERGED)
-    for _ in range(2):  # the array keeps the previous call's contents; results must not depend on them
+    # another topology's solve through the same array first, so it holds other state (and
+    # other barrier counts) when the case under test starts: results must not depend on it
+    s_o, topo_o = _case(case, 1003 if case == "protein_like" else 78)
+    other = _host(topo_o.solve_static_scratch(*_dev(s_o), precision=prec))
+    assert np.all(other[3] == B.CONVERGED)
+    for _ in range(2):  # two calls in a row, each compared with ilves_solve
         got = _host(topo.solve_static_scratch(*dev_in, precision=prec))
         _same(ref, got)
 
