@@ -124,6 +124,13 @@ typedef struct {
                                       solves also wait for this many CTAs that do not exist, so every
                                       bounded wait runs out and the molecule reports
                                       ILVES_MOL_WAIT_TIMEOUT; the kernel then returns normally */
+    int32_t overlap;               /* partitioned molecules: 0 = exact Newton with a Schur complement
+                                      over the separator constraints (default); I > 0 = overlapping
+                                      domains (supplement Sec. 3, Overlapping Partitioning Method):
+                                      each part's domain adds the atoms within I edges, every domain
+                                      solves its own system and keeps its owned constraints'
+                                      corrections (quasi-Newton, same root); 1..16.  Such topologies
+                                      solve in ILVES_PREC_FP64 and ILVES_PREC_MIXED only. */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */
@@ -326,16 +333,33 @@ ilves_status ilves_topology_molecules(const ilves_topology* topo, int32_t* atoms
 ilves_status ilves_topology_export_molecule(const ilves_topology* topo, int32_t mol, int32_t* pos_gid,
                                             int32_t* level, int32_t* up_ptr, int32_t* up_idx);
 
+/* Overlapping domains of molecule `mol` (supplement Sec. 3, Overlapping Partitioning
+ * Method; HOST outputs, any may be NULL; call once with the arrays NULL to size them):
+ *  n_dom: number of domains (0 if the molecule is not solved by overlapping domains);
+ *  atom_bounds (n_dom + 1): domain d's part owns the molecule's atoms [atom_bounds[d],
+ *    atom_bounds[d + 1]) in increasing global order (molecule-local indices);
+ *  con_ptr (n_dom + 1): domain d's constraints are con_gid[con_ptr[d] .. con_ptr[d + 1]);
+ *  con_gid: global constraint ids of each domain's constraints, increasing;
+ *  owned: 1 where the domain owns the constraint (its part holds the constraint's atom of
+ *    smaller index), else 0.
+ * Errors: ILVES_ERR_INVALID_ARG (NULL topology, mol out of range). */
+ilves_status ilves_topology_export_domains(const ilves_topology* topo, int32_t mol, int32_t* n_dom,
+                                           int32_t* atom_bounds, int32_t* con_ptr, int32_t* con_gid,
+                                           int32_t* owned);
+
 /* Data layout of molecule `mol` as the kernels see it (HOST outputs, any may be NULL), for
  * checking the planner:
  *  atom_gid[a] (n_atoms of the molecule entries): global atom of local atom a -- batched
  *    molecules order their local atoms by decreasing number of constraints;
- *  n_parts: parts of a partitioned molecule (0 otherwise); per part (n_parts entries):
- *    part_levels (elimination levels of the part) and part_prog_bytes (bytes of its
- *    shared-memory program; 0 when the parts run from the global program);
+ *  n_parts: parts of a partitioned molecule (0 otherwise; domains of a molecule solved by
+ *    overlapping domains); per part (n_parts entries): part_levels (elimination levels of
+ *    the part or domain) and part_prog_bytes (bytes of its shared-memory program; 0 when the
+ *    parts run from the global program);
  *  sep_summary[4]: the separator block's levels, its program's bytes, the number of its
  *    terms on interior pivots (read from the parts' global state), and the largest part
- *    program with its scratch area (bytes).
+ *    program with its scratch area (bytes); for overlapping domains: 0, the largest
+ *    domain's shared memory with its program staged (float32 factor), its float64-mode
+ *    state alone (bytes), and the largest domain program (bytes).
  * No counterpart in the paper: introspection of this library's planner. */
 ilves_status ilves_topology_export_layout(const ilves_topology* topo, int32_t mol, int32_t* atom_gid,
                                           int32_t* n_parts, int32_t* part_levels, int32_t* part_prog_bytes,

@@ -20,6 +20,12 @@ What it computes (paper, supplement Sec. 2.2-2.3 and Sec. 4):
   (the paper writes z = -delta with its sign convention), started from lambda_0 = 0.
 * ILVES-F (``method="chord"``), supplement Sec. 3: the simplified Newton / chord method
   with the constant symmetric matrix A(x_old, x_old), factorised once per solve.
+* Overlapping Partitioning Method (``overlap=I > 0``), supplement Sec. 3: a molecule with
+  at least ``part_min`` constraints is cut into parts by the greedy k-way partition of its
+  atoms (``greedy_partition``); part d owns the constraints whose smaller atom it holds, its
+  domain adds the atoms within I edges, and each Newton step replaces A^-1 sigma by the
+  domains' local solves with A restricted to the constraints between domain atoms, keeping
+  each domain's owned entries: a quasi-Newton iteration with the same root.
 * Stopping rule, Sec. 4: stop when max_k |sigma_k| / d_k^2 <= tol or after max_iter
   linear solves.  The convergence test happens before each solve, so an already
   feasible x_unc needs 0 solves.
@@ -35,6 +41,8 @@ pivoting).  No blocking, fusion or reordering beyond those calls.
 from __future__ import annotations
 
 from dataclasses import dataclass
+
+import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -116,8 +124,80 @@ def chord_matrix(x_old, inv_mass, atom_i, atom_j):
     return newton_matrix(x_old, x_old, inv_mass, atom_i, atom_j)
 
 
-def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lambda0=None, method="newton"):
-    """ILVES-M exact Newton (or ILVES-F, method="chord") on every molecule; see the module docstring."""
+def greedy_partition(n_atoms, atom_i, atom_j, n_parts, max_dev=0.05, cut_penalty=10.0):
+    """Greedy k-way partition of the constraint graph (supplement Sec. 3; maxDeviation 0.05,
+    cutPenalty 10).  Atoms are taken in index order; part p starts at a0 and, with target =
+    (atoms left) / (parts left), ends before atom e for the e in [a0 + target (1 - max_dev),
+    a0 + target (1 + max_dev)] (at least a0 + 1, at most n_atoms - 1) that minimises
+    cut_penalty * cut(e) + |(e - a0) - target|, cut(e) = number of constraints joining an
+    atom of [a0, e) to an atom >= e (the first such e on ties).  Returns the part bounds
+    (n_parts + 1 increasing atom indices from 0 to n_atoms; fewer if atoms run out)."""
+    lo_a = np.minimum(atom_i, atom_j)
+    hi_a = np.maximum(atom_i, atom_j)
+    bounds = [0]
+    a0 = 0
+    for p in range(n_parts - 1):
+        if a0 >= n_atoms:
+            break
+        target = (n_atoms - a0) / (n_parts - p)
+        lo = max(a0 + 1, int(math.floor(a0 + target * (1.0 - max_dev))))
+        hi = min(n_atoms - 1, int(math.ceil(a0 + target * (1.0 + max_dev))))
+        best_e, best = min(n_atoms - 1, max(lo, a0 + 1)), float("inf")
+        for e in range(lo, hi + 1):
+            cut = int(np.count_nonzero((lo_a >= a0) & (lo_a < e) & (hi_a >= e)))
+            score = cut_penalty * cut + abs((e - a0) - target)
+            if score < best:
+                best, best_e = score, e
+        if best_e <= a0:
+            break
+        bounds.append(best_e)
+        a0 = best_e
+    bounds.append(n_atoms)
+    return bounds
+
+
+def opm_domains(n_atoms, atom_i, atom_j, bounds, overlap):
+    """Domains of the Overlapping Partitioning Method (supplement Sec. 3) for one molecule with
+    local atoms 0..n_atoms-1: per part d, (constraints between domain atoms ascending, owned
+    flags), the domain being the part's atoms and every atom within `overlap` edges of them;
+    part d owns a constraint when it holds the constraint's smaller atom."""
+    adj = sp.coo_matrix((np.ones(len(atom_i)), (atom_i, atom_j)), shape=(n_atoms, n_atoms)).tocsr()
+    adj = (adj + adj.T).tocsr()
+    part = np.zeros(n_atoms, np.int64)
+    for dpart in range(len(bounds) - 1):
+        part[bounds[dpart]:bounds[dpart + 1]] = dpart
+    out = []
+    for dpart in range(len(bounds) - 1):
+        dist = csg.dijkstra(adj, directed=False, unweighted=True, limit=overlap + 0.5, min_only=True,
+                            indices=np.arange(bounds[dpart], bounds[dpart + 1]))
+        inside = np.isfinite(dist)
+        cons = np.flatnonzero(inside[atom_i] & inside[atom_j])
+        owned = part[np.minimum(atom_i[cons], atom_j[cons])] == dpart
+        out.append((cons, owned))
+    return out
+
+
+def _opm_delta(A, sigma, domains):
+    """One quasi-Newton step of the Overlapping Partitioning Method: each domain solves its
+    restriction of A delta = sigma and keeps its owned entries; None if a local system is
+    singular."""
+    delta = np.zeros_like(sigma)
+    for cons, owned in domains:
+        try:
+            z = spla.splu(A[cons][:, cons].tocsc(), permc_spec="COLAMD").solve(sigma[cons])
+        except RuntimeError:
+            return None
+        if not np.all(np.isfinite(z)):
+            return None
+        delta[cons[owned]] = z[owned]
+    return delta
+
+
+def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lambda0=None, method="newton",
+          overlap=0, part_constraints=256, part_min=4096):
+    """ILVES-M exact Newton (or ILVES-F, method="chord") on every molecule, or the
+    overlapping-domain quasi-Newton (overlap > 0) on molecules of at least part_min
+    constraints; see the module docstring."""
     x_old = np.asarray(x_old, np.float64).reshape(-1, 3)
     x_unc = np.asarray(x_unc, np.float64).reshape(-1, 3)
     inv_mass = np.asarray(inv_mass, np.float64)
@@ -132,11 +212,26 @@ def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lam
         return OracleResult(x_unc.copy(), np.zeros(0), iters, status, mol, [])
     G0 = constraint_jacobian(x_old, atom_i, atom_j, n_atoms)
     lam = np.zeros(n_c) if lambda0 is None else np.asarray(lambda0, np.float64).copy()
+    # overlapping domains of the large molecules, in global constraint ids
+    opm = {}
+    if overlap > 0:
+        for m in range(n_mol):
+            cidx = np.flatnonzero(mol == m)
+            if cidx.size < part_min:
+                continue
+            atoms = np.unique(np.concatenate([atom_i[cidx], atom_j[cidx]]))  # local atom = rank
+            li = np.searchsorted(atoms, atom_i[cidx])
+            lj = np.searchsorted(atoms, atom_j[cidx])
+            n_parts = max(2, -(-cidx.size // part_constraints))
+            bounds = greedy_partition(atoms.size, li, lj, n_parts)
+            opm[m] = [(cidx[c], o) for c, o in opm_domains(atoms.size, li, lj, bounds, overlap)]
+    chord_A0 = None
     active = np.ones(n_mol, bool)  # molecules still iterating
     history = []
     chord_lu = None
     if method == "chord":  # A(x_old, x_old), factorised once
-        chord_lu = spla.splu(chord_matrix(x_old, inv_mass, atom_i, atom_j), permc_spec="COLAMD")
+        chord_A0 = chord_matrix(x_old, inv_mass, atom_i, atom_j)
+        chord_lu = spla.splu(chord_A0, permc_spec="COLAMD")
     elif method != "newton":
         raise ValueError(method)
     for it in range(max_iter + 1):
@@ -170,6 +265,16 @@ def solve(x_old, x_unc, inv_mass, atom_i, atom_j, d, tol=1e-12, max_iter=25, lam
             A = newton_matrix(x, x_old, inv_mass, atom_i, atom_j)
             A = _restrict(A, row_active)
             delta, singular_mols = _sparse_solve(A, rhs, mol, n_mol, row_active)
+        for m, doms in opm.items():  # overlapping domains replace the exact step
+            if not active[m]:
+                continue
+            dm = _opm_delta(chord_A0.tocsr() if chord_lu is not None else newton_matrix(x, x_old, inv_mass, atom_i,
+                                                                                          atom_j).tocsr(), rhs, doms)
+            rows = mol == m
+            if dm is None:
+                singular_mols[m] = True
+            else:
+                delta[rows] = dm[rows]
         if singular_mols.any():
             status[singular_mols] = SINGULAR
             iters[singular_mols] = it

@@ -37,7 +37,7 @@ class SetupOpts(ctypes.Structure):
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_warp_constraints", ctypes.c_int32),
                 ("partition_min_constraints", ctypes.c_int32), ("part_constraints", ctypes.c_int32),
-                ("wait_test", ctypes.c_int32)]
+                ("wait_test", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
 
 _lib = None
@@ -67,6 +67,8 @@ def lib():
     L.ilves_topology_molecules.restype = I32
     L.ilves_topology_export_molecule.argtypes = [P, I32, P, P, P, P]
     L.ilves_topology_export_molecule.restype = I32
+    L.ilves_topology_export_domains.argtypes = [P, I32, P, P, P, P, P]
+    L.ilves_topology_export_domains.restype = I32
     L.ilves_topology_export_layout.argtypes = [P, I32, P, P, P, P, P]
     L.ilves_topology_export_layout.restype = I32
     L.ilves_topology_schedule.argtypes = [P, I32, I32, I32, P, P, P, P, P, P, P]
@@ -135,7 +137,7 @@ class Topology:
 
     def __init__(self, n_atoms, atom_i, atom_j, ordering=0, degree_slack=2, warps_per_cta=0,
                  ctas_per_sm=0, device=None, plan_only=False, max_warp_constraints=0,
-                 partition_min_constraints=0, part_constraints=0, wait_test=0):
+                 partition_min_constraints=0, part_constraints=0, wait_test=0, overlap=0):
         L = lib()
         ai = np.ascontiguousarray(atom_i, dtype=np.int32)
         aj = np.ascontiguousarray(atom_j, dtype=np.int32)
@@ -149,6 +151,7 @@ class Topology:
         o.partition_min_constraints = partition_min_constraints
         o.part_constraints = part_constraints
         o.wait_test = wait_test
+        o.overlap = overlap
         if plan_only:
             o.device = -2
         elif device is not None:
@@ -224,6 +227,28 @@ class Topology:
         return {"atom_gid": gid[:na], "n_parts": npart, "part_levels": lev[:npart], "part_prog_bytes": pb[:npart],
                 "sep_levels": int(sep[0]), "sep_prog_bytes": int(sep[1]), "sep_interior_terms": int(sep[2]),
                 "part_prog_max": int(sep[3])}
+
+    def export_domains(self, mol=0):
+        """``ilves_topology_export_domains``: overlapping domains of one molecule as a dict with
+        atom_bounds (n_dom + 1), and per domain d its constraints' global ids cons[d] and owned
+        flags owned[d] (numpy arrays); empty lists if the molecule is not solved by domains."""
+        L = lib()
+        nd = ctypes.c_int32()
+        _check(L.ilves_topology_export_domains(self._h, int(mol), ctypes.byref(nd), None, None, None, None),
+               "export_domains")
+        n = nd.value
+        if n == 0:
+            return {"atom_bounds": np.zeros(0, np.int32), "cons": [], "owned": []}
+        bounds = np.zeros(n + 1, np.int32)
+        ptr = np.zeros(n + 1, np.int32)
+        _check(L.ilves_topology_export_domains(self._h, int(mol), None, _ptr(bounds), _ptr(ptr), None, None),
+               "export_domains")
+        gid = np.zeros(max(1, int(ptr[-1])), np.int32)
+        own = np.zeros(max(1, int(ptr[-1])), np.int32)
+        _check(L.ilves_topology_export_domains(self._h, int(mol), None, None, None, _ptr(gid), _ptr(own)),
+               "export_domains")
+        return {"atom_bounds": bounds, "cons": [gid[ptr[d]:ptr[d + 1]] for d in range(n)],
+                "owned": [own[ptr[d]:ptr[d + 1]].astype(bool) for d in range(n)]}
 
     def schedule(self, precision="mixed", n_cta=152, arena_bytes=232448):
         """Host plan of the batched kernel's warp slots (``ilves_topology_schedule``):

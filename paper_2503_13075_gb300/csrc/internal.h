@@ -190,6 +190,83 @@ ILVES_HD SepProgLayout sep_prog_layout(uint32_t nsep, uint32_t nt, uint32_t nlev
     return L;
 }
 
+// Overlapping domains (OPM, supplement Sec. 3): one connected system solved as a
+// quasi-Newton iteration over domains.  Atoms are cut into contiguous parts; part d owns
+// the constraints whose smaller atom it holds, and its domain adds the atoms within
+// `overlap` edges of its atoms; the domain's system is A restricted to the constraints
+// between domain atoms, factorised and solved by one CTA in shared memory, and only the
+// owned constraints' corrections are kept.  Blob of an OPM molecule:
+//   OpmBlobHeader, dom_off uint32 x (n_dom + 1) (byte offsets of the domain programs from
+//   the blob start), con_gid int32 x nc (global id of each molecule-local constraint), then
+//   the domain programs.  Domain program (indices local to the domain, 16-byte aligned
+//   sections):
+//   header    DomProgHeader
+//   lvl_piv   uint16 x (nlev + 1)       positions of each level
+//   lvl_task  uint16 x (nlev + 1)       task slots of each level
+//   lane_term uint32 x kPartThreads     first term of each team thread
+//   piv       uint32 x nc               U-row slot | (number of U-row entries << 16)
+//   con       uint32 x nc               local atoms i | j << 16 of position p
+//   con_ml    uint32 x nc               molecule-local constraint | (owned << 31)
+//   atom_ml   int32  x na               molecule-local atom of each domain atom (owned atoms
+//                                       first, in order, then the halo)
+//   inc_ptr   uint16 x (na_own + 1)     incidence of the owned atoms
+//   inc       uint16 x n_inc            position p << 1 | (atom is the second atom of p)
+//   aorder    uint16 x na_own           owned atoms in update order (decreasing degree)
+//   tasks     uint2  x nt               (row | col << 16, atom | neg << 16 | nterm << 24)
+//   terms     uint32 x nterm            l | u << 11 | m << 22 (DomTerm), thread by thread
+// so a domain has fewer than 2048 task slots and 1024 constraints.
+struct DomTerm {
+    static constexpr uint32_t kMaxSlots = 2048, kMaxCons = 1024;
+    static ILVES_HD uint32_t l(uint32_t t) { return t & 0x7FFu; }
+    static ILVES_HD uint32_t u(uint32_t t) { return (t >> 11) & 0x7FFu; }
+    static ILVES_HD uint32_t m(uint32_t t) { return t >> 22; }
+    static ILVES_HD uint32_t make(uint32_t l, uint32_t u, uint32_t m) { return l | (u << 11) | (m << 22); }
+};
+struct OpmBlobHeader { uint32_t n_dom, overlap, pad0, pad1; };
+struct DomProgHeader { uint32_t na, na_own, nc, nt, nterm, nlev, n_inc, pad; };
+struct DomProgLayout {
+    uint32_t lvl_piv, lvl_task, lane_term, piv, con, con_ml, atom_ml, inc_ptr, inc, aorder, tasks, terms, bytes;
+};
+ILVES_HD DomProgLayout dom_prog_layout(uint32_t na, uint32_t na_own, uint32_t nc, uint32_t nt, uint32_t nterm,
+                                       uint32_t nlev, uint32_t n_inc) {
+    DomProgLayout L;
+    uint32_t o = (uint32_t)sizeof(DomProgHeader);
+    L.lvl_piv = o;   o = align16(o + 2u * (nlev + 1));
+    L.lvl_task = o;  o = align16(o + 2u * (nlev + 1));
+    L.lane_term = o; o = align16(o + 4u * (uint32_t)kPartThreads);
+    L.piv = o;       o = align16(o + 4u * nc);
+    L.con = o;       o = align16(o + 4u * nc);
+    L.con_ml = o;    o = align16(o + 4u * nc);
+    L.atom_ml = o;   o = align16(o + 4u * na);
+    L.inc_ptr = o;   o = align16(o + 2u * (na_own + 1));
+    L.inc = o;       o = align16(o + 2u * n_inc);
+    L.aorder = o;    o = align16(o + 2u * na_own);
+    L.tasks = o;     o = align16(o + 8u * nt);
+    L.terms = o;     o = align16(o + 4u * nterm);
+    L.bytes = o;
+    return L;
+}
+// Shared-memory state of a domain behind its program (Mode sizes: hp = 8 bytes of the
+// float64 class, lp = factor element size): X (SoA, 3 na float64), WL (na + 1, lp; the
+// extra atom has zero weight), W (na_own float64), RHO (SoA, 3 nc float64), RHOF and RF
+// (nc x 4 lp; .w = w_i + w_j and 1 / pivot), D2 (nc float64), Y (nc lp), V (nt lp).
+struct DomStateLayout { uint32_t x, wl, w, rho, rhof, rf, d2, y, v, bytes; };
+ILVES_HD DomStateLayout dom_state_layout(uint32_t na, uint32_t na_own, uint32_t nc, uint32_t nt, uint32_t lp) {
+    DomStateLayout S;
+    uint32_t o = 0;
+    S.x = o;    o = align16(o + 24u * na);
+    S.wl = o;   o = align16(o + lp * (na + 1));
+    S.w = o;    o = align16(o + 8u * na_own);
+    S.rho = o;  o = align16(o + 24u * nc);
+    S.rhof = o; o = align16(o + 4u * lp * nc);
+    S.rf = o;   o = align16(o + 4u * lp * nc);
+    S.d2 = o;   o = align16(o + 8u * nc);
+    S.y = o;    o = align16(o + lp * nc);
+    S.v = o;    o = align16(o + lp * nt);
+    S.bytes = o;
+    return S;
+}
+
 // Segment table (n_seg + 1 rows of {first position, first level-table entry, first atom}):
 // one segment for an ordinary molecule; for a partitioned molecule one per part, then the
 // separators (constraints between parts), whose atom range is empty.
@@ -278,7 +355,7 @@ struct MolDesc {
     int32_t n_sept;  // partitioned: tasks of the separator segment (they are the last ones)
     int32_t n_cent;  // partitioned: Schur contribution entries over all parts
     int32_t pprog_bytes;  // partitioned: bytes of the segment programs (parts, then separators)
-    int32_t pad_;
+    int32_t opm;          // overlapping domains: overlap depth (0 = not solved by domains)
 };
 
 }  // namespace ilves

@@ -1703,6 +1703,313 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
 }
 
 // ------------------------------------------------------------------------------------
+// overlapping domains (supplement Sec. 3, the Overlapping Partitioning Method): one CTA
+// per domain of a cooperative launch.  Each iteration every domain evaluates the violations
+// of its constraints at the current positions, factorises A(x, x_old) restricted to them
+// and solves it in shared memory -- a local approximation of z = A^-1 sigma -- and keeps
+// the corrections of the constraints it owns; after a grid barrier the owners add them to
+// lambda and move their atoms; a second barrier publishes the positions.  A quasi-Newton
+// iteration on the exact constraint equations: it converges to the same root as ILVES-M.
+// The workspace holds the molecule's positions (SoA), the owned corrections and lambda.
+// ------------------------------------------------------------------------------------
+template <class Mode>
+__global__ void __launch_bounds__(kPartThreads, 3)
+k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, uint8_t* work, PartSync* sync,
+            SolveArgs A, uint32_t phantom, uint32_t staged) {
+    using LP = typename Mode::LP;
+    using V4 = typename Mode::V4;
+    static_assert(!Mode::df, "overlapping domains run in the float64 and mixed modes");
+    extern __shared__ __align__(16) uint8_t dsm[];
+    const MolDesc D = *desc;
+    const uint8_t* mb = blob + D.blob_off;
+    const uint32_t n_dom = reinterpret_cast<const OpmBlobHeader*>(mb)->n_dom;
+    const uint32_t* dom_off = reinterpret_cast<const uint32_t*>(mb + sizeof(OpmBlobHeader));
+    const int32_t* con_gid =
+        reinterpret_cast<const int32_t*>(mb + align16((uint32_t)sizeof(OpmBlobHeader) + 4u * (n_dom + 1)));
+    const int dm = blockIdx.x, r0 = threadIdx.x, ts = blockDim.x;
+    const uint8_t* prog = mb + __ldg(dom_off + dm);  // the domain's program: in shared memory if staged
+    if (staged) {
+        const uint32_t nbytes = __ldg(dom_off + dm + 1) - __ldg(dom_off + dm);
+        for (uint32_t o = 16u * r0; o < nbytes; o += 16u * ts) cp_async16(dsm + o, prog + o);
+        cp_async_wait_all();
+        __syncthreads();
+        prog = dsm;
+    }
+    const DomProgHeader H = *reinterpret_cast<const DomProgHeader*>(prog);
+    const DomProgLayout L = dom_prog_layout(H.na, H.na_own, H.nc, H.nt, H.nterm, H.nlev, H.n_inc);
+    const uint8_t* dsmp = prog;
+    const uint16_t* LPV = reinterpret_cast<const uint16_t*>(dsmp + L.lvl_piv);
+    const uint16_t* LTK = reinterpret_cast<const uint16_t*>(dsmp + L.lvl_task);
+    const uint32_t* LANE = reinterpret_cast<const uint32_t*>(dsmp + L.lane_term);
+    const uint32_t* PV = reinterpret_cast<const uint32_t*>(dsmp + L.piv);
+    const uint32_t* CON = reinterpret_cast<const uint32_t*>(dsmp + L.con);
+    const uint32_t* CML = reinterpret_cast<const uint32_t*>(dsmp + L.con_ml);
+    const int32_t* AML = reinterpret_cast<const int32_t*>(dsmp + L.atom_ml);
+    const uint16_t* IP = reinterpret_cast<const uint16_t*>(dsmp + L.inc_ptr);
+    const uint16_t* IV = reinterpret_cast<const uint16_t*>(dsmp + L.inc);
+    const uint16_t* AORD = reinterpret_cast<const uint16_t*>(dsmp + L.aorder);
+    const uint2* TK = reinterpret_cast<const uint2*>(dsmp + L.tasks);
+    const uint32_t* TM = reinterpret_cast<const uint32_t*>(dsmp + L.terms);
+    const int na = (int)H.na, no = (int)H.na_own, nc = (int)H.nc;
+    const DomStateLayout S = dom_state_layout(H.na, H.na_own, H.nc, H.nt, (uint32_t)sizeof(LP));
+    uint8_t* st = staged ? dsm + L.bytes : dsm;
+    double* X = reinterpret_cast<double*>(st + S.x);
+    LP* WL = reinterpret_cast<LP*>(st + S.wl);
+    double* W = reinterpret_cast<double*>(st + S.w);
+    double* RHO = reinterpret_cast<double*>(st + S.rho);
+    V4* RHOF = reinterpret_cast<V4*>(st + S.rhof);
+    V4* RF = reinterpret_cast<V4*>(st + S.rf);
+    double* D2 = reinterpret_cast<double*>(st + S.d2);
+    LP* Y = reinterpret_cast<LP*>(st + S.y);
+    LP* V = reinterpret_cast<LP*>(st + S.v);
+    const int na_m = D.na, nc_m = D.nc;
+    double* GX = reinterpret_cast<double*>(work + D.work_off);          // positions, SoA
+    LP* GDL = reinterpret_cast<LP*>(work + D.work_off + 24 * (int64_t)na_m);  // owned corrections
+    double* GLAM = reinterpret_cast<double*>(work + D.work_off + 24 * (int64_t)na_m + 8 * (int64_t)nc_m);
+    auto gid = [&](int al) -> int64_t {
+        return D.atom_base >= 0 ? (int64_t)D.atom_base + al : (int64_t)A.atom_gid[D.gid_off + al];
+    };
+    auto inv = [&](int p) -> LP { return reinterpret_cast<const LP*>(RF + p)[3]; };
+    const unsigned nb = gridDim.x + phantom;
+    long long budget = kSpinBudget;
+    // ---- S1: x_old of the domain's atoms (staged in X), weights
+    for (int k = r0; k < na; k += ts) {
+        const int64_t g = gid(AML[k]);
+        for (int c = 0; c < 3; ++c) X[c * na + k] = A.x_old[3 * g + c];
+        const double w = A.inv_mass[g];
+        WL[k] = to_lp<LP>(w);
+        if (k < no) W[k] = w;
+    }
+    if (r0 == 0) WL[na] = LP(0);
+    __syncthreads();
+    // rho, reference rows, d^2; starting multipliers of the owned constraints
+    for (int p = r0; p < nc; p += ts) {
+        const int i = (int)(CON[p] & 0xFFFFu), j = (int)(CON[p] >> 16);
+        const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+        RHO[p] = rx;
+        RHO[nc + p] = ry;
+        RHO[2 * nc + p] = rz;
+        V4 v;
+        v.x = to_lp<LP>(rx);
+        v.y = to_lp<LP>(ry);
+        v.z = to_lp<LP>(rz);
+        v.w = WL[i] + WL[j];
+        RHOF[p] = v;
+        const uint32_t cm = CML[p];
+        const int cl = (int)(cm & 0x7FFFFFFFu);
+        const int32_t g = __ldg(con_gid + cl);
+        const double dd = A.d[g];
+        D2[p] = dd * dd;
+        if (cm >> 31) {
+            float l0 = A.lambda0 ? A.lambda0[g] : 0.0f;
+            if (A.start_diag) {
+                const int64_t gi = gid(AML[i]), gj = gid(AML[j]);
+                float u[3], o[3];
+                for (int c = 0; c < 3; ++c) {
+                    u[c] = narrow(A.x_unc[3 * gi + c]) - narrow(A.x_unc[3 * gj + c]);
+                    o[c] = narrow(X[c * na + i]) - narrow(X[c * na + j]);
+                }
+                l0 = diag_start(u[0], u[1], u[2], o[0], o[1], o[2], narrow(dd), f32_of(WL[i]) + f32_of(WL[j]));
+            }
+            GDL[cl] = (LP)l0;
+            GLAM[cl] = widen(l0);
+        }
+    }
+    __syncthreads();
+    for (int k = r0; k < no; k += ts) {  // owned atoms start at x_unc
+        const int al = AML[k];
+        const int64_t g = gid(al);
+        for (int c = 0; c < 3; ++c) {
+            const double v = A.x_unc[3 * g + c];
+            X[c * na + k] = v;
+            GX[c * (int64_t)na_m + al] = v;
+        }
+    }
+    // x_a -= w_a sum_p s_p(a) 2 delta_p rho_p over the owned atom's constraints, with the
+    // owners' corrections (own ones from Y)
+    auto update_owned = [&](bool from_y) {
+        for (int kk = r0; kk < no; kk += ts) {
+            const int k = (int)AORD[kk];
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            for (int e = IP[k]; e < IP[k + 1]; ++e) {
+                const uint32_t v = IV[e];
+                const int p = (int)(v >> 1);
+                const uint32_t cm = CML[p];
+                const LP dl = (from_y && (cm >> 31)) ? Y[p] : __ldcg(GDL + (cm & 0x7FFFFFFFu));
+                const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
+                ax = fma(c, RHO[p], ax);
+                ay = fma(c, RHO[nc + p], ay);
+                az = fma(c, RHO[2 * nc + p], az);
+            }
+            const double w = W[k];
+            const int al = AML[k];
+            const double x = fma(-w, ax, X[k]), y = fma(-w, ay, X[na + k]), z = fma(-w, az, X[2 * na + k]);
+            X[k] = x;
+            X[na + k] = y;
+            X[2 * na + k] = z;
+            GX[al] = x;
+            GX[(int64_t)na_m + al] = y;
+            GX[2 * (int64_t)na_m + al] = z;
+        }
+    };
+    bool alive = grid_sync(&sync->barrier, nb, budget);
+    if (alive && A.has_start()) {  // x = x_unc - M^-1 G(x_old)^T lambda0
+        update_owned(false);
+        alive = grid_sync(&sync->barrier, nb, budget);
+    }
+    int status = ILVES_MOL_MAX_ITER, iters = A.max_iter;
+    for (int it = 0; alive; ++it) {
+        const int slot = it & 3;
+        for (int k = no + r0; k < na; k += ts) {  // the halo's current positions
+            const int al = AML[k];
+            for (int c = 0; c < 3; ++c) X[c * na + k] = __ldcg(GX + c * (int64_t)na_m + al);
+        }
+        __syncthreads();
+        // ---- violations of the domain's constraints (the owned ones vote), Jacobian rows
+        const bool rows = !A.chord || it == 0;
+        bool conv = true, bad = false;
+        for (int p = r0; p < nc; p += ts) {
+            const int i = (int)(CON[p] & 0xFFFFu), j = (int)(CON[p] >> 16);
+            const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+            const double d2 = D2[p];
+            const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
+            if (CML[p] >> 31) {
+                conv = conv && abs_le(sg, A.tol * d2);
+                bad = bad || nonfinite(sg);
+            }
+            Y[p] = to_lp<LP>(sg);
+            if (rows) {
+                V4 v;
+                v.x = to_lp<LP>(rx);
+                v.y = to_lp<LP>(ry);
+                v.z = to_lp<LP>(rz);
+                v.w = LP(0);
+                RF[p] = v;
+            }
+        }
+        const int nconv = __syncthreads_count(!conv);
+        const int anybad = __syncthreads_or(bad);
+        if (r0 == 0) {
+            if (nconv) atomicAdd(&sync->notconv[slot], nconv);
+            if (anybad) atomicOr(&sync->bad[slot], 1);
+        }
+        // ---- the domain's Newton step (speculative: the vote is read after the barrier)
+        bool singular = false;
+        if (A.chord && it == 0) {  // ILVES-F: the reference rows, factorised once
+            for (int p = r0; p < nc; p += ts) RF[p] = RHOF[p];
+            __syncthreads();
+        }
+        int e = (int)LANE[r0];
+        for (int l = 0; l < (int)H.nlev; ++l) {
+            const int p0 = LPV[l], np = LPV[l + 1] - p0, t0 = LTK[l], t1 = LTK[l + 1];
+            for (int t = t0 + r0; t < t1; t += ts) {
+                const uint2 w = TK[t];
+                const int n = (int)(w.y >> 24);
+                const bool diag = t < t0 + np;
+                if (!rows) {  // ILVES-F after its first iteration: forward substitution only
+                    if (diag) {
+                        LP yv = LP(0);
+                        for (int k = e; k < e + n; ++k) {
+                            const uint32_t tr = TM[k];
+                            yv += V[DomTerm::l(tr)] * inv((int)DomTerm::m(tr)) * Y[DomTerm::m(tr)];
+                        }
+                        Y[p0 + (t - t0)] -= yv;
+                    }
+                    e += n;
+                    continue;
+                }
+                const uint32_t rc = w.x & 0xFFFFu, cc = w.x >> 16, ac = w.y & 0xFFFFu;
+                const V4 rr = RF[rc], pp = RHOF[cc];
+                const LP wv = diag ? pp.w : (ac == 0xFFFFu ? LP(0) : WL[ac]);
+                const LP cf = ((w.y >> 16) & 1u) ? LP(-4) * wv : LP(4) * wv;
+                const LP a = cf * (rr.x * pp.x + rr.y * pp.y + rr.z * pp.z);
+                LP sacc = a, yv = LP(0);
+#pragma unroll 2
+                for (int k = e; k < e + n; ++k) {
+                    const uint32_t tr = TM[k];
+                    const int m = (int)DomTerm::m(tr);
+                    const LP li = V[DomTerm::l(tr)] * inv(m);
+                    sacc -= li * V[DomTerm::u(tr)];
+                    if (diag) yv += li * Y[m];
+                }
+                e += n;
+                V[t] = sacc;
+                if (diag) {
+                    singular = singular || !(lp_abs(sacc) > Mode::pivot_rel * lp_abs(a));
+                    reinterpret_cast<LP*>(RF + rc)[3] = lp_rcp(sacc);
+                    Y[rc] -= yv;
+                }
+            }
+            __syncthreads();
+        }
+        for (int l = (int)H.nlev - 1; l >= 0; --l) {  // backward substitution
+            const int p1 = LPV[l + 1];
+            for (int p = LPV[l] + r0; p < p1; p += ts) {
+                const uint32_t pv = PV[p];
+                const int us = (int)(pv & 0xFFFFu), nu = (int)(pv >> 16);
+                LP dl = Y[p];
+                for (int k = 0; k < nu; ++k) dl -= V[us + k] * Y[TK[us + k].x >> 16];
+                Y[p] = dl * inv(p);
+            }
+            __syncthreads();
+        }
+        for (int p = r0; p < nc; p += ts)  // the owned corrections, for the other domains
+            if (CML[p] >> 31) GDL[CML[p] & 0x7FFFFFFFu] = Y[p];
+        if (__syncthreads_or(singular) && r0 == 0) atomicOr(&sync->singular[slot], 1);
+        if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+        const int any_bad = __ldcg(&sync->bad[slot]), any_nc = __ldcg(&sync->notconv[slot]);
+        const int any_sing = __ldcg(&sync->singular[slot]);
+        if (dm == 0 && r0 == 0) {  // free the slot used two iterations from now
+            sync->notconv[(it + 2) & 3] = 0;
+            sync->bad[(it + 2) & 3] = 0;
+            sync->singular[(it + 2) & 3] = 0;
+        }
+        if (any_bad) {
+            status = ILVES_MOL_NONFINITE;
+            iters = it;
+            break;
+        }
+        if (any_nc == 0) {
+            status = ILVES_MOL_CONVERGED;
+            iters = it;
+            break;
+        }
+        if (it >= A.max_iter) break;
+        if (any_sing) {
+            status = ILVES_MOL_SINGULAR_PIVOT;
+            iters = it;
+            break;
+        }
+        // ---- lambda += delta of the owned constraints; the owned atoms move
+        for (int p = r0; p < nc; p += ts)
+            if (CML[p] >> 31) {
+                const int cl = (int)(CML[p] & 0x7FFFFFFFu);
+                GLAM[cl] = GLAM[cl] + to_hp(Y[p]);
+            }
+        update_owned(true);
+        if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
+    }
+    if (!alive) {
+        status = ILVES_MOL_WAIT_TIMEOUT;
+        if (r0 == 0) atomicOr(&sync->timeout, 1);
+    }
+    for (int k = r0; k < no; k += ts) {
+        const int64_t g = gid(AML[k]);
+        for (int c = 0; c < 3; ++c) A.x_out[3 * g + c] = X[c * na + k];
+    }
+    if (A.lambda_out)
+        for (int p = r0; p < nc; p += ts)
+            if (CML[p] >> 31) {
+                const int cl = (int)(CML[p] & 0x7FFFFFFFu);
+                A.lambda_out[__ldg(con_gid + cl)] = GLAM[cl];
+            }
+    if (dm == 0 && r0 == 0) {
+        if (A.iterations_out) A.iterations_out[D.mol_id] = iters;
+        if (A.status_out) A.status_out[D.mol_id] = status;
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
 constexpr int kStaticSlotSmem = 64;  // bytes: the pool-ticket words of the slots of a CTA
@@ -1904,8 +2211,14 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     T->n_large = (int32_t)order.size() - T->n_small;
     T->parted_desc.clear();
     for (int32_t m = 0; m < T->n_mol; ++m)
-        if (T->mols[m].parted) {
+        if (T->mols[m].parted && !T->mols[m].opm) {
             T->parted_desc.push_back((int32_t)order.size());
+            order.push_back(m);
+        }
+    T->opm_desc.clear();
+    for (int32_t m = 0; m < T->n_mol; ++m)
+        if (T->mols[m].opm) {
+            T->opm_desc.push_back((int32_t)order.size());
             order.push_back(m);
         }
     std::vector<int32_t> desc_index(T->n_mol);
@@ -1934,8 +2247,12 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         D.n_sept = M.n_sept;
         D.n_cent = M.n_cent;
         D.pprog_bytes = M.pprog_bytes;
+        D.opm = M.opm;
         D.work_off = 0;
-        if (M.large) {  // state, then (partitioned) 4 contribution values per separator task
+        if (M.opm) {  // overlapping domains: positions (SoA), owned corrections, lambda
+            D.work_off = woff;
+            woff += (24 * (int64_t)na + 16 * (int64_t)D.nc + 255) & ~int64_t(255);
+        } else if (M.large) {  // state, then (partitioned) 4 contribution values per separator task
             D.work_off = woff;
             const int64_t st = std::max(state_layout(na, D.nc, M.ntask, 8, false).bytes,
                                         state_layout(na, D.nc, M.ntask, 4, true).bytes);
@@ -1959,8 +2276,8 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     if (T->n_atoms > 0 && (e = cudaMalloc((void**)&T->d_ws_atom, (size_t)T->n_atoms * sizeof(float))) != cudaSuccess)
         return to_status(e);
     if (woff > 0 && (e = cudaMalloc((void**)&T->d_work, woff)) != cudaSuccess) return to_status(e);
-    if (!T->parted_desc.empty()) {
-        T->sync_bytes = (int64_t)T->parted_desc.size() * (int64_t)sizeof(PartSync);
+    if (!T->parted_desc.empty() || !T->opm_desc.empty()) {
+        T->sync_bytes = (int64_t)(T->parted_desc.size() + T->opm_desc.size()) * (int64_t)sizeof(PartSync);
         if ((e = cudaMalloc((void**)&T->d_sync, T->sync_bytes)) != cudaSuccess) return to_status(e);
     }
     // persistent schedules, one per precision mode
@@ -1990,7 +2307,7 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         if ((e = upload(&DS.slot_mol, HS.slot_mol)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_off, HS.slot_off)) != cudaSuccess) return to_status(e);
     }
-    if (T->n_large > 0 || !T->parted_desc.empty()) {
+    if (T->n_large > 0 || !T->parted_desc.empty() || !T->opm_desc.empty()) {
         cudaStream_t s;
         cudaEvent_t a, b;
         if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return to_status(e);
@@ -2019,7 +2336,7 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
         if (e != cudaSuccess) return to_status(e);
         T->smem_attr_set[Mode::id] = true;
     }
-    const bool side_work = T->n_large > 0 || !T->parted_desc.empty();
+    const bool side_work = T->n_large > 0 || !T->parted_desc.empty() || !T->opm_desc.empty();
     if (side_work) {
         cudaStream_t side = (cudaStream_t)T->side_stream;
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_fork, stream)) != cudaSuccess) return to_status(e);
@@ -2029,8 +2346,35 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
             if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
             ++launches;
         }
-        if (!T->parted_desc.empty()) {
+        if (!T->parted_desc.empty() || !T->opm_desc.empty()) {
             if ((e = cudaMemsetAsync(sync, 0, T->sync_bytes, side)) != cudaSuccess) return to_status(e);
+        }
+        if constexpr (!Mode::df) {  // overlapping domains: one cooperative launch per molecule
+            for (size_t k = 0; k < T->opm_desc.size(); ++k) {
+                const int32_t di = T->opm_desc[k];
+                const MolHost& MH = T->mols[T->desc_mol[di]];
+                // the programs staged in shared memory when every domain still fits the SMs
+                // with them, else read from global memory (state in shared memory either way)
+                const int q = sizeof(typename Mode::LP) == 8 ? 1 : 0;
+                const int per_sm = (MH.n_dom + T->n_sm - 1) / std::max(1, T->n_sm);
+                uint32_t staged = (int64_t)per_sm * (MH.dom_smem[q] + 1024) <= 233472 && MH.dom_smem[q] <= 232448;
+                const int smem = staged ? MH.dom_smem[q] : MH.dom_smem[2 + q];
+                if ((e = cudaFuncSetAttribute(k_solve_opm<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+                    cudaSuccess)
+                    return to_status(e);
+                const MolDesc* dptr = T->d_desc + di;
+                PartSync* sp = reinterpret_cast<PartSync*>(sync) + T->parted_desc.size() + k;
+                SolveArgs Aa = A;
+                uint32_t ph = (uint32_t)T->wait_test;
+                void* args[] = {(void*)&dptr, (void*)&T->d_blob, (void*)&work, (void*)&sp,
+                                (void*)&Aa,   (void*)&ph,        (void*)&staged};
+                if ((e = cudaLaunchCooperativeKernel((const void*)k_solve_opm<Mode>, dim3(MH.n_dom), dim3(kPartThreads),
+                                                     args, (size_t)smem, side)) != cudaSuccess)
+                    return to_status(e);
+                ++launches;
+            }
+        }
+        if (!T->parted_desc.empty()) {
             for (size_t k = 0; k < T->parted_desc.size(); ++k) {
                 const int32_t di = T->parted_desc[k];
                 const MolHost& MH = T->mols[T->desc_mol[di]];
@@ -2170,6 +2514,7 @@ extern "C" void ilves_default_opts(ilves_setup_opts* o) {
     o->partition_min_constraints = 0;
     o->part_constraints = 0;
     o->wait_test = 0;
+    o->overlap = 0;
 }
 
 extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const int32_t* atom_i,
@@ -2183,7 +2528,8 @@ extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constrai
     ilves_default_opts(&o);
     if (opts) o = *opts;
     if (o.ordering < 0 || o.ordering > 2 || o.degree_slack < 0 || o.warps_per_cta < 0 ||
-        o.warps_per_cta > 16 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4 || o.wait_test < 0 || o.wait_test > 64)
+        o.warps_per_cta > 16 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4 || o.wait_test < 0 || o.wait_test > 64 ||
+        o.overlap < 0 || o.overlap > 16)
         return ILVES_ERR_INVALID_ARG;
     ilves_topology* T = new ilves_topology();
     T->wait_test = o.wait_test;
@@ -2234,6 +2580,8 @@ extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, cons
     if (A.start_diag && lambda0) return ILVES_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
+    if ((precision & ~(ILVES_CHORD | ILVES_START_DIAG)) == ILVES_PREC_MIXED_DF && !T->opm_desc.empty())
+        return ILVES_ERR_INVALID_ARG;  // overlapping domains run in the float64 and mixed modes
     switch (precision & ~(ILVES_CHORD | ILVES_START_DIAG)) {
         case ILVES_PREC_FP64: return launch_mode<ModeFP64>(T, A, s);
         case ILVES_PREC_MIXED: return launch_mode<ModeMixed>(T, A, s);
@@ -2254,6 +2602,7 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     const int32_t prec_mode = precision & ~(ILVES_CHORD | ILVES_START_DIAG);
     if ((precision & ILVES_START_DIAG) && lambda0) return ILVES_ERR_INVALID_ARG;
     if (prec_mode < ILVES_PREC_FP64 || prec_mode > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
+    if (prec_mode == ILVES_PREC_MIXED_DF && !T->opm_desc.empty()) return ILVES_ERR_INVALID_ARG;
     const uint64_t work_aligned = ((uint64_t)T->work_bytes + 255) & ~uint64_t(255);
     if (work_aligned + (uint64_t)T->sync_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
     int dev = -1;
@@ -2336,9 +2685,17 @@ extern "C" ilves_status ilves_topology_molecules(const ilves_topology* T, int32_
     return ILVES_OK;
 }
 
+extern "C" ilves_status ilves_topology_export_domains(const ilves_topology* T, int32_t mol, int32_t* n_dom,
+                                                      int32_t* atom_bounds, int32_t* con_ptr, int32_t* con_gid,
+                                                      int32_t* owned) {
+    if (!T || mol < 0 || mol >= T->n_mol) return ILVES_ERR_INVALID_ARG;
+    program_export_domains(T, mol, n_dom, atom_bounds, con_ptr, con_gid, owned);
+    return ILVES_OK;
+}
+
 extern "C" ilves_status ilves_topology_export_molecule(const ilves_topology* T, int32_t mol, int32_t* pos_gid,
                                                        int32_t* level, int32_t* up_ptr, int32_t* up_idx) {
-    if (!T || mol < 0 || mol >= T->n_mol) return ILVES_ERR_INVALID_ARG;
+    if (!T || mol < 0 || mol >= T->n_mol || T->mols[mol].opm) return ILVES_ERR_INVALID_ARG;
     program_export(T, mol, pos_gid, level, up_ptr, up_idx);
     return ILVES_OK;
 }

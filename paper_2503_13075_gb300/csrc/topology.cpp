@@ -153,6 +153,11 @@ struct Program {
     std::vector<uint32_t> pprog_off;  // per part, the separator program, its end
     uint32_t pprog_max = 0;           // largest part program (bytes)
     int32_t sep_interior = 0;         // separator-program terms on interior pivots
+    // overlapping domains: the whole blob, and per domain its part bounds (atoms), constraints
+    // (molecule-local, ascending) with owned flags, levels and program bytes
+    std::vector<uint8_t> opm_blob;
+    std::vector<int32_t> dom_bounds, dom_con_ptr, dom_cons, dom_levels, dom_bytes;
+    std::vector<uint8_t> dom_owned;
 };
 
 // Part programs of a partitioned molecule (16-bit part-local encoding of the part's
@@ -542,6 +547,229 @@ static std::vector<int32_t> partition_atoms(int32_t na, const std::vector<int32_
     return bounds;
 }
 
+// ------------------------------------------------------------------------------------
+// overlapping domains (supplement Sec. 3, the Overlapping Partitioning Method)
+// ------------------------------------------------------------------------------------
+struct DomainPlan {
+    std::vector<int32_t> atoms;  // molecule-local atoms: the part's own (in order), then the halo (ascending)
+    int32_t na_own = 0;
+    std::vector<int32_t> cons;   // molecule-local constraints between domain atoms, ascending
+    std::vector<uint8_t> owned;  // per entry of cons: the part owns it (holds its smaller atom)
+};
+
+// Part d owns atoms [bounds[d], bounds[d + 1]) and the constraints whose smaller atom it
+// owns; its domain adds every atom within `overlap` edges of its atoms (breadth-first over
+// the constraint graph) and holds the constraints whose two atoms are domain atoms.
+static std::vector<DomainPlan> opm_domains(int32_t na, const std::vector<int32_t>& ci, const std::vector<int32_t>& cj,
+                                           const std::vector<int32_t>& bounds, int32_t overlap) {
+    const int32_t nc = (int32_t)ci.size(), nd = (int32_t)bounds.size() - 1;
+    std::vector<std::vector<int32_t>> inc(na);
+    for (int32_t c = 0; c < nc; ++c) {
+        inc[ci[c]].push_back(c);
+        inc[cj[c]].push_back(c);
+    }
+    std::vector<int32_t> part_of(na), amark(na, -1), cmark(nc, -1);
+    for (int32_t d = 0; d < nd; ++d)
+        for (int32_t a = bounds[d]; a < bounds[d + 1]; ++a) part_of[a] = d;
+    std::vector<DomainPlan> D(nd);
+    std::vector<int32_t> frontier, next, halo;
+    for (int32_t d = 0; d < nd; ++d) {
+        DomainPlan& P = D[d];
+        frontier.clear();
+        halo.clear();
+        for (int32_t a = bounds[d]; a < bounds[d + 1]; ++a) {
+            amark[a] = d;
+            P.atoms.push_back(a);
+            frontier.push_back(a);
+        }
+        P.na_own = (int32_t)P.atoms.size();
+        for (int32_t step = 0; step < overlap; ++step) {
+            next.clear();
+            for (int32_t a : frontier)
+                for (int32_t c : inc[a]) {
+                    const int32_t b = ci[c] == a ? cj[c] : ci[c];
+                    if (amark[b] != d) {
+                        amark[b] = d;
+                        next.push_back(b);
+                        halo.push_back(b);
+                    }
+                }
+            frontier.swap(next);
+        }
+        std::sort(halo.begin(), halo.end());
+        P.atoms.insert(P.atoms.end(), halo.begin(), halo.end());
+        for (int32_t a : P.atoms)
+            for (int32_t c : inc[a])
+                if (cmark[c] != d && amark[ci[c]] == d && amark[cj[c]] == d) {
+                    cmark[c] = d;
+                    P.cons.push_back(c);
+                }
+        std::sort(P.cons.begin(), P.cons.end());
+        for (int32_t c : P.cons) P.owned.push_back(part_of[std::min(ci[c], cj[c])] == d ? 1 : 0);
+    }
+    return D;
+}
+
+// One domain's program (see DomProgHeader) appended to `out` (16-byte aligned); false if the
+// domain exceeds the 16-bit encoding.  loc: scratch of one entry per molecule atom, all -1.
+static bool build_domain_program(const DomainPlan& P, const std::vector<int32_t>& ci, const std::vector<int32_t>& cj,
+                                 std::vector<int32_t>& loc, std::vector<uint8_t>& out, int32_t& nlev, int32_t& ntask,
+                                 int32_t& nterm, int64_t& n_fill, uint32_t smem[4]) {
+    const int32_t na = (int32_t)P.atoms.size(), ne = (int32_t)P.cons.size(), no = P.na_own;
+    if (na >= 0xFFFF || ne >= (int32_t)DomTerm::kMaxCons) return false;
+    for (int32_t k = 0; k < na; ++k) loc[P.atoms[k]] = k;
+    std::vector<int32_t> eci(ne), ecj(ne);
+    std::vector<std::vector<int32_t>> ainc(na);
+    for (int32_t e = 0; e < ne; ++e) {
+        eci[e] = loc[ci[P.cons[e]]];
+        ecj[e] = loc[cj[P.cons[e]]];
+        ainc[eci[e]].push_back(e);
+        ainc[ecj[e]].push_back(e);
+    }
+    for (int32_t a : P.atoms) loc[a] = -1;
+    std::vector<std::vector<int32_t>> adj(ne);
+    for (int32_t a = 0; a < na; ++a)
+        for (int32_t x : ainc[a])
+            for (int32_t y : ainc[a])
+                if (x != y) adj[x].push_back(y);
+    for (auto& v : adj) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    // elimination order: rounds of independent near-minimum-degree pivots, the slack giving
+    // the fewest levels, then the fewest terms
+    Program Q;
+    int64_t best = -1;
+    for (int32_t slack : {2, 3, 4, 6}) {
+        Program C = compile(ne, eliminate_rounds(ne, adj, slack, false), eci, ecj, kPartThreads, na);
+        const int64_t key = ((int64_t)C.nlevel << 40) + (int64_t)C.terms.size();
+        if (best < 0 || key < best) {
+            best = key;
+            Q = std::move(C);
+        }
+    }
+    const int32_t nt = (int32_t)Q.tasks.size() - 1;
+    if (nt >= (int32_t)DomTerm::kMaxSlots || Q.terms.size() >= (size_t)UINT32_MAX) return false;
+    for (int32_t t = 0; t < nt; ++t)
+        if (Q.tasks[t + 1].tstart - Q.tasks[t].tstart > 255u) return false;
+    std::vector<int32_t> pos_of(ne);
+    for (int32_t p = 0; p < ne; ++p) pos_of[Q.pos_con[p]] = p;
+    int32_t n_inc = 0;
+    for (int32_t a = 0; a < no; ++a) n_inc += (int32_t)ainc[a].size();
+    const DomProgLayout L = dom_prog_layout(na, no, ne, nt, (uint32_t)Q.terms.size(), Q.nlevel, n_inc);
+    const size_t base = out.size();
+    out.resize(base + L.bytes, 0);
+    uint8_t* d = out.data() + base;
+    const DomProgHeader H{(uint32_t)na, (uint32_t)no, (uint32_t)ne, (uint32_t)nt, (uint32_t)Q.terms.size(),
+                          (uint32_t)Q.nlevel, (uint32_t)n_inc, 0u};
+    std::memcpy(d, &H, sizeof(H));
+    auto* lp = reinterpret_cast<uint16_t*>(d + L.lvl_piv);
+    auto* lt = reinterpret_cast<uint16_t*>(d + L.lvl_task);
+    for (int32_t l = 0; l <= Q.nlevel; ++l) {
+        lp[l] = (uint16_t)Q.lvl_piv[l];
+        lt[l] = (uint16_t)Q.lvl_task[l];
+    }
+    auto* lane = reinterpret_cast<uint32_t*>(d + L.lane_term);
+    auto* tm = reinterpret_cast<uint32_t*>(d + L.terms);
+    size_t o = 0;
+    for (int32_t r = 0; r < kPartThreads; ++r) {
+        lane[r] = (uint32_t)o;
+        for (int32_t l = 0; l < Q.nlevel; ++l)
+            for (int32_t t = Q.lvl_task[l] + r; t < Q.lvl_task[l + 1]; t += kPartThreads)
+                for (uint32_t k = Q.tasks[t].tstart; k < Q.tasks[t + 1].tstart; ++k)
+                    tm[o++] = DomTerm::make(Q.terms[k].l, Q.terms[k].u, Q.terms[k].m);
+    }
+    auto* pv = reinterpret_cast<uint32_t*>(d + L.piv);
+    auto* con = reinterpret_cast<uint32_t*>(d + L.con);
+    auto* cml = reinterpret_cast<uint32_t*>(d + L.con_ml);
+    for (int32_t p = 0; p < ne; ++p) {
+        const int32_t e = Q.pos_con[p];
+        pv[p] = (uint32_t)Q.ustart[p] | ((uint32_t)Q.up[p].size() << 16);
+        con[p] = (uint32_t)eci[e] | ((uint32_t)ecj[e] << 16);
+        cml[p] = (uint32_t)P.cons[e] | (P.owned[e] ? 0x80000000u : 0u);
+    }
+    std::memcpy(d + L.atom_ml, P.atoms.data(), 4u * (size_t)na);
+    auto* ip = reinterpret_cast<uint16_t*>(d + L.inc_ptr);
+    auto* iv = reinterpret_cast<uint16_t*>(d + L.inc);
+    int32_t k = 0;
+    for (int32_t a = 0; a < no; ++a) {
+        ip[a] = (uint16_t)k;
+        for (int32_t e : ainc[a]) iv[k++] = (uint16_t)(((uint32_t)pos_of[e] << 1) | (ecj[e] == a ? 1u : 0u));
+    }
+    ip[no] = (uint16_t)k;
+    std::vector<int32_t> ord(no);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return ainc[x].size() > ainc[y].size(); });
+    auto* ao = reinterpret_cast<uint16_t*>(d + L.aorder);
+    for (int32_t a = 0; a < no; ++a) ao[a] = (uint16_t)ord[a];
+    auto* tw = reinterpret_cast<uint32_t*>(d + L.tasks);
+    for (int32_t t = 0; t < nt; ++t) {
+        const TaskW& w = Q.tasks[t];
+        const uint32_t a = w.atomsign >> 1;
+        const uint32_t ac = (w.row == w.col || a >= (uint32_t)na) ? 0xFFFFu : a;
+        tw[2 * t] = w.row | (w.col << 16);
+        tw[2 * t + 1] = ac | ((w.atomsign & 1u) << 16) | ((Q.tasks[t + 1].tstart - w.tstart) << 24);
+    }
+    nlev = Q.nlevel;
+    ntask = nt;
+    nterm = (int32_t)Q.terms.size();
+    n_fill = Q.n_fill;
+    smem[2] = dom_state_layout(na, no, ne, nt, 4).bytes;
+    smem[3] = dom_state_layout(na, no, ne, nt, 8).bytes;
+    smem[0] = L.bytes + smem[2];
+    smem[1] = L.bytes + smem[3];
+    return true;
+}
+
+// The OPM blob of molecule M (OpmBlobHeader, domain offsets, constraint ids, programs) with
+// parts of about part_size constraints; false if a domain does not fit the encoding.
+static bool build_opm(Program& P, MolHost& M, int32_t part_size, int32_t overlap, int32_t max_parts) {
+    const int32_t na = (int32_t)M.atoms.size(), nc = (int32_t)M.cons.size();
+    const int32_t n_parts = std::max(2, std::min(max_parts, (nc + part_size - 1) / part_size));
+    P.dom_bounds = partition_atoms(na, M.ci, M.cj, n_parts);
+    const std::vector<DomainPlan> doms = opm_domains(na, M.ci, M.cj, P.dom_bounds, overlap);
+    const int32_t nd = (int32_t)doms.size();
+    const uint32_t head = align16((uint32_t)sizeof(OpmBlobHeader) + 4u * (nd + 1));
+    const uint32_t progs = align16(head + 4u * (uint32_t)nc);
+    P.opm_blob.assign(progs, 0);
+    std::vector<uint32_t> off(nd + 1, 0);
+    std::vector<int32_t> loc(na, -1);
+    P.dom_con_ptr.assign(1, 0);
+    P.dom_cons.clear();
+    P.dom_owned.clear();
+    P.dom_levels.assign(nd, 0);
+    P.dom_bytes.assign(nd, 0);
+    for (int32_t& v : M.dom_smem) v = 0;
+    M.nlevel = M.ntask = M.nterm = 0;
+    M.n_fill = 0;
+    for (int32_t d = 0; d < nd; ++d) {
+        off[d] = (uint32_t)P.opm_blob.size();
+        int32_t nl = 0, nt = 0, ntm = 0;
+        int64_t fill = 0;
+        uint32_t sm[4];
+        if (!build_domain_program(doms[d], M.ci, M.cj, loc, P.opm_blob, nl, nt, ntm, fill, sm)) return false;
+        P.dom_levels[d] = nl;
+        P.dom_bytes[d] = (int32_t)(P.opm_blob.size() - off[d]);
+        for (int q = 0; q < 4; ++q) M.dom_smem[q] = std::max<int32_t>(M.dom_smem[q], (int32_t)sm[q]);
+        M.nlevel = std::max(M.nlevel, nl);
+        M.ntask += nt;
+        M.nterm += ntm;
+        M.n_fill += fill;
+        P.dom_cons.insert(P.dom_cons.end(), doms[d].cons.begin(), doms[d].cons.end());
+        P.dom_owned.insert(P.dom_owned.end(), doms[d].owned.begin(), doms[d].owned.end());
+        P.dom_con_ptr.push_back((int32_t)P.dom_cons.size());
+    }
+    off[nd] = (uint32_t)P.opm_blob.size();
+    const OpmBlobHeader H{(uint32_t)nd, (uint32_t)overlap, 0u, 0u};
+    std::memcpy(P.opm_blob.data(), &H, sizeof(H));
+    std::memcpy(P.opm_blob.data() + sizeof(H), off.data(), 4u * (nd + 1));
+    std::memcpy(P.opm_blob.data() + head, M.cons.data(), 4u * (size_t)nc);  // global constraint ids
+    M.n_dom = nd;
+    M.n_seg = nd;
+    M.nlevel = std::max(M.nlevel, 1);
+    return true;
+}
+
 // Kernel cost model (cycles per Newton iteration for one team): a level pass costs
 // roughly one shared-memory round trip plus a few FMAs; work is spread over lanes.
 static double program_cost(const Program& P, int32_t team) {
@@ -808,6 +1036,41 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
         }
         M.large = nc > warp_limit || nc >= (int32_t)kCompactMaxConstraints || na > (int32_t)TaskWord::kMaxAtom;
         const int32_t part_min = o.partition_min_constraints > 0 ? o.partition_min_constraints : 4096;
+        if (nc >= part_min && o.overlap > 0) {
+            // overlapping domains: parts of ~part_size constraints, each domain widened by
+            // `overlap` edges; all domains run at once (cooperative launch), so their number
+            // and shared memory must fit the device: at most three per SM, each domain's
+            // float64-mode state within an SM's share (a domain's program is staged in shared
+            // memory too when that also fits, else read from global memory)
+            M.large = M.parted = true;
+            M.opm = o.overlap;
+            Program* P = new Program();
+            const int32_t n_sm = T->n_sm > 0 ? T->n_sm : 152;
+            int32_t part_size = o.part_constraints > 0 ? o.part_constraints : 256;
+            bool ok = false;
+            for (int attempt = 0; attempt < 16 && !ok; ++attempt) {
+                const int32_t max_parts = o.part_constraints > 0 ? 8192 : 3 * n_sm;
+                if (!build_opm(*P, M, part_size, o.overlap, max_parts)) {
+                    part_size = std::max(16, part_size * 3 / 4);  // a domain outgrew the encoding
+                    continue;
+                }
+                if (o.part_constraints > 0) {
+                    ok = true;
+                    break;
+                }
+                const int32_t per_sm = (M.n_dom + n_sm - 1) / n_sm;
+                ok = per_sm <= 3 && (int64_t)per_sm * (M.dom_smem[3] + 1024) <= 233472 &&
+                     M.dom_smem[3] <= 232448;
+                if (!ok) part_size = part_size * 5 / 4;
+            }
+            if (!ok) {
+                delete P;
+                return ILVES_ERR_TOPOLOGY;
+            }
+            M.passes = 0;
+            T->progs[m] = P;
+            continue;
+        }
         if (nc >= part_min) {
             // partitioned: parts of ~part_size constraints eliminated first, separators last
             M.large = M.parted = true;
@@ -898,12 +1161,15 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
 
 int64_t program_blob_bytes(const ilves_topology* T, int32_t m) {
     const MolHost& M = T->mols[m];
+    if (M.opm) return (int64_t)T->progs[m]->opm_blob.size();
     return M.large ? layout_for<uint32_t>(M).bytes : layout_for<uint16_t>(M).bytes;
 }
 
 void program_write_blob(const ilves_topology* T, int32_t m, uint8_t* dst) {
     const MolHost& M = T->mols[m];
-    if (M.large)
+    if (M.opm)
+        std::memcpy(dst, T->progs[m]->opm_blob.data(), T->progs[m]->opm_blob.size());
+    else if (M.large)
         write_blob<uint32_t>(dst, M, *T->progs[m]);
     else
         write_blob<uint16_t>(dst, M, *T->progs[m]);
@@ -934,6 +1200,23 @@ void program_export_layout(const ilves_topology* T, int32_t m, int32_t* atom_gid
     const int32_t na = (int32_t)M.atoms.size();
     if (atom_gid)
         for (int32_t a = 0; a < na; ++a) atom_gid[a] = M.atoms[M.aperm.empty() ? a : M.aperm[a]];
+    if (M.opm) {  // overlapping domains: the domains' levels and program bytes
+        const int32_t nd = (int32_t)P.dom_levels.size();
+        if (n_parts) *n_parts = nd;
+        int32_t mx = 0;
+        for (int32_t d = 0; d < nd; ++d) {
+            if (part_levels) part_levels[d] = P.dom_levels[d];
+            if (part_prog_bytes) part_prog_bytes[d] = P.dom_bytes[d];
+            mx = std::max(mx, P.dom_bytes[d]);
+        }
+        if (sep_summary) {  // no separator block: the domains' shared memory instead
+            sep_summary[0] = 0;
+            sep_summary[1] = M.dom_smem[0];
+            sep_summary[2] = M.dom_smem[3];
+            sep_summary[3] = mx;
+        }
+        return;
+    }
     const int32_t np = M.parted ? P.n_seg - 1 : 0;
     if (n_parts) *n_parts = np;
     const bool have_parts = M.parted && P.pprog_max > 0;
@@ -946,6 +1229,23 @@ void program_export_layout(const ilves_topology* T, int32_t m, int32_t* atom_gid
         sep_summary[1] = M.parted ? M.sprog_bytes : 0;
         sep_summary[2] = M.parted ? M.sep_interior : 0;
         sep_summary[3] = M.parted ? M.pprog_max : 0;
+    }
+}
+
+void program_export_domains(const ilves_topology* T, int32_t m, int32_t* n_dom, int32_t* atom_bounds,
+                            int32_t* con_ptr, int32_t* con_gid, int32_t* owned) {
+    const MolHost& M = T->mols[m];
+    const Program& P = *T->progs[m];
+    const int32_t nd = M.opm ? (int32_t)P.dom_levels.size() : 0;
+    if (n_dom) *n_dom = nd;
+    if (!M.opm) return;
+    for (int32_t d = 0; d <= nd; ++d) {
+        if (atom_bounds) atom_bounds[d] = P.dom_bounds[d];
+        if (con_ptr) con_ptr[d] = P.dom_con_ptr[d];
+    }
+    for (size_t k = 0; k < P.dom_cons.size(); ++k) {
+        if (con_gid) con_gid[k] = M.cons[P.dom_cons[k]];
+        if (owned) owned[k] = P.dom_owned[k];
     }
 }
 

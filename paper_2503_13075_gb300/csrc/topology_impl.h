@@ -32,6 +32,11 @@ struct MolHost {
     int32_t pprog_max = 0;           // partitioned: largest part program (bytes; 0 = none)
     int32_t sprog_bytes = 0;         // partitioned: bytes of the separator program (0 = none)
     int32_t sep_interior = 0;        // partitioned: separator terms on interior pivots (read from global)
+    int32_t opm = 0;                 // overlapping domains: overlap depth (0 = not solved by domains)
+    int32_t n_dom = 0;               // overlapping domains: number of domains (CTAs)
+    // overlapping domains: largest shared memory of a domain, program staged + state
+    // (float32 / float64 factor), then state only (program read from global memory)
+    int32_t dom_smem[4] = {0, 0, 0, 0};
     int64_t passes = 0;
 };
 
@@ -99,6 +104,7 @@ struct ilves_topology {
     int32_t parted_max_ctas = 0;
     int32_t last_launches = 0;
     int32_t wait_test = 0;                   // testing: phantom CTAs the partitioned grid barriers wait for
+    std::vector<int32_t> opm_desc;           // descriptor indices of molecules solved by overlapping domains
     bool smem_attr_set[3] = {false, false, false};
 };
 
@@ -115,4 +121,6 @@ void program_export(const ilves_topology* T, int32_t m, int32_t* pos_gid, int32_
 void program_export_layout(const ilves_topology* T, int32_t m, int32_t* atom_gid, int32_t* n_parts,
                            int32_t* part_levels, int32_t* part_prog_bytes, int32_t* sep_summary);
 void free_programs(ilves_topology* T);
+void program_export_domains(const ilves_topology* T, int32_t m, int32_t* n_dom, int32_t* atom_bounds,
+                            int32_t* con_ptr, int32_t* con_gid, int32_t* owned);
 }  // namespace ilves

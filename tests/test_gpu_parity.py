@@ -387,3 +387,62 @@ def test_hydroxyl_angle_distances(prec, case):
     for start in (None, "diag"):
         _, x, lam, it, st = run(s, prec, topo=t, start=start)
         compare(s, ref, x, lam, it, st, it_slack=1 if start is None else 2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("overlap", [2, 4])
+def test_overlapping_domains(prec, overlap):
+    """Overlapping domains (supplement Sec. 3, Overlapping Partitioning Method): every domain
+    of a cooperative launch solves its own system and keeps its owned corrections.  The
+    quasi-Newton iteration reaches the Newton oracle's root within the parity bounds, in the
+    iterations of the oracle's own overlapping-domain iteration (+-1 from a zero start)."""
+    s = wl.protein_like(n_atoms=12000, seed=1040, xoh=True)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, part_constraints=256,
+                   overlap=overlap)
+    assert t.n_large == 1 and t.export_layout(0)["n_parts"] > 10
+    ref = orc.solve_system(s, tol=TOL)
+    ref_opm = orc.solve_system(s, tol=TOL, overlap=overlap, part_constraints=256, part_min=2000)
+    for start in (None, "diag"):
+        _, x, lam, it, st = run(s, prec, topo=t, start=start)
+        assert st.tolist() == [B.CONVERGED]
+        if start is None:
+            assert abs(int(it[0]) - int(ref_opm.iterations[0])) <= 1
+        assert np.abs(x - ref.x).max() <= X_TOL
+        assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL
+        assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
+    with pytest.raises(B.IlvesError) as e:  # domains run in the float64 and mixed modes only
+        run(s, "mixed_df", topo=t)
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_overlapping_domains_chord(prec):
+    """ILVES-F over overlapping domains: each domain factorises A(x_old, x_old) on its
+    constraints once; same root, iterations within +-1 of the oracle's."""
+    s = wl.protein_like(n_atoms=8000, seed=1041)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, part_constraints=256, overlap=4)
+    ref = orc.solve_system(s, tol=TOL)
+    ref_c = orc.solve_system(s, tol=TOL, max_iter=80, method="chord", overlap=4, part_constraints=256, part_min=2000)
+    _, x, lam, it, st = run(s, prec, topo=t, method="chord", max_iter=80)
+    assert st.tolist() == [B.CONVERGED]
+    assert abs(int(it[0]) - int(ref_c.iterations[0])) <= 1
+    assert np.abs(x - ref.x).max() <= X_TOL
+    assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_overlapping_domains_full_size(prec, protein_full):
+    """The 100,001-atom system over overlapping domains (overlap 4, automatic part size):
+    parity with the Newton oracle; the planner's domains are the oracle's, and the iteration
+    count is within +-1 of the oracle's overlapping-domain iteration."""
+    s, ref, _ = protein_full
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, overlap=4)
+    D = t.export_domains(0)
+    part = int(np.ceil(s.n_constraints / (len(D["cons"]))))
+    _, x, lam, it, st = run(s, prec, topo=t)
+    assert st.tolist() == [B.CONVERGED]
+    assert np.abs(x - ref.x).max() <= X_TOL
+    assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
+    if len(D["cons"]) == -(-s.n_constraints // 256):  # the default part size held
+        ref_opm = orc.solve_system(s, tol=TOL, overlap=4, part_constraints=256, part_min=4096)
+        assert abs(int(it[0]) - int(ref_opm.iterations[0])) <= 1

@@ -305,3 +305,29 @@ def test_partition_threshold_and_ring_atom_order():
     for m in range(t.n_molecules):
         gid = t.export_layout(m)["atom_gid"]
         assert gid.size == 12 and list(deg[gid]) == [3] * 6 + [1] * 6
+
+
+@pytest.mark.parametrize("overlap,part", [(1, 256), (3, 256), (4, 180)])
+def test_overlapping_domains_match_the_oracle(overlap, part):
+    """The planner's overlapping domains (greedy partition, halo of `overlap` edges, owned
+    constraints) are exactly the oracle's, which derives them independently."""
+    from oracle import ilves_oracle as orc
+
+    s = wl.protein_like(n_atoms=8000, seed=1006, xoh=True)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, overlap=overlap, part_constraints=part,
+                   partition_min_constraints=2000)
+    D = t.export_domains(0)
+    ai, aj = s.atom_i.astype(np.int64), s.atom_j.astype(np.int64)
+    atoms = np.unique(np.concatenate([ai, aj]))
+    li, lj = np.searchsorted(atoms, ai), np.searchsorted(atoms, aj)
+    b = orc.greedy_partition(atoms.size, li, lj, max(2, -(-len(ai) // part)))
+    assert np.array_equal(np.asarray(b), D["atom_bounds"])
+    doms = orc.opm_domains(atoms.size, li, lj, b, overlap)
+    assert len(doms) == len(D["cons"])
+    for (cons, owned), c2, o2 in zip(doms, D["cons"], D["owned"]):
+        assert np.array_equal(cons, c2) and np.array_equal(owned, o2)
+    owned_all = np.concatenate([c[o] for c, o in zip(D["cons"], D["owned"])])
+    assert np.array_equal(np.sort(owned_all), np.arange(s.n_constraints))  # each owned once
+    # the exact-Newton molecule export is refused for a molecule solved by domains
+    with pytest.raises(B.IlvesError):
+        t.export_molecule(0)

@@ -375,3 +375,64 @@ def test_average_relative_error_follows_the_paper_formula():
     ai, aj, d = np.array([0, 2, 4]), np.array([1, 3, 5]), np.array([1.0, 1.0, 2.0])
     assert orc.average_relative_error(x, ai, aj, d) == pytest.approx(0.04 / 6.0, rel=1e-12)
     assert orc.max_relative_violation(x, ai, aj, d) == pytest.approx(0.02, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------- overlapping domains
+def _chain_indices(n):
+    return np.arange(n - 1), np.arange(1, n)
+
+
+def test_greedy_partition_of_a_chain_is_even():
+    """On a path every boundary cuts one constraint, so the greedy partition (supplement
+    Sec. 3) ends each part at the size nearest its target: equal parts when they divide."""
+    ai, aj = _chain_indices(600)
+    assert orc.greedy_partition(600, ai, aj, 6) == [0, 100, 200, 300, 400, 500, 600]
+
+
+def test_greedy_partition_avoids_cuts_within_its_window():
+    """A part boundary inside a 3-cycle cuts two constraints; the partition moves it to a
+    single-cut position within maxDeviation of the target (cutPenalty 10 outweighs the size
+    term)."""
+    n = 200
+    ai, aj = list(range(n - 1)), list(range(1, n))
+    ai.append(99)  # triangle 99-100-101: a boundary at 100 or 101 cuts two constraints
+    aj.append(101)
+    b = orc.greedy_partition(n, np.array(ai), np.array(aj), 2)
+    assert b == [0, 102, 200] or b == [0, 99, 200]
+
+
+def test_overlapping_domains_of_a_chain():
+    """Chain of 40 atoms in parts [0, 10), [10, 20), ...: with overlap I the domain of part
+    [a, b) holds atoms [a - I, b + I) (clipped) and the constraints between them; the part
+    owns the constraints (k, k + 1) with a <= k < b."""
+    n, I = 40, 3
+    ai, aj = _chain_indices(n)
+    doms = orc.opm_domains(n, ai, aj, [0, 10, 20, 30, 40], I)
+    for dpart, (cons, owned) in enumerate(doms):
+        a, b = 10 * dpart, 10 * dpart + 10
+        lo, hi = max(0, a - I), min(n, b + I)
+        assert cons.tolist() == list(range(lo, hi - 1))
+        assert cons[owned].tolist() == [k for k in range(a, b) if k < n - 1]
+
+
+@pytest.mark.parametrize("overlap", [2, 4])
+def test_opm_reaches_the_newton_root(overlap):
+    """The overlapping-domain quasi-Newton iteration solves the same constraint equations: it
+    converges to ILVES-M's root (supplement Sec. 3), in more iterations for a small overlap."""
+    s = wl.protein_like(n_atoms=5000, seed=1003)
+    ref = orc.solve_system(s, tol=1e-13)
+    got = orc.solve_system(s, tol=1e-13, overlap=overlap, part_constraints=300, part_min=1000)
+    assert np.all(got.status == orc.CONVERGED)
+    assert np.abs(got.x - ref.x).max() <= 1e-10
+    np.testing.assert_allclose(got.lam, ref.lam, rtol=1e-7, atol=1e-12 * np.abs(ref.lam).max())
+    assert got.iterations[0] >= ref.iterations[0]
+
+
+def test_opm_with_domains_covering_the_molecule_is_newton():
+    """When every domain holds the whole molecule, each domain's local solve is the full
+    Newton solve and the owned entries assemble A^-1 sigma: the iterates are Newton's."""
+    s = wl.protein_like(n_atoms=1500, seed=1004)
+    ref = orc.solve_system(s, tol=1e-13)
+    got = orc.solve_system(s, tol=1e-13, overlap=10_000, part_constraints=400, part_min=500)
+    assert np.array_equal(got.iterations, ref.iterations)
+    np.testing.assert_allclose(got.history, ref.history, rtol=1e-6, atol=1e-15)
