@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-precision comparators")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="tree_batch", choices=["tree_batch", "protein_like", "chain64", "serving"],
+    p.add_argument("--workload", default="tree_batch",
+                   choices=["tree_batch", "protein_like", "chain64", "serving", "learned_start"],
                    help="tree_batch (default line); protein_like / chain64 print lines for the other configurations")
     p.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson request rate (1/s)")
     p.add_argument("--duration", type=float, default=1.0, help="serving: seconds of arrivals")
@@ -640,6 +641,102 @@ def run_ilves(args):
     print(json.dumps(res))
 
 
+def run_learned_start(args):
+    """Learned warm start on the chain64 distribution: the network is trained on 500,000
+    (features, lambda) pairs of the plain float64 solver (7,937 chains, seed 2000) by the
+    library's kernels, then held-out chains (4096, seed 9100) are solved from the zero, the
+    diagonal and the learned start at the same tolerance.  Reported per start: time per step
+    (the learned start's feature and network kernels included), Newton solves, and the
+    starting violation max_k |sigma_k| / d_k^2 per chain; for the network also its error
+    relative to each chain's largest |lambda| (float64 solve as reference)."""
+    import torch
+
+    from paper_2503_13075_gb300 import binding as B
+    from paper_2503_13075_gb300 import warmstart as ws
+    from paper_2503_13075_gb300 import workloads as wl
+
+    rank, world, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    feat, y, ok = ws.chain_training_set(n_pairs=500_000, seed=2000, dev=dev)
+    t1 = time.perf_counter()
+    mlp = B.Mlp(max_batch=8192, seed=1)
+    losses = ws.train(mlp, feat, y, epochs=30, batch=8192, lr=3e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    train = {"pairs": int(feat.shape[0]), "labels_converged": bool(ok), "epochs": 30, "final_mse": losses[-1],
+             "target_variance": float(y.var().item()), "data_s": round(t1 - t0, 2),
+             "train_s": round(time.perf_counter() - t1, 2), "train_seed": 2000}
+    s = wl.chain_batch(4096, seed=9100)
+    topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    dev_in = (f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d))
+    out = (torch.empty_like(dev_in[1]), torch.empty(s.n_constraints, dtype=torch.float64, device=dev),
+           torch.empty(topo.n_molecules, dtype=torch.int32, device=dev),
+           torch.empty(topo.n_molecules, dtype=torch.int32, device=dev))
+    lam0 = torch.empty(s.n_constraints, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    mol = np.repeat(np.arange(4096), 63)
+    _, lam_ref, _, _ = topo.solve(*dev_in, tol=args.tol, precision="fp64")
+    lam_ref = lam_ref.cpu().numpy()
+    scale = np.zeros(4096)
+    np.maximum.at(scale, mol, np.abs(lam_ref))
+    rows, rows_loose = {}, {}
+    for start in ("none", "diag", "mlp"):  # the same three starts at a looser tolerance, 1e-8
+        step = make_step(topo, dev_in, out, args.precision, 1e-8, start, mlp, lam0)
+        ms, _ = time_device(step, max(3, args.steps // 2), 2, flush, stream)
+        it = out[2].cpu().numpy()
+        rows_loose[start] = {"ms_per_step": sum(ms) / len(ms), "all_converged": bool(np.all(out[3].cpu().numpy() == 0)),
+                             "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(it)) if v}}
+    for start in ("none", "diag", "mlp"):
+        l0 = None
+        if start == "diag":
+            l0 = B.warm_start(None, topo, *dev_in, out=lam0)
+        elif start == "mlp":
+            l0 = B.warm_start(mlp, topo, *dev_in, out=lam0)
+        x0 = topo.solve(*dev_in, tol=args.tol, precision=args.precision, lambda0=l0, max_iter=0)[0].cpu().numpy()
+        r = x0[s.atom_i] - x0[s.atom_j]
+        v0 = np.abs(np.einsum("ij,ij->i", r, r) - s.d ** 2) / s.d ** 2
+        vm = np.zeros(4096)
+        np.maximum.at(vm, mol, v0)
+        step = make_step(topo, dev_in, out, args.precision, args.tol, start, mlp, lam0)
+        ms, launches = time_device(step, args.steps, args.warmup, flush, stream)
+        st = out[3].cpu().numpy()
+        it = out[2].cpu().numpy()
+        per = sum(ms) / len(ms)
+        row = {"ms_per_step": per, "value": s.n_atoms / (per * 1e-3), "all_converged": bool(np.all(st == 0)),
+               "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(it)) if v},
+               "max_rel_violation": max_rel_violation(out[0].cpu().numpy(), s.atom_i, s.atom_j, s.d),
+               "start_violation_per_chain": {"median": float(np.median(vm)), "p90": float(np.percentile(vm, 90)),
+                                             "max": float(vm.max())},
+               "gpu_launches": launches}
+        if l0 is not None:
+            e = np.abs(l0.cpu().numpy().astype(np.float64) - lam_ref) / scale[mol]
+            row["lambda0_error_over_chain_max"] = {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)),
+                                                   "max": float(e.max())}
+        rows[start] = row
+    if rank != 0:
+        return
+    res = {
+        "metric": METRIC, "value": rows["mlp"]["value"], "unit": "atoms*solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows["mlp"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f64+f32", "fp64": "f64", "mixed_df": "f32x2+f32"}[args.precision], "data": "synthetic",
+        "config": {"workload": "learned_start: 4096 held-out chain64-distribution chains (262,144 atoms, 258,048 "
+                               "constraints), network trained on 500,000 pairs of other chains",
+                   "precision": args.precision, "tol": args.tol, "l2": "flushed (256 MiB write) before every timed step",
+                   "network": "16-128-128-1, bfloat16 weights and inputs, float32 accumulation (tcgen05)"},
+        "starts": rows,
+        "speedup_mlp_vs_zero": rows["none"]["ms_per_step"] / rows["mlp"]["ms_per_step"],
+        "speedup_mlp_vs_diag": rows["diag"]["ms_per_step"] / rows["mlp"]["ms_per_step"],
+        "training": train,
+        "two_solve_requirement": "2 Newton solves at 1e-12 need a starting violation below ~1.7e-3 per chain",
+        "starts_at_tol_1e-8": rows_loose,
+    }
+    print(json.dumps(res))
+
+
 def run_serving(args):
     """Serving loop: Poisson requests over a pool of device-resident topologies."""
     import torch
@@ -704,6 +801,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "learned_start":
+        run_learned_start(args)
     else:
         run_ilves(args)
 

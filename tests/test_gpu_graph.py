@@ -1,5 +1,5 @@
-"""ilves_solve inside a captured CUDA graph: the batched (persistent) and the partitioned
-(cooperative, side stream) solves capture into one graph whose replays give, bit for
+"""ilves_solve inside a captured CUDA graph: the batched (persistent), the partitioned and
+the overlapping-domain (cooperative, side stream) solves capture into one graph whose replays give, bit for
 bit, the eager solve's results -- also after new inputs are copied into the captured
 buffers (one replay per MD step).  The solve allocates nothing, so capture needs no
 special mode."""
@@ -14,12 +14,16 @@ from paper_2503_13075_gb300 import workloads as wl  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("case", ["trees", "protein_parted"])
+@pytest.mark.parametrize("case", ["trees", "protein_parted", "protein_domains"])
 def test_solve_replays_from_a_cuda_graph(case):
     dev = torch.device("cuda:0")
     if case == "trees":
         s = wl.tree_batch(n_mol=256, seed=1012)
         t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    elif case == "protein_domains":
+        s = wl.protein_like(n_atoms=12000, seed=1014)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, overlap=4)
+        assert t.n_large == 1
     else:
         s = wl.protein_like(n_atoms=12000, seed=1013)
         t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000)

@@ -340,12 +340,13 @@ def test_partitioned_grid_barrier_wait_runs_out():
     import time
 
     s = wl.protein_like(n_atoms=6000, seed=1020)
-    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=1000, wait_test=1)
-    assert t.n_large == 1
-    t0 = time.perf_counter()
-    _, x, lam, it, st = run(s, "mixed", topo=t)
-    assert time.perf_counter() - t0 < 20.0
-    assert st.tolist() == [B.WAIT_TIMEOUT]
+    for overlap in (0, 4):  # the Schur-complement and the overlapping-domain kernels
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=1000, wait_test=1, overlap=overlap)
+        assert t.n_large == 1
+        t0 = time.perf_counter()
+        _, x, lam, it, st = run(s, "mixed", topo=t)
+        assert time.perf_counter() - t0 < 20.0
+        assert st.tolist() == [B.WAIT_TIMEOUT]
     ref = orc.solve_system(s, tol=TOL)
     t2 = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=1000)
     _, x, lam, it, st = run(s, "mixed", topo=t2)
