@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-precision comparators")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default set-up options (no ilves_autotune)")
     p.add_argument("--workload", default="tree_batch",
                    choices=["tree_batch", "protein_like", "chain64", "serving", "learned_start"],
                    help="tree_batch (default line); protein_like / chain64 print lines for the other configurations")
@@ -436,6 +437,12 @@ def run_ilves(args):
     lam0 = torch.empty(s.n_constraints, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tuning = None
+    if not args.no_autotune and args.method == "newton":  # set-up time, outside every timed region
+        t_tune = time.perf_counter()
+        tuning = topo.autotune(*dev_in, tol=args.tol, precision=args.precision,
+                               start="diag" if args.warm_start == "diag" else None, reps=5)
+        tuning["seconds"] = round(time.perf_counter() - t_tune, 2)
 
     mlp, mlp_info = None, None
     if args.warm_start == "mlp" or (not args.no_compare and args.workload == "tree_batch"):
@@ -450,7 +457,8 @@ def run_ilves(args):
     ablation = []
     value64 = per64 = None
     if not args.no_compare:
-        precs = ("fp64", "mixed") if args.overlap else ("fp64", "mixed", "mixed_df")
+        precs = ("fp64", "mixed") if (args.overlap or (tuning and tuning["chosen"]["overlap"])) \
+            else ("fp64", "mixed", "mixed_df")
         combos = [(p, w, "newton") for p in precs for w in ("none", "diag", "mlp")]
         combos += [(p, w, "chord") for p in precs for w in ("none", "diag")]
         for prec, wsn, meth in combos:
@@ -471,7 +479,8 @@ def run_ilves(args):
     # overlapping domains are a quasi-Newton method: the plain FP64 GPU Newton solve they are
     # compared with is ILVES-M itself (exact Newton, Schur complement over the separators)
     exact64 = None
-    if args.overlap and not args.no_compare:
+    uses_domains = bool(args.overlap or (tuning and tuning["chosen"]["overlap"]))
+    if uses_domains and not args.no_compare:
         topo_exact = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
         step_e = make_step(topo_exact, dev_in, out, "fp64", args.tol, "none", None, lam0, "newton")
         msa, _ = time_device(step_e, max(3, args.steps // 4), 2, flush, stream)
@@ -566,7 +575,7 @@ def run_ilves(args):
     ab = algorithmic_bytes(s)
     solve_per = sum(solve_ms) / len(solve_ms)
     achieved = ab / (solve_per * 1e-3) / 1e9
-    kname = ("k_solve_opm" if args.overlap else "k_solve_parted") if s.name == "protein_like" else "k_solve_small"
+    kname = ("k_solve_opm" if uses_domains else "k_solve_parted") if s.name == "protein_like" else "k_solve_small"
     fp64 = None
     if args.precision == "mixed" and args.method == "newton":  # the float64 pipe, beside the HBM roofline
         mol_atoms, mol_cons, _, _ = topo.molecules()
@@ -610,9 +619,10 @@ def run_ilves(args):
             "method": {"newton": "ILVES-M (Newton)", "chord": "ILVES-F (chord)"}[args.method],
             "tol": args.tol,
             "l2": "flushed (256 MiB write) before every timed step",
-            "schedule": (("cooperative CTAs over overlapping domains (overlap %d), quasi-Newton" % args.overlap
-                          if args.overlap else "cooperative CTAs over partitions + separator (Schur) block")
+            "schedule": (("cooperative CTAs over overlapping domains (overlap %d), quasi-Newton" % topo.tuning()["chosen"]["overlap"]
+                          if uses_domains else "cooperative CTAs over partitions + separator (Schur) block")
                          if s.name == "protein_like" else "persistent CTAs, one 96-thread team per molecule"),
+            "autotune": tuning,
         },
         "valid": valid,
         "max_rel_violation": viol,

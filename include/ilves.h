@@ -136,6 +136,16 @@ typedef struct {
 /* Fills `opts` with the defaults. */
 void ilves_default_opts(ilves_setup_opts* opts);
 
+/* Outcome of ilves_autotune: the set-up options the topology now runs with (`chosen`), how
+ * many configurations were timed, and the mean time of one solve (ms, CUDA events) in the
+ * chosen configuration and in the one the topology had before tuning. */
+typedef struct {
+    ilves_setup_opts chosen;
+    int32_t candidates;   /* 0: the topology was never tuned */
+    float best_ms;
+    float before_ms;
+} ilves_tuning;
+
 /*
  * Builds the solver's view of a constraint topology (supplement Sec. 3,
  * initialisation): connected components (molecules), the line graph L(G) whose
@@ -225,6 +235,33 @@ ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_ol
                                         int32_t max_iter, int32_t precision, const float* lambda0,
                                         double* x_out, double* lambda_out, int32_t* iterations_out,
                                         int32_t* mol_status_out, void* stream);
+
+/*
+ * Measured autotuning of a set-up topology (no counterpart in the paper: the paper tunes
+ * nothing at run time).  Re-plans the topology under candidate set-up options, one knob at
+ * a time from its current options -- the batched kernel's molecule slots per CTA
+ * (warps_per_cta 8, 7, 6), CTAs per SM (1, 2), the elimination order (per-molecule cost
+ * model, or rounds with degree slack 1 or 3), and for molecules above the partition
+ * threshold the exact Schur complement (overlap 0) or overlapping domains of depth 2, 3, 4
+ * or 6 -- times `reps` solves of each on the given inputs (CUDA events on `stream`, after
+ * one untimed solve), and keeps the fastest configuration whose solves all converge.  The
+ * topology keeps its identity; its programs, schedules and workspace are replaced.
+ * Results of the tuned topology meet the same tolerances; they may differ in rounding
+ * (another elimination order) and in iteration counts (overlapping domains).
+ *  Inputs as for ilves_solve (DEVICE or page-locked host buffers); precision as for
+ *  ilves_solve (the mode to tune for; overlapping domains are skipped for ILVES_PREC_MIXED_DF);
+ *  reps >= 1; out: HOST, may be NULL.
+ * Synchronous (it synchronises `stream`); allocates device memory for its own outputs and the
+ * candidate topologies, so call it at set-up, not inside a time step or a stream capture.
+ * Errors: ILVES_ERR_INVALID_ARG, ILVES_ERR_OOM, ILVES_ERR_CUDA.
+ */
+ilves_status ilves_autotune(ilves_topology* topo, const double* x_old, const double* x_unc, const double* inv_mass,
+                            const double* d, double tol, int32_t precision, int32_t reps, void* stream,
+                            ilves_tuning* out);
+
+/* The topology's last tuning (out->candidates == 0 if ilves_autotune never ran on it; the
+ * chosen options are then the set-up options). */
+ilves_status ilves_topology_tuning(const ilves_topology* topo, ilves_tuning* out);
 
 /* Device memory (bytes) a set-up topology holds: programs, schedules, workspaces. */
 int64_t ilves_topology_device_bytes(const ilves_topology* topo);

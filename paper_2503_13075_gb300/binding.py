@@ -40,6 +40,11 @@ class SetupOpts(ctypes.Structure):
                 ("wait_test", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("chosen", SetupOpts), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("before_ms", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -67,6 +72,10 @@ def lib():
     L.ilves_topology_molecules.restype = I32
     L.ilves_topology_export_molecule.argtypes = [P, I32, P, P, P, P]
     L.ilves_topology_export_molecule.restype = I32
+    L.ilves_autotune.argtypes = [P, P, P, P, P, D, I32, I32, VP, ctypes.POINTER(Tuning)]
+    L.ilves_autotune.restype = I32
+    L.ilves_topology_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+    L.ilves_topology_tuning.restype = I32
     L.ilves_topology_export_domains.argtypes = [P, I32, P, P, P, P, P]
     L.ilves_topology_export_domains.restype = I32
     L.ilves_topology_export_layout.argtypes = [P, I32, P, P, P, P, P]
@@ -164,13 +173,16 @@ class Topology:
         self.n_constraints = int(ai.size)
         self.plan_only = plan_only
         self._device_index = None if device is None else int(device)
+        self._refresh_info()
+
+    def _refresh_info(self):
         n = ctypes.c_int32()
         nnz = ctypes.c_int64()
         ml = ctypes.c_int32()
         fill = ctypes.c_int64()
         nl = ctypes.c_int32()
-        _check(L.ilves_topology_info(h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(ml), ctypes.byref(fill),
-                                     ctypes.byref(nl)), "ilves_topology_info")
+        _check(lib().ilves_topology_info(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(ml),
+                                         ctypes.byref(fill), ctypes.byref(nl)), "ilves_topology_info")
         self.n_molecules, self.nnz_factor, self.max_levels = n.value, nnz.value, ml.value
         self.n_fill, self.n_large = fill.value, nl.value
 
@@ -227,6 +239,34 @@ class Topology:
         return {"atom_gid": gid[:na], "n_parts": npart, "part_levels": lev[:npart], "part_prog_bytes": pb[:npart],
                 "sep_levels": int(sep[0]), "sep_prog_bytes": int(sep[1]), "sep_interior_terms": int(sep[2]),
                 "part_prog_max": int(sep[3])}
+
+    @staticmethod
+    def _tuning_dict(t):
+        c = t.chosen
+        return {"candidates": t.candidates, "best_ms": t.best_ms, "before_ms": t.before_ms,
+                "chosen": {f: getattr(c, f) for f, _ in SetupOpts._fields_ if f not in ("device", "wait_test")}}
+
+    def autotune(self, x_old, x_unc, inv_mass, d, tol=1e-12, precision="mixed", start=None, reps=5, stream=None):
+        """``ilves_autotune``: time candidate set-up options on these inputs and keep the fastest
+        (the topology is re-planned in place); returns the tuning as a dict."""
+        import torch
+
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if start == "diag":
+            prec |= START_DIAG
+        t = Tuning()
+        s = torch.cuda.current_stream(x_unc.device if x_unc.is_cuda else None).cuda_stream if stream is None \
+            else stream.cuda_stream
+        _check(lib().ilves_autotune(self._h, _ptr(x_old), _ptr(x_unc), _ptr(inv_mass), _ptr(d), float(tol), prec,
+                                    int(reps), ctypes.c_void_p(s), ctypes.byref(t)), "ilves_autotune")
+        self._refresh_info()
+        return self._tuning_dict(t)
+
+    def tuning(self):
+        """``ilves_topology_tuning``: the last autotuning (candidates == 0: never tuned)."""
+        t = Tuning()
+        _check(lib().ilves_topology_tuning(self._h, ctypes.byref(t)), "ilves_topology_tuning")
+        return self._tuning_dict(t)
 
     def export_domains(self, mol=0):
         """``ilves_topology_export_domains``: overlapping domains of one molecule as a dict with

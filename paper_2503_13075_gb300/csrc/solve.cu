@@ -25,6 +25,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -2174,6 +2175,21 @@ static const void* small_kernel() {
     return (const void*)k_solve_small<Mode>;
 }
 
+// The batched kernel's dynamic shared-memory limit belongs to the kernel (per device), not
+// to a topology: it is raised to the largest arena any topology launches it with, so
+// topologies with different arenas (CTAs per SM) can alternate on one device.
+constexpr int kMaxAttrDevices = 64;
+static std::mutex g_attr_mutex;
+static int g_small_smem[kMaxAttrDevices][3] = {};
+static cudaError_t ensure_small_smem(int dev, int mode, const void* fn, int arena) {
+    if (dev < 0 || dev >= kMaxAttrDevices) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, arena);
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (g_small_smem[dev][mode] >= arena) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, arena);
+    if (e == cudaSuccess) g_small_smem[dev][mode] = arena;
+    return e;
+}
+
 static ilves_status to_status(cudaError_t e) {
     if (e == cudaSuccess) return ILVES_OK;
     if (e == cudaErrorMemoryAllocation) return ILVES_ERR_OOM;
@@ -2331,11 +2347,8 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
     cudaError_t e;
     int launches = 0;
     const DeviceSchedule& DS = T->sched[Mode::id];
-    if (!T->smem_attr_set[Mode::id]) {
-        e = cudaFuncSetAttribute(small_kernel<Mode>(), cudaFuncAttributeMaxDynamicSharedMemorySize, DS.arena);
-        if (e != cudaSuccess) return to_status(e);
-        T->smem_attr_set[Mode::id] = true;
-    }
+    if ((e = ensure_small_smem(T->device, Mode::id, small_kernel<Mode>(), DS.arena)) != cudaSuccess)
+        return to_status(e);
     const bool side_work = T->n_large > 0 || !T->parted_desc.empty() || !T->opm_desc.empty();
     if (side_work) {
         cudaStream_t side = (cudaStream_t)T->side_stream;
@@ -2533,6 +2546,8 @@ extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constrai
         return ILVES_ERR_INVALID_ARG;
     ilves_topology* T = new ilves_topology();
     T->wait_test = o.wait_test;
+    T->opts = o;
+    T->tuning.chosen = o;
     // the planner sizes partitioned molecules for the device's SM count (all parts of a
     // cooperative launch must be resident at once); a host-only plan assumes 152 SMs
     if (o.device != -2) {
@@ -2634,6 +2649,155 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
         case ILVES_PREC_MIXED: return launch_all<ModeMixed>(T, A, s, scratch, sync);
         default: return launch_all<ModeMixedDF>(T, A, s, scratch, sync);
     }
+}
+
+// ------------------------------------------------------------------------------------
+// autotuning: candidate set-up options, each timed on the caller's inputs
+// ------------------------------------------------------------------------------------
+namespace {
+struct TuneBuffers {
+    double* x = nullptr;
+    double* lam = nullptr;
+    int32_t* it = nullptr;
+    int32_t* st = nullptr;
+    ~TuneBuffers() {
+        cudaFree(x);
+        cudaFree(lam);
+        cudaFree(it);
+        cudaFree(st);
+    }
+};
+
+// Mean milliseconds of one ilves_solve over `reps` (after one untimed solve); < 0 if a solve
+// failed or some molecule did not converge.
+float time_solves(ilves_topology* T, const double* x_old, const double* x_unc, const double* inv_mass,
+                  const double* d, double tol, int32_t precision, int32_t reps, cudaStream_t s, TuneBuffers& B,
+                  std::vector<int32_t>& status_host) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.f;
+    float ms = -1.f;
+    const int32_t max_iter = (precision & ILVES_CHORD) ? 60 : 25;
+    auto one = [&]() {
+        return ilves_solve(T, x_old, x_unc, inv_mass, d, tol, max_iter, precision, nullptr, B.x, B.lam, B.it, B.st, s);
+    };
+    bool ok = one() == ILVES_OK && cudaStreamSynchronize(s) == cudaSuccess;
+    if (ok) {
+        cudaEventRecord(e0, s);
+        for (int32_t r = 0; r < reps && ok; ++r) ok = one() == ILVES_OK;
+        cudaEventRecord(e1, s);
+        ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (ok) ms /= (float)reps;
+    }
+    status_host.assign(T->n_mol, 0);
+    if (ok && T->n_mol > 0)
+        ok = cudaMemcpy(status_host.data(), B.st, sizeof(int32_t) * T->n_mol, cudaMemcpyDeviceToHost) == cudaSuccess;
+    for (int32_t v : status_host) ok = ok && v == ILVES_MOL_CONVERGED;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ok ? ms : -1.f;
+}
+
+bool same_opts(const ilves_setup_opts& a, const ilves_setup_opts& b) { return std::memcmp(&a, &b, sizeof(a)) == 0; }
+}  // namespace
+
+extern "C" ilves_status ilves_autotune(ilves_topology* T, const double* x_old, const double* x_unc,
+                                       const double* inv_mass, const double* d, double tol, int32_t precision,
+                                       int32_t reps, void* stream, ilves_tuning* out) {
+    if (!T || !T->on_device || reps < 1) return ILVES_ERR_INVALID_ARG;
+    const int32_t mode = precision & ~(ILVES_CHORD | ILVES_START_DIAG);
+    if (mode < ILVES_PREC_FP64 || mode > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
+    if (T->n_atoms > 0 && (!x_old || !x_unc || !inv_mass)) return ILVES_ERR_INVALID_ARG;
+    if (T->n_c > 0 && !d) return ILVES_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != T->device) return ILVES_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    TuneBuffers buf;
+    cudaError_t e;
+    if (T->n_atoms > 0 && (e = cudaMalloc((void**)&buf.x, sizeof(double) * 3 * (size_t)T->n_atoms)) != cudaSuccess)
+        return to_status(e);
+    if (T->n_c > 0 && (e = cudaMalloc((void**)&buf.lam, sizeof(double) * (size_t)T->n_c)) != cudaSuccess)
+        return to_status(e);
+    if (T->n_mol > 0) {
+        if ((e = cudaMalloc((void**)&buf.it, sizeof(int32_t) * T->n_mol)) != cudaSuccess) return to_status(e);
+        if ((e = cudaMalloc((void**)&buf.st, sizeof(int32_t) * T->n_mol)) != cudaSuccess) return to_status(e);
+    }
+    std::vector<int32_t> stat;
+    const ilves_setup_opts base = T->opts;
+    const float before = time_solves(T, x_old, x_unc, inv_mass, d, tol, precision, reps, s, buf, stat);
+    if (before < 0.f) return ILVES_ERR_CUDA;
+    // candidates: one knob at a time away from the current options
+    bool has_small = T->n_small > 0, has_parted = false;
+    for (const auto& M : T->mols) has_parted = has_parted || M.parted;
+    std::vector<ilves_setup_opts> cands;
+    auto add = [&](ilves_setup_opts c) {
+        for (const auto& x : cands)
+            if (same_opts(x, c)) return;
+        if (!same_opts(c, base)) cands.push_back(c);
+    };
+    if (has_small) {
+        for (int32_t w : {8, 7, 6}) {
+            ilves_setup_opts c = base;
+            c.warps_per_cta = w;
+            add(c);
+        }
+        {
+            ilves_setup_opts c = base;
+            c.ctas_per_sm = base.ctas_per_sm == 2 ? 1 : 2;
+            add(c);
+        }
+        for (int32_t slack : {-1, 1, 3}) {
+            ilves_setup_opts c = base;
+            c.ordering = slack < 0 ? 0 : 2;
+            c.degree_slack = slack < 0 ? 2 : slack;
+            add(c);
+        }
+    }
+    if (has_parted) {
+        for (int32_t ov : {0, 2, 3, 4, 6}) {
+            if (ov > 0 && mode == ILVES_PREC_MIXED_DF) continue;
+            ilves_setup_opts c = base;
+            c.overlap = ov;
+            add(c);
+        }
+    }
+    float best = before;
+    ilves_topology* winner = nullptr;
+    ilves_setup_opts best_opts = base;
+    for (const ilves_setup_opts& c : cands) {
+        ilves_topology* C = new ilves_topology();
+        C->n_sm = T->n_sm;
+        C->wait_test = c.wait_test;
+        C->opts = c;
+        ilves_status st = plan_topology(C, T->n_atoms, T->n_c, T->con_i.data(), T->con_j.data(), c);
+        if (st == ILVES_OK) st = upload_topology(C, c);
+        float ms = -1.f;
+        if (st == ILVES_OK) ms = time_solves(C, x_old, x_unc, inv_mass, d, tol, precision, reps, s, buf, stat);
+        if (st == ILVES_OK && ms >= 0.f && ms < best) {
+            if (winner) ilves_destroy_topology(winner);
+            winner = C;
+            best = ms;
+            best_opts = c;
+        } else {
+            ilves_destroy_topology(C);
+        }
+    }
+    if (winner) {  // the topology takes the winner's plan; the old plan goes with the winner object
+        std::swap(*T, *winner);
+        ilves_destroy_topology(winner);
+    }
+    T->opts = best_opts;
+    T->tuning.chosen = best_opts;
+    T->tuning.candidates = (int32_t)cands.size() + 1;
+    T->tuning.best_ms = best;
+    T->tuning.before_ms = before;
+    if (out) *out = T->tuning;
+    return ILVES_OK;
+}
+
+extern "C" ilves_status ilves_topology_tuning(const ilves_topology* T, ilves_tuning* out) {
+    if (!T || !out) return ILVES_ERR_INVALID_ARG;
+    *out = T->tuning;
+    return ILVES_OK;
 }
 
 extern "C" int64_t ilves_static_scratch_bytes(void) { return (int64_t)kStaticScratchBytes; }

@@ -105,7 +105,8 @@ struct ilves_topology {
     int32_t last_launches = 0;
     int32_t wait_test = 0;                   // testing: phantom CTAs the partitioned grid barriers wait for
     std::vector<int32_t> opm_desc;           // descriptor indices of molecules solved by overlapping domains
-    bool smem_attr_set[3] = {false, false, false};
+    ilves_setup_opts opts{};                 // the options the topology was planned with
+    ilves_tuning tuning{};                   // the last ilves_autotune (candidates == 0: none)
 };
 
 namespace ilves {

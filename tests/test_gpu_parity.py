@@ -447,3 +447,28 @@ def test_overlapping_domains_full_size(prec, protein_full):
     if len(D["cons"]) == -(-s.n_constraints // 256):  # the default part size held
         ref_opm = orc.solve_system(s, tol=TOL, overlap=4, part_constraints=256, part_min=4096)
         assert abs(int(it[0]) - int(ref_opm.iterations[0])) <= 1
+
+
+def test_autotune_keeps_the_fastest_converging_configuration():
+    """ilves_autotune times candidate set-up options on the caller's inputs and keeps the
+    fastest; the tuned topologies still meet the parity bounds.  Batched molecules tune slots,
+    CTAs per SM and elimination order; a partitioned molecule also the Schur complement
+    against overlapping domains."""
+    s = wl.tree_batch(n_mol=512, seed=1050)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    tun = t.autotune(*to_dev(s), precision="mixed", start="diag", reps=3)
+    assert tun["candidates"] >= 5 and 0 < tun["best_ms"] <= tun["before_ms"]
+    assert t.tuning() == tun
+    ref = orc.solve_system(s, tol=TOL)
+    _, x, lam, it, st = run(s, "mixed", topo=t, start="diag")
+    compare(s, ref, x, lam, it, st, it_slack=2)
+    p = wl.protein_like(n_atoms=12000, seed=1051)
+    tp = B.Topology(p.n_atoms, p.atom_i, p.atom_j, partition_min_constraints=2000)
+    tun = tp.autotune(*to_dev(p), precision="mixed", start="diag", reps=3)
+    assert tun["candidates"] >= 5 and tun["chosen"]["overlap"] in (0, 2, 3, 4, 6)
+    assert tp.n_large == 1
+    refp = orc.solve_system(p, tol=TOL)
+    _, x, lam, it, st = run(p, "mixed", topo=tp, start="diag")
+    assert st.tolist() == [B.CONVERGED]
+    assert np.abs(x - refp.x).max() <= X_TOL
+    assert np.all(np.abs(lam - refp.lam) <= LAM_RTOL * np.abs(refp.lam) + 1e-10 * np.abs(refp.lam).max())

@@ -42,6 +42,13 @@ def test_invalid_arguments():
         B.Topology(4, [0], [1], wait_test=65, plan_only=True)
     assert e.value.code == 1
     B.Topology(4, [0], [1], wait_test=1, plan_only=True)
+    with pytest.raises(B.IlvesError) as e:  # the overlap depth is bounded
+        B.Topology(4, [0], [1], overlap=17, plan_only=True)
+    assert e.value.code == 1
+    t = B.Topology(4, [0], [1], plan_only=True)  # a host-only plan cannot be tuned or solved
+    tune = B.Tuning()
+    assert B.lib().ilves_autotune(t._h, None, None, None, None, 1e-12, 1, 3, None, ctypes.byref(tune)) == 1
+    assert t.tuning()["candidates"] == 0
 
 
 def _line_graph(ai, aj):
