@@ -129,8 +129,10 @@ typedef struct {
                                       domains (supplement Sec. 3, Overlapping Partitioning Method):
                                       each part's domain adds the atoms within I edges, every domain
                                       solves its own system and keeps its owned constraints'
-                                      corrections (quasi-Newton, same root); 1..16.  Such topologies
-                                      solve in ILVES_PREC_FP64 and ILVES_PREC_MIXED only. */
+                                      corrections (quasi-Newton, same root); 1..16.  A molecule whose
+                                      domains cannot all be resident at once keeps the Schur path.
+                                      Topologies with domains solve in ILVES_PREC_FP64 and
+                                      ILVES_PREC_MIXED only. */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */

@@ -2314,6 +2314,15 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         DS.arena = HS.arena;
         DS.n_slots = (int32_t)HS.slot_off.size();
         DS.pool_n = (int32_t)HS.pool_mol.size();
+        DS.launch_cta = 0;
+        DS.launch_smem = 16;
+        for (int32_t c = 0; c < HS.n_cta; ++c) {
+            const int32_t s0 = HS.cta_slot_ptr[c], s1 = HS.cta_slot_ptr[c + 1];
+            if (s1 > s0) DS.launch_cta = c + 1;
+            int32_t used = 0;
+            for (int32_t sl = s0; sl < s1; ++sl) used = std::max(used, HS.slot_off[sl] + HS.slot_bytes[sl]);
+            DS.launch_smem = std::max(DS.launch_smem, (used + 15) & ~15);
+        }
         if (!HS.pool_mol.empty()) {
             if ((e = upload(&DS.pool_mol, HS.pool_mol)) != cudaSuccess) return to_status(e);
             if ((e = upload(&DS.pool_ctr, std::vector<uint32_t>(2, 0u))) != cudaSuccess) return to_status(e);
@@ -2462,10 +2471,11 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
         }
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
     }
-    if (T->n_small > 0) {
+    if (T->n_small > 0 && DS.launch_cta > 0) {
         SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off, DS.pool_mol, DS.pool_ctr,
                      DS.pool_n, DS.n_slots};
-        k_solve_small<Mode><<<DS.n_cta, DS.warps * kSlotThreads, DS.arena, stream>>>(T->d_desc, T->d_blob, S, A);
+        k_solve_small<Mode><<<DS.launch_cta, DS.warps * kSlotThreads, DS.launch_smem, stream>>>(T->d_desc, T->d_blob,
+                                                                                                S, A);
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;
     }

@@ -1063,13 +1063,17 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
                      M.dom_smem[3] <= 232448;
                 if (!ok) part_size = part_size * 5 / 4;
             }
-            if (!ok) {
-                delete P;
-                return ILVES_ERR_TOPOLOGY;
+            if (ok) {
+                M.passes = 0;
+                T->progs[m] = P;
+                continue;
             }
-            M.passes = 0;
-            T->progs[m] = P;
-            continue;
+            // no domain plan fits the device (halos too large for co-resident domains):
+            // the molecule takes the Schur-complement path below
+            delete P;
+            M.opm = 0;
+            M.n_dom = 0;
+            for (int32_t& v : M.dom_smem) v = 0;
         }
         if (nc >= part_min) {
             // partitioned: parts of ~part_size constraints eliminated first, separators last

@@ -55,6 +55,10 @@ struct HostSchedule {
 struct DeviceSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
     int32_t n_slots = 0, pool_n = 0;
+    // launch shape: only the CTAs that own slots (a prefix: slots are dealt from CTA 0), each
+    // with the shared memory of its slices -- a topology of a few molecules then occupies a
+    // few SMs, and solves of several topologies on different streams run side by side
+    int32_t launch_cta = 0, launch_smem = 0;
     int32_t* cta_slot_ptr = nullptr;
     int32_t* slot_ptr = nullptr;
     int32_t* slot_mol = nullptr;  // index into the small-molecule descriptor array

@@ -12,7 +12,10 @@ A request carries one molecule topology (constrained atom pairs) and its coordin
 * batches requests as they arrive: a batch closes after ``max_wait_s`` or ``max_batch``
   requests; all solves of a batch are enqueued back to back on a pool of CUDA streams,
   one stream per topology so that solves sharing a topology's workspace stay ordered,
-  and the batch completes when every stream has finished.  Each ilves_solve reads the
+  and the batch completes when every stream has finished.  A request's batched kernel
+  launches only the CTAs that own its molecules (with the shared memory they use), so
+  the solves of a batch run side by side on disjoint SMs rather than one after another;
+  requests above the partition threshold are solved by overlapping domains,  Each ilves_solve reads the
   request's page-locked host inputs and writes its page-locked host outputs in place
   (no staging copies) and computes the diagonal start itself,
 * records per-request latency (arrival -> results on the host), iterations and status;
@@ -117,7 +120,7 @@ class Engine:
     """Dynamic-batching solve engine on one GPU."""
 
     def __init__(self, hbm_budget_bytes=8 << 30, n_streams=8, max_batch=64, max_wait_s=0.002,
-                 precision="mixed", warm_start="diag", tol=1e-12, device="cuda:0"):
+                 precision="mixed", warm_start="diag", tol=1e-12, device="cuda:0", overlap=2):
         import torch
 
         from . import binding as B
@@ -132,7 +135,8 @@ class Engine:
         self.warm_start = warm_start
         self.tol = tol
         self.budget = hbm_budget_bytes
-        self.cache = TopologyCache(hbm_budget_bytes, lambda n, i, j: B.Topology(n, i, j),
+        ov = overlap if precision != "mixed_df" else 0  # overlapping domains: float64 and mixed modes
+        self.cache = TopologyCache(hbm_budget_bytes, lambda n, i, j: B.Topology(n, i, j, overlap=ov),
                                    lambda t: t.device_bytes())
         self.stats = ServingStats()
         self.t0 = time.perf_counter()

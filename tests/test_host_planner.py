@@ -338,3 +338,13 @@ def test_overlapping_domains_match_the_oracle(overlap, part):
     # the exact-Newton molecule export is refused for a molecule solved by domains
     with pytest.raises(B.IlvesError):
         t.export_molecule(0)
+
+
+def test_overlapping_domains_fall_back_to_the_schur_path():
+    """Domains that cannot all be resident at once (a random tree's 4-edge halos double
+    them) leave the molecule on the Schur-complement path instead of failing set-up."""
+    s = wl.tree_molecules_of_sizes([40000], seed=77)
+    t4 = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, overlap=4)
+    assert len(t4.export_domains(0)["cons"]) == 0 and t4.export_layout(0)["n_parts"] > 100
+    t2 = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, overlap=2)
+    assert len(t2.export_domains(0)["cons"]) == t2.export_layout(0)["n_parts"] > 100
