@@ -44,7 +44,7 @@ def test_traffic_records_are_well_formed():
                 recs.append(kv)
     assert recs
     for kv in recs:
-        assert kv["kernel"] in ("k_solve_small", "k_solve_parted")
+        assert kv["kernel"] in ("k_solve_small", "k_solve_parted", "k_solve_opm")
         assert kv["mode"] in ("fp64", "mixed", "mixed_df")
         assert int(kv["dram_bytes"]) > 0 and int(kv["atoms"]) > 0
         assert len(kv["sources"]) == 16 and int(kv["sources"], 16) >= 0
