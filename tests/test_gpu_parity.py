@@ -276,11 +276,17 @@ def test_diag_start_inside_the_solve(prec, case):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("case", ["trees", "cta_path", "protein_parted"])
+@pytest.mark.parametrize("case", ["trees", "cta_path", "protein_parted", "protein_domains"])
 def test_pinned_host_buffers(prec, case):
     """ilves_solve on page-locked host buffers (read and written in place by the kernels)
     gives bit for bit the results of the same solve on device buffers."""
-    if case == "trees":
+    if case == "protein_domains":
+        if prec == "mixed_df":
+            pytest.skip("overlapping domains run in the float64 and mixed modes")
+        s = wl.protein_like(n_atoms=12000, seed=1008)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, overlap=4)
+        assert len(t.export_domains(0)["cons"]) > 10
+    elif case == "trees":
         s = wl.tree_batch(n_mol=128, seed=1004)
         t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
     elif case == "cta_path":
