@@ -459,8 +459,7 @@ def run_ilves(args):
     ablation = []
     value64 = per64 = None
     if not args.no_compare:
-        precs = ("fp64", "mixed") if (args.overlap or (tuning and tuning["chosen"]["overlap"])) \
-            else ("fp64", "mixed", "mixed_df")
+        precs = ("fp64", "mixed", "mixed_df")
         combos = [(p, w, "newton") for p in precs for w in ("none", "diag", "mlp")]
         combos += [(p, w, "chord") for p in precs for w in ("none", "diag")]
         for prec, wsn, meth in combos:

@@ -130,9 +130,7 @@ typedef struct {
                                       each part's domain adds the atoms within I edges, every domain
                                       solves its own system and keeps its owned constraints'
                                       corrections (quasi-Newton, same root); 1..16.  A molecule whose
-                                      domains cannot all be resident at once keeps the Schur path.
-                                      Topologies with domains solve in ILVES_PREC_FP64 and
-                                      ILVES_PREC_MIXED only. */
+                                      domains cannot all be resident at once keeps the Schur path. */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */
@@ -251,7 +249,7 @@ ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_ol
  * Results of the tuned topology meet the same tolerances; they may differ in rounding
  * (another elimination order) and in iteration counts (overlapping domains).
  *  Inputs as for ilves_solve (DEVICE or page-locked host buffers); precision as for
- *  ilves_solve (the mode to tune for; overlapping domains are skipped for ILVES_PREC_MIXED_DF);
+ *  ilves_solve (the mode to tune for);
  *  reps >= 1; out: HOST, may be NULL.
  * Synchronous (it synchronises `stream`); allocates device memory for its own outputs and the
  * candidate topologies, so call it at set-up, not inside a time step or a stream capture.

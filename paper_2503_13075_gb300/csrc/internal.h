@@ -249,15 +249,20 @@ ILVES_HD DomProgLayout dom_prog_layout(uint32_t na, uint32_t na_own, uint32_t nc
 // Shared-memory state of a domain behind its program (Mode sizes: hp = 8 bytes of the
 // float64 class, lp = factor element size): X (SoA, 3 na float64), WL (na + 1, lp; the
 // extra atom has zero weight), W (na_own float64), RHO (SoA, 3 nc float64), RHOF and RF
-// (nc x 4 lp; .w = w_i + w_j and 1 / pivot), D2 (nc float64), Y (nc lp), V (nt lp).
-struct DomStateLayout { uint32_t x, wl, w, rho, rhof, rf, d2, y, v, bytes; };
-ILVES_HD DomStateLayout dom_state_layout(uint32_t na, uint32_t na_own, uint32_t nc, uint32_t nt, uint32_t lp) {
+// (nc x 4 lp; .w = w_i + w_j and 1 / pivot), D2 (nc float64), Y (nc lp), V (nt lp).  With
+// `disp` (float-float mode) X holds displacements x - x_unc, RHO only the low float parts
+// of rho (the high parts are RHOF.xyz) and SK the differences x_unc,i - x_unc,j (SoA, 3 nc
+// float-float pairs); the float64-class values are float-float pairs in the same 8 bytes.
+struct DomStateLayout { uint32_t x, wl, w, rho, sk, rhof, rf, d2, y, v, bytes; };
+ILVES_HD DomStateLayout dom_state_layout(uint32_t na, uint32_t na_own, uint32_t nc, uint32_t nt, uint32_t lp,
+                                         bool disp = false) {
     DomStateLayout S;
     uint32_t o = 0;
     S.x = o;    o = align16(o + 24u * na);
     S.wl = o;   o = align16(o + lp * (na + 1));
     S.w = o;    o = align16(o + 8u * na_own);
-    S.rho = o;  o = align16(o + 24u * nc);
+    S.rho = o;  o = align16(o + (disp ? 12u : 24u) * nc);
+    S.sk = o;   o = align16(o + (disp ? 24u * nc : 0u));
     S.rhof = o; o = align16(o + 4u * lp * nc);
     S.rf = o;   o = align16(o + 4u * lp * nc);
     S.d2 = o;   o = align16(o + 8u * nc);

@@ -1711,7 +1711,8 @@ k_solve_parted(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blo
 // the corrections of the constraints it owns; after a grid barrier the owners add them to
 // lambda and move their atoms; a second barrier publishes the positions.  A quasi-Newton
 // iteration on the exact constraint equations: it converges to the same root as ILVES-M.
-// The workspace holds the molecule's positions (SoA), the owned corrections and lambda.
+// The workspace holds the molecule's positions (SoA; displacements x - x_unc as float-float
+// pairs in the float-float mode), the owned corrections and lambda.
 // ------------------------------------------------------------------------------------
 template <class Mode>
 __global__ void __launch_bounds__(kPartThreads, 3)
@@ -1719,7 +1720,7 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
             SolveArgs A, uint32_t phantom, uint32_t staged) {
     using LP = typename Mode::LP;
     using V4 = typename Mode::V4;
-    static_assert(!Mode::df, "overlapping domains run in the float64 and mixed modes");
+    constexpr bool DF = Mode::df;  // float-float: displacements x - x_unc, float-float pairs
     extern __shared__ __align__(16) uint8_t dsm[];
     const MolDesc D = *desc;
     const uint8_t* mb = blob + D.blob_off;
@@ -1752,12 +1753,14 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
     const uint2* TK = reinterpret_cast<const uint2*>(dsmp + L.tasks);
     const uint32_t* TM = reinterpret_cast<const uint32_t*>(dsmp + L.terms);
     const int na = (int)H.na, no = (int)H.na_own, nc = (int)H.nc;
-    const DomStateLayout S = dom_state_layout(H.na, H.na_own, H.nc, H.nt, (uint32_t)sizeof(LP));
+    const DomStateLayout S = dom_state_layout(H.na, H.na_own, H.nc, H.nt, (uint32_t)sizeof(LP), DF);
     uint8_t* st = staged ? dsm + L.bytes : dsm;
     double* X = reinterpret_cast<double*>(st + S.x);
     LP* WL = reinterpret_cast<LP*>(st + S.wl);
     double* W = reinterpret_cast<double*>(st + S.w);
     double* RHO = reinterpret_cast<double*>(st + S.rho);
+    float* RHOL = reinterpret_cast<float*>(st + S.rho);  // float-float mode: low parts of rho (SoA)
+    double* SK = reinterpret_cast<double*>(st + S.sk);   // float-float mode: x_unc,i - x_unc,j
     V4* RHOF = reinterpret_cast<V4*>(st + S.rhof);
     V4* RF = reinterpret_cast<V4*>(st + S.rf);
     double* D2 = reinterpret_cast<double*>(st + S.d2);
@@ -1779,7 +1782,7 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
         for (int c = 0; c < 3; ++c) X[c * na + k] = A.x_old[3 * g + c];
         const double w = A.inv_mass[g];
         WL[k] = to_lp<LP>(w);
-        if (k < no) W[k] = w;
+        if (k < no) W[k] = DF ? as_bits(df_split(w)) : w;
     }
     if (r0 == 0) WL[na] = LP(0);
     __syncthreads();
@@ -1787,9 +1790,17 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
     for (int p = r0; p < nc; p += ts) {
         const int i = (int)(CON[p] & 0xFFFFu), j = (int)(CON[p] >> 16);
         const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
-        RHO[p] = rx;
-        RHO[nc + p] = ry;
-        RHO[2 * nc + p] = rz;
+        if constexpr (DF) {
+            RHOL[p] = df_split(rx).lo;
+            RHOL[nc + p] = df_split(ry).lo;
+            RHOL[2 * nc + p] = df_split(rz).lo;
+            const int64_t gi = gid(AML[i]), gj = gid(AML[j]);
+            for (int c = 0; c < 3; ++c) SK[c * nc + p] = as_bits(df_split(A.x_unc[3 * gi + c] - A.x_unc[3 * gj + c]));
+        } else {
+            RHO[p] = rx;
+            RHO[nc + p] = ry;
+            RHO[2 * nc + p] = rz;
+        }
         V4 v;
         v.x = to_lp<LP>(rx);
         v.y = to_lp<LP>(ry);
@@ -1800,7 +1811,7 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
         const int cl = (int)(cm & 0x7FFFFFFFu);
         const int32_t g = __ldg(con_gid + cl);
         const double dd = A.d[g];
-        D2[p] = dd * dd;
+        D2[p] = DF ? as_bits(df_split(dd * dd)) : dd * dd;
         if (cm >> 31) {
             float l0 = A.lambda0 ? A.lambda0[g] : 0.0f;
             if (A.start_diag) {
@@ -1813,15 +1824,15 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
                 l0 = diag_start(u[0], u[1], u[2], o[0], o[1], o[2], narrow(dd), f32_of(WL[i]) + f32_of(WL[j]));
             }
             GDL[cl] = (LP)l0;
-            GLAM[cl] = widen(l0);
+            GLAM[cl] = DF ? as_bits(dfloat{l0, 0.0f}) : widen(l0);
         }
     }
     __syncthreads();
-    for (int k = r0; k < no; k += ts) {  // owned atoms start at x_unc
+    for (int k = r0; k < no; k += ts) {  // owned atoms start at x_unc (displacement 0)
         const int al = AML[k];
         const int64_t g = gid(al);
         for (int c = 0; c < 3; ++c) {
-            const double v = A.x_unc[3 * g + c];
+            const double v = DF ? 0.0 : A.x_unc[3 * g + c];
             X[c * na + k] = v;
             GX[c * (int64_t)na_m + al] = v;
         }
@@ -1831,20 +1842,42 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
     auto update_owned = [&](bool from_y) {
         for (int kk = r0; kk < no; kk += ts) {
             const int k = (int)AORD[kk];
-            double ax = 0.0, ay = 0.0, az = 0.0;
-            for (int e = IP[k]; e < IP[k + 1]; ++e) {
-                const uint32_t v = IV[e];
-                const int p = (int)(v >> 1);
-                const uint32_t cm = CML[p];
-                const LP dl = (from_y && (cm >> 31)) ? Y[p] : __ldcg(GDL + (cm & 0x7FFFFFFFu));
-                const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
-                ax = fma(c, RHO[p], ax);
-                ay = fma(c, RHO[nc + p], ay);
-                az = fma(c, RHO[2 * nc + p], az);
+            double x, y, z;
+            if constexpr (DF) {
+                dfloat ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
+                for (int e = IP[k]; e < IP[k + 1]; ++e) {
+                    const uint32_t v = IV[e];
+                    const int p = (int)(v >> 1);
+                    const uint32_t cm = CML[p];
+                    const float dl = (float)((from_y && (cm >> 31)) ? Y[p] : __ldcg(GDL + (cm & 0x7FFFFFFFu)));
+                    const float c = (v & 1u) ? -(dl + dl) : (dl + dl);
+                    const V4 hi = RHOF[p];
+                    ax = df_add(ax, df_mul_f(dfloat{hi.x, RHOL[p]}, c));
+                    ay = df_add(ay, df_mul_f(dfloat{hi.y, RHOL[nc + p]}, c));
+                    az = df_add(az, df_mul_f(dfloat{hi.z, RHOL[2 * nc + p]}, c));
+                }
+                const dfloat w = as_df(W[k]);
+                x = as_bits(df_sub(as_df(X[k]), df_mul(w, ax)));
+                y = as_bits(df_sub(as_df(X[na + k]), df_mul(w, ay)));
+                z = as_bits(df_sub(as_df(X[2 * na + k]), df_mul(w, az)));
+            } else {
+                double ax = 0.0, ay = 0.0, az = 0.0;
+                for (int e = IP[k]; e < IP[k + 1]; ++e) {
+                    const uint32_t v = IV[e];
+                    const int p = (int)(v >> 1);
+                    const uint32_t cm = CML[p];
+                    const LP dl = (from_y && (cm >> 31)) ? Y[p] : __ldcg(GDL + (cm & 0x7FFFFFFFu));
+                    const double c = to_hp((v & 1u) ? -(dl + dl) : (dl + dl));
+                    ax = fma(c, RHO[p], ax);
+                    ay = fma(c, RHO[nc + p], ay);
+                    az = fma(c, RHO[2 * nc + p], az);
+                }
+                const double w = W[k];
+                x = fma(-w, ax, X[k]);
+                y = fma(-w, ay, X[na + k]);
+                z = fma(-w, az, X[2 * na + k]);
             }
-            const double w = W[k];
             const int al = AML[k];
-            const double x = fma(-w, ax, X[k]), y = fma(-w, ay, X[na + k]), z = fma(-w, az, X[2 * na + k]);
             X[k] = x;
             X[na + k] = y;
             X[2 * na + k] = z;
@@ -1871,22 +1904,47 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
         bool conv = true, bad = false;
         for (int p = r0; p < nc; p += ts) {
             const int i = (int)(CON[p] & 0xFFFFu), j = (int)(CON[p] >> 16);
-            const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
-            const double d2 = D2[p];
-            const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
-            if (CML[p] >> 31) {
-                conv = conv && abs_le(sg, A.tol * d2);
-                bad = bad || nonfinite(sg);
-            }
-            Y[p] = to_lp<LP>(sg);
-            if (rows) {
-                V4 v;
+            V4 v;
+            if constexpr (DF) {  // r = s + (dx_i - dx_j) and |r|^2 - d^2 by error-free transformations
+                const dfloat rx = df_add(as_df(SK[p]), df_sub(as_df(X[i]), as_df(X[j])));
+                const dfloat ry = df_add(as_df(SK[nc + p]), df_sub(as_df(X[na + i]), as_df(X[na + j])));
+                const dfloat rz = df_add(as_df(SK[2 * nc + p]), df_sub(as_df(X[2 * na + i]), as_df(X[2 * na + j])));
+                const dfloat d2 = as_df(D2[p]);
+                const float px = __fmul_rn(rx.hi, rx.hi), ex = __fmaf_rn(rx.hi, rx.hi, -px);
+                const float py = __fmul_rn(ry.hi, ry.hi), ey = __fmaf_rn(ry.hi, ry.hi, -py);
+                const float pz = __fmul_rn(rz.hi, rz.hi), ez = __fmaf_rn(rz.hi, rz.hi, -pz);
+                float s1, e1, s2, e2, s3, e3;
+                two_sum(px, py, s1, e1);
+                two_sum(s1, pz, s2, e2);
+                two_sum(s2, -d2.hi, s3, e3);
+                float cross = __fmul_rn(rx.hi, rx.lo);
+                cross = __fmaf_rn(ry.hi, ry.lo, cross);
+                cross = __fmaf_rn(rz.hi, rz.lo, cross);
+                const float tail = ((ex + ey) + (ez + e1)) + ((e2 + e3) - d2.lo) + (cross + cross);
+                const float sg = s3 + tail;
+                if (CML[p] >> 31) {
+                    conv = conv && fabsf(sg) <= (float)A.tol * d2.hi;
+                    bad = bad || nonfinite(sg);
+                }
+                Y[p] = (LP)sg;
+                v.x = rx.hi;
+                v.y = ry.hi;
+                v.z = rz.hi;
+            } else {
+                const double rx = X[i] - X[j], ry = X[na + i] - X[na + j], rz = X[2 * na + i] - X[2 * na + j];
+                const double d2 = D2[p];
+                const double sg = fma(rx, rx, fma(ry, ry, fma(rz, rz, -d2)));
+                if (CML[p] >> 31) {
+                    conv = conv && abs_le(sg, A.tol * d2);
+                    bad = bad || nonfinite(sg);
+                }
+                Y[p] = to_lp<LP>(sg);
                 v.x = to_lp<LP>(rx);
                 v.y = to_lp<LP>(ry);
                 v.z = to_lp<LP>(rz);
-                v.w = LP(0);
-                RF[p] = v;
             }
+            v.w = LP(0);
+            if (rows) RF[p] = v;
         }
         const int nconv = __syncthreads_count(!conv);
         const int anybad = __syncthreads_or(bad);
@@ -1985,7 +2043,7 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
         for (int p = r0; p < nc; p += ts)
             if (CML[p] >> 31) {
                 const int cl = (int)(CML[p] & 0x7FFFFFFFu);
-                GLAM[cl] = GLAM[cl] + to_hp(Y[p]);
+                GLAM[cl] = DF ? as_bits(df_add_f(as_df(GLAM[cl]), (float)Y[p])) : GLAM[cl] + to_hp(Y[p]);
             }
         update_owned(true);
         if (!(alive = grid_sync(&sync->barrier, nb, budget))) break;
@@ -1996,13 +2054,14 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
     }
     for (int k = r0; k < no; k += ts) {
         const int64_t g = gid(AML[k]);
-        for (int c = 0; c < 3; ++c) A.x_out[3 * g + c] = X[c * na + k];
+        for (int c = 0; c < 3; ++c)
+            A.x_out[3 * g + c] = DF ? A.x_unc[3 * g + c] + df_join(as_df(X[c * na + k])) : X[c * na + k];
     }
     if (A.lambda_out)
         for (int p = r0; p < nc; p += ts)
             if (CML[p] >> 31) {
                 const int cl = (int)(CML[p] & 0x7FFFFFFFu);
-                A.lambda_out[__ldg(con_gid + cl)] = GLAM[cl];
+                A.lambda_out[__ldg(con_gid + cl)] = DF ? df_join(as_df(GLAM[cl])) : GLAM[cl];
             }
     if (dm == 0 && r0 == 0) {
         if (A.iterations_out) A.iterations_out[D.mol_id] = iters;
@@ -2371,16 +2430,18 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
         if (!T->parted_desc.empty() || !T->opm_desc.empty()) {
             if ((e = cudaMemsetAsync(sync, 0, T->sync_bytes, side)) != cudaSuccess) return to_status(e);
         }
-        if constexpr (!Mode::df) {  // overlapping domains: one cooperative launch per molecule
+        {  // overlapping domains: one cooperative launch per molecule
             for (size_t k = 0; k < T->opm_desc.size(); ++k) {
                 const int32_t di = T->opm_desc[k];
                 const MolHost& MH = T->mols[T->desc_mol[di]];
                 // the programs staged in shared memory when every domain still fits the SMs
                 // with them, else read from global memory (state in shared memory either way)
-                const int q = sizeof(typename Mode::LP) == 8 ? 1 : 0;
+                // sizes: mixed [0] / [2], float64 [1] / [3], float-float [4] / [5]
+                const int qs = Mode::df ? 4 : (sizeof(typename Mode::LP) == 8 ? 1 : 0);
+                const int qn = Mode::df ? 5 : 2 + qs;
                 const int per_sm = (MH.n_dom + T->n_sm - 1) / std::max(1, T->n_sm);
-                uint32_t staged = (int64_t)per_sm * (MH.dom_smem[q] + 1024) <= 233472 && MH.dom_smem[q] <= 232448;
-                const int smem = staged ? MH.dom_smem[q] : MH.dom_smem[2 + q];
+                uint32_t staged = (int64_t)per_sm * (MH.dom_smem[qs] + 1024) <= 233472 && MH.dom_smem[qs] <= 232448;
+                const int smem = staged ? MH.dom_smem[qs] : MH.dom_smem[qn];
                 if ((e = cudaFuncSetAttribute(k_solve_opm<Mode>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
                     cudaSuccess)
                     return to_status(e);
@@ -2605,8 +2666,6 @@ extern "C" ilves_status ilves_solve(ilves_topology* T, const double* x_old, cons
     if (A.start_diag && lambda0) return ILVES_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     T->last_launches = 0;
-    if ((precision & ~(ILVES_CHORD | ILVES_START_DIAG)) == ILVES_PREC_MIXED_DF && !T->opm_desc.empty())
-        return ILVES_ERR_INVALID_ARG;  // overlapping domains run in the float64 and mixed modes
     switch (precision & ~(ILVES_CHORD | ILVES_START_DIAG)) {
         case ILVES_PREC_FP64: return launch_mode<ModeFP64>(T, A, s);
         case ILVES_PREC_MIXED: return launch_mode<ModeMixed>(T, A, s);
@@ -2627,7 +2686,6 @@ extern "C" ilves_status ilves_solve_static_scratch(ilves_topology* T, const doub
     const int32_t prec_mode = precision & ~(ILVES_CHORD | ILVES_START_DIAG);
     if ((precision & ILVES_START_DIAG) && lambda0) return ILVES_ERR_INVALID_ARG;
     if (prec_mode < ILVES_PREC_FP64 || prec_mode > ILVES_PREC_MIXED_DF) return ILVES_ERR_INVALID_ARG;
-    if (prec_mode == ILVES_PREC_MIXED_DF && !T->opm_desc.empty()) return ILVES_ERR_INVALID_ARG;
     const uint64_t work_aligned = ((uint64_t)T->work_bytes + 255) & ~uint64_t(255);
     if (work_aligned + (uint64_t)T->sync_bytes > (uint64_t)kStaticScratchBytes) return ILVES_ERR_TOO_LARGE;
     int dev = -1;
@@ -2764,7 +2822,6 @@ extern "C" ilves_status ilves_autotune(ilves_topology* T, const double* x_old, c
     }
     if (has_parted) {
         for (int32_t ov : {0, 2, 3, 4, 6}) {
-            if (ov > 0 && mode == ILVES_PREC_MIXED_DF) continue;
             ilves_setup_opts c = base;
             c.overlap = ov;
             add(c);

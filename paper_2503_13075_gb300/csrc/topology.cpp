@@ -614,7 +614,7 @@ static std::vector<DomainPlan> opm_domains(int32_t na, const std::vector<int32_t
 // domain exceeds the 16-bit encoding.  loc: scratch of one entry per molecule atom, all -1.
 static bool build_domain_program(const DomainPlan& P, const std::vector<int32_t>& ci, const std::vector<int32_t>& cj,
                                  std::vector<int32_t>& loc, std::vector<uint8_t>& out, int32_t& nlev, int32_t& ntask,
-                                 int32_t& nterm, int64_t& n_fill, uint32_t smem[4]) {
+                                 int32_t& nterm, int64_t& n_fill, uint32_t smem[6]) {
     const int32_t na = (int32_t)P.atoms.size(), ne = (int32_t)P.cons.size(), no = P.na_own;
     if (na >= 0xFFFF || ne >= (int32_t)DomTerm::kMaxCons) return false;
     for (int32_t k = 0; k < na; ++k) loc[P.atoms[k]] = k;
@@ -716,8 +716,10 @@ static bool build_domain_program(const DomainPlan& P, const std::vector<int32_t>
     n_fill = Q.n_fill;
     smem[2] = dom_state_layout(na, no, ne, nt, 4).bytes;
     smem[3] = dom_state_layout(na, no, ne, nt, 8).bytes;
+    smem[5] = dom_state_layout(na, no, ne, nt, 4, true).bytes;
     smem[0] = L.bytes + smem[2];
     smem[1] = L.bytes + smem[3];
+    smem[4] = L.bytes + smem[5];
     return true;
 }
 
@@ -746,11 +748,11 @@ static bool build_opm(Program& P, MolHost& M, int32_t part_size, int32_t overlap
         off[d] = (uint32_t)P.opm_blob.size();
         int32_t nl = 0, nt = 0, ntm = 0;
         int64_t fill = 0;
-        uint32_t sm[4];
+        uint32_t sm[6];
         if (!build_domain_program(doms[d], M.ci, M.cj, loc, P.opm_blob, nl, nt, ntm, fill, sm)) return false;
         P.dom_levels[d] = nl;
         P.dom_bytes[d] = (int32_t)(P.opm_blob.size() - off[d]);
-        for (int q = 0; q < 4; ++q) M.dom_smem[q] = std::max<int32_t>(M.dom_smem[q], (int32_t)sm[q]);
+        for (int q = 0; q < 6; ++q) M.dom_smem[q] = std::max<int32_t>(M.dom_smem[q], (int32_t)sm[q]);
         M.nlevel = std::max(M.nlevel, nl);
         M.ntask += nt;
         M.nterm += ntm;

@@ -35,8 +35,9 @@ struct MolHost {
     int32_t opm = 0;                 // overlapping domains: overlap depth (0 = not solved by domains)
     int32_t n_dom = 0;               // overlapping domains: number of domains (CTAs)
     // overlapping domains: largest shared memory of a domain, program staged + state
-    // (float32 / float64 factor), then state only (program read from global memory)
-    int32_t dom_smem[4] = {0, 0, 0, 0};
+    // (float32 / float64 factor), then state only (program read from global memory), then
+    // staged and state only in the float-float mode
+    int32_t dom_smem[6] = {0, 0, 0, 0, 0, 0};
     int64_t passes = 0;
 };
 

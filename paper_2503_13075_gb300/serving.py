@@ -135,8 +135,7 @@ class Engine:
         self.warm_start = warm_start
         self.tol = tol
         self.budget = hbm_budget_bytes
-        ov = overlap if precision != "mixed_df" else 0  # overlapping domains: float64 and mixed modes
-        self.cache = TopologyCache(hbm_budget_bytes, lambda n, i, j: B.Topology(n, i, j, overlap=ov),
+        self.cache = TopologyCache(hbm_budget_bytes, lambda n, i, j: B.Topology(n, i, j, overlap=overlap),
                                    lambda t: t.device_bytes())
         self.stats = ServingStats()
         self.t0 = time.perf_counter()

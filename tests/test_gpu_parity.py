@@ -281,8 +281,6 @@ def test_pinned_host_buffers(prec, case):
     """ilves_solve on page-locked host buffers (read and written in place by the kernels)
     gives bit for bit the results of the same solve on device buffers."""
     if case == "protein_domains":
-        if prec == "mixed_df":
-            pytest.skip("overlapping domains run in the float64 and mixed modes")
         s = wl.protein_like(n_atoms=12000, seed=1008)
         t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, overlap=4)
         assert len(t.export_domains(0)["cons"]) > 10
@@ -396,7 +394,7 @@ def test_hydroxyl_angle_distances(prec, case):
         compare(s, ref, x, lam, it, st, it_slack=1 if start is None else 2)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("overlap", [2, 4])
 def test_overlapping_domains(prec, overlap):
     """Overlapping domains (supplement Sec. 3, Overlapping Partitioning Method): every domain
@@ -417,12 +415,9 @@ def test_overlapping_domains(prec, overlap):
         assert np.abs(x - ref.x).max() <= X_TOL
         assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL
         assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
-    with pytest.raises(B.IlvesError) as e:  # domains run in the float64 and mixed modes only
-        run(s, "mixed_df", topo=t)
-    assert e.value.code == 1
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_overlapping_domains_chord(prec):
     """ILVES-F over overlapping domains: each domain factorises A(x_old, x_old) on its
     constraints once; same root, iterations within +-1 of the oracle's."""
@@ -437,7 +432,7 @@ def test_overlapping_domains_chord(prec):
     assert np.all(np.abs(lam - ref.lam) <= LAM_RTOL * np.abs(ref.lam) + 1e-10 * np.abs(ref.lam).max())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", PRECS)
 def test_overlapping_domains_full_size(prec, protein_full):
     """The 100,001-atom system over overlapping domains (overlap 4, automatic part size):
     parity with the Newton oracle; the planner's domains are the oracle's, and the iteration

@@ -56,8 +56,6 @@ def _case(case, seed):
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 @pytest.mark.parametrize("case", ["protein_like", "protein_domains", "forced_large"])
 def test_static_scratch_matches_solve(case, prec):
-    if case == "protein_domains" and prec == "mixed_df":
-        pytest.skip("overlapping domains run in the float64 and mixed modes")
     s, topo = _case(case, 77 if case == "forced_large" else 1002)
     assert topo.n_large > 0
     assert 0 < topo.workspace_bytes() <= B.lib().ilves_static_scratch_bytes()
