@@ -772,12 +772,13 @@ static bool build_opm(Program& P, MolHost& M, int32_t part_size, int32_t overlap
     return true;
 }
 
-// Kernel cost model (cycles per Newton iteration for one team): a level pass costs
-// roughly one shared-memory round trip plus a few FMAs; work is spread over lanes.
+// Kernel cost model (cycles per Newton iteration for one team), with the pass costs
+// measured by clock counters in the batched kernel on GB300 (eight teams per SM): a
+// factorisation level pass ~1390 cycles, a back-substitution level pass ~620; the work of
+// tasks and terms is spread over the team's lanes.
 static double program_cost(const Program& P, int32_t team) {
-    const double pass_lat = 90.0;
     const double work = (double)P.tasks.size() * 6.0 + (double)P.terms.size() * 4.0;
-    return pass_lat * (double)(P.passes_factor + P.passes_solve) + work / team;
+    return 1390.0 * (double)P.passes_factor + 620.0 * (double)P.passes_solve + work / team;
 }
 
 static Program choose_order(int32_t nc, int32_t na, const std::vector<std::vector<int32_t>>& adj,
