@@ -363,6 +363,14 @@ def chain_batch(n_chains: int, seed: int, sigma: float = 0.002, box: float = 20.
     return _exact_lengths(_assemble(f"chain_batch{n_chains}", mols, rng, sigma, seed, box))
 
 
+def chain_molecules(sizes, seed: int, sigma: float = 0.002, box: float = 20.0) -> System:
+    """Carbon chains of the given atom counts (the chain64 distribution: 0.153 nm bonds,
+    111 deg angles, uniform dihedrals); long chains give deep elimination orders."""
+    rng = np.random.default_rng(seed)
+    mols = [_chain(rng, n_atoms=int(n)) for n in sizes]
+    return _exact_lengths(_assemble("chains", mols, rng, sigma, seed, box))
+
+
 def tree_batch(n_mol: int = 4096, lo: int = 20, hi: int = 200, seed: int = 1001,
                sigma: float = 0.003, box: float | None = None, xoh: bool = False) -> System:
     """Batch of independent random tree molecules with U{lo..hi} atoms each; with ``xoh``

@@ -176,6 +176,27 @@ def test_edge_cases(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_batched_encoding_limits(prec):
+    """Molecules at the batched kernel's encoding limits (fewer than 256 constraints, at
+    most 511 atoms) and just past them, which take the CTA-per-molecule path, in one
+    topology; and long chains (deep elimination orders) on both paths."""
+    sizes = [2, 3, 254, 255, 256, 257, 258, 400]
+    s = wl.tree_molecules_of_sizes(sizes, seed=1030)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    assert sorted(t.molecules()[0].tolist()) == sorted(sizes)
+    assert 3 <= t.n_large < len(sizes)  # trees of 257, 258, 400 atoms have 256+ constraints
+    ref = orc.solve_system(s, tol=TOL)
+    _, x, lam, it, st = run(s, prec, topo=t, start="diag")
+    compare(s, ref, x, lam, it, st, it_slack=2)
+    c = wl.chain_molecules([64, 128, 255, 256, 257, 300], seed=1031)
+    tc = B.Topology(c.n_atoms, c.atom_i, c.atom_j)
+    assert tc.n_large == 2  # 256 and 299 bonds
+    ref = orc.solve_system(c, tol=TOL)
+    _, x, lam, it, st = run(c, prec, topo=tc)
+    compare(c, ref, x, lam, it, st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_warm_start_and_aliasing(prec, trees):
     s, ref = trees
     t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
