@@ -22,6 +22,7 @@ import argparse
 import glob
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -145,6 +146,23 @@ def measured_traffic(kernel, precision, n_atoms):
                 if kv.get("kernel") == kernel and kv.get("mode") == precision and kv.get("sources") == digest:
                     return float(kv["dram_bytes"]) * n_atoms / float(kv["atoms"]), os.path.basename(path)
     return None, None
+
+
+def rounded(obj, digits=6):
+    """The JSON line's floats to `digits` significant digits (integers and strings as they are)."""
+    if isinstance(obj, float):
+        return float(f"{obj:.{digits}g}") if math.isfinite(obj) else obj
+    if isinstance(obj, dict):
+        return {k: rounded(v, digits) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [rounded(v, digits) for v in obj]
+    return obj
+
+
+def compact_ablation(a):
+    """One ablation row in short form: precision/start/method, ms, mean solves, converged, violation."""
+    return {"cfg": f"{a['precision']}/{a['warm_start']}/{a['method']}", "ms": a["ms_per_step"],
+            "solves": a["mean_iterations"], "ok": a["all_converged"], "viol": a["max_rel_violation"]}
 
 
 def max_rel_violation(x, atom_i, atom_j, d):
@@ -353,7 +371,7 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "atoms*solves/s", "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "atoms*solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(out))
+    print(json.dumps(rounded(out)))
 
 
 WS_LAUNCHES = {"none": 0, "diag": 0, "mlp": 2}  # kernels a warm start adds per step (diag: inside the solve)
@@ -625,31 +643,33 @@ def run_ilves(args):
                          if s.name == "protein_like" else "persistent CTAs, one 96-thread team per molecule"),
             "autotune": tuning,
         },
+        # the long diagnostic blocks first: a reader that keeps only the end of the line
+        # still sees the measurement, the roofline and the speed-up
+        "ablation": [compact_ablation(a) for a in ablation],
+        "warm_start_training": mlp_info,
+        "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(iters)) if v},
         "valid": valid,
         "max_rel_violation": viol,
         "avg_rel_error": avg_err,
-        "iterations": {str(k): int(v) for k, v in enumerate(np.bincount(iters)) if v},
-        "plain_fp64": None if value64 is None else (exact64 or {"value": value64, "ms_per_step": per64,
-                                                               "precision": "fp64", "warm_start": "none"}),
-        "speedup_vs_plain_fp64": None if value64 is None else value / value64,
         "oracle_error": err,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
-                     "kernel": kname,
-                     "kernel_ms": solve_per},
+        "cpu_baseline": cpu,
         "fp64_alu": fp64,
+        "gpu_launches": launches,
+        "wall_s_timed_region": t_wall,
+        "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "atoms*solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_per, "all_converged": e2e_ok,
                 "transfer": "ilves_solve on page-locked host buffers: the kernels read the inputs and write "
                             "the results in place over the host link, inside the timed region"},
-        "gpu_launches": launches,
-        "wall_s_timed_region": t_wall,
-        "clocks": clk,
-        "cpu_baseline": cpu,
-        "warm_start_training": mlp_info,
-        "ablation": ablation,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": ab,
+                     "kernel": kname,
+                     "kernel_ms": solve_per},
+        "plain_fp64": None if value64 is None else (exact64 or {"value": value64, "ms_per_step": per64,
+                                                               "precision": "fp64", "warm_start": "none"}),
+        "speedup_vs_plain_fp64": None if value64 is None else value / value64,
     }
-    print(json.dumps(res))
+    print(json.dumps(rounded(res)))
 
 
 def run_learned_start(args):
@@ -745,7 +765,7 @@ def run_learned_start(args):
         "two_solve_requirement": "2 Newton solves at 1e-12 need a starting violation below ~1.7e-3 per chain",
         "starts_at_tol_1e-8": rows_loose,
     }
-    print(json.dumps(res))
+    print(json.dumps(rounded(res)))
 
 
 def run_serving(args):
@@ -807,7 +827,7 @@ def run_serving(args):
                                                          "hits": eng.cache.hits, "misses": eng.cache.misses},
         "wall_s": wall,
     }
-    print(json.dumps(res))
+    print(json.dumps(rounded(res)))
 
 
 def main():
