@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 / other-precision comparators")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the default set-up options (no ilves_autotune)")
+    p.add_argument("--eager", action="store_true", help="time eager launches instead of CUDA graph replays")
     p.add_argument("--workload", default="tree_batch",
                    choices=["tree_batch", "protein_like", "chain64", "serving", "learned_start"],
                    help="tree_batch (default line); protein_like / chain64 print lines for the other configurations")
@@ -397,6 +398,33 @@ def make_step(topo, dev_in, out, prec, tol, ws, mlp, lam0, method="newton"):
     return step
 
 
+def graph_step(step, stream):
+    """The step captured into a CUDA graph (after one eager run on a side stream): returns a
+    replay function with the step's launch count, or (None, reason) if capture fails."""
+    import torch
+
+    side = torch.cuda.Stream(stream.device)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        n = step()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    try:
+        with torch.cuda.graph(g):
+            step()
+    except Exception as e:  # noqa: BLE001 -- reported in the JSON line, the step runs eagerly
+        torch.cuda.synchronize()
+        return None, f"eager launches (graph capture failed: {type(e).__name__})"
+
+    def replay():
+        g.replay()
+        return n
+
+    replay.graph = g
+    return replay, "CUDA graph replay (one captured solve per step)"
+
+
 def time_device(step, steps, warmup, flush, stream):
     """Per-step CUDA-event time (L2 flushed before each step, outside the events)."""
     import torch
@@ -512,6 +540,10 @@ def run_ilves(args):
         topo_exact.close()
 
     step = make_step(topo, dev_in, out, args.precision, args.tol, args.warm_start, mlp, lam0, args.method)
+    launch_mode = "eager launches"
+    if not args.eager:
+        replay, launch_mode = graph_step(step, stream)
+        step = replay or step
 
     def roll(seconds):  # keep the GPU busy with the same step (clock sampling window)
         t0 = time.perf_counter()
@@ -642,6 +674,7 @@ def run_ilves(args):
                           if uses_domains else "cooperative CTAs over partitions + separator (Schur) block")
                          if s.name == "protein_like" else "persistent CTAs, one 96-thread team per molecule"),
             "autotune": tuning,
+            "launch": launch_mode,
         },
         # the long diagnostic blocks first: a reader that keeps only the end of the line
         # still sees the measurement, the roofline and the speed-up
