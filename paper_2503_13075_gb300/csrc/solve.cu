@@ -133,9 +133,21 @@ __device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
 }
 // float64 -> float-float: hi = the truncated leading 24 bits (integer pipe), lo = the
 // rounded remainder (one float64 subtraction)
+// v = hi + lo with hi = v truncated to float (narrow) and lo = the rest rounded to float.
+// For 2^-75 <= |v| < 2^128 the rest is exactly the 29 mantissa bits below hi's, times
+// 2^(exponent - 52), and lo stays in float's normal range: lo is built from those bits on the
+// integer pipe (one int-to-float conversion, then the power of two added to its exponent
+// field), bit for bit what rounding v - hi would give; smaller, huge and non-finite v take
+// the float64 route.
 __device__ __forceinline__ dfloat df_split(double v) {
     const float hi = narrow(v);
-    return {hi, __double2float_rn(v - widen(hi))};
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    if (e <= 948 || e >= 1151) return {hi, __double2float_rn(v - widen(hi))};
+    const unsigned rem = (unsigned)(b & 0x1FFFFFFFull);
+    const unsigned fb = __float_as_uint(__uint2float_rn(rem));  // 0, or its exponent field in [127, 156]
+    const unsigned lb = (fb & 0x007FFFFFu) | ((unsigned)((int)(fb >> 23) + (e - 1075)) << 23);
+    return {hi, __uint_as_float(rem != 0u ? (lb | ((unsigned)(b >> 32) & 0x80000000u)) : 0u)};
 }
 __device__ __forceinline__ double df_join(dfloat a) { return widen(a.hi) + widen(a.lo); }
 __device__ __forceinline__ dfloat as_df(double v) { return *reinterpret_cast<dfloat*>(&v); }
