@@ -9,15 +9,17 @@ A request carries one molecule topology (constrained atom pairs) and its coordin
   request (``ilves_setup_topology``) and reused afterwards,
 * admits a request only if its topology and its input/output footprint fit the budget
   (otherwise it is rejected with a reason, never queued forever),
-* batches requests as they arrive: a batch closes after ``max_wait_s`` or ``max_batch``
-  requests; all solves of a batch are enqueued back to back on a pool of CUDA streams,
-  one stream per topology so that solves sharing a topology's workspace stay ordered,
-  and the batch completes when every stream has finished.  A request's batched kernel
-  launches only the CTAs that own its molecules (with the shared memory they use), so
-  the solves of a batch run side by side on disjoint SMs rather than one after another;
-  requests above the partition threshold are solved by overlapping domains,  Each ilves_solve reads the
-  request's page-locked host inputs and writes its page-locked host outputs in place
-  (no staging copies) and computes the diagonal start itself,
+* dispatches requests continuously: the requests that have arrived go out together once
+  the oldest has waited ``max_wait_s`` (0: on arrival) or ``max_batch`` are waiting, with
+  at most ``max_batch`` in flight; their solves are enqueued back to back on a pool of
+  CUDA streams, one stream per topology so that solves sharing a topology's workspace stay
+  ordered, and each request completes on its own (its stream's event is polled), without
+  waiting for the others.  A request's batched kernel launches only the CTAs that own its
+  molecules (with the shared memory they use), so solves run side by side on disjoint SMs
+  rather than one after another; requests above the partition threshold are solved by
+  overlapping domains.  Each ilves_solve reads the request's page-locked host inputs and
+  writes its page-locked host outputs in place (no staging copies) and computes the
+  diagonal start itself,
 * records per-request latency (arrival -> results on the host), iterations and status;
   ``max_relative_violation`` reports the accuracy of returned positions.
 """
@@ -162,11 +164,11 @@ class Engine:
                      torch.empty(n_mol_max, dtype=torch.int32).pin_memory(),
                      torch.empty(max(1, len(req.d)), dtype=torch.float64).pin_memory()]
 
-    def _run_batch(self, batch):
+    def _launch(self, batch):
+        """Enqueues the solves of `batch`; returns (request, event, outputs) per admitted request."""
         torch = self.torch
-        B = self.B
         jobs = []
-        for k, req in enumerate(batch):
+        for req in batch:
             topo = self.cache.get(req.key, (req.n_atoms, req.atom_i, req.atom_j), reserve=req.io_bytes())
             if topo is None:
                 req.status = "rejected: topology and buffers exceed the HBM budget"
@@ -185,35 +187,45 @@ class Engine:
             ev = torch.cuda.Event()
             ev.record(s)
             jobs.append((req, ev, hx, hi, hs))
-        for req, ev, hx, hi, hs in jobs:
-            ev.synchronize()
-            req.done = self.now()
-            req.x, req.iterations, req.mol_status = hx.numpy().copy(), hi.numpy().copy(), hs.numpy().copy()
-            req.status = "ok" if np.all(req.mol_status == 0) else "not converged"
-            self.stats.latencies.append(req.done - req.arrival)
-            self.stats.completed += 1
-            self.stats.atoms += req.n_atoms
-            self.stats.iterations.extend(req.iterations.tolist())
-        self.stats.batches += 1
+        return jobs
+
+    def _finish(self, job):
+        req, ev, hx, hi, hs = job
+        req.done = self.now()
+        req.x, req.iterations, req.mol_status = hx.numpy().copy(), hi.numpy().copy(), hs.numpy().copy()
+        req.status = "ok" if np.all(req.mol_status == 0) else "not converged"
+        self.stats.latencies.append(req.done - req.arrival)
+        self.stats.completed += 1
+        self.stats.atoms += req.n_atoms
+        self.stats.iterations.extend(req.iterations.tolist())
 
     def serve(self, requests):
         """Serve requests (sorted by arrival time, engine clock) in real time."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        inflight = []
         self.t0 = time.perf_counter()
-        while pending:
-            first = pending[0]
-            wait = first.arrival - self.now()
-            if wait > 0:
-                time.sleep(wait)
-            close_at = max(self.now(), first.arrival) + self.max_wait_s
-            batch = []
-            while pending and len(batch) < self.max_batch and pending[0].arrival <= close_at:
-                if pending[0].arrival > self.now():
-                    time.sleep(max(0.0, min(pending[0].arrival, close_at) - self.now()))
-                    if pending[0].arrival > self.now():
-                        break
-                batch.append(pending.popleft())
-            self._run_batch(batch)
+        while pending or inflight:
+            now = self.now()
+            ready = 0
+            while ready < len(pending) and pending[ready].arrival <= now:
+                ready += 1
+            room = self.max_batch - len(inflight)
+            if ready and room > 0 and (now - pending[0].arrival >= self.max_wait_s or ready >= self.max_batch):
+                inflight += self._launch([pending.popleft() for _ in range(min(ready, room))])
+                self.stats.batches += 1
+                continue
+            done, still = [], []
+            for job in inflight:
+                (done if job[1].query() else still).append(job)
+            if done:
+                for job in done:
+                    self._finish(job)
+                inflight = still
+                continue
+            if not inflight and pending:  # idle: sleep until the next request can go out
+                wait = pending[0].arrival + (self.max_wait_s if ready else 0.0) - self.now()
+                if wait > 2e-4:
+                    time.sleep(wait - 1e-4)
         return self.stats
 
 
