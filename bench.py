@@ -713,7 +713,9 @@ def run_learned_start(args):
     diagonal and the learned start at the same tolerance.  Reported per start: time per step
     (the learned start's feature and network kernels included), Newton solves, and the
     starting violation max_k |sigma_k| / d_k^2 per chain; for the network also its error
-    relative to each chain's largest |lambda| (float64 solve as reference)."""
+    relative to each chain's largest |lambda| (float64 solve as reference).  The oracle solves
+    the same chains from the zero start (the CPU baseline) and every start's result is
+    compared with it."""
     import torch
 
     from paper_2503_13075_gb300 import binding as B
@@ -747,7 +749,7 @@ def run_learned_start(args):
     lam_ref = lam_ref.cpu().numpy()
     scale = np.zeros(4096)
     np.maximum.at(scale, mol, np.abs(lam_ref))
-    rows, rows_loose = {}, {}
+    rows, rows_loose, finals = {}, {}, {}
     for start in ("none", "diag", "mlp"):  # the same three starts at a looser tolerance, 1e-8
         step = make_step(topo, dev_in, out, args.precision, 1e-8, start, mlp, lam0)
         ms, _ = time_device(step, max(3, args.steps // 2), 2, flush, stream)
@@ -780,7 +782,17 @@ def run_learned_start(args):
             e = np.abs(l0.cpu().numpy().astype(np.float64) - lam_ref) / scale[mol]
             row["lambda0_error_over_chain_max"] = {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)),
                                                    "max": float(e.max())}
+        finals[start] = (out[0].cpu().numpy(), out[1].cpu().numpy(), it, st)
         rows[start] = row
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle (zero start) on the same held-out chains: the CPU baseline, and the
+        # reference of every start's error report
+        ref, single, allc = cpu_oracle(s, args.tol)
+        cpu = dict(allc or single)
+        cpu["single_core"] = single
+        for start, (x_f, lam_f, it_f, st_f) in finals.items():
+            rows[start]["oracle_error"] = oracle_error(ref, x_f, lam_f, it_f, st_f)
     if rank != 0:
         return
     res = {
@@ -798,8 +810,39 @@ def run_learned_start(args):
         "training": train,
         "two_solve_requirement": "2 Newton solves at 1e-12 need a starting violation below ~1.7e-3 per chain",
         "starts_at_tol_1e-8": rows_loose,
+        "cpu_baseline": cpu,
+        "oracle_error": rows["mlp"].get("oracle_error"),
     }
     print(json.dumps(rounded(res)))
+
+
+def serving_oracle(done, tol, n_sample=96):
+    """The oracle on a bounded sample of served requests (every k-th completed request, in
+    arrival order, one core): its throughput is the serving line's CPU baseline, and each
+    sampled request's returned x, lambda, iterations and statuses are compared with it (the
+    error figures are the maxima over the sample)."""
+    from oracle import ilves_oracle as orc
+
+    k = max(1, len(done) // n_sample)
+    sample = done[::k][:n_sample]
+    errs, atoms, secs = [], 0, 0.0
+    for r in sample:
+        t0 = time.perf_counter()
+        ref = orc.solve(r.x_old, r.x_unc, r.inv_mass, r.atom_i, r.atom_j, r.d, tol=tol)
+        secs += time.perf_counter() - t0
+        atoms += r.n_atoms
+        nm = len(r.iterations)
+        lam = r.host[7][: len(r.d)].numpy()
+        errs.append(oracle_error(ref, r.x, lam, r.iterations, r.mol_status[:nm]))
+    err = {"sample": f"{len(sample)} of {len(done)} requests (every {k}-th), {atoms} atoms",
+           "max_abs_x_nm": max(e["max_abs_x_nm"] for e in errs),
+           "lambda_over_bound": max(e["lambda_over_bound"] for e in errs),
+           "max_rel_lambda_above_1e-3_of_max": max(e["max_rel_lambda_above_1e-3_of_max"] for e in errs),
+           "max_abs_iterations_diff": max(e["max_abs_iterations_diff"] for e in errs),
+           "statuses_equal": all(e["statuses_equal"] for e in errs)}
+    cpu = {"value": atoms / secs, "unit": "atoms*solves/s", "cores": 1, "kind": "oracle",
+           "sample": f"{len(sample)} served requests ({atoms} atoms), one solve each, sequential", "seconds": round(secs, 2)}
+    return cpu, err
 
 
 def run_serving(args):
@@ -836,6 +879,9 @@ def run_serving(args):
     viol = max((sv.max_relative_violation(r.x, r.atom_i, r.atom_j, r.d) for r in done), default=0.0)
     lat = np.array(stats.latencies) * 1e3
     sizes = np.array([r.n_atoms for r in reqs])
+    cpu, err = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and done:
+        cpu, err = serving_oracle(done, args.tol)
     if rank != 0:
         return
     res = {
@@ -858,6 +904,7 @@ def run_serving(args):
         "throughput_req_s": stats.completed / wall, "completed": stats.completed, "rejected": stats.rejected,
         "batches": stats.batches, "all_converged": all(r.status == "ok" for r in done),
         "max_rel_violation": viol, "mean_iterations": float(np.mean(stats.iterations)) if stats.iterations else None,
+        "cpu_baseline": cpu, "oracle_error": err,
         "topology_setup_s": round(setup_s, 2), "cache": {"topologies": len(eng.cache.entries),
                                                          "device_bytes": eng.cache.used,
                                                          "hits": eng.cache.hits, "misses": eng.cache.misses},

@@ -49,3 +49,30 @@ def test_traffic_records_are_well_formed():
         assert int(kv["dram_bytes"]) > 0 and int(kv["atoms"]) > 0
         assert len(kv["sources"]) == 16 and int(kv["sources"], 16) >= 0
     assert bench.measured_traffic("k_solve_small", "no-such-mode", 1000) == (None, None)
+
+
+def test_serving_oracle_report():
+    """The serving line's oracle sample: results equal to the oracle's give zero errors and
+    equal statuses; a moved atom and a wrong status show up in the report."""
+    import torch
+
+    from oracle import ilves_oracle as orc
+    from paper_2503_13075_gb300 import serving as sv
+    from paper_2503_13075_gb300 import workloads as wl
+
+    done = []
+    for k, n in enumerate((20, 35, 60)):
+        s = wl.tree_molecules_of_sizes([n], seed=400 + k)
+        r = sv.Request(k, 0.0, s.n_atoms, s.atom_i, s.atom_j, s.x_old, s.x_unc, s.inv_mass, s.d)
+        ref = orc.solve(s.x_old, s.x_unc, s.inv_mass, s.atom_i, s.atom_j, s.d, tol=1e-12)
+        r.x, r.iterations, r.mol_status = ref.x.copy(), ref.iterations.astype(np.int32), ref.status.astype(np.int32)
+        r.host = [None] * 7 + [torch.from_numpy(ref.lam.copy())]
+        done.append(r)
+    cpu, err = bench.serving_oracle(done, 1e-12, n_sample=3)
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] > 0
+    assert err["max_abs_x_nm"] == 0.0 and err["lambda_over_bound"] == 0.0
+    assert err["max_abs_iterations_diff"] == 0 and err["statuses_equal"]
+    done[1].x[3, 0] += 1e-9
+    done[2].mol_status[0] = 1
+    _, err = bench.serving_oracle(done, 1e-12, n_sample=3)
+    assert abs(err["max_abs_x_nm"] - 1e-9) < 1e-12 and not err["statuses_equal"]
