@@ -112,7 +112,8 @@ typedef struct {
     int32_t ordering;        /* 0 = autotuned (default); 1 = minimum degree, one pivot per step;
                                 2 = rounds of independent low-degree pivots with `degree_slack` */
     int32_t degree_slack;    /* ordering 2: admit pivots up to min degree + slack per round */
-    int32_t warps_per_cta;   /* 0 = autotuned; else 1..8 molecule slots (96-thread teams) per persistent CTA */
+    int32_t warps_per_cta;   /* 0 = autotuned; else 1..8 molecule slots (96-thread teams) per persistent CTA
+                                of the 96-thread-team class */
     int32_t ctas_per_sm;     /* 0 = autotuned; else 1..4 */
     int32_t device;          /* CUDA device ordinal the topology lives on (-1 = current device,
                                 -2 = plan on the host only: no CUDA call, ilves_solve refused) */
@@ -131,6 +132,13 @@ typedef struct {
                                       solves its own system and keeps its owned constraints'
                                       corrections (quasi-Newton, same root); 1..16.  A molecule whose
                                       domains cannot all be resident at once keeps the Schur path. */
+    int32_t narrow_atoms;          /* batched molecules of at most this many atoms are solved by
+                                      one-warp teams (up to 24 per persistent CTA, beside its
+                                      96-thread teams) instead of 96-thread teams: three small
+                                      molecules then share the shared memory and the warps of one
+                                      large one.  0 = automatic (100 atoms when such molecules hold
+                                      at least 90 % of the batched atoms and outnumber the 96-thread
+                                      teams the GPU holds, else none), -1 = none, else 1..255 */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */
@@ -402,21 +410,25 @@ ilves_status ilves_topology_export_layout(const ilves_topology* topo, int32_t mo
                                           int32_t* n_parts, int32_t* part_levels, int32_t* part_prog_bytes,
                                           int32_t* sep_summary);
 
-/* Host-side plan of the batched kernel's warp-slot schedule for one precision mode
+/* Host-side plan of the batched kernel's slot schedule for one precision mode
  * (ILVES_PREC_*), as it would be built for a grid of n_cta CTAs with arena_bytes of
  * shared memory each; no device is needed (introspection and tests).  Outputs (any may
- * be NULL): n_slots, pool_n (molecules drawn at run time from the shared pool);
- * per slot (HOST arrays of n_slots entries; call once with them NULL to size them):
- * slot_cta (CTA of the slot), slot_bytes (its shared-memory slice), slot_queue (number
- * of statically queued molecules); per molecule (n_molecules entries): mol_slot (slot
- * whose queue holds it, -1 for the pool, -2 for molecules off the warp path) and
- * mol_bytes (its shared-memory footprint in this mode, 0 off the warp path).  No
- * counterpart in the paper: the schedule is this library's batching of independent
- * molecules. */
+ * be NULL): n_slots, pool_n (molecules drawn at run time from the pools); per slot (HOST
+ * arrays of n_slots entries; call once with them NULL to size them): slot_cta (CTA of the
+ * slot), slot_bytes (its shared-memory slice), slot_queue (number of statically queued
+ * molecules), slot_team (threads of its team: 96, or 32 for the narrow class; a CTA's
+ * 96-thread slots come first); per molecule (n_molecules entries): mol_slot (slot whose
+ * queue holds it, -1 for its class's pool, -2 for molecules off the batched path),
+ * mol_bytes (its shared-memory footprint in this mode, 0 off the batched path) and
+ * mol_team (threads of the team that solves it, 0 off the batched path); class_info[4]:
+ * the 96-thread slots, the 96-thread class's pool molecules, the threads per CTA of the
+ * launch and the most slots of one CTA.  No counterpart in the paper: the schedule is this
+ * library's batching of independent molecules. */
 ilves_status ilves_topology_schedule(const ilves_topology* topo, int32_t precision, int32_t n_cta,
                                      int32_t arena_bytes, int32_t* n_slots, int32_t* pool_n,
                                      int32_t* slot_cta, int32_t* slot_bytes, int32_t* slot_queue,
-                                     int32_t* mol_slot, int32_t* mol_bytes);
+                                     int32_t* slot_team, int32_t* mol_slot, int32_t* mol_bytes,
+                                     int32_t* mol_team, int32_t* class_info);
 
 /* Measures the float64 FMA rate of the current device (GFLOP/s, 2 flops per FMA) with
  * a kernel of eight independent FMA chains per thread over every SM, timed with CUDA events

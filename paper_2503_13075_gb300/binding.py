@@ -37,7 +37,7 @@ class SetupOpts(ctypes.Structure):
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("max_warp_constraints", ctypes.c_int32),
                 ("partition_min_constraints", ctypes.c_int32), ("part_constraints", ctypes.c_int32),
-                ("wait_test", ctypes.c_int32), ("overlap", ctypes.c_int32)]
+                ("wait_test", ctypes.c_int32), ("overlap", ctypes.c_int32), ("narrow_atoms", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -80,7 +80,7 @@ def lib():
     L.ilves_topology_export_domains.restype = I32
     L.ilves_topology_export_layout.argtypes = [P, I32, P, P, P, P, P]
     L.ilves_topology_export_layout.restype = I32
-    L.ilves_topology_schedule.argtypes = [P, I32, I32, I32, P, P, P, P, P, P, P]
+    L.ilves_topology_schedule.argtypes = [P, I32, I32, I32, P, P, P, P, P, P, P, P, P, P]
     L.ilves_topology_schedule.restype = I32
     L.ilves_destroy_topology.argtypes = [P]
     L.ilves_destroy_topology.restype = None
@@ -146,7 +146,7 @@ class Topology:
 
     def __init__(self, n_atoms, atom_i, atom_j, ordering=0, degree_slack=2, warps_per_cta=0,
                  ctas_per_sm=0, device=None, plan_only=False, max_warp_constraints=0,
-                 partition_min_constraints=0, part_constraints=0, wait_test=0, overlap=0):
+                 partition_min_constraints=0, part_constraints=0, wait_test=0, overlap=0, narrow_atoms=0):
         L = lib()
         ai = np.ascontiguousarray(atom_i, dtype=np.int32)
         aj = np.ascontiguousarray(atom_j, dtype=np.int32)
@@ -161,6 +161,7 @@ class Topology:
         o.part_constraints = part_constraints
         o.wait_test = wait_test
         o.overlap = overlap
+        o.narrow_atoms = narrow_atoms
         if plan_only:
             o.device = -2
         elif device is not None:
@@ -291,21 +292,26 @@ class Topology:
                 "owned": [own[ptr[d]:ptr[d + 1]].astype(bool) for d in range(n)]}
 
     def schedule(self, precision="mixed", n_cta=152, arena_bytes=232448):
-        """Host plan of the batched kernel's warp slots (``ilves_topology_schedule``):
-        dict with slot_cta, slot_bytes, slot_queue (per slot), mol_slot (slot, -1 pool,
-        -2 off the warp path) and mol_bytes (per molecule), and pool_n."""
+        """Host plan of the batched kernel's slots (``ilves_topology_schedule``): dict with
+        slot_cta, slot_bytes, slot_queue, slot_team (per slot), mol_slot (slot, -1 pool, -2
+        off the batched path), mol_bytes and mol_team (per molecule), pool_n, and the
+        96-thread class's n_slots_wide and pool_wide, the launch's block_threads and the
+        most slots of one CTA (max_slots)."""
         L = lib()
         prec = PRECISIONS[precision]
         ns, pn = ctypes.c_int32(), ctypes.c_int32()
         _check(L.ilves_topology_schedule(self._h, prec, int(n_cta), int(arena_bytes), ctypes.byref(ns),
-                                         ctypes.byref(pn), None, None, None, None, None), "ilves_topology_schedule")
-        out = {k: np.zeros(ns.value, np.int32) for k in ("slot_cta", "slot_bytes", "slot_queue")}
-        out.update({k: np.zeros(self.n_molecules, np.int32) for k in ("mol_slot", "mol_bytes")})
+                                         ctypes.byref(pn), *([None] * 8)), "ilves_topology_schedule")
+        slot_keys = ("slot_cta", "slot_bytes", "slot_queue", "slot_team")
+        mol_keys = ("mol_slot", "mol_bytes", "mol_team")
+        out = {k: np.zeros(ns.value, np.int32) for k in slot_keys}
+        out.update({k: np.zeros(self.n_molecules, np.int32) for k in mol_keys})
+        ci = np.zeros(4, np.int32)
         _check(L.ilves_topology_schedule(self._h, prec, int(n_cta), int(arena_bytes), None, None,
-                                         *[_ptr(out[k]) for k in ("slot_cta", "slot_bytes", "slot_queue",
-                                                                  "mol_slot", "mol_bytes")]),
+                                         *[_ptr(out[k]) for k in slot_keys + mol_keys], _ptr(ci)),
                "ilves_topology_schedule")
         out["pool_n"] = pn.value
+        out["n_slots_wide"], out["pool_wide"], out["block_threads"], out["max_slots"] = (int(v) for v in ci)
         return out
 
     def last_launch_count(self):

@@ -156,43 +156,50 @@ __device__ __forceinline__ double as_bits(dfloat v) { return *reinterpret_cast<d
 // ------------------------------------------------------------------------------------
 // teams
 // ------------------------------------------------------------------------------------
-// The kSlotThreads threads (whole warps) of a batched-kernel slot; more than one warp
-// synchronises on named barrier 1 + slot (barrier 0 is the CTA's).
-struct SlotTeam {
-    __device__ __forceinline__ int rank() const { return threadIdx.x % kSlotThreads; }
-    __device__ __forceinline__ int size() const { return kSlotThreads; }
-    __device__ __forceinline__ int id() const { return threadIdx.x / kSlotThreads; }
+// The kThreads threads (whole warps) of a batched-kernel slot: kSlotThreads for the wide
+// slots, one warp for the narrow ones; more than one warp synchronises on named barrier
+// 1 + slot (barrier 0 is the CTA's).
+template <int kThreads>
+struct SlotTeamT {
+    static constexpr int kSize = kThreads;
+    __device__ __forceinline__ int rank() const { return threadIdx.x % kThreads; }
+    __device__ __forceinline__ int size() const { return kThreads; }
+    __device__ __forceinline__ int id() const { return threadIdx.x / kThreads; }
     __device__ __forceinline__ void sync() const {
-        if constexpr (kSlotThreads == 32) __syncwarp();
-        else asm volatile("bar.sync %0, %1;" ::"r"(id() + 1), "n"(kSlotThreads) : "memory");
+        if constexpr (kThreads == 32) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(id() + 1), "n"(kThreads) : "memory");
     }
     __device__ __forceinline__ bool all(bool p) const {
-        if constexpr (kSlotThreads == 32) {
+        if constexpr (kThreads == 32) {
             return __all_sync(0xFFFFFFFFu, p);
         } else {
             unsigned r;
             asm volatile("{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.and.pred po, %2, %3, pi;\n"
                          "selp.u32 %0, 1, 0, po;\n}\n"
                          : "=r"(r)
-                         : "r"((unsigned)p), "r"(id() + 1), "n"(kSlotThreads)
+                         : "r"((unsigned)p), "r"(id() + 1), "n"(kThreads)
                          : "memory");
             return r != 0;
         }
     }
     __device__ __forceinline__ bool any(bool p) const {
-        if constexpr (kSlotThreads == 32) {
+        if constexpr (kThreads == 32) {
             return __any_sync(0xFFFFFFFFu, p);
         } else {
             unsigned r;
             asm volatile("{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, %2, %3, pi;\n"
                          "selp.u32 %0, 1, 0, po;\n}\n"
                          : "=r"(r)
-                         : "r"((unsigned)p), "r"(id() + 1), "n"(kSlotThreads)
+                         : "r"((unsigned)p), "r"(id() + 1), "n"(kThreads)
                          : "memory");
             return r != 0;
         }
     }
 };
+using SlotTeam = SlotTeamT<kSlotThreads>;
+using NarrowTeam = SlotTeamT<kNarrowThreads>;
+template <class T> struct IsSlotTeam : std::false_type {};
+template <int N> struct IsSlotTeam<SlotTeamT<N>> : std::true_type {};
 struct BlockTeam {
     __device__ __forceinline__ int rank() const { return threadIdx.x; }
     __device__ __forceinline__ int size() const { return blockDim.x; }
@@ -914,10 +921,11 @@ struct MolView {
         const int e1 = ldp<kCoh>(tasks + t + 1).tstart;
         task_core(t, tk.row, tk.col, tk.atomsign >> 1, tk.atomsign & 1, tk.tstart, e1, diag, singular);
     }
-    // warp molecules: one level's tasks t0 + lane + 32 k; the lane walks its terms from
-    //      offset e
+    // batched molecules: one level's tasks t0 + lane + kTeam k for a team of kTeam threads
+    //      (the width the program was laid out for); the lane walks its terms from offset e
+    template <int kTeam>
     __device__ __forceinline__ void level_tasks(int t0, int t1, int np, int lane, int& e, bool& singular) {
-        for (int t = t0 + lane; t < t1; t += kSlotThreads) {
+        for (int t = t0 + lane; t < t1; t += kTeam) {
             const uint32_t w = lds<kCoh>(tasks + t);
             const int n = (int)TaskWord::nterm(w);
             const bool diag = t < t0 + np;
@@ -1206,13 +1214,13 @@ struct MolView {
 template <class Mode, class IdxT, class Team>
 __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* prog, uint8_t* st,
                                const SolveArgs& A, const uint8_t* gprog) {
-    constexpr bool kCompact = sizeof(IdxT) == 2;  // batched-kernel molecules (Team = SlotTeam)
+    constexpr bool kCompact = sizeof(IdxT) == 2;  // batched-kernel molecules (a SlotTeamT)
     MolView<Mode, IdxT, false> M;
     M.init(D, prog, st, A, gprog);
     const int na = D.na, nc = D.nc;
     const int r0 = tm.rank(), ts = tm.size();
     // ---- S1
-    if constexpr (std::is_same<Team, SlotTeam>::value) {
+    if constexpr (IsSlotTeam<Team>::value) {
         M.s1_gather(r0, ts);
         tm.sync();
         for (int a = r0; a < na; a += ts) M.s1_atom_local(a);
@@ -1266,7 +1274,7 @@ __device__ void solve_molecule(const Team& tm, const MolDesc& D, const uint8_t* 
                 const int p0 = M.lvl_piv[l], np = M.lvl_piv[l + 1] - p0;
                 const int t0 = M.lvl_task[l], t1 = M.lvl_task[l + 1];
                 if constexpr (kCompact) {
-                    M.level_tasks(t0, t1, np, r0, e, singular);
+                    M.template level_tasks<Team::kSize>(t0, t1, np, r0, e, singular);
                 } else {
                     for (int t = t0 + r0; t < t1; t += ts) M.task(t, t < t0 + np, singular);
                 }
@@ -2084,61 +2092,68 @@ k_solve_opm(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, 
 // ------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------
-constexpr int kStaticSlotSmem = 64;  // bytes: the pool-ticket words of the slots of a CTA
+constexpr int kStaticSlotSmem = 128;  // bytes: the pool-ticket words of the slots of a CTA
 static_assert(kStaticSlotSmem >= (int)(kMaxSlotsPerCta * sizeof(unsigned)), "ticket words");
+static_assert(kStaticSlotSmem >= (int)(kNarrowSlotsPerCta * sizeof(unsigned)), "ticket words");
 
 struct SmallSched {
     const int32_t* cta_slot_ptr;
+    const int32_t* cta_nwide;  // per CTA: its first slots are wide (96-thread teams)
     const int32_t* slot_ptr;
     const int32_t* slot_mol;
     const int32_t* slot_off;
-    const int32_t* pool_mol;
-    uint32_t* pool_ctr;  // {next ticket, slots done}
-    int32_t pool_n, n_slots;
+    const int32_t* pool_mol;  // the wide class's pool, then the narrow class's
+    uint32_t* pool_ctr;       // {next ticket, slots done} of the wide pool, then of the narrow pool
+    int32_t pool_n, n_slots;                // wide class
+    int32_t pool_n_narrow, n_slots_narrow;  // narrow class
 };
 
-// Persistent batched kernel: warp w of CTA c owns one slot (a fixed slice of the CTA's
-// shared-memory arena), solves its queue of molecules one after the other, then draws
-// molecules from the shared pool (one atomic ticket each) until the pool is empty; warps
-// never wait for each other.  Each molecule's program blob is staged into the slice with
-// asynchronous 16-byte copies, and the next queued molecule's program and atom inputs
-// are prefetched into L2 while the current one is solved.  The last warp to finish
-// resets the pool counters for the next launch.
-__device__ __forceinline__ int pool_ticket(const SmallSched& S, const SlotTeam& tm, unsigned* box) {
-    if (tm.rank() == 0) *box = atomicAdd(S.pool_ctr, 1u);
+// One class's pool: the molecules, their number, the ticket counters and the class's slots.
+struct SlotPool {
+    const int32_t* mol;
+    uint32_t* ctr;
+    int32_t n, n_slots;
+};
+
+template <class Team>
+__device__ __forceinline__ int pool_ticket(const SlotPool& P, const Team& tm, unsigned* box) {
+    if (tm.rank() == 0) *box = atomicAdd(P.ctr, 1u);
     tm.sync();
     const unsigned t = *box;
     tm.sync();  // every thread has read the box before the next ticket is written
-    return t < (unsigned)S.pool_n ? __ldg(S.pool_mol + t) : -1;
+    return t < (unsigned)P.n ? __ldg(P.mol + t) : -1;
 }
 
-template <class Mode>
-__global__ void __launch_bounds__(kSlotCtaThreads, 1)
-k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
-              SolveArgs A) {
-    extern __shared__ __align__(16) uint8_t arena[];
-    __shared__ __align__(16) unsigned ticket_box[kStaticSlotSmem / sizeof(unsigned)];
-    const SlotTeam tm;
+// One slot of a CTA, run by a team of Team::kSize threads: the slot owns a fixed slice of
+// the CTA's shared-memory arena, solves its queue
+// of molecules one after the other, then draws molecules from its class's pool (one
+// atomic ticket each) until the pool is empty; teams never wait for each other.  Each
+// molecule's program blob is staged into the slice with asynchronous 16-byte copies, and
+// the next queued molecule's program and atom inputs are prefetched into L2 while the
+// current one is solved.  The last team of the class to finish resets the class's pool
+// counters for the next launch.
+template <class Mode, class Team>
+__device__ __forceinline__ void run_slot(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob,
+                                         const SmallSched& S, const SlotPool& P, const SolveArgs& A,
+                                         uint8_t* arena, unsigned* box, int slot) {
+    const Team tm;
     const int lane = tm.rank();
-    const int slot = S.cta_slot_ptr[blockIdx.x] + tm.id();
-    if (slot >= S.cta_slot_ptr[blockIdx.x + 1]) return;
-    unsigned* box = ticket_box + tm.id();
     uint8_t* slice = arena + S.slot_off[slot];
     const int q1 = S.slot_ptr[slot + 1];
     int q = S.slot_ptr[slot];
-    int mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S, tm, box) : -1);
+    int mol = q < q1 ? S.slot_mol[q] : (P.n > 0 ? pool_ticket(P, tm, box) : -1);
     while (mol >= 0) {
         const MolDesc D = desc[mol];
         const ProgLayout PL = prog_layout<uint16_t>(D.na, D.nc, D.ntask, D.nterm, D.nlevel, D.n_seg);
         const uint4* src = reinterpret_cast<const uint4*>(blob + D.blob_off);
         uint4* dst = reinterpret_cast<uint4*>(slice);
         const int n16 = (int)(PL.staged >> 4);
-        for (int k = lane; k < n16; k += kSlotThreads) cp_async16(dst + k, src + k);  // all in flight
+        for (int k = lane; k < n16; k += Team::kSize) cp_async16(dst + k, src + k);  // all in flight
         if (q + 1 < q1) {  // the next queued molecule's program and atom inputs into L2 meanwhile
             const MolDesc Dn = desc[S.slot_mol[q + 1]];
             const uint32_t nb = prog_layout<uint16_t>(Dn.na, Dn.nc, Dn.ntask, Dn.nterm, Dn.nlevel, Dn.n_seg).bytes;
             const uint8_t* pb = blob + Dn.blob_off;
-            constexpr uint32_t kStep = 128u * kSlotThreads;
+            constexpr uint32_t kStep = 128u * Team::kSize;
             for (uint32_t o = 128u * lane; o < nb; o += kStep) prefetch_l2(pb + o);
             if (Dn.atom_base >= 0) {
                 const uint8_t* xo = reinterpret_cast<const uint8_t*>(A.x_old + 3 * (int64_t)Dn.atom_base);
@@ -2153,19 +2168,43 @@ k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob
         }
         cp_async_wait_all();
         tm.sync();
-        solve_molecule<Mode, uint16_t, SlotTeam>(tm, D, slice, slice + PL.staged, A, blob + D.blob_off);
+        solve_molecule<Mode, uint16_t, Team>(tm, D, slice, slice + PL.staged, A, blob + D.blob_off);
         tm.sync();
         ++q;
-        mol = q < q1 ? S.slot_mol[q] : (S.pool_n > 0 ? pool_ticket(S, tm, box) : -1);
+        mol = q < q1 ? S.slot_mol[q] : (P.n > 0 ? pool_ticket(P, tm, box) : -1);
     }
-    if (S.pool_n > 0 && lane == 0) {
-        __threadfence();  // this warp's last ticket is ordered before its "done"
-        const unsigned done = atomicAdd(S.pool_ctr + 1, 1u);
-        if (done == (unsigned)S.n_slots - 1u) {  // every warp has drawn its last ticket
+    if (P.n > 0 && lane == 0) {
+        __threadfence();  // this team's last ticket is ordered before its "done"
+        const unsigned done = atomicAdd(P.ctr + 1, 1u);
+        if (done == (unsigned)P.n_slots - 1u) {  // every team of the class has drawn its last ticket
             __threadfence();
-            atomicExch(S.pool_ctr, 0u);
-            atomicExch(S.pool_ctr + 1, 0u);
+            atomicExch(P.ctr, 0u);
+            atomicExch(P.ctr + 1, 0u);
         }
+    }
+}
+
+// Persistent batched kernel.  In CTA c the first 3 nw warps (nw = cta_nwide[c]) form the
+// 96-thread teams of the wide slots, each following warp is the one-warp team of a narrow
+// slot (molecules small enough that three of them fit the shared memory of one wide
+// molecule); a CTA's narrow slots follow its wide ones.  The pool-ticket word of a team is
+// that of its first warp.
+static_assert(kSlotThreads == 3 * 32, "a wide slot's team is three warps");
+template <class Mode>
+__global__ void __launch_bounds__(kSlotCtaThreads, 1)
+k_solve_small(const MolDesc* __restrict__ desc, const uint8_t* __restrict__ blob, SmallSched S,
+              SolveArgs A) {
+    extern __shared__ __align__(16) uint8_t arena[];
+    __shared__ __align__(16) unsigned ticket_box[kStaticSlotSmem / sizeof(unsigned)];
+    const int s0 = S.cta_slot_ptr[blockIdx.x], s1 = S.cta_slot_ptr[blockIdx.x + 1];
+    const int nw = S.cta_nwide[blockIdx.x];
+    const int warp = (int)(threadIdx.x / 32);
+    if (warp < 3 * nw) {
+        const SlotPool P{S.pool_mol, S.pool_ctr, S.pool_n, S.n_slots};
+        run_slot<Mode, SlotTeam>(desc, blob, S, P, A, arena, ticket_box + 3 * (warp / 3), s0 + warp / 3);
+    } else if (s0 + nw + (warp - 3 * nw) < s1) {
+        const SlotPool P{S.pool_mol + S.pool_n, S.pool_ctr + 2, S.pool_n_narrow, S.n_slots_narrow};
+        run_slot<Mode, NarrowTeam>(desc, blob, S, P, A, arena, ticket_box + warp, s0 + nw + (warp - 3 * nw));
     }
 }
 
@@ -2220,6 +2259,7 @@ static void free_device(ilves_topology* T) {
     f(T->d_work);
     for (auto& s : T->sched) {
         f(s.cta_slot_ptr);
+        f(s.cta_nwide);
         f(s.slot_ptr);
         f(s.slot_mol);
         f(s.slot_off);
@@ -2369,22 +2409,22 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
     }
     // persistent schedules, one per precision mode
     for (int mode = 0; mode < 3; ++mode) {
-        std::vector<uint32_t> fps;
-        for (int32_t m = 0; m < T->n_mol; ++m)
-            if (!T->mols[m].large) fps.push_back(footprint(T->mols[m], mode));
-        // auto: the largest warp count per CTA whose slices fit the arena (searched downwards)
+        // auto: the largest slot count per CTA whose slices fit the arena (searched downwards)
         int warps = o.warps_per_cta > 0 ? o.warps_per_cta : kMaxSlotsPerCta;
         warps = std::max(1, std::min(kMaxSlotsPerCta, warps));
         HostSchedule HS;
-        build_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
+        build_batched_schedule(T, mode, n_sm * ctas_per_sm, warps, arena, HS);
         for (auto& km : HS.slot_mol) km = desc_index[km];
         for (auto& km : HS.pool_mol) km = desc_index[km];
         DeviceSchedule& DS = T->sched[mode];
         DS.n_cta = HS.n_cta;
         DS.warps = HS.warps;
         DS.arena = HS.arena;
-        DS.n_slots = (int32_t)HS.slot_off.size();
-        DS.pool_n = (int32_t)HS.pool_mol.size();
+        DS.n_slots = HS.n_slots_wide;
+        DS.pool_n = HS.pool_wide;
+        DS.n_slots_narrow = (int32_t)HS.slot_off.size() - HS.n_slots_wide;
+        DS.pool_n_narrow = (int32_t)HS.pool_mol.size() - HS.pool_wide;
+        DS.block_threads = HS.block_threads;
         DS.launch_cta = 0;
         DS.launch_smem = 16;
         for (int32_t c = 0; c < HS.n_cta; ++c) {
@@ -2396,9 +2436,10 @@ static ilves_status upload_topology(ilves_topology* T, const ilves_setup_opts& o
         }
         if (!HS.pool_mol.empty()) {
             if ((e = upload(&DS.pool_mol, HS.pool_mol)) != cudaSuccess) return to_status(e);
-            if ((e = upload(&DS.pool_ctr, std::vector<uint32_t>(2, 0u))) != cudaSuccess) return to_status(e);
+            if ((e = upload(&DS.pool_ctr, std::vector<uint32_t>(4, 0u))) != cudaSuccess) return to_status(e);
         }
         if ((e = upload(&DS.cta_slot_ptr, HS.cta_slot_ptr)) != cudaSuccess) return to_status(e);
+        if ((e = upload(&DS.cta_nwide, HS.cta_nwide)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_ptr, HS.slot_ptr)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_mol, HS.slot_mol)) != cudaSuccess) return to_status(e);
         if ((e = upload(&DS.slot_off, HS.slot_off)) != cudaSuccess) return to_status(e);
@@ -2545,10 +2586,10 @@ static ilves_status launch_all(ilves_topology* T, const SolveArgs& A, cudaStream
         if ((e = cudaEventRecord((cudaEvent_t)T->ev_join, side)) != cudaSuccess) return to_status(e);
     }
     if (T->n_small > 0 && DS.launch_cta > 0) {
-        SmallSched S{DS.cta_slot_ptr, DS.slot_ptr, DS.slot_mol, DS.slot_off, DS.pool_mol, DS.pool_ctr,
-                     DS.pool_n, DS.n_slots};
-        k_solve_small<Mode><<<DS.launch_cta, DS.warps * kSlotThreads, DS.launch_smem, stream>>>(T->d_desc, T->d_blob,
-                                                                                                S, A);
+        SmallSched S{DS.cta_slot_ptr, DS.cta_nwide, DS.slot_ptr,     DS.slot_mol,       DS.slot_off,
+                     DS.pool_mol,     DS.pool_ctr,  DS.pool_n,       DS.n_slots,        DS.pool_n_narrow,
+                     DS.n_slots_narrow};
+        k_solve_small<Mode><<<DS.launch_cta, DS.block_threads, DS.launch_smem, stream>>>(T->d_desc, T->d_blob, S, A);
         if ((e = cudaGetLastError()) != cudaSuccess) return to_status(e);
         ++launches;
     }
@@ -2611,6 +2652,7 @@ extern "C" void ilves_default_opts(ilves_setup_opts* o) {
     o->part_constraints = 0;
     o->wait_test = 0;
     o->overlap = 0;
+    o->narrow_atoms = 0;
 }
 
 extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constraints, const int32_t* atom_i,
@@ -2625,7 +2667,7 @@ extern "C" ilves_status ilves_setup_topology(int32_t n_atoms, int32_t n_constrai
     if (opts) o = *opts;
     if (o.ordering < 0 || o.ordering > 2 || o.degree_slack < 0 || o.warps_per_cta < 0 ||
         o.warps_per_cta > 16 || o.ctas_per_sm < 0 || o.ctas_per_sm > 4 || o.wait_test < 0 || o.wait_test > 64 ||
-        o.overlap < 0 || o.overlap > 16)
+        o.overlap < 0 || o.overlap > 16 || o.narrow_atoms < -1 || o.narrow_atoms > 255)
         return ILVES_ERR_INVALID_ARG;
     ilves_topology* T = new ilves_topology();
     T->wait_test = o.wait_test;
@@ -2831,6 +2873,11 @@ extern "C" ilves_status ilves_autotune(ilves_topology* T, const double* x_old, c
             c.degree_slack = slack < 0 ? 2 : slack;
             add(c);
         }
+        for (int32_t na : {-1, 60, 100}) {  // the narrow class: none, up to 60 or 100 atoms
+            ilves_setup_opts c = base;
+            c.narrow_atoms = na;
+            add(c);
+        }
     }
     if (has_parted) {
         for (int32_t ov : {0, 2, 3, 4, 6}) {
@@ -2954,10 +3001,11 @@ extern "C" ilves_status ilves_topology_export_layout(const ilves_topology* T, in
 extern "C" ilves_status ilves_topology_schedule(const ilves_topology* T, int32_t precision, int32_t n_cta,
                                                 int32_t arena_bytes, int32_t* n_slots, int32_t* pool_n,
                                                 int32_t* slot_cta, int32_t* slot_bytes, int32_t* slot_queue,
-                                                int32_t* mol_slot, int32_t* mol_bytes) {
+                                                int32_t* slot_team, int32_t* mol_slot, int32_t* mol_bytes,
+                                                int32_t* mol_team, int32_t* class_info) {
     if (!T || precision < 0 || precision > 2 || n_cta < 1 || arena_bytes < 1) return ILVES_ERR_INVALID_ARG;
     HostSchedule HS;
-    build_schedule(const_cast<ilves_topology*>(T), precision, n_cta, 16, arena_bytes, HS);
+    build_batched_schedule(const_cast<ilves_topology*>(T), precision, n_cta, kMaxSlotsPerCta, arena_bytes, HS);
     const int32_t ns = (int32_t)HS.slot_off.size();
     if (n_slots) *n_slots = ns;
     if (pool_n) *pool_n = (int32_t)HS.pool_mol.size();
@@ -2966,12 +3014,20 @@ extern "C" ilves_status ilves_topology_schedule(const ilves_topology* T, int32_t
             if (slot_cta) slot_cta[s] = c;
             if (slot_bytes) slot_bytes[s] = HS.slot_bytes[s];
             if (slot_queue) slot_queue[s] = HS.slot_ptr[s + 1] - HS.slot_ptr[s];
+            if (slot_team) slot_team[s] = HS.slot_team[s];
         }
-    if (mol_slot || mol_bytes) {
+    if (class_info) {
+        class_info[0] = HS.n_slots_wide;
+        class_info[1] = HS.pool_wide;
+        class_info[2] = HS.block_threads;
+        class_info[3] = HS.warps;
+    }
+    if (mol_slot || mol_bytes || mol_team) {
         for (int32_t m = 0; m < T->n_mol; ++m) {
             const bool warp = !T->mols[m].large;
             if (mol_slot) mol_slot[m] = warp ? -1 : -2;
             if (mol_bytes) mol_bytes[m] = warp ? (int32_t)footprint(T->mols[m], precision) : 0;
+            if (mol_team) mol_team[m] = warp ? T->mols[m].team : 0;
         }
         if (mol_slot)
             for (int32_t s = 0; s < ns; ++s)

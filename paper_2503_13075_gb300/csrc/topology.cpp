@@ -857,8 +857,8 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
     }
     auto term_of = [&](size_t k) { return TermOf<IdxT>::make(P.terms[k].l, P.terms[k].u, P.terms[k].m); };
     if constexpr (kCompact) {
-        // task words; terms thread by thread (team thread r owns t0 + r + kSlotThreads k of
-        // every level), each thread's terms in level order
+        // task words; terms thread by thread (thread r of the molecule's team of M.team
+        // threads owns t0 + r + M.team k of every level), each thread's terms in level order
         auto* tasks = reinterpret_cast<uint32_t*>(dst + L.tasks);
         auto* lane_term = reinterpret_cast<IdxT*>(dst + L.lane_term);
         const int32_t ntask = (int32_t)P.tasks.size() - 1;
@@ -869,11 +869,12 @@ static void write_blob(uint8_t* dst, const MolHost& M, const Program& P) {
         }
         size_t o = 0;
         const int32_t nl = (int32_t)P.lvl_task.size() - 1;
-        for (int32_t r = 0; r < kSlotThreads; ++r) {
+        const int32_t team = M.team;
+        for (int32_t r = 0; r < team; ++r) {
             lane_term[r] = (IdxT)o;
             for (int32_t l = 0; l < nl; ++l) {
                 const int32_t t0 = P.lvl_task[l], t1 = P.lvl_task[l + 1];
-                for (int32_t t = t0 + r; t < t1; t += kSlotThreads)
+                for (int32_t t = t0 + r; t < t1; t += team)
                     for (uint32_t k = P.tasks[t].tstart; k < P.tasks[t + 1].tstart; ++k) terms[o++] = term_of(k);
             }
         }
@@ -1013,6 +1014,25 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
     std::vector<int32_t> local(n_atoms, -1);
     const int32_t warp_limit = o.max_warp_constraints > 0 ? o.max_warp_constraints : 1024;
     T->progs.assign(n_mol, nullptr);
+    // narrow class threshold.  Explicit (narrow_atoms > 0): every batched molecule of at
+    // most that many atoms.  Default (0): kDefaultNarrowAtoms, but only for a batch made of
+    // such molecules -- at least 90 % of the batched atoms, and more batched molecules than
+    // the wide teams the GPU holds (eight per SM) -- where one-warp teams measured faster;
+    // on batches of mixed sizes they did not (20-200 atoms: no threshold from 40 to 140 beat
+    // the 96-thread teams alone), and a lone molecule finishes sooner on 96 threads.
+    int32_t narrow = o.narrow_atoms > 0 ? o.narrow_atoms : -1;
+    if (o.narrow_atoms == 0) {
+        int64_t batched = 0, small = 0, n_batched = 0;
+        for (int32_t m = 0; m < n_mol; ++m) {
+            const int64_t na = (int64_t)T->mols[m].atoms.size(), nc = (int64_t)T->mols[m].cons.size();
+            if (nc > warp_limit || nc >= (int64_t)kCompactMaxConstraints || na > (int64_t)TaskWord::kMaxAtom) continue;
+            batched += na;
+            ++n_batched;
+            if (na <= kDefaultNarrowAtoms) small += na;
+        }
+        const int64_t wide_teams = (int64_t)kMaxSlotsPerCta * (T->n_sm > 0 ? T->n_sm : 152);
+        if (n_batched > wide_teams && small * 10 >= batched * 9) narrow = kDefaultNarrowAtoms;
+    }
     std::vector<std::vector<int32_t>> inc, adj;
     for (int32_t m = 0; m < n_mol; ++m) {
         MolHost& M = T->mols[m];
@@ -1150,9 +1170,11 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
             T->progs[m] = P;
             continue;
         }
-        Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : kSlotThreads));
+        M.team = (!M.large && na <= narrow) ? kNarrowThreads : kSlotThreads;
+        Program* P = new Program(choose_order(nc, na, adj, M.ci, M.cj, o, M.large ? 1024 : M.team));
         if (!M.large && !fits_compact(*P)) {
             M.large = true;
+            M.team = kSlotThreads;
             *P = choose_order(nc, na, adj, M.ci, M.cj, o, 1024);
         }
         if (!M.large) relabel_atoms_by_degree(M, *P);
@@ -1270,112 +1292,190 @@ uint32_t footprint(const MolHost& M, int mode) {
     return L.staged + S.bytes;
 }
 
-// Warp-slot schedule.  Warp-sized molecules are sorted by shared-memory footprint
-// (largest first).  The smallest ones, holding about kPoolShare of the estimated cost,
-// form a pool that every warp draws from at run time once its own queue is done; they
-// fill the gaps of the static queues, so slots finish within about one small molecule
-// of each other.  The rest is cut into G = n_cta * warps consecutive queues: a queue
-// takes molecules while its estimated cost stays under the per-queue target, and
-// molecules that find no queue go to the front of the pool.  Each queue's slot gets a
-// fixed slice sized for its first (largest) molecule, queues are dealt to CTAs in snake
-// order, so every CTA mixes large and small slices, and the number of warps per CTA is
-// the largest that fits the arena.  Warps never wait for each other.
+// Slot schedule of the batched kernel.  Molecules of each class (96-thread teams, and the
+// narrow class of one-warp teams) are sorted by shared-memory footprint (largest first).
+// The smallest ones of a class, holding about kPoolShare of its estimated cost, form the
+// class's pool, which every slot of the class draws from at run time once its own queue
+// is done; they fill the gaps of the static queues, so slots finish within about one small
+// molecule of each other.  The rest is cut into G consecutive queues: a queue takes
+// molecules while its estimated cost stays under the per-queue target, and molecules that
+// find no queue go to the front of the pool.  Each queue's slot gets a fixed slice sized
+// for its first (largest) molecule.  Every CTA holds x wide and y narrow slots (96 x + 32 y
+// threads at most kSlotCtaThreads): the slots of each class are dealt to the CTAs in snake
+// order, so every CTA mixes large and small slices, and (x, y) is the pair of least
+// estimated time whose slices fit the arena.  Slots never wait for each other.
 constexpr double kPoolShare = 0.10, kQueueSlack = 1.05;
 
-void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
-                    HostSchedule& S) {
-    std::vector<int32_t> small;
-    std::vector<uint32_t> fp(T->n_mol, 0);
-    std::vector<double> cost(T->n_mol, 0.0);
+// estimated cost of one molecule for the schedule (level passes and work of its team)
+double schedule_cost(const MolHost& M) {
+    return 90.0 * (double)M.passes + (6.0 * M.ntask + 4.0 * M.nterm + 60.0 * M.cons.size()) / 32.0;
+}
+
+// Time a one-warp team takes per unit of schedule cost, relative to a 96-thread team, with
+// y one-warp teams per SM: 1.37x at 14 and 1.91x at 24 (batches of 50-100 and 20-50 atoms,
+// mixed, measured), interpolated linearly, and at least 1.15x (a molecule's level chain is
+// the same; its atom-parallel passes take more rounds on one warp).
+static double narrow_team_time(int32_t y) { return std::max(1.15, 1.37 + 0.054 * (double)(y - 14)); }
+
+namespace {
+struct ClassPlan {
+    std::vector<int32_t> sorted;  // the class's molecules, largest footprint first
+    std::vector<uint32_t> fp;     // footprint per molecule id
+    std::vector<double> cost;     // schedule cost per molecule id
+    size_t cut = 0;               // sorted[cut..) is the pool part
+    double head_cost = 0.0, total = 0.0;
+};
+struct ClassSlots {
+    std::vector<std::vector<int32_t>> queue;  // per slot
+    std::vector<uint32_t> slice;              // per slot
+    std::vector<int32_t> pool;
+};
+
+ClassPlan class_plan(const ilves_topology* T, int mode, const std::vector<int32_t>& mols) {
+    ClassPlan C;
+    C.fp.assign(T->n_mol, 0u);
+    C.cost.assign(T->n_mol, 0.0);
+    for (int32_t m : mols) {
+        C.sorted.push_back(m);
+        C.fp[m] = footprint(T->mols[m], mode);
+        C.cost[m] = schedule_cost(T->mols[m]);
+        C.total += C.cost[m];
+    }
+    std::sort(C.sorted.begin(), C.sorted.end(), [&](int32_t a, int32_t b) {
+        return C.fp[a] != C.fp[b] ? C.fp[a] > C.fp[b] : a < b;
+    });
+    // pool: the longest suffix whose cost stays within kPoolShare of the total
+    C.cut = C.sorted.size();
+    double pool_cost = 0.0;
+    while (C.cut > 0 && pool_cost + C.cost[C.sorted[C.cut - 1]] <= kPoolShare * C.total)
+        pool_cost += C.cost[C.sorted[--C.cut]];
+    C.head_cost = C.total - pool_cost;
+    return C;
+}
+
+// The slots of one class for G queues: every non-empty queue, plus pool-only slots (at most
+// one per pool molecule), in queue order (largest slices first).
+ClassSlots class_slots(const ClassPlan& C, int64_t G) {
+    ClassSlots S;
+    if (G <= 0 || C.sorted.empty()) return S;
+    const double target = C.head_cost / (double)G * kQueueSlack;
+    std::vector<std::vector<int32_t>> groups(G);
+    int64_t g = 0;
+    double acc = 0.0;
+    bool full = false;  // every queue closed: the rest joins the pool (it stays the smallest)
+    for (size_t k = 0; k < C.cut; ++k) {
+        const int32_t m = C.sorted[k];
+        if (!full && !groups[g].empty() && acc + C.cost[m] > target) {
+            if (g + 1 < G) {
+                ++g;
+                acc = 0.0;
+            } else {
+                full = true;
+            }
+        }
+        if (full) {
+            S.pool.push_back(m);
+            continue;
+        }
+        groups[g].push_back(m);
+        acc += C.cost[m];
+    }
+    for (size_t k = C.cut; k < C.sorted.size(); ++k) S.pool.push_back(C.sorted[k]);
+    const uint32_t pool_fp = S.pool.empty() ? 0u : C.fp[S.pool.front()];
+    for (int64_t gi = 0, po = 0; gi < G; ++gi) {
+        if (!groups[gi].empty()) {
+            S.slice.push_back(C.fp[groups[gi].front()]);
+            S.queue.push_back(std::move(groups[gi]));
+        } else if (po < (int64_t)S.pool.size()) {
+            S.slice.push_back(pool_fp);
+            S.queue.emplace_back();
+            ++po;
+        }
+    }
+    return S;
+}
+
+// CTA of each slot when n slots are dealt to n_cta CTAs in snake order
+int32_t snake_cta(size_t si, int32_t n_cta) {
+    const int64_t r = (int64_t)si / n_cta, k = (int64_t)si % n_cta;
+    return (int32_t)((r % 2 == 0) ? k : n_cta - 1 - k);
+}
+}  // namespace
+
+void build_batched_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
+                            HostSchedule& S) {
+    std::vector<int32_t> wide, narrow;
     for (int32_t m = 0; m < T->n_mol; ++m) {
         const MolHost& M = T->mols[m];
         if (M.large) continue;
-        small.push_back(m);
-        fp[m] = footprint(M, mode);
-        cost[m] = 90.0 * (double)M.passes + (6.0 * M.ntask + 4.0 * M.nterm + 60.0 * M.cons.size()) / 32.0;
+        (M.team == kNarrowThreads ? narrow : wide).push_back(m);
     }
-    std::sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
-        return fp[a] != fp[b] ? fp[a] > fp[b] : a < b;
+    const ClassPlan CW = class_plan(T, mode, wide), CN = class_plan(T, mode, narrow);
+    // candidate (x, y) pairs, least estimated time first
+    struct Cand { int32_t x, y; double t; };
+    std::vector<Cand> cands;
+    const int32_t xmax = wide.empty() ? 0 : std::max(1, std::min(kMaxSlotsPerCta, warps));
+    for (int32_t x = wide.empty() ? 0 : 1; x <= xmax; ++x) {
+        const int32_t ymax = narrow.empty() ? 0 : (kSlotCtaThreads - kSlotThreads * x) / kNarrowThreads;
+        for (int32_t y = narrow.empty() ? 0 : 1; y <= std::min(ymax, kNarrowSlotsPerCta); ++y) {
+            const double tw = x > 0 ? CW.total / (double)x : 0.0;
+            const double tn = y > 0 ? CN.total * narrow_team_time(y) / (double)y : 0.0;
+            cands.push_back({x, y, std::max(tw, tn)});
+        }
+    }
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) {
+        if (a.t != b.t) return a.t < b.t;
+        return a.x + a.y > b.x + b.y;
     });
-    double total = 0.0;
-    for (int32_t m : small) total += cost[m];
-    // pool: the longest suffix whose cost stays within kPoolShare of the total
-    size_t cut = small.size();
-    double pool_cost = 0.0;
-    while (cut > 0 && pool_cost + cost[small[cut - 1]] <= kPoolShare * total) pool_cost += cost[small[--cut]];
-    const double head_cost = total - pool_cost;
-    for (int32_t w = std::max(1, std::min(kMaxSlotsPerCta, warps)); w >= 1; --w) {
-        const int64_t G = (int64_t)n_cta * w;
-        const double target = head_cost / (double)G * kQueueSlack;
-        std::vector<std::vector<int32_t>> groups(G);
-        std::vector<int32_t> pool;
-        int64_t g = 0;
-        double acc = 0.0;
-        bool full = false;  // every queue closed: the rest joins the pool (it stays the smallest)
-        for (size_t k = 0; k < cut; ++k) {
-            const int32_t m = small[k];
-            if (!full && !groups[g].empty() && acc + cost[m] > target) {
-                if (g + 1 < G) {
-                    ++g;
-                    acc = 0.0;
-                } else {
-                    full = true;
-                }
-            }
-            if (full) {
-                pool.push_back(m);
-                continue;
-            }
-            groups[g].push_back(m);
-            acc += cost[m];
-        }
-        for (size_t k = cut; k < small.size(); ++k) pool.push_back(small[k]);
-        const uint32_t pool_fp = pool.empty() ? 0u : fp[pool.front()];
-        // slots: every non-empty queue, plus pool-only slots (at most one per pool molecule)
-        std::vector<int64_t> slots;
-        for (int64_t gi = 0, po = 0; gi < G; ++gi) {
-            if (!groups[gi].empty()) slots.push_back(gi);
-            else if (po < (int64_t)pool.size()) {
-                slots.push_back(gi);
-                ++po;
-            }
-        }
-        auto slice_of = [&](int64_t gi) { return groups[gi].empty() ? pool_fp : fp[groups[gi].front()]; };
-        std::vector<std::vector<int64_t>> cta_groups(n_cta);
-        for (size_t si = 0; si < slots.size(); ++si) {
-            const int64_t r = (int64_t)si / n_cta, k = (int64_t)si % n_cta;
-            cta_groups[(r % 2 == 0) ? k : n_cta - 1 - k].push_back(slots[si]);
-        }
+    ClassSlots SW, SN;
+    std::vector<std::vector<int32_t>> cw(n_cta), cn(n_cta);  // slot indices per CTA
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        const Cand& c = cands[ci];
+        SW = class_slots(CW, (int64_t)n_cta * c.x);
+        SN = class_slots(CN, (int64_t)n_cta * c.y);
+        for (auto& v : cw) v.clear();
+        for (auto& v : cn) v.clear();
+        for (size_t si = 0; si < SW.slice.size(); ++si) cw[snake_cta(si, n_cta)].push_back((int32_t)si);
+        for (size_t si = 0; si < SN.slice.size(); ++si) cn[snake_cta(si, n_cta)].push_back((int32_t)si);
         bool fits = true;
-        for (int32_t c = 0; c < n_cta && fits; ++c) {
+        for (int32_t k = 0; k < n_cta && fits; ++k) {
             uint64_t used = 0;
-            for (int64_t gi : cta_groups[c]) used += slice_of(gi);
-            fits = used <= (uint64_t)arena && cta_groups[c].size() <= (size_t)kMaxSlotsPerCta;
+            for (int32_t si : cw[k]) used += SW.slice[si];
+            for (int32_t si : cn[k]) used += SN.slice[si];
+            fits = used <= (uint64_t)arena && (int32_t)cw[k].size() <= c.x && (int32_t)cn[k].size() <= c.y;
         }
-        if (!fits && w > 1) continue;
-        S.n_cta = n_cta;
-        S.warps = 1;
-        S.arena = arena;
-        S.cta_slot_ptr.assign(1, 0);
-        S.slot_ptr.assign(1, 0);
-        S.slot_mol.clear();
-        S.slot_off.clear();
-        S.slot_bytes.clear();
-        S.pool_mol = pool;
-        for (int32_t c = 0; c < n_cta; ++c) {
-            uint32_t off = 0;
-            for (int64_t gi : cta_groups[c]) {
-                S.slot_off.push_back((int32_t)off);
-                S.slot_bytes.push_back((int32_t)slice_of(gi));
-                off += slice_of(gi);
-                for (int32_t m : groups[gi]) S.slot_mol.push_back(m);
-                S.slot_ptr.push_back((int32_t)S.slot_mol.size());
-            }
-            S.cta_slot_ptr.push_back((int32_t)S.slot_off.size());
-            S.warps = std::max<int32_t>(S.warps, (int32_t)cta_groups[c].size());
-        }
-        return;
+        if (fits || ci + 1 == cands.size()) break;
     }
+    S = HostSchedule{};
+    S.arena = arena;
+    S.cta_slot_ptr.assign(1, 0);
+    S.slot_ptr.assign(1, 0);
+    S.pool_mol = SW.pool;
+    S.pool_mol.insert(S.pool_mol.end(), SN.pool.begin(), SN.pool.end());
+    S.pool_wide = (int32_t)SW.pool.size();
+    int32_t used_cta = 0;
+    for (int32_t k = 0; k < n_cta; ++k)
+        if (!cw[k].empty() || !cn[k].empty()) used_cta = k + 1;
+    for (int32_t k = 0; k < used_cta; ++k) {  // the slot-owning CTAs are a prefix (snake order)
+        uint32_t off = 0;
+        auto put = [&](const ClassSlots& CS, int32_t si, int32_t team) {
+            S.slot_off.push_back((int32_t)off);
+            S.slot_bytes.push_back((int32_t)CS.slice[si]);
+            S.slot_team.push_back(team);
+            off += CS.slice[si];
+            S.slot_mol.insert(S.slot_mol.end(), CS.queue[si].begin(), CS.queue[si].end());
+            S.slot_ptr.push_back((int32_t)S.slot_mol.size());
+        };
+        for (int32_t si : cw[k]) put(SW, si, kSlotThreads);
+        for (int32_t si : cn[k]) put(SN, si, kNarrowThreads);
+        S.cta_slot_ptr.push_back((int32_t)S.slot_off.size());
+        S.cta_nwide.push_back((int32_t)cw[k].size());
+        S.warps = std::max<int32_t>(S.warps, (int32_t)(cw[k].size() + cn[k].size()));
+        S.block_threads =
+            std::max<int32_t>(S.block_threads, (int32_t)(kSlotThreads * cw[k].size() + kNarrowThreads * cn[k].size()));
+        S.n_slots_wide += (int32_t)cw[k].size();
+    }
+    S.n_cta = used_cta;
 }
 
 }  // namespace ilves

@@ -23,6 +23,9 @@ struct MolHost {
     std::vector<int32_t> aperm;
     bool large = false;
     bool parted = false;  // partitioned: solved by a cooperative multi-CTA launch
+    // batched molecules: threads of the team the program is laid out for (kSlotThreads, or
+    // kNarrowThreads for the narrow class)
+    int32_t team = kSlotThreads;
     int32_t n_seg = 1;
     int32_t nlevel = 0, ntask = 0, nterm = 0, n_fill = 0;
     int32_t n_sept = 0, n_cent = 0;  // partitioned: separator tasks, Schur contribution entries
@@ -43,29 +46,36 @@ struct MolHost {
 
 struct Program;  // topology.cpp
 
-// Warp-slot schedule of the batched kernel: slot s (warp s - cta_slot_ptr[c] of CTA c)
-// owns the shared-memory slice at slot_off[s] and solves slot_mol[slot_ptr[s] ..
-// slot_ptr[s + 1]) in order, then takes molecules from the shared pool (pool_mol, one
-// atomic ticket each) until it is empty.  Pool molecules are the smallest ones and fit
-// every slice.
+// Slot schedule of the batched kernel: CTA c owns slots [cta_slot_ptr[c],
+// cta_slot_ptr[c + 1]), the first cta_nwide[c] of them run by 96-thread teams (warps
+// 0 .. 3 cta_nwide[c] - 1), the others by one-warp teams (the narrow class, the warps after
+// them).  Slot s owns the shared-memory slice at slot_off[s] and solves slot_mol[slot_ptr[s]
+// .. slot_ptr[s + 1]) in order, then takes molecules from its class's pool (pool_mol: the
+// wide class's pool_wide molecules, then the narrow class's; one atomic ticket each) until
+// it is empty.  Pool molecules are the smallest of their class and fit every slice of it.
 struct HostSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
-    std::vector<int32_t> cta_slot_ptr, slot_ptr, slot_mol, slot_off, slot_bytes, pool_mol;
+    std::vector<int32_t> cta_slot_ptr, cta_nwide, slot_ptr, slot_mol, slot_off, slot_bytes, slot_team, pool_mol;
+    int32_t n_slots_wide = 0, pool_wide = 0, block_threads = 0;
 };
 
 struct DeviceSchedule {
     int32_t n_cta = 0, warps = 0, arena = 0;
-    int32_t n_slots = 0, pool_n = 0;
+    int32_t n_slots = 0, pool_n = 0;                // wide class
+    int32_t n_slots_narrow = 0, pool_n_narrow = 0;  // narrow class (its pool follows the wide pool)
+    int32_t block_threads = 0;                      // threads per launched CTA
     // launch shape: only the CTAs that own slots (a prefix: slots are dealt from CTA 0), each
     // with the shared memory of its slices -- a topology of a few molecules then occupies a
     // few SMs, and solves of several topologies on different streams run side by side
     int32_t launch_cta = 0, launch_smem = 0;
     int32_t* cta_slot_ptr = nullptr;
+    int32_t* cta_nwide = nullptr;
     int32_t* slot_ptr = nullptr;
     int32_t* slot_mol = nullptr;  // index into the small-molecule descriptor array
     int32_t* slot_off = nullptr;
     int32_t* pool_mol = nullptr;
-    uint32_t* pool_ctr = nullptr;  // {next ticket, slots done}; zero between launches
+    uint32_t* pool_ctr = nullptr;  // {next ticket, slots done} of the wide, then of the narrow
+                                   // pool; zero between launches
 };
 
 }  // namespace ilves
@@ -118,8 +128,9 @@ namespace ilves {
 ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, const int32_t* ai,
                            const int32_t* aj, const ilves_setup_opts& o);
 uint32_t footprint(const MolHost& M, int mode);
-void build_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
-                    HostSchedule& S);
+double schedule_cost(const MolHost& M);
+void build_batched_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t warps, int32_t arena,
+                            HostSchedule& S);
 int64_t program_blob_bytes(const ilves_topology* T, int32_t m);
 void program_write_blob(const ilves_topology* T, int32_t m, uint8_t* dst);
 void program_export(const ilves_topology* T, int32_t m, int32_t* pos_gid, int32_t* level,

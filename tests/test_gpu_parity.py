@@ -60,6 +60,41 @@ def trees_full():
     return s, orc.solve_system(s, tol=TOL)
 
 
+@pytest.fixture(scope="module")
+def small_trees():
+    """1,300 trees of 20..100 atoms: more molecules than the GPU's 96-thread teams, all at
+    most 100 atoms, so the automatic choice solves every one on a one-warp team."""
+    s = wl.tree_batch(n_mol=1300, lo=20, hi=100, seed=1701)
+    return s, orc.solve_system(s, tol=TOL)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("narrow", [0, 60, 100])
+def test_narrow_teams(prec, narrow, small_trees, trees):
+    """One-warp teams (the narrow class): all molecules of a batch of small trees
+    (automatic choice), and both classes side by side in every CTA (explicit thresholds on
+    the 20..200-atom batch; then each CTA's wide and narrow slots run at once)."""
+    s, ref = small_trees if narrow == 0 else trees
+    topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j, narrow_atoms=narrow)
+    team = topo.schedule(prec)["mol_team"]
+    assert np.all(team == 32) if narrow == 0 else (np.any(team == 32) and np.any(team == 96))
+    for start in (None, "diag"):
+        t, x, lam, it, st = run(s, prec, topo=topo, start=start)
+        compare(s, ref, x, lam, it, st, it_slack=1 if start is None else 2)
+    if narrow == 60:  # ILVES-F on both classes: same root, chord iterations within +-1
+        ref_chord = orc.solve_system(s, tol=TOL, max_iter=60, method="chord")
+        t, x, lam, it, st = run(s, prec, topo=topo, method="chord", max_iter=60)
+        assert np.all(st == B.CONVERGED)
+        assert np.abs(it - ref_chord.iterations).max() <= 1
+        assert np.abs(x - ref.x).max() <= X_TOL
+        # the float-float mode tests convergence on |r|^2 - d^2 evaluated with ~48 significant
+        # bits of |r|^2 (absolute error up to ~2^-47 |r|^2, 1.6 % of the tolerance for d^2 >=
+        # 0.01 nm^2); the chord method's linear convergence stops just under the tolerance,
+        # so its float64 recomputation may exceed it by that much
+        slack = 2.0 ** -46 if prec == "mixed_df" else 0.0
+        assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL + slack
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_chain64(prec):
     s = wl.chain64()

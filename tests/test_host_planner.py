@@ -223,28 +223,72 @@ def test_symbolic_factorisation_benzene_rings():
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df"])
 @pytest.mark.parametrize("n_mol,n_cta", [(600, 152), (37, 152), (1, 152), (300, 4)])
-def test_warp_slot_schedule(prec, n_mol, n_cta):
-    """Every warp-path molecule is queued exactly once (a slot or the pool), fits its
-    slot's slice, pool molecules fit every slice, and each CTA's slices fit the arena."""
+@pytest.mark.parametrize("narrow", [0, -1, 60, 140])
+def test_warp_slot_schedule(prec, n_mol, n_cta, narrow):
+    """Every batched molecule is queued exactly once (a slot of its class or its class's
+    pool), fits its slot's slice, pool molecules fit every slice of their class, each
+    CTA's slices fit the arena and its teams the CTA's threads, and a CTA's 96-thread slots
+    come before its one-warp slots."""
     arena = 232448
     s = wl.tree_batch(n_mol=n_mol, seed=11)
-    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True)
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, narrow_atoms=narrow)
     sc = t.schedule(prec, n_cta=n_cta, arena_bytes=arena)
-    ms, mb = sc["mol_slot"], sc["mol_bytes"]
-    ns = len(sc["slot_cta"])
+    ms, mb, team = sc["mol_slot"], sc["mol_bytes"], sc["mol_team"]
+    st, cta = sc["slot_team"], sc["slot_cta"]
+    atoms = t.molecules()[0]
+    ns = len(cta)
     assert ns >= 1 and np.all(mb > 0)
+    # the class follows the size threshold (-1: no narrow class; 0: none for these batches
+    # of 20-200 atoms)
+    assert np.array_equal(team == 32, atoms <= (-1 if narrow <= 0 else narrow))
+    assert np.all((team == 32) | (team == 96)) and np.all((st == 32) | (st == 96))
     queued = ms >= 0
     assert np.array_equal(np.bincount(ms[queued], minlength=ns), sc["slot_queue"])
     assert int((ms == -1).sum()) == sc["pool_n"]
+    assert int(((ms == -1) & (team == 96)).sum()) == sc["pool_wide"]
     assert np.all(mb[queued] <= sc["slot_bytes"][ms[queued]])
-    if sc["pool_n"]:
-        assert mb[ms == -1].max() <= sc["slot_bytes"].min()
-        # the pool holds the smallest molecules
-        assert mb[ms == -1].max() <= mb[queued].min() if queued.any() else True
-    per_cta = np.bincount(sc["slot_cta"], weights=sc["slot_bytes"], minlength=n_cta)
+    assert np.all(st[ms[queued]] == team[queued])  # queued in a slot of its class
+    assert int((st == 96).sum()) == sc["n_slots_wide"]
+    for cls in (96, 32):
+        pool = (ms == -1) & (team == cls)
+        if pool.any():
+            assert (st == cls).any()
+            assert mb[pool].max() <= sc["slot_bytes"][st == cls].min()
+            q = queued & (team == cls)  # the pool holds the class's smallest molecules
+            assert mb[pool].max() <= mb[q].min() if q.any() else True
+    per_cta = np.bincount(cta, weights=sc["slot_bytes"], minlength=n_cta)
     assert per_cta.max() <= arena
-    assert np.bincount(sc["slot_cta"], minlength=n_cta).max() <= 16
-    assert np.all(np.diff(sc["slot_cta"]) >= 0)  # slots are numbered CTA by CTA
+    threads = np.bincount(cta, weights=st, minlength=n_cta)
+    assert threads.max() == sc["block_threads"] <= 768
+    assert np.bincount(cta).max() == sc["max_slots"]
+    assert np.all(np.diff(cta) >= 0)  # slots are numbered CTA by CTA
+    for c in range(cta.max() + 1):  # the used CTAs are a prefix; wide slots first
+        tc = st[cta == c]
+        assert tc.size > 0 and np.all(np.diff(tc) <= 0)
+        assert (tc == 96).sum() <= 8
+
+
+def test_narrow_class_automatic_choice():
+    """narrow_atoms = 0: one-warp teams for molecules of at most 100 atoms only in a batch of
+    such molecules (>= 90 % of the batched atoms) larger than the GPU's 96-thread teams
+    (8 per SM, 152 SMs); the schedule then gives them one-warp slots, up to 24 per CTA."""
+    small = wl.tree_batch(n_mol=1300, lo=20, hi=100, seed=5)
+    t = B.Topology(small.n_atoms, small.atom_i, small.atom_j, plan_only=True)
+    sc = t.schedule("mixed")
+    assert np.all(sc["mol_team"] == 32) and np.all(sc["slot_team"] == 32)
+    assert sc["max_slots"] > 8 and sc["n_slots_wide"] == 0
+    few = wl.tree_batch(n_mol=1000, lo=20, hi=100, seed=5)  # fewer molecules than wide teams
+    t = B.Topology(few.n_atoms, few.atom_i, few.atom_j, plan_only=True)
+    assert np.all(t.schedule("mixed")["mol_team"] == 96)
+    mixed = wl.tree_batch(n_mol=1300, lo=20, hi=200, seed=5)  # mixed sizes: no narrow class
+    t = B.Topology(mixed.n_atoms, mixed.atom_i, mixed.atom_j, plan_only=True)
+    assert np.all(t.schedule("mixed")["mol_team"] == 96)
+    # explicit threshold on the mixed batch: both classes, every CTA mixing them
+    t = B.Topology(mixed.n_atoms, mixed.atom_i, mixed.atom_j, plan_only=True, narrow_atoms=60)
+    sc = t.schedule("mixed")
+    atoms = t.molecules()[0]
+    assert np.array_equal(sc["mol_team"] == 32, atoms <= 60)
+    assert 0 < sc["n_slots_wide"] < len(sc["slot_team"])
 
 
 def test_batched_atoms_ordered_by_degree():
