@@ -219,8 +219,9 @@ ilves_status ilves_solve(ilves_topology* topo, const double* x_old, const double
  *
  * Semantics, arguments and results are those of ilves_solve.  The difference: the solver
  * state of every molecule that a whole CTA or a cooperative group of CTAs solves (molecules
- * too large for one warp team, and partitioned molecules with their Schur contribution
- * slots), and the grid-barrier areas of partitioned molecules, live in one file-scope
+ * too large for one warp team, partitioned molecules with their Schur contribution slots,
+ * and molecules solved by overlapping domains with their positions, corrections and
+ * multipliers), and the grid-barrier areas of those solves, live in one file-scope
  * device array of ilves_static_scratch_bytes() bytes (16 MiB) instead of the topology's
  * workspace.  Every GPU that loads the library holds that array until exit.
  *  - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
@@ -249,7 +250,8 @@ ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_ol
  * nothing at run time).  Re-plans the topology under candidate set-up options, one knob at
  * a time from its current options -- the batched kernel's molecule slots per CTA
  * (warps_per_cta 8, 7, 6), CTAs per SM (1, 2), the elimination order (per-molecule cost
- * model, or rounds with degree slack 1 or 3), and for molecules above the partition
+ * model, or rounds with degree slack 1 or 3), the one-warp team class (narrow_atoms -1, 60,
+ * 100), and for molecules above the partition
  * threshold the exact Schur complement (overlap 0) or overlapping domains of depth 2, 3, 4
  * or 6 -- times `reps` solves of each on the given inputs (CUDA events on `stream`, after
  * one untimed solve), and keeps the fastest configuration whose solves all converge.  The
