@@ -14,12 +14,17 @@ from paper_2503_13075_gb300 import workloads as wl  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("case", ["trees", "protein_parted", "protein_domains"])
+@pytest.mark.parametrize("case", ["trees", "trees_one_warp_teams", "protein_parted", "protein_domains"])
 def test_solve_replays_from_a_cuda_graph(case):
     dev = torch.device("cuda:0")
     if case == "trees":
         s = wl.tree_batch(n_mol=256, seed=1012)
         t = B.Topology(s.n_atoms, s.atom_i, s.atom_j)
+    elif case == "trees_one_warp_teams":  # both slot classes in every CTA, each with its pool
+        s = wl.tree_batch(n_mol=2000, seed=1015)
+        t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, narrow_atoms=80)
+        sc = t.schedule("mixed")
+        assert 0 < sc["n_slots_wide"] < len(sc["slot_team"]) and sc["pool_wide"] < sc["pool_n"]
     elif case == "protein_domains":
         s = wl.protein_like(n_atoms=12000, seed=1014)
         t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, partition_min_constraints=2000, overlap=4)
