@@ -70,19 +70,25 @@ def parse():
                    help="protein_like: solve by overlapping domains with this overlap (0 = exact Schur complement)")
     p.add_argument("--xoh", action="store_true",
                    help="add X-O-H triangle-closing distances on every hydroxyl (main text, h-angles)")
+    p.add_argument("--tree-atoms", default="20-200",
+                   help="tree_batch: molecule sizes LO-HI in atoms (uniform; the headline batch is 20-200)")
+    p.add_argument("--narrow-atoms", type=int, default=0,
+                   help="set-up option narrow_atoms: one-warp teams for batched molecules of at most this many "
+                        "atoms (0 = automatic, -1 = none)")
     p.add_argument("--warm-start", default="diag", choices=["none", "diag", "mlp"],
                    help="initial multipliers: zero, diagonal (Jacobi) guess, or the learned network")
     return p.parse_args()
 
 
-def workload(name, n_mol, seed, n_atoms=100_000, xoh=False):
+def workload(name, n_mol, seed, n_atoms=100_000, xoh=False, tree_atoms="20-200"):
     from paper_2503_13075_gb300 import workloads as wl
 
     if name == "protein_like":
         return wl.protein_like(n_atoms=n_atoms, seed=1002 + (seed - 1001), xoh=xoh)
     if name == "chain64":
         return wl.chain64(seed=1000 + (seed - 1001))
-    return wl.tree_batch(n_mol=n_mol, seed=seed, xoh=xoh)
+    lo, hi = (int(v) for v in tree_atoms.split("-"))
+    return wl.tree_batch(n_mol=n_mol, lo=lo, hi=hi, seed=seed, xoh=xoh)
 
 
 def workload_name(s):
@@ -94,8 +100,22 @@ def workload_name(s):
     if s.name == "chain64":
         return "chain64: one 64-carbon chain, 63 bonds, batch of 1 (latency)"
     extra = "all bonds and X-O-H distances" if s.n_constraints > s.n_atoms - s.n_molecules else "all bonds"
-    return (f"tree_batch: {s.n_molecules} tree molecules of U{{20..200}} atoms "
+    sizes = np.diff(np.asarray(s.mol_atom_ptr)) if s.mol_atom_ptr is not None else np.array([s.n_atoms])
+    return (f"tree_batch: {s.n_molecules} tree molecules of U{{{sizes.min()}..{sizes.max()}}} atoms "
             f"({s.n_atoms} atoms, {s.n_constraints} constraints), {extra} constrained")
+
+
+def slot_summary(topo, precision):
+    """The batched kernel's slots: how many 96-thread and one-warp teams, on how many CTAs
+    (the host plan for 152 SMs at the topology's CTAs per SM)."""
+    cps = max(1, int(topo.tuning().get("chosen", {}).get("ctas_per_sm", 0) or 1))
+    arena = min(232448 - 128, 233472 // cps - 1024) & ~15
+    sc = topo.schedule(precision, n_cta=152 * cps, arena_bytes=arena)
+    nw = int((sc["slot_team"] == 96).sum())
+    nn = len(sc["slot_team"]) - nw
+    ctas = int(sc["slot_cta"].max()) + 1 if len(sc["slot_cta"]) else 0
+    return (f"persistent CTAs ({ctas}), {nw} molecule slots of 96-thread teams"
+            + (f" and {nn} of one-warp teams" if nn else ""))
 
 
 def algorithmic_bytes(s):
@@ -341,7 +361,7 @@ def run_reference(args):
     rank, world, local = dist_setup(args)
     if rank != 0:
         return
-    s = workload(args.workload, args.n_mol, 1001, args.n_atoms, args.xoh)
+    s = workload(args.workload, args.n_mol, 1001, args.n_atoms, args.xoh, args.tree_atoms)
     cores = os.cpu_count() or 1
     tasks = molecule_chunks(s, 4 * cores, args.tol)
     use_pool = len(tasks) > 1 and cores > 1
@@ -476,8 +496,9 @@ def run_ilves(args):
     dev = torch.device("cuda", local)
     from paper_2503_13075_gb300 import binding as B
 
-    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank, args.n_atoms, args.xoh)  # weak scaling: own batch per rank
-    topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j, overlap=args.overlap)
+    s = workload(args.workload, args.n_mol, 1001 + 7919 * rank, args.n_atoms, args.xoh,
+                 args.tree_atoms)  # weak scaling: own batch per rank
+    topo = B.Topology(s.n_atoms, s.atom_i, s.atom_j, overlap=args.overlap, narrow_atoms=args.narrow_atoms)
     f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     dev_in = (f(s.x_old), f(s.x_unc), f(s.inv_mass), f(s.d))
     out = (torch.empty_like(dev_in[1]), torch.empty(s.n_constraints, dtype=torch.float64, device=dev),
@@ -673,7 +694,7 @@ def run_ilves(args):
             "l2": "flushed (256 MiB write) before every timed step",
             "schedule": (("cooperative CTAs over overlapping domains (overlap %d), quasi-Newton" % topo.tuning()["chosen"]["overlap"]
                           if uses_domains else "cooperative CTAs over partitions + separator (Schur) block")
-                         if s.name == "protein_like" else "persistent CTAs, one 96-thread team per molecule"),
+                         if s.name == "protein_like" else slot_summary(topo, args.precision)),
             "autotune": tuning,
             "launch": launch_mode,
         },
