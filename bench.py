@@ -544,6 +544,18 @@ def run_ilves(args):
                              "mean_iterations": float(it.mean())})
             if (prec, wsn, meth) == ("fp64", "none", "newton"):
                 value64, per64 = s.n_atoms / (per * 1e-3), per
+        # the plain float64 solve on a topology tuned for it (zero start): set-up options
+        # that suit the mixed mode (one-warp teams, CTAs per SM) may not suit float64, and the
+        # comparator takes the faster of the two
+        if tuning is not None and value64 is not None:
+            topo64 = B.Topology(s.n_atoms, s.atom_i, s.atom_j, overlap=args.overlap)
+            topo64.autotune(*dev_in, tol=args.tol, precision="fp64", start=None, reps=3)
+            step = make_step(topo64, dev_in, out, "fp64", args.tol, "none", None, lam0, "newton")
+            msa, _ = time_device(step, max(3, args.steps // 4), 2, flush, stream)
+            per = sum(msa) / len(msa)
+            if per < per64 and check()[0]:
+                value64, per64 = s.n_atoms / (per * 1e-3), per
+            del topo64
 
     # overlapping domains are a quasi-Newton method: the plain FP64 GPU Newton solve they are
     # compared with is ILVES-M itself (exact Newton, Schur complement over the separators)
@@ -721,7 +733,9 @@ def run_ilves(args):
                      "kernel": kname,
                      "kernel_ms": solve_per},
         "plain_fp64": None if value64 is None else (exact64 or {"value": value64, "ms_per_step": per64,
-                                                               "precision": "fp64", "warm_start": "none"}),
+                                                               "precision": "fp64", "warm_start": "none",
+                                                               "setup": "the faster of the headline's topology and "
+                                                                        "one autotuned for float64"}),
         "speedup_vs_plain_fp64": None if value64 is None else value / value64,
     }
     print(json.dumps(rounded(res)))

@@ -136,9 +136,11 @@ typedef struct {
                                       one-warp teams (up to 24 per persistent CTA, beside its
                                       96-thread teams) instead of 96-thread teams: three small
                                       molecules then share the shared memory and the warps of one
-                                      large one.  0 = automatic (100 atoms when such molecules hold
+                                      large one; the planner puts them on as many CTAs as balance the
+                                      two classes.  0 = automatic (100 atoms when such molecules hold
                                       at least 90 % of the batched atoms and outnumber the 96-thread
-                                      teams the GPU holds, else none), -1 = none, else 1..255 */
+                                      teams the GPU holds, else none; ilves_autotune tries other
+                                      thresholds), -1 = none, else 1..255 */
 } ilves_setup_opts;
 
 /* Fills `opts` with the defaults. */
@@ -250,8 +252,8 @@ ilves_status ilves_solve_static_scratch(ilves_topology* topo, const double* x_ol
  * nothing at run time).  Re-plans the topology under candidate set-up options, one knob at
  * a time from its current options -- the batched kernel's molecule slots per CTA
  * (warps_per_cta 8, 7, 6), CTAs per SM (1, 2), the elimination order (per-molecule cost
- * model, or rounds with degree slack 1 or 3), the one-warp team class (narrow_atoms -1, 60,
- * 100), and for molecules above the partition
+ * model, or rounds with degree slack 1 or 3), the one-warp team class (narrow_atoms -1, 50,
+ * 60, 70, 100), and for molecules above the partition
  * threshold the exact Schur complement (overlap 0) or overlapping domains of depth 2, 3, 4
  * or 6 -- times `reps` solves of each on the given inputs (CUDA events on `stream`, after
  * one untimed solve), and keeps the fastest configuration whose solves all converge.  The

@@ -2873,7 +2873,7 @@ extern "C" ilves_status ilves_autotune(ilves_topology* T, const double* x_old, c
             c.degree_slack = slack < 0 ? 2 : slack;
             add(c);
         }
-        for (int32_t na : {-1, 60, 100}) {  // the narrow class: none, up to 60 or 100 atoms
+        for (int32_t na : {-1, 50, 60, 70, 100}) {  // the one-warp class: none, or up to na atoms
             ilves_setup_opts c = base;
             c.narrow_atoms = na;
             add(c);

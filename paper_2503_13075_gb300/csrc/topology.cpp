@@ -1018,8 +1018,9 @@ ilves_status plan_topology(ilves_topology* T, int32_t n_atoms, int32_t n_c, cons
     // most that many atoms.  Default (0): kDefaultNarrowAtoms, but only for a batch made of
     // such molecules -- at least 90 % of the batched atoms, and more batched molecules than
     // the wide teams the GPU holds (eight per SM) -- where one-warp teams measured faster;
-    // on batches of mixed sizes they did not (20-200 atoms: no threshold from 40 to 140 beat
-    // the 96-thread teams alone), and a lone molecule finishes sooner on 96 threads.
+    // on batches of mixed sizes the gain depends on the precision mode (20-200 atoms with
+    // one-warp teams up to 60 atoms: 6 % faster in mixed mode, 5 % slower in float64), so
+    // there the autotuner decides; a lone molecule finishes sooner on 96 threads.
     int32_t narrow = o.narrow_atoms > 0 ? o.narrow_atoms : -1;
     if (o.narrow_atoms == 0) {
         int64_t batched = 0, small = 0, n_batched = 0;
@@ -1300,10 +1301,12 @@ uint32_t footprint(const MolHost& M, int mode) {
 // molecule of each other.  The rest is cut into G consecutive queues: a queue takes
 // molecules while its estimated cost stays under the per-queue target, and molecules that
 // find no queue go to the front of the pool.  Each queue's slot gets a fixed slice sized
-// for its first (largest) molecule.  Every CTA holds x wide and y narrow slots (96 x + 32 y
-// threads at most kSlotCtaThreads): the slots of each class are dealt to the CTAs in snake
-// order, so every CTA mixes large and small slices, and (x, y) is the pair of least
-// estimated time whose slices fit the arena.  Slots never wait for each other.
+// for its first (largest) molecule.  The first k CTAs hold x wide and y narrow slots (96 x
+// + 32 y threads at most kSlotCtaThreads), the others only wide slots (as many as the
+// options allow): the slots of each class are dealt to the CTAs that take them in snake
+// order, so every CTA mixes large and small slices, and (x, y, k) is the triple of least
+// estimated time (the slower class's cost over its slots) whose slices fit the arena.
+// Slots never wait for each other.
 constexpr double kPoolShare = 0.10, kQueueSlack = 1.05;
 
 // estimated cost of one molecule for the schedule (level passes and work of its team)
@@ -1311,11 +1314,11 @@ double schedule_cost(const MolHost& M) {
     return 90.0 * (double)M.passes + (6.0 * M.ntask + 4.0 * M.nterm + 60.0 * M.cons.size()) / 32.0;
 }
 
-// Time a one-warp team takes per unit of schedule cost, relative to a 96-thread team, with
-// y one-warp teams per SM: 1.37x at 14 and 1.91x at 24 (batches of 50-100 and 20-50 atoms,
-// mixed, measured), interpolated linearly, and at least 1.15x (a molecule's level chain is
-// the same; its atom-parallel passes take more rounds on one warp).
-static double narrow_team_time(int32_t y) { return std::max(1.15, 1.37 + 0.054 * (double)(y - 14)); }
+// Time a one-warp team takes per unit of schedule cost (the cost of its 32-lane program),
+// relative to a 96-thread team: calibrated on the 20-200-atom batch (mixed), where 1.2-1.4
+// balanced the two classes' end times and gave the fastest launches (1.8 left the one-warp
+// slots idle for the last ~25 % of the launch).
+constexpr double kNarrowTeamTime = 1.3;
 
 namespace {
 struct ClassPlan {
@@ -1395,10 +1398,26 @@ ClassSlots class_slots(const ClassPlan& C, int64_t G) {
     return S;
 }
 
-// CTA of each slot when n slots are dealt to n_cta CTAs in snake order
-int32_t snake_cta(size_t si, int32_t n_cta) {
-    const int64_t r = (int64_t)si / n_cta, k = (int64_t)si % n_cta;
-    return (int32_t)((r % 2 == 0) ? k : n_cta - 1 - k);
+// n slots dealt to CTAs [0, cap.size()) in snake order (largest slices first, so every CTA
+// mixes large and small ones), skipping CTAs that hold cap[c] slots already; false if the
+// capacities do not hold them all
+bool deal(size_t n, const std::vector<int32_t>& cap, std::vector<std::vector<int32_t>>& out) {
+    const int64_t nc = (int64_t)cap.size();
+    int64_t room = 0;
+    for (int32_t c : cap) room += c;
+    if ((int64_t)n > room) return false;
+    int64_t p = 0;
+    for (size_t si = 0; si < n; ++si) {
+        for (;; ++p) {
+            const int64_t r = p / nc, k = p % nc, c = (r % 2 == 0) ? k : nc - 1 - k;
+            if ((int32_t)out[c].size() < cap[c]) {
+                out[c].push_back((int32_t)si);
+                ++p;
+                break;
+            }
+        }
+    }
+    return true;
 }
 }  // namespace
 
@@ -1411,16 +1430,32 @@ void build_batched_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t 
         (M.team == kNarrowThreads ? narrow : wide).push_back(m);
     }
     const ClassPlan CW = class_plan(T, mode, wide), CN = class_plan(T, mode, narrow);
-    // candidate (x, y) pairs, least estimated time first
-    struct Cand { int32_t x, y; double t; };
+    // candidates: CTAs [0, k) hold x wide and y narrow slots, CTAs [k, n_cta) xmax wide
+    // slots only (k = n_cta: every CTA alike); least estimated time first
+    struct Cand { int32_t x, y, k; double t; };
     std::vector<Cand> cands;
     const int32_t xmax = wide.empty() ? 0 : std::max(1, std::min(kMaxSlotsPerCta, warps));
-    for (int32_t x = wide.empty() ? 0 : 1; x <= xmax; ++x) {
-        const int32_t ymax = narrow.empty() ? 0 : (kSlotCtaThreads - kSlotThreads * x) / kNarrowThreads;
-        for (int32_t y = narrow.empty() ? 0 : 1; y <= std::min(ymax, kNarrowSlotsPerCta); ++y) {
-            const double tw = x > 0 ? CW.total / (double)x : 0.0;
-            const double tn = y > 0 ? CN.total * narrow_team_time(y) / (double)y : 0.0;
-            cands.push_back({x, y, std::max(tw, tn)});
+    auto est = [&](int64_t w_slots, int64_t n_slots) {
+        const double tw = CW.total > 0.0 ? CW.total / (double)std::max<int64_t>(1, w_slots) : 0.0;
+        const double tn = CN.total > 0.0 ? CN.total * kNarrowTeamTime / (double)std::max<int64_t>(1, n_slots) : 0.0;
+        return std::max(tw, tn);
+    };
+    if (narrow.empty()) {
+        for (int32_t x = 1; x <= xmax; ++x) cands.push_back({x, 0, n_cta, est((int64_t)n_cta * x, 0)});
+    } else {
+        for (int32_t x = wide.empty() ? 0 : 1; x <= (wide.empty() ? 0 : xmax); ++x) {
+            const int32_t ymax = std::min(kNarrowSlotsPerCta, (kSlotCtaThreads - kSlotThreads * x) / kNarrowThreads);
+            for (int32_t y = 1; y <= ymax; ++y) {
+                const int32_t k0 = (wide.empty() || x == xmax) ? n_cta : 1;
+                Cand best{x, y, n_cta, 1e300};
+                for (int32_t k = k0; k <= n_cta; ++k) {
+                    const double t = est((int64_t)k * x + (int64_t)(n_cta - k) * xmax, (int64_t)k * y);
+                    if (t < best.t) best = {x, y, k, t};
+                }
+                cands.push_back(best);
+                if (best.k != n_cta)  // every CTA alike, in case the best split does not fit
+                    cands.push_back({x, y, n_cta, est((int64_t)n_cta * x, (int64_t)n_cta * y)});
+            }
         }
     }
     std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) {
@@ -1431,18 +1466,27 @@ void build_batched_schedule(ilves_topology* T, int mode, int32_t n_cta, int32_t 
     std::vector<std::vector<int32_t>> cw(n_cta), cn(n_cta);  // slot indices per CTA
     for (size_t ci = 0; ci < cands.size(); ++ci) {
         const Cand& c = cands[ci];
-        SW = class_slots(CW, (int64_t)n_cta * c.x);
-        SN = class_slots(CN, (int64_t)n_cta * c.y);
+        std::vector<int32_t> capw(n_cta), capn(n_cta);
+        int64_t nw = 0, nn = 0;
+        for (int32_t q = 0; q < n_cta; ++q) {
+            capw[q] = q < c.k ? c.x : xmax;
+            capn[q] = q < c.k ? c.y : 0;
+            nw += capw[q];
+            nn += capn[q];
+        }
+        SW = class_slots(CW, nw);
+        SN = class_slots(CN, nn);
         for (auto& v : cw) v.clear();
         for (auto& v : cn) v.clear();
-        for (size_t si = 0; si < SW.slice.size(); ++si) cw[snake_cta(si, n_cta)].push_back((int32_t)si);
-        for (size_t si = 0; si < SN.slice.size(); ++si) cn[snake_cta(si, n_cta)].push_back((int32_t)si);
-        bool fits = true;
-        for (int32_t k = 0; k < n_cta && fits; ++k) {
+        std::vector<int32_t> capk(capn.begin(), capn.begin() + std::max<int32_t>(1, c.k));
+        std::vector<std::vector<int32_t>> cnk(capk.size());
+        bool fits = deal(SW.slice.size(), capw, cw) && deal(SN.slice.size(), capk, cnk);
+        for (size_t q = 0; q < cnk.size(); ++q) cn[q] = cnk[q];
+        for (int32_t q = 0; q < n_cta && fits; ++q) {
             uint64_t used = 0;
-            for (int32_t si : cw[k]) used += SW.slice[si];
-            for (int32_t si : cn[k]) used += SN.slice[si];
-            fits = used <= (uint64_t)arena && (int32_t)cw[k].size() <= c.x && (int32_t)cn[k].size() <= c.y;
+            for (int32_t si : cw[q]) used += SW.slice[si];
+            for (int32_t si : cn[q]) used += SN.slice[si];
+            fits = used <= (uint64_t)arena;
         }
         if (fits || ci + 1 == cands.size()) break;
     }
