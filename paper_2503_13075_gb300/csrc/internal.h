@@ -100,8 +100,9 @@ constexpr int kMaxSlotsPerCta = kSlotCtaThreads / kSlotThreads;
 // Narrow class: molecules of at most narrow_atoms atoms get one-warp teams, up to
 // kNarrowSlotsPerCta per CTA beside its 96-thread teams.  Their slices are small, so an
 // SM's shared memory holds about three times as many of them: batches of 20-50 and 50-100
-// atoms (mixed) ran 1.54x and 1.28x faster that way than on 96-thread teams; batches of
-// mixed sizes (20-200 atoms) did not gain, so the automatic choice keeps them on 96 threads.
+// atoms (mixed) ran 1.54x and 1.28x faster that way than on 96-thread teams; on batches of
+// mixed sizes (20-200 atoms) the gain depends on the precision mode, so the automatic
+// choice keeps them on 96 threads and leaves the threshold to the autotuner.
 constexpr int kNarrowThreads = 32;
 constexpr int kNarrowSlotsPerCta = kSlotCtaThreads / kNarrowThreads;
 constexpr int kDefaultNarrowAtoms = 100;
