@@ -87,11 +87,13 @@ def test_narrow_teams(prec, narrow, small_trees, trees):
         assert np.all(st == B.CONVERGED)
         assert np.abs(it - ref_chord.iterations).max() <= 1
         assert np.abs(x - ref.x).max() <= X_TOL
-        # the float-float mode tests convergence on |r|^2 - d^2 evaluated with ~48 significant
-        # bits of |r|^2 (absolute error up to ~2^-47 |r|^2, 1.6 % of the tolerance for d^2 >=
-        # 0.01 nm^2); the chord method's linear convergence stops just under the tolerance,
-        # so its float64 recomputation may exceed it by that much
-        slack = 2.0 ** -46 if prec == "mixed_df" else 0.0
+        # the float-float mode tests convergence on |r|^2 - d^2 evaluated in float-float
+        # arithmetic (rounding errors of ~2^-48 |r|^2 in each of about six tail terms) from
+        # displacements, and returns x_unc + displacement rounded to float64 (coordinates of
+        # a few nm: up to ~1.5e-14 d^2 in |r|^2 - d^2); together below 2^-44 ~ 5.7e-14 of d^2.
+        # The chord method's linear convergence stops just under the tolerance, so the float64
+        # recomputation of its returned positions may exceed the tolerance by that much
+        slack = 2.0 ** -44 if prec == "mixed_df" else 0.0
         assert orc.max_relative_violation(x, s.atom_i, s.atom_j, s.d) <= TOL + slack
 
 
