@@ -268,6 +268,38 @@ def test_warp_slot_schedule(prec, n_mol, n_cta, narrow):
         assert (tc == 96).sum() <= 8
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_slot_schedule_random_batches(seed):
+    """Random batches (2..250 atoms per molecule), thresholds, grids and arenas: every batched
+    molecule lands in exactly one slot queue or pool of its own class, no CTA exceeds its
+    arena, its threads or eight 96-thread slots, and 96-thread slots come first in a CTA."""
+    rng = np.random.default_rng(900 + seed)
+    sizes = rng.integers(2, 251, size=int(rng.integers(1, 400)))
+    s = wl.tree_molecules_of_sizes(sizes.tolist(), seed=seed)
+    narrow = int(rng.choice([0, -1, 40, 70, 100, 200]))
+    t = B.Topology(s.n_atoms, s.atom_i, s.atom_j, plan_only=True, narrow_atoms=narrow)
+    n_cta = int(rng.choice([1, 3, 17, 152, 304]))
+    arena = int(rng.choice([232320, 115712]))
+    for prec in ("fp64", "mixed", "mixed_df"):
+        sc = t.schedule(prec, n_cta=n_cta, arena_bytes=arena)
+        ms, team, st, cta = sc["mol_slot"], sc["mol_team"], sc["slot_team"], sc["slot_cta"]
+        batched = team > 0
+        assert np.all(ms[batched] >= -1) and np.all(ms[~batched] == -2)
+        q = ms >= 0
+        assert np.array_equal(np.bincount(ms[q], minlength=len(cta)), sc["slot_queue"])
+        assert np.all(st[ms[q]] == team[q])
+        assert int((batched & (ms == -1)).sum()) == sc["pool_n"]
+        for cls in (96, 32):  # a class with batched molecules has slots
+            assert not np.any(team == cls) or np.any(st == cls)
+        if len(cta):
+            assert cta.max() < n_cta and np.all(np.diff(cta) >= 0)
+            assert np.bincount(cta, weights=sc["slot_bytes"]).max() <= arena
+            assert np.bincount(cta, weights=st).max() <= 768
+            for c in range(cta.max() + 1):
+                tc = st[cta == c]
+                assert tc.size and np.all(np.diff(tc) <= 0) and (tc == 96).sum() <= 8
+
+
 def test_narrow_class_automatic_choice():
     """narrow_atoms = 0: one-warp teams for molecules of at most 100 atoms only in a batch of
     such molecules (>= 90 % of the batched atoms) larger than the GPU's 96-thread teams
